@@ -1,0 +1,227 @@
+/*
+ * sop.h - C ABI of the GB300 (sm_103a) SOP-model overdamped Langevin library.
+ *
+ * The library advances Calpha-level Self-Organized-Polymer models of proteins
+ * with the first-order (Ermak-McCammon) Langevin update, as described in
+ * Zhmurov, Dima, Kholodov, Barsegov, "Langevin dynamics simulations of
+ * biomolecules on graphics processors" (arXiv 1003.1148):
+ *   - forces of Eq. 1: FENE bonds (i, i+1), the native-contact 12-6 attraction
+ *     eps_h [(r0/r)^12 - 2 (r0/r)^6] and the non-native repulsion
+ *     eps_l (sigma/r)^6 over a Verlet pair list (Sec. IV.A, Sec. III.A);
+ *   - Gaussian random forces (Sec. III.C), drawn from counter-based
+ *     Philox4x32-10 and transformed by Box-Muller;
+ *   - the update r += F h/zeta + g sqrt(2 kT h/zeta) (Algorithm 7);
+ *   - the Verlet list rebuilt every K steps (Algorithm 3), here from a cell
+ *     list built by counting sort;
+ *   - constant-velocity cantilever pulling (Sec. IV.B) and a repulsive
+ *     spherical indenter (force-indentation runs named in the Conclusion).
+ *
+ * Conventions for every entry point:
+ *   - Units: Angstrom, kcal/mol, ps, K. Bead indices are 0-based and count
+ *     beads of one replica (0 .. n_beads-1).
+ *   - Host arrays are owned by the caller and only read or written during the
+ *     call. The context owns all device memory it allocates.
+ *   - Positions cross the boundary as FP64 xyz triples ([3*n] doubles, bead
+ *     major); inside they are FP32 with a compensated (Kahan) update, so a
+ *     value read back is the FP32 state converted exactly to FP64.
+ *   - Work is queued on params.cuda_stream (NULL = the legacy default stream).
+ *     Calls that return data to the host synchronise that stream.
+ *   - No C++ exception crosses the ABI. Every call returns a sop_status; the
+ *     text of the last error of a context is sop_last_error(ctx).
+ *   - A context is used by one host thread at a time.
+ *   - Replica r of a context is an independent copy of the whole topology;
+ *     its random forces use the Philox key seed + r and the counter
+ *     (step, bead, 0).
+ */
+#ifndef SOP_H
+#define SOP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SOP_ABI_VERSION 1
+
+typedef enum {
+    SOP_OK = 0,
+    SOP_ERR_INVALID_ARG = 1,       /* a pointer, size or parameter was rejected */
+    SOP_ERR_CUDA = 2,              /* a CUDA runtime call failed (see sop_last_error) */
+    SOP_ERR_OOM = 3,               /* device allocation failed */
+    SOP_ERR_FENE_BREAK = 4,        /* a bond reached |r - r0| >= R0; that replica is frozen */
+    SOP_ERR_NONFINITE = 5,         /* a position became NaN/Inf; that replica is frozen */
+    SOP_ERR_PAIRLIST_OVERFLOW = 6, /* the Verlet list outgrew its capacity; the run stopped */
+    SOP_ERR_ABORTED = 7,           /* sop_abort() stopped the run */
+    SOP_ERR_TIMEOUT = 8,           /* a bounded device-side wait gave up */
+    SOP_ERR_INDENTER_OVERLAP = 9,  /* a bead entered the indenter sphere; that replica is frozen */
+    SOP_ERR_UNSUPPORTED = 10,      /* the request is valid but this build cannot serve it */
+    SOP_ERR_CAPACITY = 11          /* a caller-provided output buffer is too small */
+} sop_status;
+
+/* How the steps are executed (the schedule). */
+typedef enum {
+    SOP_SCHED_AUTO = 0,      /* choose per workload (autotuned) */
+    SOP_SCHED_BATCHED = 1,   /* persistent fused kernel, one CTA per (replica, system), state in shared memory */
+    SOP_SCHED_STREAMED = 2,  /* per-step kernels over global memory, cell-list rebuilds, CUDA-graph replay */
+    SOP_SCHED_PLAIN = 3      /* the plain form: per-step launches, one system after another, no graph */
+} sop_schedule;
+
+typedef struct sop_ctx sop_ctx;
+
+/* Topology of one replica. Chains are contiguous bead ranges; systems are
+ * contiguous chain ranges. Beads interact (native contacts, repulsion) only
+ * with beads of the same system. */
+typedef struct {
+    int32_t n_beads;                 /* beads per replica, >= 1 */
+    int32_t n_chains;                /* >= 1 */
+    const int32_t *chain_offsets;    /* [n_chains+1], 0 = off[0] < off[1] < ... = n_beads */
+    int32_t n_systems;               /* 0: every chain is its own system */
+    const int32_t *system_offsets;   /* [n_systems+1] in chains, or NULL when n_systems == 0 */
+    const uint8_t *fixed_mask;       /* [n_beads], 1 = bead never moves; NULL = none fixed */
+} sop_topology;
+
+/* Parameters (Eq. 1, Algorithm 7, the Verlet list and the run). */
+typedef struct {
+    double k_fene;          /* FENE spring constant k, kcal/(mol A^2) */
+    double R0;              /* FENE tolerance R0, A (paper: 2) */
+    double eps_h;           /* native contact depth, kcal/mol */
+    double native_cut;      /* native contact cutoff R_C, A (paper: 8) */
+    double eps_l;           /* repulsion strength, kcal/mol (paper: 1) */
+    double sigma;           /* repulsion range, A (paper: 3.8) */
+    double T;               /* temperature, K */
+    double zeta;            /* friction, (kcal/mol) ps / A^2 */
+    double dt;              /* time step h, ps */
+    double pair_cut;        /* Verlet-list cutoff, A */
+    int32_t rebuild_every;  /* K: the list is rebuilt at steps 0, K, 2K, ... */
+    int32_t n_replicas;     /* >= 1 */
+    uint64_t seed;          /* Philox key of replica r is seed + r */
+    int32_t obs_every;      /* observable cadence in steps (0 = none) */
+    int32_t obs_capacity;   /* ring-buffer capacity in records (0 = 4096) */
+    int32_t pairs_per_bead; /* Verlet-list capacity per bead (0 = automatic) */
+    int32_t schedule;       /* a sop_schedule */
+    void *cuda_stream;      /* cudaStream_t to queue work on (NULL = default stream) */
+} sop_params;
+
+/* Cantilever on one system (Sec. IV.B): `anchor` is held fixed; a spring of
+ * constant k_s acts on `pulled`, whose tip starts at the pulled bead's
+ * position when sop_pull is called and moves at v A/step along the unit
+ * vector from anchor to pulled at that moment. */
+typedef struct {
+    int32_t system;
+    int32_t anchor;
+    int32_t pulled;
+    double k_s;             /* kcal/(mol A^2) */
+    double v;               /* A per step */
+} sop_pull_params;
+
+/* One observable record (all FP64). */
+typedef struct {
+    double step;            /* step at which the record was taken */
+    double replica;
+    double system;
+    double energy;          /* Eq. 1 energy of the system (FENE + native + listed repulsion) */
+    double f_ext;           /* pull: k_s (tip - r_pulled) . dir; indenter: force on the system's beads along its motion */
+    double extension;       /* pull: |r_pulled - r_anchor|; indenter: distance travelled */
+    double q;               /* fraction of native contacts with r < r0 + 2 A */
+    double r_ee;            /* end-to-end distance of the system's first chain */
+} sop_record;
+
+/* Counters of the work queued so far. */
+typedef struct {
+    int64_t steps;                /* steps completed (the global step counter) */
+    int64_t kernel_launches;      /* kernels launched by this context (graph nodes counted) */
+    int64_t graph_launches;       /* CUDA-graph launches */
+    int64_t rebuilds;             /* Verlet-list rebuilds */
+    int32_t schedule;             /* the sop_schedule in use */
+    int32_t block_threads;        /* CTA size of the step kernel */
+    int32_t pairs_per_bead;       /* Verlet-list capacity per bead */
+    int32_t beads_per_thread;     /* batched schedule: beads owned by one thread */
+    int64_t pairlist_entries;     /* entries in the last Verlet list of replica 0 */
+    int64_t native_entries;       /* native contacts (i < j) */
+} sop_stats;
+
+/* Create a context: validates the arguments, builds the bonds (r0 from the
+ * native coordinates) and the native contact map (pairs |i-j| > 2 in a chain,
+ * or in different chains of one system, with FP64 native distance below
+ * native_cut; Eq. 1, Sec. IV.A) on the GPU, uploads the native coordinates as
+ * the starting positions of every replica and builds the first Verlet list.
+ * native_xyz: [3*n_beads] FP64, host. On success *out owns the device state;
+ * on failure *out is NULL. */
+sop_status sop_create(const sop_topology *topo, const double *native_xyz, const sop_params *params,
+                      sop_ctx **out);
+
+/* Advance every replica by n_steps >= 0 steps (Algorithm 7 with the forces of
+ * Eq. 1, the Verlet list rebuilt at multiples of rebuild_every). Returns after
+ * the work is queued and the status word has been read (one stream sync).
+ * A replica whose bond breaks, whose position becomes non-finite or whose bead
+ * enters the indenter is frozen and reported; the others continue. */
+sop_status sop_step(sop_ctx *ctx, int64_t n_steps);
+
+/* Forces (FP32 arithmetic) at the current positions of `replica`, with a
+ * Verlet list built from those positions, and the Eq. 1 energy (FP64
+ * accumulation). out_f: [3*n_beads] FP64 host (may be NULL); out_energy: one
+ * double (may be NULL). Does not change the simulation state. */
+sop_status sop_forces(sop_ctx *ctx, int32_t replica, double *out_f, double *out_energy);
+
+/* Rebuild the Verlet list of every replica from the current positions now. */
+sop_status sop_pairlist_rebuild(sop_ctx *ctx);
+
+/* Start (or replace) cantilever pulling on the listed systems (all replicas).
+ * Anchors become fixed. n = 0 removes all springs. */
+sop_status sop_pull(sop_ctx *ctx, int32_t n, const sop_pull_params *pulls);
+
+/* Start (or replace) a repulsive spherical indenter acting on every bead of
+ * every replica: V = eps_l (sigma / (|r - c| - radius))^6, centre c starting
+ * at `center` and moving v A/step along unit `direction`. radius <= 0 removes it. */
+sop_status sop_indenter(sop_ctx *ctx, const double center[3], const double direction[3], double radius,
+                        double v);
+
+/* Positions of one replica ([3*n_beads] FP64 host), or of all replicas when
+ * replica == -1 ([3*n_beads*n_replicas], replica major). */
+sop_status sop_get_positions(sop_ctx *ctx, int32_t replica, double *out_xyz);
+/* Set positions (converted to FP32, compensation reset). replica == -1 sets
+ * all replicas from a [3*n_beads*n_replicas] array. */
+sop_status sop_set_positions(sop_ctx *ctx, int32_t replica, const double *xyz);
+
+/* Verlet list of `replica` as canonical CSR over its beads: row i holds every
+ * partner j (both directions, ascending). row_ptr: [n_beads+1]; col: [cap].
+ * *nnz receives the entry count; SOP_ERR_CAPACITY when cap < nnz. */
+sop_status sop_get_pairlist(sop_ctx *ctx, int32_t replica, int32_t *row_ptr, int32_t *col, int64_t cap,
+                            int64_t *nnz);
+
+/* Native contact map as canonical CSR (both directions, ascending) with the
+ * FP64 native distance r0 of each entry. */
+sop_status sop_get_native_map(sop_ctx *ctx, int32_t *row_ptr, int32_t *col, double *r0, int64_t cap,
+                              int64_t *nnz);
+
+/* Copy out and clear the observable records taken since the last call, in
+ * order of step, then replica, then system. When more records were taken than
+ * the ring holds, the oldest are lost and *n_lost says how many. */
+sop_status sop_get_observables(sop_ctx *ctx, sop_record *out, int64_t cap, int64_t *n_records, int64_t *n_lost);
+
+/* Checkpoint: the step counter, positions, compensation terms, pulling and
+ * indenter set-up and status. Resuming from it continues bit-exactly.
+ * With buf == NULL, *size receives the byte count needed. */
+sop_status sop_get_state(sop_ctx *ctx, void *buf, int64_t cap, int64_t *size);
+sop_status sop_set_state(sop_ctx *ctx, const void *buf, int64_t size);
+
+/* Per-replica status ([n_replicas] int32 host): a sop_status value each. */
+sop_status sop_replica_status(sop_ctx *ctx, int32_t *out);
+
+/* Ask a running sop_step to stop at the next check (thread-safe, async). */
+void sop_abort(sop_ctx *ctx);
+
+/* Counters and the schedule in use. */
+sop_status sop_get_stats(sop_ctx *ctx, sop_stats *out);
+
+/* Text of the last error of ctx (or of the last failed sop_create when ctx is NULL). */
+const char *sop_last_error(const sop_ctx *ctx);
+
+/* Free all device and host memory of ctx. NULL is allowed. */
+void sop_destroy(sop_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SOP_H */

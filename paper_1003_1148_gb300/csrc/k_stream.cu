@@ -1,0 +1,876 @@
+// Streamed schedule: per-step kernels over global memory (sm_103a).
+//
+//   setup      bonds and the native contact map (Eq. 1, Sec. IV.A), FP64 exact
+//   rebuild    Verlet list (Sec. III.A, Algorithm 3) from a cell list built by
+//              counting sort: per-segment bounding box -> cell id per bead ->
+//              histogram -> exclusive scan -> scatter -> per-cell order; then one
+//              warp per bead scans its 27 cells and writes its sorted row
+//   step       fused forces (Eq. 1 over bonds, natives and the list, each bead
+//              gathered by a group of L lanes with a shuffle reduction, as in
+//              the particle-based Algorithm 2) + cantilever/indenter + Philox
+//              noise + compensated first-order update (Algorithm 7)
+//   observables FP64 energy, pulling force, extension, Q and end-to-end distance
+//
+// A "segment" is one system of one replica; its beads are a contiguous range of
+// the replica-major global bead index.
+#include <cuda_runtime.h>
+
+#include "sop_internal.h"
+
+namespace sop {
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// Setup: bonds and native map
+// ---------------------------------------------------------------------------
+__global__ void k_setup_bonds(const double *X, const int32_t *chain, float *bond_r0, double *bond_r0d, int32_t n) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    if (i + 1 < n && chain[i] == chain[i + 1]) {
+        const double d2 = dist2_d(X[3 * i], X[3 * i + 1], X[3 * i + 2], X[3 * i + 3], X[3 * i + 4], X[3 * i + 5]);
+        const double r0 = __dsqrt_rn(d2);
+        bond_r0[i] = (float)r0;
+        bond_r0d[i] = r0;
+    } else {
+        bond_r0[i] = -1.0f;
+        bond_r0d[i] = -1.0;
+    }
+}
+
+// Native candidates: same system, and |i-j| > 2 when in the same chain.
+// Decided on the FP64 native coordinates: d^2 < cut^2 with d^2 = ((dx*dx+dy*dy)+dz*dz).
+// An FP32 distance screens out pairs that are clearly beyond the cutoff.
+template <bool kFill>
+__global__ void k_native(const double *X, const int32_t *chain, const int32_t *sys, const int32_t *sys_lo,
+                         int32_t n, double cut, int32_t *count, const int32_t *row, int32_t *col, double *r0,
+                         float *r0sq) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int s = sys[i];
+    const int lo = sys_lo[s], hi = sys_lo[s + 1];
+    const double xi = X[3 * i], yi = X[3 * i + 1], zi = X[3 * i + 2];
+    const float fxi = (float)xi, fyi = (float)yi, fzi = (float)zi;
+    const double cut2 = __dmul_rn(cut, cut);
+    const float screen = (float)cut2 * 1.001f + 1e-3f;
+    const int ci = chain[i];
+    int c = 0;
+    int out = kFill ? row[i] : 0;
+    for (int j = lo; j < hi; ++j) {
+        if (j == i) continue;
+        const double xj = X[3 * j], yj = X[3 * j + 1], zj = X[3 * j + 2];
+        const float dx = fxi - (float)xj, dy = fyi - (float)yj, dz = fzi - (float)zj;
+        if (dx * dx + dy * dy + dz * dz > screen) continue;
+        if (chain[j] == ci && (j - i <= 2 && i - j <= 2)) continue;
+        const double d2 = dist2_d(xi, yi, zi, xj, yj, zj);
+        if (d2 < cut2) {
+            if (kFill) {
+                col[out] = j;
+                const double r = __dsqrt_rn(d2);
+                r0[out] = r;
+                r0sq[out] = (float)__dmul_rn(r, r);
+                ++out;
+            } else {
+                ++c;
+            }
+        }
+    }
+    if (!kFill) count[i] = c;
+}
+
+// ---------------------------------------------------------------------------
+// Exclusive scan (three passes: block sums, scan of sums, block scans)
+// ---------------------------------------------------------------------------
+constexpr int kScanThreads = 1024;
+constexpr int kScanTile = 2 * kScanThreads;
+
+__device__ __forceinline__ int warp_inclusive_scan(int v) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += t;
+    }
+    return v;
+}
+
+// Exclusive scan of one value per thread across the block; returns the prefix and
+// writes the block total to *total.
+__device__ __forceinline__ int block_exclusive_scan(int v, int *total) {
+    __shared__ int warp_sums[kScanThreads / 32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int inc = warp_inclusive_scan(v);
+    if (lane == 31) warp_sums[w] = inc;
+    __syncthreads();
+    if (w == 0) {
+        const int nw = blockDim.x >> 5;
+        int s = lane < nw ? warp_sums[lane] : 0;
+        s = warp_inclusive_scan(s);
+        if (lane < nw) warp_sums[lane] = s;
+    }
+    __syncthreads();
+    const int before = (w > 0 ? warp_sums[w - 1] : 0) + inc - v;
+    *total = warp_sums[(blockDim.x >> 5) - 1];
+    __syncthreads();
+    return before;
+}
+
+__global__ void k_scan_reduce(const int32_t *in, int64_t n, int32_t *sums) {
+    const int64_t base = (int64_t)blockIdx.x * kScanTile + 2 * threadIdx.x;
+    int v = 0;
+    if (base < n) v += in[base];
+    if (base + 1 < n) v += in[base + 1];
+    int total;
+    block_exclusive_scan(v, &total);
+    if (threadIdx.x == 0) sums[blockIdx.x] = total;
+}
+
+__global__ void k_scan_sums(int32_t *sums, int64_t nb) {
+    int carry = 0;
+    for (int64_t base = 0; base < nb; base += kScanThreads) {
+        const int64_t k = base + threadIdx.x;
+        const int v = k < nb ? sums[k] : 0;
+        int total;
+        const int ex = block_exclusive_scan(v, &total);
+        if (k < nb) sums[k] = carry + ex;
+        carry += total;
+    }
+    if (threadIdx.x == 0) sums[nb] = carry;
+}
+
+__global__ void k_scan_final(const int32_t *in, int32_t *out, int64_t n, const int32_t *sums, int64_t nb) {
+    const int64_t base = (int64_t)blockIdx.x * kScanTile + 2 * threadIdx.x;
+    const int a = base < n ? in[base] : 0;
+    const int b = base + 1 < n ? in[base + 1] : 0;
+    int total;
+    const int ex = block_exclusive_scan(a + b, &total) + sums[blockIdx.x];
+    if (base < n) out[base] = ex;
+    if (base + 1 < n) out[base + 1] = ex + a;
+    if (blockIdx.x == 0 && threadIdx.x == 0) out[n] = sums[nb];
+}
+
+// ---------------------------------------------------------------------------
+// Rebuild
+// ---------------------------------------------------------------------------
+struct RebuildArgs {
+    const float4 *pos;
+    float4 *snap;
+    const int32_t *sys;
+    const int32_t *chain;
+    int32_t n, n_sys;
+    int32_t g_lo;
+    float cell_edge;
+    const int32_t *seg_bead_lo;
+    const int32_t *seg_cell_base;
+    float4 *seg_lo;
+    int4 *seg_dims;
+    int32_t *cell_of;
+    int32_t *cell_cnt;
+    int32_t *cell_start;   // range-relative offsets
+    int32_t *sorted;       // sorted[sorted_base + k]
+    int32_t sorted_base;   // first bead of the range
+    int32_t cell_base0;    // first cell of the range
+    int32_t *rep_status;
+};
+
+// One CTA per segment: bounding box, then a grid of cubic cells of edge >= cutoff
+// with at most the segment's cell budget.
+__global__ void k_seg_setup(RebuildArgs a, int32_t *pl_cursor, const int64_t *pl_seg_base) {
+    // every thread of the CTA works on segment g
+    const int g = a.g_lo + blockIdx.x;
+    const int lo = a.seg_bead_lo[g], hi = a.seg_bead_lo[g + 1];
+    float mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
+    bool bad = false;
+    for (int b = lo + threadIdx.x; b < hi; b += blockDim.x) {
+        const float4 p = a.pos[b];
+        const float v[3] = {p.x, p.y, p.z};
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            if (!isfinite(v[k])) bad = true;
+            mn[k] = fminf(mn[k], v[k]);
+            mx[k] = fmaxf(mx[k], v[k]);
+        }
+    }
+    __shared__ float smn[3][32], smx[3][32];
+    __shared__ int sbad;
+    if (threadIdx.x == 0) sbad = 0;
+    __syncthreads();
+    if (bad) sbad = 1;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        for (int o = 16; o > 0; o >>= 1) {
+            mn[k] = fminf(mn[k], __shfl_xor_sync(0xffffffffu, mn[k], o));
+            mx[k] = fmaxf(mx[k], __shfl_xor_sync(0xffffffffu, mx[k], o));
+        }
+    }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0)
+        for (int k = 0; k < 3; ++k) { smn[k][w] = mn[k]; smx[k][w] = mx[k]; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const int nw = blockDim.x >> 5;
+        float l[3], h[3];
+        for (int k = 0; k < 3; ++k) {
+            l[k] = smn[k][0];
+            h[k] = smx[k][0];
+            for (int q = 1; q < nw; ++q) { l[k] = fminf(l[k], smn[k][q]); h[k] = fmaxf(h[k], smx[k][q]); }
+        }
+        const int budget = a.seg_cell_base[g + 1] - a.seg_cell_base[g];
+        float edge = a.cell_edge;
+        int d[3] = {1, 1, 1};
+        if (!sbad && hi > lo) {
+            for (int it = 0; it < 64; ++it) {
+                long long prod = 1;
+                for (int k = 0; k < 3; ++k) {
+                    const float e = (h[k] - l[k]) / edge;
+                    d[k] = e < 1e6f ? (int)floorf(e) + 1 : 1000000;
+                    prod *= d[k];
+                }
+                if (prod <= budget) break;
+                edge *= 1.25f;
+            }
+        } else {
+            l[0] = l[1] = l[2] = 0.0f;
+        }
+        a.seg_lo[g] = make_float4(l[0], l[1], l[2], 1.0f / edge);
+        a.seg_dims[g] = make_int4(d[0], d[1], d[2], d[0] * d[1] * d[2]);
+        if (pl_cursor) pl_cursor[g] = (int32_t)pl_seg_base[g];
+    }
+}
+
+__device__ __forceinline__ int cell_coord(float x, float lo, float inv, int dim) {
+    int c = (int)((x - lo) * inv);
+    c = c < 0 ? 0 : c;
+    return c >= dim ? dim - 1 : c;
+}
+
+// Cell id of every bead, per-cell counts (histogram), and the snapshot of the
+// positions the list is built from.
+__global__ void k_cell_count(RebuildArgs a, int b_lo, int b_hi) {
+    const int gb = b_lo + blockIdx.x * blockDim.x + threadIdx.x;
+    if (gb >= b_hi) return;
+    const int r = gb / a.n, i = gb - r * a.n;
+    const int g = r * a.n_sys + a.sys[i];
+    const float4 p = a.pos[gb];
+    if (a.snap) a.snap[gb] = p;
+    const float4 lo = a.seg_lo[g];
+    const int4 d = a.seg_dims[g];
+    int cx = 0, cy = 0, cz = 0;
+    if (isfinite(p.x) && isfinite(p.y) && isfinite(p.z)) {
+        cx = cell_coord(p.x, lo.x, lo.w, d.x);
+        cy = cell_coord(p.y, lo.y, lo.w, d.y);
+        cz = cell_coord(p.z, lo.z, lo.w, d.z);
+    }
+    const int gc = a.seg_cell_base[g] + (cz * d.y + cy) * d.x + cx;
+    a.cell_of[gb] = gc;
+    atomicAdd(&a.cell_cnt[gc], 1);
+}
+
+// Counting-sort scatter. Counts are consumed (they return to zero for the next rebuild).
+__global__ void k_cell_scatter(RebuildArgs a, int b_lo, int b_hi) {
+    const int gb = b_lo + blockIdx.x * blockDim.x + threadIdx.x;
+    if (gb >= b_hi) return;
+    const int gc = a.cell_of[gb];
+    const int slot = atomicSub(&a.cell_cnt[gc], 1) - 1;
+    a.sorted[a.sorted_base + a.cell_start[gc - a.cell_base0] + slot] = gb;
+}
+
+// Beads of a cell in ascending order, so that every later traversal is deterministic.
+__global__ void k_cell_sort(RebuildArgs a, int c_lo, int c_hi) {
+    const int c = c_lo + blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= c_hi) return;
+    const int s = a.sorted_base + a.cell_start[c - a.cell_base0];
+    const int e = a.sorted_base + a.cell_start[c - a.cell_base0 + 1];
+    for (int k = s + 1; k < e; ++k) {
+        const int v = a.sorted[k];
+        int m = k - 1;
+        while (m >= s && a.sorted[m] > v) {
+            a.sorted[m + 1] = a.sorted[m];
+            --m;
+        }
+        a.sorted[m + 1] = v;
+    }
+}
+
+constexpr int kBuildWarps = 8;
+constexpr int kRowBuf = 256;   // candidates a row may hold before it is an overflow
+constexpr int kNatBuf = 64;    // native partners kept in shared memory per warp
+
+struct BuildExtra {
+    const int32_t *nat_row;
+    const int32_t *nat_col;
+    double cut2_d;
+    float cut2_f;
+    int32_t *pl_start;
+    int32_t *pl_len;
+    int32_t *pl_col;
+    int32_t *pl_cursor;         // [n_seg]
+    const int64_t *pl_seg_end;  // [n_seg] capacity limit of each segment
+    int32_t *rep_status;
+};
+
+__device__ __forceinline__ void set_status(int32_t *st, int32_t code) { atomicCAS(st, 0, code); }
+
+// One warp per bead: scan the 27 neighbouring cells (as 9 runs of 3 consecutive
+// cells along x), keep partners j with |i-j| != 1 in a chain, j not native, j != i
+// and r^2 < cut^2; order them ascending (rank sort) and append the row to the
+// segment's column range.
+__global__ void __launch_bounds__(kBuildWarps * 32) k_pl_build(RebuildArgs a, BuildExtra x, int b_lo, int b_hi) {
+    __shared__ int32_t buf[kBuildWarps][kRowBuf];
+    __shared__ int32_t nat[kBuildWarps][kNatBuf];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int gb = b_lo + blockIdx.x * kBuildWarps + w;
+    if (gb >= b_hi) return;
+    const int r = gb / a.n, i = gb - r * a.n;
+    const int g = r * a.n_sys + a.sys[i];
+    if (a.rep_status[r] != 0) {
+        if (lane == 0) { x.pl_start[gb] = 0; x.pl_len[gb] = 0; }
+        return;
+    }
+    const float4 pi = a.pos[gb];
+    const int nlo = x.nat_row[i], nhi = x.nat_row[i + 1];
+    const int nn = nhi - nlo;
+    for (int k = lane; k < nn && k < kNatBuf; k += 32) nat[w][k] = x.nat_col[nlo + k];
+    __syncwarp();
+    const float4 lo = a.seg_lo[g];
+    const int4 d = a.seg_dims[g];
+    const int cx = cell_coord(pi.x, lo.x, lo.w, d.x);
+    const int cy = cell_coord(pi.y, lo.y, lo.w, d.y);
+    const int cz = cell_coord(pi.z, lo.z, lo.w, d.z);
+    const int cbase = a.seg_cell_base[g] - a.cell_base0;
+    const int ci = a.chain[i];
+    const int rbase = r * a.n;
+    int cnt = 0;
+    const int x0 = cx > 0 ? cx - 1 : 0, x1 = cx + 1 < d.x ? cx + 1 : d.x - 1;
+    for (int zz = cz - 1; zz <= cz + 1; ++zz) {
+        if (zz < 0 || zz >= d.z) continue;
+        for (int yy = cy - 1; yy <= cy + 1; ++yy) {
+            if (yy < 0 || yy >= d.y) continue;
+            const int c0 = cbase + (zz * d.y + yy) * d.x + x0;
+            const int c1 = cbase + (zz * d.y + yy) * d.x + x1;
+            const int q0 = a.cell_start[c0], q1 = a.cell_start[c1 + 1];
+            for (int q = q0 + lane; q - lane < q1; q += 32) {
+                bool keep = false;
+                int jl = 0;
+                if (q < q1) {
+                    const int j = a.sorted[a.sorted_base + q];
+                    jl = j - rbase;
+                    if (jl != i && !((jl == i + 1 || jl == i - 1) && a.chain[jl] == ci)) {
+                        if (within_cut(pi, a.pos[j], x.cut2_f, x.cut2_d)) {
+                            keep = true;
+                            for (int k = 0; k < nn; ++k) {
+                                const int v = k < kNatBuf ? nat[w][k] : x.nat_col[nlo + k];
+                                if (v == jl) { keep = false; break; }
+                            }
+                        }
+                    }
+                }
+                const unsigned m = __ballot_sync(0xffffffffu, keep);
+                if (keep) {
+                    const int slot = cnt + __popc(m & ((1u << lane) - 1u));
+                    if (slot < kRowBuf) buf[w][slot] = jl;
+                }
+                cnt += __popc(m);
+            }
+        }
+    }
+    __syncwarp();
+    int base = 0;
+    bool ok = cnt <= kRowBuf;
+    if (lane == 0 && ok) {
+        base = atomicAdd(&x.pl_cursor[g], cnt);
+        if ((int64_t)base + cnt > x.pl_seg_end[g]) ok = false;
+    }
+    base = __shfl_sync(0xffffffffu, base, 0);
+    ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+    if (!ok) {
+        if (lane == 0) {
+            set_status(&a.rep_status[r], (int32_t)SOP_ERR_PAIRLIST_OVERFLOW);
+            x.pl_start[gb] = 0;
+            x.pl_len[gb] = 0;
+        }
+        return;
+    }
+    for (int k = lane; k < cnt; k += 32) {
+        const int v = buf[w][k];
+        int rank = 0;
+        for (int m2 = 0; m2 < cnt; ++m2) rank += buf[w][m2] < v;
+        x.pl_col[base + rank] = v;
+    }
+    if (lane == 0) {
+        x.pl_start[gb] = base;
+        x.pl_len[gb] = cnt;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Forces and the fused step
+// ---------------------------------------------------------------------------
+// Sum of the Eq. 1 pair forces on bead i of replica r, gathered by L lanes
+// (particle-based, Algorithm 2): lanes stride over the native row and the
+// Verlet row, bonds go to lanes 0 and 1, a shuffle reduction leaves the sum in
+// every lane.
+// Lanes of this thread's group of L (groups are aligned within the warp).
+template <int L>
+__device__ __forceinline__ unsigned group_mask() {
+    return L == 32 ? 0xffffffffu : (((1u << L) - 1u) << ((threadIdx.x & 31) & ~(L - 1)));
+}
+
+template <int L>
+__device__ __forceinline__ float3 gather_force(const StepArgs &a, const DevPairList &pl, const float4 *P, int i,
+                                               int gb, int lane, bool *broken) {
+    const DevTopo &t = a.topo;
+    const float4 pi = P[i];
+    float fx = 0.f, fy = 0.f, fz = 0.f;
+    bool brk = false;
+    if (lane == 0 && i > 0) {
+        const float r0 = t.bond_r0[i - 1];
+        if (r0 > 0.f) {
+            const float4 pj = P[i - 1];
+            const float dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
+            const float c = fene_coef(fmaf(dz, dz, fmaf(dy, dy, dx * dx)), r0, a.fp, &brk);
+            fx = fmaf(c, dx, fx); fy = fmaf(c, dy, fy); fz = fmaf(c, dz, fz);
+        }
+    }
+    if (lane == (1 % L) && i + 1 < t.n) {
+        const float r0 = t.bond_r0[i];
+        if (r0 > 0.f) {
+            const float4 pj = P[i + 1];
+            const float dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
+            const float c = fene_coef(fmaf(dz, dz, fmaf(dy, dy, dx * dx)), r0, a.fp, &brk);
+            fx = fmaf(c, dx, fx); fy = fmaf(c, dy, fy); fz = fmaf(c, dz, fz);
+        }
+    }
+    const int n0 = t.nat_row[i], n1 = t.nat_row[i + 1];
+    for (int p = n0 + lane; p < n1; p += L) {
+        const float4 pj = P[t.nat_col[p]];
+        const float dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
+        const float c = native_coef(fmaf(dz, dz, fmaf(dy, dy, dx * dx)), t.nat_r0sq[p], a.fp);
+        fx = fmaf(c, dx, fx); fy = fmaf(c, dy, fy); fz = fmaf(c, dz, fz);
+    }
+    const int p0 = pl.start[gb], p1 = p0 + pl.len[gb];
+    for (int p = p0 + lane; p < p1; p += L) {
+        const float4 pj = P[pl.col[p]];
+        const float dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
+        const float c = repulsive_coef(fmaf(dz, dz, fmaf(dy, dy, dx * dx)), a.fp);
+        fx = fmaf(c, dx, fx); fy = fmaf(c, dy, fy); fz = fmaf(c, dz, fz);
+    }
+#pragma unroll
+    for (int o = L / 2; o > 0; o >>= 1) {
+        fx += __shfl_xor_sync(group_mask<L>(), fx, o, L);
+        fy += __shfl_xor_sync(group_mask<L>(), fy, o, L);
+        fz += __shfl_xor_sync(group_mask<L>(), fz, o, L);
+    }
+    *broken = brk;
+    return make_float3(fx, fy, fz);
+}
+
+// Cantilever and indenter forces on bead i (FP64 tip / centre, FP32 force).
+__device__ __forceinline__ float3 external_force(const StepArgs &a, int r, int i, float4 pi, int64_t step,
+                                                 bool *overlap) {
+    float3 f = make_float3(0.f, 0.f, 0.f);
+    const DevTopo &t = a.topo;
+    const DevExternal &e = a.ext;
+    if (t.flags[i] & kFlagPulled) {
+        const int q = e.pull_of_sys[t.sys[i]];
+        if (q >= 0 && e.pull_bead[q] == i) {
+            const double tt = e.pull_v[q] * ((double)step - e.pull_n0[q]);
+            const double *tip0 = e.pull_tip0 + ((size_t)r * e.n_pull + q) * 3;
+            const float ks = (float)e.pull_ks[q];
+            f.x += ks * (float)(tip0[0] + tt * e.pull_dir[3 * q] - (double)pi.x);
+            f.y += ks * (float)(tip0[1] + tt * e.pull_dir[3 * q + 1] - (double)pi.y);
+            f.z += ks * (float)(tip0[2] + tt * e.pull_dir[3 * q + 2] - (double)pi.z);
+        }
+    }
+    if (e.has_indenter) {
+        const double tt = e.ind_v * ((double)step - e.ind_n0);
+        const float cx = (float)(e.ind_c0[0] + tt * e.ind_dir[0]);
+        const float cy = (float)(e.ind_c0[1] + tt * e.ind_dir[1]);
+        const float cz = (float)(e.ind_c0[2] + tt * e.ind_dir[2]);
+        const float ex = pi.x - cx, ey = pi.y - cy, ez = pi.z - cz;
+        const float rr = sqrtf(fmaf(ez, ez, fmaf(ey, ey, ex * ex)));
+        const float rho = rr - (float)e.ind_radius;
+        if (!(rho > 0.f)) {
+            *overlap = true;
+        } else {
+            const float q = a.fp.sigma2 > 0.f ? sqrtf(a.fp.sigma2) / rho : 0.f;
+            const float q2 = q * q;
+            const float q6 = q2 * q2 * q2;
+            const float c = a.fp.eps6_l * q6 / (rho * rr);
+            f.x = fmaf(c, ex, f.x); f.y = fmaf(c, ey, f.y); f.z = fmaf(c, ez, f.z);
+        }
+    }
+    return f;
+}
+
+template <int L>
+__global__ void __launch_bounds__(256) k_step(StepArgs a, DevPairList pl, const float4 *__restrict__ pos_in,
+                                              float4 *__restrict__ pos_out, float4 *__restrict__ comp, int b_lo,
+                                              int b_hi, int k_off) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int gb = b_lo + t / L;
+    const int lane = t % L;
+    if (gb >= b_hi) return;   // whole groups of L lanes leave together
+    const int n = a.topo.n;
+    const int r = gb / n, i = gb - r * n;
+    const float4 *P = pos_in + (size_t)r * n;
+    if (*a.halt != 0 || a.rep_status[r] != 0) {
+        if (lane == 0) pos_out[gb] = P[i];
+        return;
+    }
+    const int64_t step = *a.d_step + k_off;
+    bool broken = false;
+    const float3 f = gather_force<L>(a, pl, P, i, gb, lane, &broken);
+    broken = __any_sync(group_mask<L>(), broken);
+    if (lane != 0) return;
+    float4 pi = P[i];
+    if (broken) {
+        set_status(&a.rep_status[r], (int32_t)SOP_ERR_FENE_BREAK);
+        pos_out[gb] = pi;
+        return;
+    }
+    bool overlap = false;
+    const float3 fe = external_force(a, r, i, pi, step, &overlap);
+    if (overlap) {
+        set_status(&a.rep_status[r], (int32_t)SOP_ERR_INDENTER_OVERLAP);
+        pos_out[gb] = pi;
+        return;
+    }
+    if (a.topo.flags[i] & kFlagFixed) {
+        pos_out[gb] = pi;
+        return;
+    }
+    const float3 g = bead_noise(a.seed + (uint64_t)r, step, (uint32_t)i);
+    float4 c = comp[gb];
+    kahan_add(pi.x, c.x, fmaf(f.x + fe.x, a.fp.mob, g.x * a.fp.amp));
+    kahan_add(pi.y, c.y, fmaf(f.y + fe.y, a.fp.mob, g.y * a.fp.amp));
+    kahan_add(pi.z, c.z, fmaf(f.z + fe.z, a.fp.mob, g.z * a.fp.amp));
+    if (!(isfinite(pi.x) && isfinite(pi.y) && isfinite(pi.z))) {
+        set_status(&a.rep_status[r], (int32_t)SOP_ERR_NONFINITE);
+        pos_out[gb] = P[i];
+        return;
+    }
+    comp[gb] = c;
+    pos_out[gb] = pi;
+}
+
+template <int L>
+__global__ void __launch_bounds__(256) k_forces(StepArgs a, DevPairList pl, const float4 *__restrict__ pos,
+                                                float4 *__restrict__ force, int b_lo, int b_hi, int64_t step) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int gb = b_lo + t / L;
+    const int lane = t % L;
+    if (gb >= b_hi) return;
+    const int n = a.topo.n;
+    const int r = gb / n, i = gb - r * n;
+    const float4 *P = pos + (size_t)r * n;
+    bool broken = false;
+    float3 f = gather_force<L>(a, pl, P, i, gb, lane, &broken);
+    broken = __any_sync(group_mask<L>(), broken);
+    if (lane != 0) return;
+    bool overlap = false;
+    const float3 fe = external_force(a, r, i, P[i], step, &overlap);
+    force[gb] = make_float4(f.x + fe.x, f.y + fe.y, f.z + fe.z, (broken || overlap) ? 1.f : 0.f);
+}
+
+// ---------------------------------------------------------------------------
+// Observables (FP64)
+// ---------------------------------------------------------------------------
+constexpr int kObsThreads = 256;
+
+__device__ __forceinline__ double block_sum_d(double v, double *sh) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) sh[w] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0)
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) s += sh[k];
+    return s;   // valid in thread 0
+}
+
+struct ObsArgs {
+    StepArgs a;
+    DevPairList pl;
+    DevObs o;
+    const float4 *pos;
+    int32_t k_off;
+    int32_t gate;
+    double eps_h, eps_l, sigma, k_fene, R0;
+    const double *bond_r0d;   // [n] FP64 bond lengths
+};
+
+__global__ void __launch_bounds__(kObsThreads) k_obs_partial(ObsArgs q) {
+    const int64_t step = *q.a.d_step + q.k_off;
+    if (q.gate > 0 && step % q.gate != 0) return;
+    const int ch = blockIdx.x;
+    const int lo = q.o.chunk_lo[ch], hi = q.o.chunk_hi[ch];
+    const DevTopo &t = q.a.topo;
+    const DevExternal &e = q.a.ext;
+    const int n = t.n;
+    double E = 0.0, fpull = 0.0, ext = 0.0, formed = 0.0, fwall = 0.0, ree = 0.0;
+    const double R02 = q.R0 * q.R0;
+    const double sig2 = q.sigma * q.sigma;
+    for (int gb = lo + threadIdx.x; gb < hi; gb += blockDim.x) {
+        const int r = gb / n, i = gb - r * n;
+        const float4 *P = q.pos + (size_t)r * n;
+        const float4 pi = P[i];
+        const double xi = pi.x, yi = pi.y, zi = pi.z;
+        if (t.bond_r0[i] > 0.f) {
+            const float4 pj = P[i + 1];
+            const double rr = __dsqrt_rn(dist2_d(xi, yi, zi, pj.x, pj.y, pj.z));
+            const double dr = rr - q.bond_r0d[i];
+            const double arg = 1.0 - dr * dr / R02;
+            if (arg > 0.0) E += -0.5 * q.k_fene * R02 * log(arg);
+        }
+        for (int p = t.nat_row[i]; p < t.nat_row[i + 1]; ++p) {
+            const int j = t.nat_col[p];
+            if (j < i) continue;
+            const float4 pj = P[j];
+            const double d2 = dist2_d(xi, yi, zi, pj.x, pj.y, pj.z);
+            const double r0 = t.nat_r0[p];
+            const double s = r0 * r0 / d2;
+            const double s3 = s * s * s;
+            E += q.eps_h * (s3 * s3 - 2.0 * s3);
+            if (__dsqrt_rn(d2) < r0 + 2.0) formed += 1.0;
+        }
+        const int p0 = q.pl.start[gb], p1 = p0 + q.pl.len[gb];
+        for (int p = p0; p < p1; ++p) {
+            const int j = q.pl.col[p];
+            if (j < i) continue;
+            const float4 pj = P[j];
+            const double c = sig2 / dist2_d(xi, yi, zi, pj.x, pj.y, pj.z);
+            E += q.eps_l * c * c * c;
+        }
+        if (t.flags[i] & kFlagPulled) {
+            const int qq = e.pull_of_sys[t.sys[i]];
+            if (qq >= 0 && e.pull_bead[qq] == i) {
+                const double tt = e.pull_v[qq] * ((double)step - e.pull_n0[qq]);
+                const double *tip0 = e.pull_tip0 + ((size_t)r * e.n_pull + qq) * 3;
+                const double *dir = e.pull_dir + 3 * qq;
+                const double x[3] = {xi, yi, zi};
+                double f = 0.0;
+                for (int k = 0; k < 3; ++k) f += e.pull_ks[qq] * (tip0[k] + tt * dir[k] - x[k]) * dir[k];
+                fpull += f;
+                const float4 pa = P[e.pull_anchor[qq]];
+                ext += __dsqrt_rn(dist2_d(xi, yi, zi, pa.x, pa.y, pa.z));
+            }
+        }
+        if (e.has_indenter) {
+            const double tt = e.ind_v * ((double)step - e.ind_n0);
+            const double c[3] = {e.ind_c0[0] + tt * e.ind_dir[0], e.ind_c0[1] + tt * e.ind_dir[1],
+                                 e.ind_c0[2] + tt * e.ind_dir[2]};
+            const double ex = xi - c[0], ey = yi - c[1], ez = zi - c[2];
+            const double rr = __dsqrt_rn((ex * ex + ey * ey) + ez * ez);
+            const double rho = rr - e.ind_radius;
+            if (rho > 0.0) {
+                const double qq = q.sigma / rho;
+                const double q2 = qq * qq;
+                const double q6 = q2 * q2 * q2;
+                const double coef = 6.0 * q.eps_l * q6 / rho / rr;
+                fwall += coef * ((ex * e.ind_dir[0] + ey * e.ind_dir[1]) + ez * e.ind_dir[2]);
+            }
+        }
+        if (t.flags[i] & kFlagFirstOfSystem) {
+            const float4 pl_ = P[t.sys_ree_last[t.sys[i]]];
+            ree += __dsqrt_rn(dist2_d(xi, yi, zi, pl_.x, pl_.y, pl_.z));
+        }
+    }
+    __shared__ double sh[kObsThreads / 32];
+    const double v0 = block_sum_d(E, sh);
+    const double v1 = block_sum_d(fpull, sh);
+    const double v2 = block_sum_d(ext, sh);
+    const double v3 = block_sum_d(formed, sh);
+    const double v4 = block_sum_d(fwall, sh);
+    const double v5 = block_sum_d(ree, sh);
+    if (threadIdx.x == 0) {
+        double *out = q.o.partial + (size_t)ch * 8;
+        out[0] = v0; out[1] = v1; out[2] = v2; out[3] = v3; out[4] = v4; out[5] = v5; out[6] = 0; out[7] = 0;
+    }
+}
+
+__global__ void k_obs_final(ObsArgs q, int n_seg) {
+    const int64_t step = *q.a.d_step + q.k_off;
+    if (q.gate > 0 && step % q.gate != 0) return;
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= n_seg) return;
+    double acc[6] = {0, 0, 0, 0, 0, 0};
+    for (int ch = q.o.seg_chunk_lo[g]; ch < q.o.seg_chunk_lo[g + 1]; ++ch)
+        for (int k = 0; k < 6; ++k) acc[k] += q.o.partial[(size_t)ch * 8 + k];
+    const int ns = q.a.topo.n_sys;
+    const int r = g / ns, s = g - r * ns;
+    const DevExternal &e = q.a.ext;
+    sop_record rec;
+    rec.step = (double)step;
+    rec.replica = (double)r;
+    rec.system = (double)s;
+    rec.energy = acc[0];
+    const bool pulled = e.pull_of_sys[s] >= 0;
+    rec.f_ext = pulled ? acc[1] : (e.has_indenter ? acc[4] : 0.0);
+    rec.extension = pulled ? acc[2] : (e.has_indenter ? e.ind_v * ((double)step - e.ind_n0) : 0.0);
+    const int np = q.a.topo.sys_nat_pairs[s];
+    rec.q = np > 0 ? acc[3] / (double)np : 0.0;
+    rec.r_ee = acc[5];
+    const int64_t slot = (*q.o.events * n_seg + g) % q.o.cap;
+    q.o.ring[slot] = rec;
+}
+
+// Per-replica energy (for sop_forces): sum of the replica's chunk partials.
+__global__ void k_energy_sum(const double *partial, const int32_t *seg_chunk_lo, int g_lo, int g_hi, double *out) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double e = 0.0;
+    for (int ch = seg_chunk_lo[g_lo]; ch < seg_chunk_lo[g_hi]; ++ch) e += partial[(size_t)ch * 8];
+    *out = e;
+}
+
+__global__ void k_tick(int64_t *d_step, int64_t k, int64_t *events, int32_t gate, int64_t n_events) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        const int64_t s = *d_step + k;
+        if (events) *events += gate > 0 ? (s % gate == 0 ? 1 : 0) : n_events;
+        *d_step = s;
+    }
+}
+
+inline int blocks_for(int64_t work, int threads) { return (int)((work + threads - 1) / threads); }
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Launchers
+// ---------------------------------------------------------------------------
+int64_t scan_tmp_elems(int64_t n) { return (n + kScanTile - 1) / kScanTile + 2; }
+
+void scan_exclusive(const int32_t *in, int32_t *out, int64_t n, int32_t *tmp, cudaStream_t s, int64_t *launches) {
+    const int64_t nb = (n + kScanTile - 1) / kScanTile;
+    if (nb > 0) k_scan_reduce<<<(unsigned)nb, kScanThreads, 0, s>>>(in, n, tmp);
+    k_scan_sums<<<1, kScanThreads, 0, s>>>(tmp, nb);
+    k_scan_final<<<(unsigned)(nb > 0 ? nb : 1), kScanThreads, 0, s>>>(in, out, n, tmp, nb);
+    if (launches) *launches += nb > 0 ? 3 : 2;
+}
+
+void launch_setup_bonds(const double *X, const int32_t *chain, float *bond_r0, double *bond_r0d, int32_t n,
+                        cudaStream_t s) {
+    k_setup_bonds<<<blocks_for(n, 256), 256, 0, s>>>(X, chain, bond_r0, bond_r0d, n);
+}
+
+void launch_native_count(const double *X, const int32_t *chain, const int32_t *sys, const int32_t *sys_lo, int32_t n,
+                         double cut, int32_t *count, cudaStream_t s) {
+    k_native<false><<<blocks_for(n, 128), 128, 0, s>>>(X, chain, sys, sys_lo, n, cut, count, nullptr, nullptr,
+                                                       nullptr, nullptr);
+}
+
+void launch_native_fill(const double *X, const int32_t *chain, const int32_t *sys, const int32_t *sys_lo, int32_t n,
+                        double cut, const int32_t *row, int32_t *col, double *r0, float *r0sq, cudaStream_t s) {
+    k_native<true><<<blocks_for(n, 128), 128, 0, s>>>(X, chain, sys, sys_lo, n, cut, nullptr, row, col, r0, r0sq);
+}
+
+void launch_rebuild(const StepArgs &sa, const DevCells &c, const DevPairList &pl, const float4 *pos, float4 *snap,
+                    const SegRange &rg, cudaStream_t s, int64_t *launches) {
+    if (rg.g_hi <= rg.g_lo) return;
+    RebuildArgs a;
+    a.pos = pos;
+    a.snap = snap;
+    a.sys = sa.topo.sys;
+    a.chain = sa.topo.chain;
+    a.n = sa.topo.n;
+    a.n_sys = sa.topo.n_sys;
+    a.g_lo = rg.g_lo;
+    a.cell_edge = sqrtf(sa.cut2_f);
+    a.seg_bead_lo = c.seg_bead_lo;
+    a.seg_cell_base = c.seg_cell_base;
+    a.seg_lo = c.seg_lo;
+    a.seg_dims = c.seg_dims;
+    a.cell_of = c.cell_of;
+    a.cell_cnt = c.cell_cnt;
+    a.cell_start = c.cell_start;
+    a.sorted = c.sorted;
+    a.sorted_base = rg.b_lo;
+    a.cell_base0 = rg.c_lo;
+    a.rep_status = sa.rep_status;
+    const int nb = rg.b_hi - rg.b_lo, nc = rg.c_hi - rg.c_lo;
+    k_seg_setup<<<rg.g_hi - rg.g_lo, 128, 0, s>>>(a, pl.cursor, pl.seg_base);
+    k_cell_count<<<blocks_for(nb, 256), 256, 0, s>>>(a, rg.b_lo, rg.b_hi);
+    scan_exclusive(c.cell_cnt + rg.c_lo, c.cell_start, nc, c.scan_tmp, s, launches);
+    k_cell_scatter<<<blocks_for(nb, 256), 256, 0, s>>>(a, rg.b_lo, rg.b_hi);
+    k_cell_sort<<<blocks_for(nc, 256), 256, 0, s>>>(a, rg.c_lo, rg.c_hi);
+    BuildExtra x;
+    x.nat_row = sa.topo.nat_row;
+    x.nat_col = sa.topo.nat_col;
+    x.cut2_d = sa.cut2_d;
+    x.cut2_f = sa.cut2_f;
+    x.pl_start = pl.start;
+    x.pl_len = pl.len;
+    x.pl_col = pl.col;
+    x.pl_cursor = pl.cursor;
+    x.pl_seg_end = pl.seg_end;
+    x.rep_status = sa.rep_status;
+    k_pl_build<<<blocks_for(nb, kBuildWarps), kBuildWarps * 32, 0, s>>>(a, x, rg.b_lo, rg.b_hi);
+    if (launches) *launches += 5;
+}
+
+void launch_step(const StepArgs &a, const DevPairList &pl, const float4 *pos_in, float4 *pos_out, float4 *comp,
+                 int32_t b_lo, int32_t b_hi, int32_t k_off, int lanes, cudaStream_t s, int64_t *launches) {
+    const int64_t threads = (int64_t)(b_hi - b_lo) * lanes;
+    const int blocks = blocks_for(threads, 256);
+    if (blocks <= 0) return;
+    switch (lanes) {
+    case 4: k_step<4><<<blocks, 256, 0, s>>>(a, pl, pos_in, pos_out, comp, b_lo, b_hi, k_off); break;
+    case 16: k_step<16><<<blocks, 256, 0, s>>>(a, pl, pos_in, pos_out, comp, b_lo, b_hi, k_off); break;
+    default: k_step<8><<<blocks, 256, 0, s>>>(a, pl, pos_in, pos_out, comp, b_lo, b_hi, k_off); break;
+    }
+    if (launches) *launches += 1;
+}
+
+void launch_forces(const StepArgs &a, const DevPairList &pl, const float4 *pos, float4 *force, int32_t b_lo,
+                   int32_t b_hi, int64_t step, cudaStream_t s, int64_t *launches) {
+    const int64_t threads = (int64_t)(b_hi - b_lo) * 8;
+    const int blocks = blocks_for(threads, 256);
+    if (blocks <= 0) return;
+    k_forces<8><<<blocks, 256, 0, s>>>(a, pl, pos, force, b_lo, b_hi, step);
+    if (launches) *launches += 1;
+}
+
+static ObsArgs make_obs_args(const StepArgs &a, const DevPairList &pl, const DevObs &o, const float4 *pos,
+                             int32_t k_off, int32_t gate) {
+    ObsArgs q;
+    q.a = a;
+    q.pl = pl;
+    q.o = o;
+    q.pos = pos;
+    q.k_off = k_off;
+    q.gate = gate;
+    q.eps_h = a.eps_h;
+    q.eps_l = a.eps_l;
+    q.sigma = a.sigma;
+    q.k_fene = a.k_fene;
+    q.R0 = a.R0;
+    q.bond_r0d = a.topo.bond_r0d;
+    return q;
+}
+
+void launch_observables(const StepArgs &a, const DevPairList &pl, const DevObs &o, const float4 *pos, int32_t n_seg,
+                        int32_t k_off, int32_t gate, cudaStream_t s, int64_t *launches) {
+    if (o.n_chunks <= 0) return;
+    ObsArgs q = make_obs_args(a, pl, o, pos, k_off, gate);
+    k_obs_partial<<<o.n_chunks, kObsThreads, 0, s>>>(q);
+    k_obs_final<<<blocks_for(n_seg, 128), 128, 0, s>>>(q, n_seg);
+    if (launches) *launches += 2;
+}
+
+void launch_energy(const StepArgs &a, const DevPairList &pl, const DevObs &o, const float4 *pos, int32_t g_lo,
+                   int32_t g_hi, double *out, cudaStream_t s, int64_t *launches) {
+    if (o.n_chunks <= 0) return;
+    ObsArgs q = make_obs_args(a, pl, o, pos, 0, 0);
+    k_obs_partial<<<o.n_chunks, kObsThreads, 0, s>>>(q);
+    k_energy_sum<<<1, 32, 0, s>>>(o.partial, o.seg_chunk_lo, g_lo, g_hi, out);
+    if (launches) *launches += 2;
+}
+
+void launch_tick(int64_t *d_step, int64_t k, int64_t *events, int32_t gate, int64_t n_events, cudaStream_t s,
+                 int64_t *launches) {
+    k_tick<<<1, 32, 0, s>>>(d_step, k, events, gate, n_events);
+    if (launches) *launches += 1;
+}
+
+}  // namespace sop

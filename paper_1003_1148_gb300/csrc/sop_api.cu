@@ -1,0 +1,1343 @@
+// C ABI of the SOP-model Langevin library: context life cycle, schedules,
+// CUDA-graph replay, host I/O and checkpoints. Declared in include/sop.h.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "sop_internal.h"
+
+using namespace sop;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+constexpr int kObsChunk = 2048;        // beads per FP64 observable partial
+constexpr int kBatchedMaxBeads = 2048; // largest system the batched schedule takes
+constexpr int64_t kBatchedChunk = 4096;  // steps per batched launch
+
+// k_B in kcal/(mol K): molar gas constant 8.314462618 J/(mol K) / 4184 J/kcal.
+constexpr double kBoltzmannKcal = 8.314462618 / 4184.0;
+
+}  // namespace
+
+struct sop_ctx {
+    // sizes
+    int32_t n = 0, n_chains = 0, n_sys = 0, R = 0, n_seg = 0;
+    sop_params prm{};
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int device = 0;
+    // host topology
+    std::vector<int32_t> chain_off, sys_lo, chain_of, sys_of, sys_ree_last;
+    std::vector<uint8_t> flags;
+    std::vector<int32_t> h_nat_row, h_nat_col;
+    std::vector<double> h_nat_r0;
+    std::vector<int32_t> h_seg_bead_lo, h_seg_cell_base, h_seg_chunk_lo;
+    // device memory
+    std::vector<void *> allocs;
+    int32_t *d_chain = nullptr, *d_sys = nullptr, *d_sys_lo = nullptr, *d_sys_ree_last = nullptr,
+            *d_sys_nat_pairs = nullptr;
+    uint8_t *d_flags = nullptr;
+    float *d_bond_r0 = nullptr;
+    double *d_bond_r0d = nullptr;
+    int32_t *d_nat_row = nullptr, *d_nat_col = nullptr;
+    float *d_nat_r0sq = nullptr;
+    double *d_nat_r0 = nullptr;
+    int64_t nat_nnz = 0;
+    // batched natives (ELL)
+    int32_t *d_nat_ell_off = nullptr, *d_nat_ell_cnt = nullptr;
+    uint16_t *d_nat_ell_col = nullptr;
+    float *d_nat_ell_r0sq = nullptr;
+    // state
+    float4 *d_pos[2] = {nullptr, nullptr};
+    float4 *d_comp = nullptr, *d_snap = nullptr, *d_force = nullptr;
+    int cur = 0;
+    int64_t step = 0, list_step = -1, events = 0, consumed = 0;
+    int64_t *d_step = nullptr, *d_events = nullptr;
+    int32_t *d_rep_status = nullptr, *d_halt = nullptr;
+    double *d_energy = nullptr;
+    int32_t *h_abort = nullptr;      // host-mapped
+    int32_t *d_abort = nullptr;
+    // streamed list and cells
+    DevPairList pl, pl2;
+    DevCells cells;
+    int64_t pl_cap = 0;
+    int ppb = 64;
+    // dumps of the batched list
+    int32_t *d_dump_start = nullptr, *d_dump_len = nullptr, *d_dump_col = nullptr;
+    // observables
+    DevObs obs;
+    // external forces (host mirrors)
+    std::vector<int32_t> pull_of_sys, pull_anchor, pull_bead, pull_sys;
+    std::vector<double> pull_ks, pull_v, pull_dir, pull_n0, pull_tip0;
+    int32_t *d_pull_of_sys = nullptr, *d_pull_anchor = nullptr, *d_pull_bead = nullptr;
+    double *d_pull_ks = nullptr, *d_pull_v = nullptr, *d_pull_dir = nullptr, *d_pull_n0 = nullptr,
+           *d_pull_tip0 = nullptr;
+    size_t pull_alloc = 0;
+    bool has_ind = false;
+    double ind_c0[3] = {0, 0, 0}, ind_dir[3] = {0, 0, 0}, ind_radius = 0, ind_v = 0, ind_n0 = 0;
+    // kernel arguments
+    StepArgs sa;
+    // batched schedule
+    int schedule = SOP_SCHED_STREAMED;
+    BatchedConfig bcfg;
+    int batched_cap = 64;
+    int max_sys = 0;
+    int32_t n_items = 0;
+    int32_t *d_item_rep = nullptr, *d_item_sys = nullptr;
+    // graphs: [start buffer] for the streamed K-step chunk, one for the batched chunk
+    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+    cudaGraphExec_t bexec = nullptr;
+    // in-flight limiter: at most kInFlight chunks queued ahead of the device, so that
+    // sop_abort takes effect within a few chunks and the step counter stays exact
+    cudaEvent_t chunk_ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    int64_t chunk_no = 0;
+    bool graphs_enabled = true;
+    int lanes = 8;
+    sop_stats st{};
+    std::string err;
+};
+
+namespace {
+
+sop_status fail(sop_ctx *c, sop_status code, const std::string &msg) {
+    if (c) c->err = msg;
+    else g_create_error = msg;
+    return code;
+}
+
+#define CUDA_OR_RETURN(ctx, expr)                                                                      \
+    do {                                                                                               \
+        cudaError_t e_ = (expr);                                                                       \
+        if (e_ != cudaSuccess)                                                                         \
+            return fail((ctx), e_ == cudaErrorMemoryAllocation ? SOP_ERR_OOM : SOP_ERR_CUDA,           \
+                        std::string(#expr) + ": " + cudaGetErrorString(e_));                           \
+    } while (0)
+
+template <typename T>
+cudaError_t dalloc(sop_ctx *c, T **p, size_t count) {
+    void *q = nullptr;
+    cudaError_t e = cudaMalloc(&q, std::max<size_t>(1, count) * sizeof(T));
+    if (e == cudaSuccess) {
+        c->allocs.push_back(q);
+        *p = static_cast<T *>(q);
+    }
+    return e;
+}
+
+template <typename T>
+cudaError_t upload(sop_ctx *c, T **p, const std::vector<T> &v) {
+    cudaError_t e = dalloc(c, p, v.size());
+    if (e != cudaSuccess) return e;
+    if (!v.empty()) e = cudaMemcpy(*p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
+    return e;
+}
+
+bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
+
+constexpr int kInFlight = 3;
+
+// Wait until no more than kInFlight chunks are queued, then record this chunk's slot.
+sop_status throttle_before_chunk(sop_ctx *c) {
+    if (!c->chunk_ev[0])
+        for (auto &e : c->chunk_ev) CUDA_OR_RETURN(c, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    if (c->chunk_no >= kInFlight) CUDA_OR_RETURN(c, cudaEventSynchronize(c->chunk_ev[(c->chunk_no - kInFlight) % 4]));
+    return SOP_OK;
+}
+
+sop_status record_chunk(sop_ctx *c) {
+    CUDA_OR_RETURN(c, cudaEventRecord(c->chunk_ev[c->chunk_no % 4], c->stream));
+    c->chunk_no++;
+    return SOP_OK;
+}
+
+void destroy_graphs(sop_ctx *c) {
+    for (auto &g : c->gexec)
+        if (g) { cudaGraphExecDestroy(g); g = nullptr; }
+    if (c->bexec) { cudaGraphExecDestroy(c->bexec); c->bexec = nullptr; }
+}
+
+SegRange full_range(const sop_ctx *c) {
+    SegRange r;
+    r.g_lo = 0;
+    r.g_hi = c->n_seg;
+    r.b_lo = c->h_seg_bead_lo[0];
+    r.b_hi = c->h_seg_bead_lo[c->n_seg];
+    r.c_lo = c->h_seg_cell_base[0];
+    r.c_hi = c->h_seg_cell_base[c->n_seg];
+    return r;
+}
+
+SegRange seg_range(const sop_ctx *c, int g_lo, int g_hi) {
+    SegRange r;
+    r.g_lo = g_lo;
+    r.g_hi = g_hi;
+    r.b_lo = c->h_seg_bead_lo[g_lo];
+    r.b_hi = c->h_seg_bead_lo[g_hi];
+    r.c_lo = c->h_seg_cell_base[g_lo];
+    r.c_hi = c->h_seg_cell_base[g_hi];
+    return r;
+}
+
+// Refresh the pulling / indenter part of the kernel arguments.
+void sync_external(sop_ctx *c) {
+    DevExternal &e = c->sa.ext;
+    e.pull_of_sys = c->d_pull_of_sys;
+    e.pull_anchor = c->d_pull_anchor;
+    e.pull_bead = c->d_pull_bead;
+    e.pull_ks = c->d_pull_ks;
+    e.pull_v = c->d_pull_v;
+    e.pull_dir = c->d_pull_dir;
+    e.pull_n0 = c->d_pull_n0;
+    e.pull_tip0 = c->d_pull_tip0;
+    e.n_pull = (int32_t)c->pull_bead.size();
+    e.has_indenter = c->has_ind ? 1 : 0;
+    for (int k = 0; k < 3; ++k) { e.ind_c0[k] = c->ind_c0[k]; e.ind_dir[k] = c->ind_dir[k]; }
+    e.ind_radius = c->ind_radius;
+    e.ind_v = c->ind_v;
+    e.ind_n0 = c->ind_n0;
+}
+
+sop_status rebuild_streamed(sop_ctx *c) {
+    launch_rebuild(c->sa, c->cells, c->pl, c->d_pos[c->cur], c->d_snap, full_range(c), c->stream,
+                   &c->st.kernel_launches);
+    c->list_step = c->step;
+    c->st.rebuilds++;
+    CUDA_OR_RETURN(c, cudaGetLastError());
+    return SOP_OK;
+}
+
+BatchedArgs batched_args(sop_ctx *c) {
+    BatchedArgs a;
+    a.sa = c->sa;
+    a.n_items = c->n_items;
+    a.item_rep = c->d_item_rep;
+    a.item_sys = c->d_item_sys;
+    a.nat_ell_off = c->d_nat_ell_off;
+    a.nat_ell_cnt = c->d_nat_ell_cnt;
+    a.nat_ell_col = c->d_nat_ell_col;
+    a.nat_ell_r0sq = c->d_nat_ell_r0sq;
+    a.pos = c->d_pos[0];
+    a.comp = c->d_comp;
+    a.snap = c->d_snap;
+    a.d_step = c->d_step;
+    a.d_events = c->d_events;
+    a.K = c->prm.rebuild_every;
+    a.cap = c->batched_cap;
+    a.max_n = c->max_sys;
+    a.obs = c->obs;
+    a.obs_every = c->prm.obs_every;
+    a.n_seg = c->n_seg;
+    return a;
+}
+
+int64_t events_in(int64_t s0, int64_t s1, int32_t every) {   // multiples of every in (s0, s1]
+    if (every <= 0) return 0;
+    auto fl = [every](int64_t x) { return x >= 0 ? x / every : -((-x + every - 1) / every); };
+    return fl(s1) - fl(s0);
+}
+
+void note_events(sop_ctx *c, int64_t s0, int64_t s1) { c->events += events_in(s0, s1, c->prm.obs_every); }
+
+// ---- streamed schedule --------------------------------------------------------------
+// One K-step chunk from an aligned step whose list is current: K fused steps, the
+// rebuild for the next chunk, the observables of the chunk's last step (gated on the
+// device), and the step counter advance.
+void enqueue_streamed_chunk(sop_ctx *c, int start_buf, int64_t *launches) {
+    const int K = c->prm.rebuild_every;
+    const SegRange all = full_range(c);
+    int b = start_buf;
+    for (int k = 0; k < K; ++k) {
+        launch_step(c->sa, c->pl, c->d_pos[b], c->d_pos[b ^ 1], c->d_comp, all.b_lo, all.b_hi, k, c->lanes, c->stream,
+                    launches);
+        b ^= 1;
+    }
+    // the list of step + K is built from the positions of step + K (the next chunk's first step)
+    StepArgs sa2 = c->sa;
+    launch_rebuild(sa2, c->cells, c->pl, c->d_pos[b], c->d_snap, all, c->stream, launches);
+    if (c->prm.obs_every > 0)
+        launch_observables(c->sa, c->pl, c->obs, c->d_pos[b], c->n_seg, K, c->prm.obs_every, c->stream, launches);
+    launch_tick(c->d_step, K, c->d_events, c->prm.obs_every > 0 ? c->prm.obs_every : 0, 0, c->stream, launches);
+}
+
+sop_status build_streamed_graph(sop_ctx *c, int start_buf) {
+    cudaGraph_t g = nullptr;
+    int64_t launches = 0;
+    CUDA_OR_RETURN(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+    enqueue_streamed_chunk(c, start_buf, &launches);
+    cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+    if (e != cudaSuccess) return fail(c, SOP_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&c->gexec[start_buf], g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return fail(c, SOP_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+    return SOP_OK;
+}
+
+int64_t streamed_chunk_launches(const sop_ctx *c) {
+    // K steps + rebuild (8 or 7) + observables (2) + tick
+    return c->prm.rebuild_every + 8 + (c->prm.obs_every > 0 ? 2 : 0) + 1;
+}
+
+sop_status step_streamed(sop_ctx *c, int64_t n_steps) {
+    const int K = c->prm.rebuild_every;
+    const int32_t every = c->prm.obs_every;
+    const bool aligned_obs = every <= 0 || every % K == 0;
+    const SegRange all = full_range(c);
+    int64_t left = n_steps;
+    while (left > 0) {
+        if (*(volatile int32_t *)c->h_abort) break;
+        if (c->step % K == 0 && left >= K && aligned_obs && c->graphs_enabled) {
+            if (c->list_step != c->step) {
+                sop_status s = rebuild_streamed(c);
+                if (s != SOP_OK) return s;
+            }
+            if (!c->gexec[c->cur]) {
+                sop_status s = build_streamed_graph(c, c->cur);
+                if (s != SOP_OK) return s;
+            }
+            sop_status th = throttle_before_chunk(c);
+            if (th != SOP_OK) return th;
+            CUDA_OR_RETURN(c, cudaGraphLaunch(c->gexec[c->cur], c->stream));
+            th = record_chunk(c);
+            if (th != SOP_OK) return th;
+            c->st.graph_launches++;
+            c->st.kernel_launches += streamed_chunk_launches(c);
+            c->st.rebuilds++;
+            if (K & 1) c->cur ^= 1;
+            note_events(c, c->step, c->step + K);
+            c->step += K;
+            c->list_step = c->step;
+            left -= K;
+            continue;
+        }
+        // single step
+        if (c->step % K == 0 && c->list_step != c->step) {
+            sop_status s = rebuild_streamed(c);
+            if (s != SOP_OK) return s;
+        }
+        launch_step(c->sa, c->pl, c->d_pos[c->cur], c->d_pos[c->cur ^ 1], c->d_comp, all.b_lo, all.b_hi, 0, c->lanes,
+                    c->stream, &c->st.kernel_launches);
+        c->cur ^= 1;
+        const int64_t s1 = c->step + 1;
+        if (every > 0 && s1 % every == 0) {
+            if (s1 % K == 0) {
+                launch_rebuild(c->sa, c->cells, c->pl, c->d_pos[c->cur], c->d_snap, all, c->stream,
+                               &c->st.kernel_launches);
+                c->st.rebuilds++;
+                c->list_step = s1;
+            }
+            launch_observables(c->sa, c->pl, c->obs, c->d_pos[c->cur], c->n_seg, 1, 0, c->stream,
+                               &c->st.kernel_launches);
+        }
+        launch_tick(c->d_step, 1, c->d_events, 0, (every > 0 && s1 % every == 0) ? 1 : 0, c->stream,
+                    &c->st.kernel_launches);
+        note_events(c, c->step, s1);
+        c->step = s1;
+        --left;
+    }
+    CUDA_OR_RETURN(c, cudaGetLastError());
+    return SOP_OK;
+}
+
+// ---- plain schedule: one system after another, per-step launches, no graph ---------------
+sop_status step_plain(sop_ctx *c, int64_t n_steps) {
+    const int K = c->prm.rebuild_every;
+    const int64_t s0 = c->step;
+    for (int g = 0; g < c->n_seg; ++g) {
+        if (*(volatile int32_t *)c->h_abort) break;
+        const SegRange rg = seg_range(c, g, g + 1);
+        int b = c->cur;
+        for (int64_t k = 0; k < n_steps; ++k) {
+            const int64_t s = s0 + k;
+            if (s % K == 0 && !(k == 0 && c->list_step == s))
+                launch_rebuild(c->sa, c->cells, c->pl, c->d_pos[b], c->d_snap, rg, c->stream, &c->st.kernel_launches);
+            launch_step(c->sa, c->pl, c->d_pos[b], c->d_pos[b ^ 1], c->d_comp, rg.b_lo, rg.b_hi, (int32_t)k, c->lanes,
+                        c->stream, &c->st.kernel_launches);
+            b ^= 1;
+        }
+    }
+    launch_tick(c->d_step, n_steps, c->d_events, 0, 0, c->stream, &c->st.kernel_launches);
+    if (n_steps & 1) c->cur ^= 1;
+    c->step = s0 + n_steps;
+    // the list in use is the one built at the last multiple of K inside this call, if any
+    if (n_steps > 0) {
+        const int64_t last = ((c->step - 1) / K) * K;
+        if (last >= s0) c->list_step = last;
+    }
+    CUDA_OR_RETURN(c, cudaGetLastError());
+    return SOP_OK;
+}
+
+// ---- batched schedule -----------------------------------------------------------------
+sop_status step_batched(sop_ctx *c, int64_t n_steps) {
+    // The batched kernel reads and writes layer 0; bring the state there first.
+    if (c->cur != 0) {
+        CUDA_OR_RETURN(c, cudaMemcpyAsync(c->d_pos[0], c->d_pos[1], sizeof(float4) * (size_t)c->R * c->n,
+                                          cudaMemcpyDeviceToDevice, c->stream));
+        c->cur = 0;
+    }
+    int64_t left = n_steps;
+    while (left > 0) {
+        if (*(volatile int32_t *)c->h_abort) break;
+        const int64_t chunk = std::min<int64_t>(left, kBatchedChunk);
+        const int64_t nev = events_in(c->step, c->step + chunk, c->prm.obs_every);
+        sop_status th = throttle_before_chunk(c);
+        if (th != SOP_OK) return th;
+        BatchedArgs a = batched_args(c);
+        a.n_steps = (int32_t)chunk;
+        // a full chunk whose cadence divides it always holds the same number of records:
+        // replay it from a graph; anything else is launched directly
+        const bool regular = c->prm.obs_every <= 0 || kBatchedChunk % c->prm.obs_every == 0;
+        if (c->graphs_enabled && chunk == kBatchedChunk && regular) {
+            if (!c->bexec) {
+                cudaGraph_t g = nullptr;
+                CUDA_OR_RETURN(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+                int64_t dummy = 0;
+                cudaError_t e1 = launch_batched(a, c->bcfg, c->stream, &dummy);
+                launch_tick(c->d_step, chunk, c->d_events, 0, nev, c->stream, &dummy);
+                cudaError_t e2 = cudaStreamEndCapture(c->stream, &g);
+                if (e1 != cudaSuccess || e2 != cudaSuccess)
+                    return fail(c, SOP_ERR_CUDA, std::string("batched graph capture: ") +
+                                                     cudaGetErrorString(e1 != cudaSuccess ? e1 : e2));
+                cudaError_t e3 = cudaGraphInstantiate(&c->bexec, g, 0);
+                cudaGraphDestroy(g);
+                if (e3 != cudaSuccess)
+                    return fail(c, SOP_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e3));
+            }
+            CUDA_OR_RETURN(c, cudaGraphLaunch(c->bexec, c->stream));
+            c->st.graph_launches++;
+            c->st.kernel_launches += 2;
+        } else {
+            cudaError_t e = launch_batched(a, c->bcfg, c->stream, &c->st.kernel_launches);
+            if (e != cudaSuccess) return fail(c, SOP_ERR_CUDA, std::string("batched launch: ") + cudaGetErrorString(e));
+            launch_tick(c->d_step, chunk, c->d_events, 0, nev, c->stream, &c->st.kernel_launches);
+        }
+        th = record_chunk(c);
+        if (th != SOP_OK) return th;
+        c->st.rebuilds += events_in(c->step - 1, c->step + chunk - 1, c->prm.rebuild_every);
+        note_events(c, c->step, c->step + chunk);
+        c->step += chunk;
+        c->list_step = (c->step / c->prm.rebuild_every) * c->prm.rebuild_every;
+        left -= chunk;
+    }
+    CUDA_OR_RETURN(c, cudaGetLastError());
+    return SOP_OK;
+}
+
+// Validate and normalise inputs; fill the host topology tables.
+sop_status build_host_topology(sop_ctx *c, const sop_topology *t) {
+    if (!t || t->n_beads < 1 || t->n_chains < 1 || !t->chain_offsets)
+        return fail(nullptr, SOP_ERR_INVALID_ARG, "topology: n_beads >= 1, n_chains >= 1 and chain_offsets required");
+    if (t->n_beads > (1 << 26)) return fail(nullptr, SOP_ERR_INVALID_ARG, "topology: too many beads per replica");
+    c->n = t->n_beads;
+    c->n_chains = t->n_chains;
+    c->chain_off.assign(t->chain_offsets, t->chain_offsets + t->n_chains + 1);
+    if (c->chain_off[0] != 0 || c->chain_off[t->n_chains] != t->n_beads)
+        return fail(nullptr, SOP_ERR_INVALID_ARG, "topology: chain_offsets must start at 0 and end at n_beads");
+    for (int k = 0; k < t->n_chains; ++k)
+        if (c->chain_off[k + 1] <= c->chain_off[k])
+            return fail(nullptr, SOP_ERR_INVALID_ARG, "topology: chain_offsets must be strictly increasing");
+    std::vector<int32_t> sys_chain;   // [n_sys+1] in chains
+    if (t->n_systems == 0) {
+        sys_chain.resize(t->n_chains + 1);
+        for (int k = 0; k <= t->n_chains; ++k) sys_chain[k] = k;
+    } else {
+        if (t->n_systems < 0 || !t->system_offsets)
+            return fail(nullptr, SOP_ERR_INVALID_ARG, "topology: system_offsets required when n_systems > 0");
+        sys_chain.assign(t->system_offsets, t->system_offsets + t->n_systems + 1);
+        if (sys_chain[0] != 0 || sys_chain[t->n_systems] != t->n_chains)
+            return fail(nullptr, SOP_ERR_INVALID_ARG, "topology: system_offsets must start at 0 and end at n_chains");
+        for (int k = 0; k < t->n_systems; ++k)
+            if (sys_chain[k + 1] <= sys_chain[k])
+                return fail(nullptr, SOP_ERR_INVALID_ARG, "topology: system_offsets must be strictly increasing");
+    }
+    c->n_sys = (int32_t)sys_chain.size() - 1;
+    c->sys_lo.resize(c->n_sys + 1);
+    for (int s = 0; s <= c->n_sys; ++s) c->sys_lo[s] = c->chain_off[sys_chain[s]];
+    c->chain_of.resize(c->n);
+    c->sys_of.resize(c->n);
+    for (int k = 0; k < c->n_chains; ++k)
+        for (int i = c->chain_off[k]; i < c->chain_off[k + 1]; ++i) c->chain_of[i] = k;
+    for (int s = 0; s < c->n_sys; ++s)
+        for (int i = c->sys_lo[s]; i < c->sys_lo[s + 1]; ++i) c->sys_of[i] = s;
+    c->flags.assign(c->n, 0);
+    if (t->fixed_mask)
+        for (int i = 0; i < c->n; ++i) c->flags[i] = t->fixed_mask[i] ? kFlagFixed : 0;
+    c->sys_ree_last.resize(c->n_sys);
+    for (int s = 0; s < c->n_sys; ++s) {
+        const int first = c->sys_lo[s];
+        c->flags[first] |= kFlagFirstOfSystem;
+        c->sys_ree_last[s] = c->chain_off[c->chain_of[first] + 1] - 1;
+        c->max_sys = std::max(c->max_sys, c->sys_lo[s + 1] - c->sys_lo[s]);
+    }
+    return SOP_OK;
+}
+
+sop_status validate_params(const sop_params *p) {
+    if (!p) return fail(nullptr, SOP_ERR_INVALID_ARG, "params is NULL");
+    const double pos[] = {p->k_fene, p->R0, p->native_cut, p->sigma, p->zeta, p->dt, p->pair_cut};
+    for (double v : pos)
+        if (!finite_pos(v)) return fail(nullptr, SOP_ERR_INVALID_ARG, "params: k_fene, R0, native_cut, sigma, zeta, dt, pair_cut must be finite and > 0");
+    if (!std::isfinite(p->eps_h) || !std::isfinite(p->eps_l) || p->eps_h < 0 || p->eps_l < 0)
+        return fail(nullptr, SOP_ERR_INVALID_ARG, "params: eps_h, eps_l must be finite and >= 0");
+    if (!std::isfinite(p->T) || p->T < 0) return fail(nullptr, SOP_ERR_INVALID_ARG, "params: T must be finite and >= 0");
+    if (p->rebuild_every < 1) return fail(nullptr, SOP_ERR_INVALID_ARG, "params: rebuild_every >= 1");
+    if (p->n_replicas < 1) return fail(nullptr, SOP_ERR_INVALID_ARG, "params: n_replicas >= 1");
+    if (p->obs_every < 0 || p->obs_capacity < 0 || p->pairs_per_bead < 0)
+        return fail(nullptr, SOP_ERR_INVALID_ARG, "params: obs_every, obs_capacity, pairs_per_bead >= 0");
+    if (p->schedule < SOP_SCHED_AUTO || p->schedule > SOP_SCHED_PLAIN)
+        return fail(nullptr, SOP_ERR_INVALID_ARG, "params: unknown schedule");
+    return SOP_OK;
+}
+
+sop_status alloc_pull_arrays(sop_ctx *c, size_t n_pull) {
+    if (n_pull <= c->pull_alloc && c->d_pull_anchor) return SOP_OK;
+    const size_t m = std::max<size_t>(1, n_pull);
+    CUDA_OR_RETURN(c, dalloc(c, &c->d_pull_anchor, m));
+    CUDA_OR_RETURN(c, dalloc(c, &c->d_pull_bead, m));
+    CUDA_OR_RETURN(c, dalloc(c, &c->d_pull_ks, m));
+    CUDA_OR_RETURN(c, dalloc(c, &c->d_pull_v, m));
+    CUDA_OR_RETURN(c, dalloc(c, &c->d_pull_dir, 3 * m));
+    CUDA_OR_RETURN(c, dalloc(c, &c->d_pull_n0, m));
+    CUDA_OR_RETURN(c, dalloc(c, &c->d_pull_tip0, 3 * m * (size_t)c->R));
+    c->pull_alloc = m;
+    return SOP_OK;
+}
+
+sop_status upload_pulls(sop_ctx *c) {
+    const size_t np = c->pull_bead.size();
+    sop_status s = alloc_pull_arrays(c, np);
+    if (s != SOP_OK) return s;
+    CUDA_OR_RETURN(c, cudaMemcpy(c->d_pull_of_sys, c->pull_of_sys.data(), sizeof(int32_t) * c->n_sys, cudaMemcpyHostToDevice));
+    if (np) {
+        CUDA_OR_RETURN(c, cudaMemcpy(c->d_pull_anchor, c->pull_anchor.data(), sizeof(int32_t) * np, cudaMemcpyHostToDevice));
+        CUDA_OR_RETURN(c, cudaMemcpy(c->d_pull_bead, c->pull_bead.data(), sizeof(int32_t) * np, cudaMemcpyHostToDevice));
+        CUDA_OR_RETURN(c, cudaMemcpy(c->d_pull_ks, c->pull_ks.data(), sizeof(double) * np, cudaMemcpyHostToDevice));
+        CUDA_OR_RETURN(c, cudaMemcpy(c->d_pull_v, c->pull_v.data(), sizeof(double) * np, cudaMemcpyHostToDevice));
+        CUDA_OR_RETURN(c, cudaMemcpy(c->d_pull_dir, c->pull_dir.data(), sizeof(double) * 3 * np, cudaMemcpyHostToDevice));
+        CUDA_OR_RETURN(c, cudaMemcpy(c->d_pull_n0, c->pull_n0.data(), sizeof(double) * np, cudaMemcpyHostToDevice));
+        CUDA_OR_RETURN(c, cudaMemcpy(c->d_pull_tip0, c->pull_tip0.data(), sizeof(double) * 3 * np * c->R,
+                                     cudaMemcpyHostToDevice));
+    }
+    CUDA_OR_RETURN(c, cudaMemcpy(c->d_flags, c->flags.data(), c->n, cudaMemcpyHostToDevice));
+    sync_external(c);
+    destroy_graphs(c);   // kernel arguments changed
+    return SOP_OK;
+}
+
+// Copy positions of every replica to the host as float4.
+sop_status positions_f4(sop_ctx *c, std::vector<float4> &h) {
+    h.resize((size_t)c->R * c->n);
+    CUDA_OR_RETURN(c, cudaMemcpyAsync(h.data(), c->d_pos[c->cur], sizeof(float4) * h.size(), cudaMemcpyDeviceToHost,
+                                      c->stream));
+    CUDA_OR_RETURN(c, cudaStreamSynchronize(c->stream));
+    return SOP_OK;
+}
+
+sop_status read_status(sop_ctx *c, bool aborted) {
+    std::vector<int32_t> st(c->R);
+    CUDA_OR_RETURN(c, cudaMemcpyAsync(st.data(), c->d_rep_status, sizeof(int32_t) * c->R, cudaMemcpyDeviceToHost,
+                                      c->stream));
+    CUDA_OR_RETURN(c, cudaStreamSynchronize(c->stream));
+    for (int r = 0; r < c->R; ++r)
+        if (st[r] != 0 && st[r] != SOP_ERR_ABORTED) {
+            char buf[160];
+            std::snprintf(buf, sizeof buf, "replica %d stopped with status %d (first failing replica)", r, st[r]);
+            return fail(c, (sop_status)st[r], buf);
+        }
+    if (aborted) return fail(c, SOP_ERR_ABORTED, "aborted by sop_abort");
+    return SOP_OK;
+}
+
+// Batched natives: per system, column-major ELL of system-local partner indices.
+sop_status build_batched_tables(sop_ctx *c) {
+    std::vector<int32_t> off(c->n_sys), cnt(c->n);
+    std::vector<uint16_t> col;
+    std::vector<float> r0sq;
+    std::vector<float> h_r0sq(c->nat_nnz);
+    if (c->nat_nnz) {
+        CUDA_OR_RETURN(c, cudaMemcpy(h_r0sq.data(), c->d_nat_r0sq, sizeof(float) * c->nat_nnz, cudaMemcpyDeviceToHost));
+    }
+    size_t total = 0;
+    for (int s = 0; s < c->n_sys; ++s) {
+        const int lo = c->sys_lo[s], hi = c->sys_lo[s + 1], ns = hi - lo;
+        int w = 0;
+        for (int i = lo; i < hi; ++i) {
+            cnt[i] = c->h_nat_row[i + 1] - c->h_nat_row[i];
+            w = std::max(w, cnt[i]);
+        }
+        off[s] = (int32_t)total;
+        total += (size_t)w * ns;
+    }
+    if (total > (size_t)INT32_MAX) return fail(c, SOP_ERR_UNSUPPORTED, "batched native table too large");
+    col.assign(std::max<size_t>(1, total), 0);
+    r0sq.assign(std::max<size_t>(1, total), 0.f);
+    for (int s = 0; s < c->n_sys; ++s) {
+        const int lo = c->sys_lo[s], hi = c->sys_lo[s + 1], ns = hi - lo;
+        for (int i = lo; i < hi; ++i)
+            for (int k = 0; k < cnt[i]; ++k) {
+                const int p = c->h_nat_row[i] + k;
+                const size_t e = (size_t)off[s] + (size_t)k * ns + (i - lo);
+                col[e] = (uint16_t)(c->h_nat_col[p] - lo);
+                r0sq[e] = h_r0sq[p];
+            }
+    }
+    CUDA_OR_RETURN(c, upload(c, &c->d_nat_ell_off, off));
+    CUDA_OR_RETURN(c, upload(c, &c->d_nat_ell_cnt, cnt));
+    CUDA_OR_RETURN(c, upload(c, &c->d_nat_ell_col, col));
+    CUDA_OR_RETURN(c, upload(c, &c->d_nat_ell_r0sq, r0sq));
+    // work items, heaviest system first
+    std::vector<int32_t> order(c->n_sys);
+    for (int s = 0; s < c->n_sys; ++s) order[s] = s;
+    std::stable_sort(order.begin(), order.end(), [c](int a, int b) {
+        return c->sys_lo[a + 1] - c->sys_lo[a] > c->sys_lo[b + 1] - c->sys_lo[b];
+    });
+    std::vector<int32_t> ir, is;
+    for (int s : order)
+        for (int r = 0; r < c->R; ++r) { ir.push_back(r); is.push_back(s); }
+    c->n_items = (int32_t)ir.size();
+    CUDA_OR_RETURN(c, upload(c, &c->d_item_rep, ir));
+    CUDA_OR_RETURN(c, upload(c, &c->d_item_sys, is));
+    return SOP_OK;
+}
+
+// Largest Verlet row of replica 0 after the initial build.
+sop_status max_row(sop_ctx *c, int *out) {
+    std::vector<int32_t> len(c->n);
+    CUDA_OR_RETURN(c, cudaMemcpy(len.data(), c->pl.len, sizeof(int32_t) * c->n, cudaMemcpyDeviceToHost));
+    int m = 0;
+    int64_t tot = 0;
+    for (int v : len) { m = std::max(m, v); tot += v; }
+    c->st.pairlist_entries = tot;
+    *out = m;
+    return SOP_OK;
+}
+
+sop_status create_impl(sop_ctx *c, const sop_topology *topo, const double *xyz, const sop_params *p) {
+    sop_status s = validate_params(p);
+    if (s != SOP_OK) return s;
+    if (!xyz) return fail(nullptr, SOP_ERR_INVALID_ARG, "native_xyz is NULL");
+    s = build_host_topology(c, topo);
+    if (s != SOP_OK) return s;
+    for (int64_t k = 0; k < 3 * (int64_t)c->n; ++k)
+        if (!std::isfinite(xyz[k])) return fail(nullptr, SOP_ERR_INVALID_ARG, "native_xyz holds a non-finite value");
+    c->prm = *p;
+    c->R = p->n_replicas;
+    if ((int64_t)c->R * c->n > (1LL << 28)) return fail(nullptr, SOP_ERR_INVALID_ARG, "n_replicas * n_beads too large");
+    c->n_seg = c->R * c->n_sys;
+    if (p->obs_capacity == 0) c->prm.obs_capacity = 4096;
+    c->ppb = p->pairs_per_bead > 0 ? p->pairs_per_bead : 64;
+    CUDA_OR_RETURN(c, cudaGetDevice(&c->device));
+    if (p->cuda_stream) {
+        c->stream = static_cast<cudaStream_t>(p->cuda_stream);
+    } else {
+        CUDA_OR_RETURN(c, cudaStreamCreate(&c->stream));
+        c->own_stream = true;
+    }
+    const int n = c->n, R = c->R;
+    // ---- topology on the device
+    CUDA_OR_RETURN(c, upload(c, &c->d_chain, c->chain_of));
+    CUDA_OR_RETURN(c, upload(c, &c->d_sys, c->sys_of));
+    CUDA_OR_RETURN(c, upload(c, &c->d_sys_lo, c->sys_lo));
+    CUDA_OR_RETURN(c, upload(c, &c->d_sys_ree_last, c->sys_ree_last));
+    CUDA_OR_RETURN(c, upload(c, &c->d_flags, c->flags));
+    CUDA_OR_RETURN(c, dalloc(c, &c->d_bond_r0, n));
+    CUDA_OR_RETURN(c, dalloc(c, &c->d_bond_r0d, n));
+    double *d_xyz = nullptr;
+    CUDA_OR_RETURN(c, dalloc(c, &d_xyz, 3 * (size_t)n));
+    CUDA_OR_RETURN(c, cudaMemcpy(d_xyz, xyz, sizeof(double) * 3 * n, cudaMemcpyHostToDevice));
+    launch_setup_bonds(d_xyz, c->d_chain, c->d_bond_r0, c->d_bond_r0d, n, c->stream);
+    CUDA_OR_RETURN(c, cudaGetLastError());
+    // ---- native map: count, host prefix sum, fill (FP64 decisions on the GPU)
+    int32_t *d_cnt = nullptr;
+    CUDA_OR_RETURN(c, dalloc(c, &d_cnt, n));
+    launch_native_count(d_xyz, c->d_chain, c->d_sys, c->d_sys_lo, n, p->native_cut, d_cnt, c->stream);
+    std::vector<int32_t> cnt(n);
+    CUDA_OR_RETURN(c, cudaMemcpyAsync(cnt.data(), d_cnt, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, c->stream));
+    CUDA_OR_RETURN(c, cudaStreamSynchronize(c->stream));
+    c->h_nat_row.assign(n + 1, 0);
+    for (int i = 0; i < n; ++i) c->h_nat_row[i + 1] = c->h_nat_row[i] + cnt[i];
+    c->nat_nnz = c->h_nat_row[n];
+    CUDA_OR_RETURN(c, upload(c, &c->d_nat_row, c->h_nat_row));
+    CUDA_OR_RETURN(c, dalloc(c, &c->d_nat_col, c->nat_nnz));
+    CUDA_OR_RETURN(c, dalloc(c, &c->d_nat_r0, c->nat_nnz));
+    CUDA_OR_RETURN(c, dalloc(c, &c->d_nat_r0sq, c->nat_nnz));
+    launch_native_fill(d_xyz, c->d_chain, c->d_sys, c->d_sys_lo, n, p->native_cut, c->d_nat_row, c->d_nat_col,
+                       c->d_nat_r0, c->d_nat_r0sq, c->stream);
+    CUDA_OR_RETURN(c, cudaGetLastError());
+    c->h_nat_col.resize(c->nat_nnz);
+    c->h_nat_r0.resize(c->nat_nnz);
+    if (c->nat_nnz) {
+        CUDA_OR_RETURN(c, cudaMemcpyAsync(c->h_nat_col.data(), c->d_nat_col, sizeof(int32_t) * c->nat_nnz,
+                                          cudaMemcpyDeviceToHost, c->stream));
+        CUDA_OR_RETURN(c, cudaMemcpyAsync(c->h_nat_r0.data(), c->d_nat_r0, sizeof(double) * c->nat_nnz,
+                                          cudaMemcpyDeviceToHost, c->stream));
+    }
+    CUDA_OR_RETURN(c, cudaStreamSynchronize(c->stream));
+    c->st.native_entries = c->nat_nnz / 2;
+    std::vector<int32_t> sys_np(c->n_sys, 0);
+    for (int i = 0; i < n; ++i)
+        for (int q = c->h_nat_row[i]; q < c->h_nat_row[i + 1]; ++q)
+            if (c->h_nat_col[q] > i) sys_np[c->sys_of[i]]++;
+    CUDA_OR_RETURN(c, upload(c, &c->d_sys_nat_pairs, sys_np));
+    // ---- state: every replica starts at the native coordinates (FP32)
+    std::vector<float4> p4((size_t)R * n);
+    for (int i = 0; i < n; ++i) {
+        const float4 v = make_float4((float)xyz[3 * i], (float)xyz[3 * i + 1], (float)xyz[3 * i + 2], 0.f);
+        for (int r = 0; r < R; ++r) p4[(size_t)r * n + i] = v;
+    }
+    for (int b = 0; b < 2; ++b) CUDA_OR_RETURN(c, dalloc(c, &c->d_pos[b], (size_t)R * n));
+    CUDA_OR_RETURN(c, dalloc(c, &c->d_comp, (size_t)R * n));
+    CUDA_OR_RETURN(c, dalloc(c, &c->d_snap, (size_t)R * n));
+    CUDA_OR_RETURN(c, dalloc(c, &c->d_force, (size_t)R * n));
+    CUDA_OR_RETURN(c, cudaMemcpy(c->d_pos[0], p4.data(), sizeof(float4) * p4.size(), cudaMemcpyHostToDevice));
+    CUDA_OR_RETURN(c, cudaMemcpy(c->d_pos[1], p4.data(), sizeof(float4) * p4.size(), cudaMemcpyHostToDevice));
+    CUDA_OR_RETURN(c, cudaMemset(c->d_comp, 0, sizeof(float4) * p4.size()));
+    CUDA_OR_RETURN(c, dalloc(c, &c->d_step, 1));
+    CUDA_OR_RETURN(c, dalloc(c, &c->d_events, 1));
+    CUDA_OR_RETURN(c, cudaMemset(c->d_step, 0, sizeof(int64_t)));
+    CUDA_OR_RETURN(c, cudaMemset(c->d_events, 0, sizeof(int64_t)));
+    CUDA_OR_RETURN(c, dalloc(c, &c->d_rep_status, R));
+    CUDA_OR_RETURN(c, cudaMemset(c->d_rep_status, 0, sizeof(int32_t) * R));
+    CUDA_OR_RETURN(c, dalloc(c, &c->d_halt, 1));
+    CUDA_OR_RETURN(c, cudaMemset(c->d_halt, 0, sizeof(int32_t)));
+    CUDA_OR_RETURN(c, dalloc(c, &c->d_energy, 1));
+    CUDA_OR_RETURN(c, cudaHostAlloc((void **)&c->h_abort, sizeof(int32_t), cudaHostAllocMapped));
+    *c->h_abort = 0;
+    CUDA_OR_RETURN(c, cudaHostGetDevicePointer((void **)&c->d_abort, c->h_abort, 0));
+    // ---- segments: (replica, system), cells and Verlet-list ranges
+    c->h_seg_bead_lo.resize(c->n_seg + 1);
+    c->h_seg_cell_base.resize(c->n_seg + 1);
+    std::vector<int64_t> pl_base(c->n_seg), pl_end(c->n_seg);
+    int64_t cells = 0, cols = 0;
+    for (int r = 0; r < R; ++r)
+        for (int s2 = 0; s2 < c->n_sys; ++s2) {
+            const int g = r * c->n_sys + s2;
+            const int ng = c->sys_lo[s2 + 1] - c->sys_lo[s2];
+            c->h_seg_bead_lo[g] = r * n + c->sys_lo[s2];
+            c->h_seg_cell_base[g] = (int32_t)cells;
+            cells += 2 * (int64_t)ng + 8;
+            pl_base[g] = cols;
+            cols += (int64_t)c->ppb * ng;
+            pl_end[g] = cols;
+        }
+    c->h_seg_bead_lo[c->n_seg] = R * n;
+    if (cells > INT32_MAX || cols > INT32_MAX) return fail(c, SOP_ERR_UNSUPPORTED, "too many cells or list entries");
+    c->h_seg_cell_base[c->n_seg] = (int32_t)cells;
+    int32_t *d_sbl = nullptr, *d_scb = nullptr;
+    CUDA_OR_RETURN(c, upload(c, &d_sbl, c->h_seg_bead_lo));
+    CUDA_OR_RETURN(c, upload(c, &d_scb, c->h_seg_cell_base));
+    c->cells.n_seg = c->n_seg;
+    c->cells.seg_bead_lo = d_sbl;
+    c->cells.seg_cell_base = d_scb;
+    c->cells.n_cells = cells;
+    CUDA_OR_RETURN(c, dalloc(c, &c->cells.seg_lo, c->n_seg));
+    CUDA_OR_RETURN(c, dalloc(c, &c->cells.seg_dims, c->n_seg));
+    CUDA_OR_RETURN(c, dalloc(c, &c->cells.cell_of, (size_t)R * n));
+    CUDA_OR_RETURN(c, dalloc(c, &c->cells.cell_cnt, cells));
+    CUDA_OR_RETURN(c, cudaMemset(c->cells.cell_cnt, 0, sizeof(int32_t) * cells));
+    CUDA_OR_RETURN(c, dalloc(c, &c->cells.cell_start, cells + 1));
+    CUDA_OR_RETURN(c, dalloc(c, &c->cells.sorted, (size_t)R * n));
+    CUDA_OR_RETURN(c, dalloc(c, &c->cells.scan_tmp, scan_tmp_elems(cells)));
+    int64_t *d_plb = nullptr, *d_ple = nullptr;
+    CUDA_OR_RETURN(c, upload(c, &d_plb, pl_base));
+    CUDA_OR_RETURN(c, upload(c, &d_ple, pl_end));
+    c->pl_cap = cols;
+    for (DevPairList *L : {&c->pl, &c->pl2}) {
+        L->seg_base = d_plb;
+        L->seg_end = d_ple;
+        L->cap = cols;
+    }
+    CUDA_OR_RETURN(c, dalloc(c, &c->pl.start, (size_t)R * n));
+    CUDA_OR_RETURN(c, dalloc(c, &c->pl.len, (size_t)R * n));
+    CUDA_OR_RETURN(c, dalloc(c, &c->pl.col, cols));
+    CUDA_OR_RETURN(c, dalloc(c, &c->pl.cursor, c->n_seg));
+    // ---- observables: chunks of at most kObsChunk beads per segment
+    std::vector<int32_t> ch_seg, ch_lo, ch_hi;
+    c->h_seg_chunk_lo.assign(c->n_seg + 1, 0);
+    for (int g = 0; g < c->n_seg; ++g) {
+        c->h_seg_chunk_lo[g] = (int32_t)ch_seg.size();
+        for (int b = c->h_seg_bead_lo[g]; b < c->h_seg_bead_lo[g + 1]; b += kObsChunk) {
+            ch_seg.push_back(g);
+            ch_lo.push_back(b);
+            ch_hi.push_back(std::min(b + kObsChunk, c->h_seg_bead_lo[g + 1]));
+        }
+    }
+    c->h_seg_chunk_lo[c->n_seg] = (int32_t)ch_seg.size();
+    int32_t *d_cs = nullptr, *d_cl = nullptr, *d_chh = nullptr, *d_scl = nullptr;
+    CUDA_OR_RETURN(c, upload(c, &d_cs, ch_seg));
+    CUDA_OR_RETURN(c, upload(c, &d_cl, ch_lo));
+    CUDA_OR_RETURN(c, upload(c, &d_chh, ch_hi));
+    CUDA_OR_RETURN(c, upload(c, &d_scl, c->h_seg_chunk_lo));
+    c->obs.n_chunks = (int32_t)ch_seg.size();
+    c->obs.chunk_seg = d_cs;
+    c->obs.chunk_lo = d_cl;
+    c->obs.chunk_hi = d_chh;
+    c->obs.seg_chunk_lo = d_scl;
+    CUDA_OR_RETURN(c, dalloc(c, &c->obs.partial, 8 * (size_t)c->obs.n_chunks));
+    c->obs.cap = std::max<int64_t>(c->prm.obs_capacity, c->n_seg);
+    CUDA_OR_RETURN(c, dalloc(c, &c->obs.ring, c->obs.cap));
+    c->obs.events = c->d_events;
+    c->obs.obs_every = c->prm.obs_every;
+    // ---- externals (none yet)
+    c->pull_of_sys.assign(c->n_sys, -1);
+    CUDA_OR_RETURN(c, upload(c, &c->d_pull_of_sys, c->pull_of_sys));
+    s = alloc_pull_arrays(c, 0);
+    if (s != SOP_OK) return s;
+    // ---- kernel arguments
+    StepArgs &a = c->sa;
+    a.topo.n = n;
+    a.topo.n_sys = c->n_sys;
+    a.topo.chain = c->d_chain;
+    a.topo.sys = c->d_sys;
+    a.topo.flags = c->d_flags;
+    a.topo.bond_r0 = c->d_bond_r0;
+    a.topo.bond_r0d = c->d_bond_r0d;
+    a.topo.nat_row = c->d_nat_row;
+    a.topo.nat_col = c->d_nat_col;
+    a.topo.nat_r0sq = c->d_nat_r0sq;
+    a.topo.nat_r0 = c->d_nat_r0;
+    a.topo.sys_lo = c->d_sys_lo;
+    a.topo.sys_ree_last = c->d_sys_ree_last;
+    a.topo.sys_nat_pairs = c->d_sys_nat_pairs;
+    const double kT = kBoltzmannKcal * p->T;
+    a.fp.k_fene = (float)p->k_fene;
+    a.fp.inv_R02 = (float)(1.0 / (p->R0 * p->R0));
+    a.fp.eps12_h = (float)(12.0 * p->eps_h);
+    a.fp.eps6_l = (float)(6.0 * p->eps_l);
+    a.fp.sigma2 = (float)(p->sigma * p->sigma);
+    a.fp.mob = (float)(p->dt / p->zeta);
+    a.fp.amp = (float)std::sqrt(2.0 * kT * p->dt / p->zeta);
+    a.cut2_d = p->pair_cut * p->pair_cut;
+    a.cut2_f = (float)a.cut2_d;
+    a.k_fene = p->k_fene;
+    a.R0 = p->R0;
+    a.eps_h = p->eps_h;
+    a.eps_l = p->eps_l;
+    a.sigma = p->sigma;
+    a.seed = p->seed;
+    a.R = R;
+    a.d_step = c->d_step;
+    a.rep_status = c->d_rep_status;
+    a.halt = c->d_halt;
+    sync_external(c);
+    // ---- the first Verlet list (streamed builder; also fills the snapshot)
+    s = rebuild_streamed(c);
+    if (s != SOP_OK) return s;
+    CUDA_OR_RETURN(c, cudaStreamSynchronize(c->stream));
+    int mrow = 0;
+    s = max_row(c, &mrow);
+    if (s != SOP_OK) return s;
+    // ---- schedule
+    int sched = p->schedule;
+    BatchedConfig cfg;
+    const int bcap = std::min(128, std::max(32, ((mrow * 3) / 2 + 8 + 7) / 8 * 8));
+    const bool batched_ok = c->max_sys <= kBatchedMaxBeads && batched_config(c->max_sys, bcap, 0, &cfg);
+    if (sched == SOP_SCHED_AUTO) sched = batched_ok ? SOP_SCHED_BATCHED : SOP_SCHED_STREAMED;
+    if (sched == SOP_SCHED_BATCHED && !batched_ok)
+        return fail(c, SOP_ERR_UNSUPPORTED, "batched schedule needs systems of at most 2048 beads that fit shared memory");
+    c->schedule = sched;
+    c->batched_cap = bcap;
+    c->bcfg = cfg;
+    if (sched == SOP_SCHED_BATCHED) {
+        s = build_batched_tables(c);
+        if (s != SOP_OK) return s;
+    }
+    c->st.schedule = sched;
+    c->st.block_threads = sched == SOP_SCHED_BATCHED ? cfg.threads : 256;
+    c->st.pairs_per_bead = sched == SOP_SCHED_BATCHED ? bcap : c->ppb;
+    c->st.beads_per_thread = sched == SOP_SCHED_BATCHED ? cfg.beads_per_thread : 0;
+    CUDA_OR_RETURN(c, cudaStreamSynchronize(c->stream));
+    return SOP_OK;
+}
+
+void free_all(sop_ctx *c) {
+    destroy_graphs(c);
+    for (auto &e : c->chunk_ev)
+        if (e) { cudaEventDestroy(e); e = nullptr; }
+    for (void *q : c->allocs) cudaFree(q);
+    c->allocs.clear();
+    if (c->h_abort) cudaFreeHost(c->h_abort);
+    c->h_abort = nullptr;
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    c->stream = nullptr;
+}
+
+// Canonical CSR (rows ascending, both directions) from per-bead rows.
+void to_csr(int n, const std::vector<int32_t> &start, const std::vector<int32_t> &len, const std::vector<int32_t> &col,
+            int32_t base_index, std::vector<int32_t> &row_ptr, std::vector<int32_t> &out) {
+    row_ptr.assign(n + 1, 0);
+    out.clear();
+    for (int i = 0; i < n; ++i) {
+        std::vector<int32_t> row(col.begin() + start[i], col.begin() + start[i] + len[i]);
+        for (auto &v : row) v -= base_index;
+        std::sort(row.begin(), row.end());
+        out.insert(out.end(), row.begin(), row.end());
+        row_ptr[i + 1] = (int32_t)out.size();
+    }
+}
+
+}  // namespace
+
+// =====================================================================================
+// Entry points
+// =====================================================================================
+extern "C" {
+
+sop_status sop_create(const sop_topology *topo, const double *native_xyz, const sop_params *params, sop_ctx **out) {
+    if (!out) return fail(nullptr, SOP_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    sop_ctx *c = new (std::nothrow) sop_ctx();
+    if (!c) return fail(nullptr, SOP_ERR_OOM, "host allocation failed");
+    sop_status s;
+    try {
+        s = create_impl(c, topo, native_xyz, params);
+    } catch (const std::exception &e) {
+        s = fail(c, SOP_ERR_OOM, std::string("host exception: ") + e.what());
+    }
+    if (s != SOP_OK) {
+        if (!c->err.empty()) g_create_error = c->err;
+        free_all(c);
+        delete c;
+        return s;
+    }
+    *out = c;
+    return SOP_OK;
+}
+
+sop_status sop_step(sop_ctx *c, int64_t n_steps) {
+    if (!c) return fail(nullptr, SOP_ERR_INVALID_ARG, "ctx is NULL");
+    if (n_steps < 0) return fail(c, SOP_ERR_INVALID_ARG, "n_steps < 0");
+    try {
+        *c->h_abort = 0;
+        sop_status s = SOP_OK;
+        if (n_steps > 0) {
+            switch (c->schedule) {
+            case SOP_SCHED_BATCHED: s = step_batched(c, n_steps); break;
+            case SOP_SCHED_PLAIN: s = step_plain(c, n_steps); break;
+            default: s = step_streamed(c, n_steps); break;
+            }
+        }
+        if (s != SOP_OK) return s;
+        c->st.steps = c->step;
+        const bool aborted = *(volatile int32_t *)c->h_abort != 0;
+        return read_status(c, aborted);
+    } catch (const std::exception &e) {
+        return fail(c, SOP_ERR_OOM, std::string("host exception: ") + e.what());
+    }
+}
+
+sop_status sop_forces(sop_ctx *c, int32_t replica, double *out_f, double *out_energy) {
+    if (!c) return fail(nullptr, SOP_ERR_INVALID_ARG, "ctx is NULL");
+    if (replica < 0 || replica >= c->R) return fail(c, SOP_ERR_INVALID_ARG, "replica out of range");
+    try {
+        // a list for these positions, in separate buffers so the run's list is untouched
+        if (!c->pl2.col) {
+            CUDA_OR_RETURN(c, dalloc(c, &c->pl2.start, (size_t)c->R * c->n));
+            CUDA_OR_RETURN(c, dalloc(c, &c->pl2.len, (size_t)c->R * c->n));
+            CUDA_OR_RETURN(c, dalloc(c, &c->pl2.col, c->pl_cap));
+            CUDA_OR_RETURN(c, dalloc(c, &c->pl2.cursor, c->n_seg));
+        }
+        const int g_lo = replica * c->n_sys, g_hi = g_lo + c->n_sys;
+        const SegRange rg = seg_range(c, g_lo, g_hi);
+        launch_rebuild(c->sa, c->cells, c->pl2, c->d_pos[c->cur], nullptr, rg, c->stream, &c->st.kernel_launches);
+        if (c->schedule == SOP_SCHED_BATCHED) {
+            BatchedArgs a = batched_args(c);
+            a.pos = c->d_pos[c->cur];
+            a.n_steps = 0;
+            a.force_out = c->d_force;
+            // only this replica's items: items are ordered (system, replica); run all, cheap
+            cudaError_t e = launch_batched(a, c->bcfg, c->stream, &c->st.kernel_launches);
+            if (e != cudaSuccess) return fail(c, SOP_ERR_CUDA, std::string("batched forces: ") + cudaGetErrorString(e));
+        } else {
+            int64_t step_now = c->step;
+            launch_forces(c->sa, c->pl2, c->d_pos[c->cur], c->d_force, rg.b_lo, rg.b_hi, step_now, c->stream,
+                          &c->st.kernel_launches);
+        }
+        // energy: the observable partials of this replica's segments at the current step
+        launch_energy(c->sa, c->pl2, c->obs, c->d_pos[c->cur], g_lo, g_hi, c->d_energy, c->stream,
+                      &c->st.kernel_launches);
+        CUDA_OR_RETURN(c, cudaGetLastError());
+        std::vector<float4> f(c->n);
+        CUDA_OR_RETURN(c, cudaMemcpyAsync(f.data(), c->d_force + (size_t)replica * c->n, sizeof(float4) * c->n,
+                                          cudaMemcpyDeviceToHost, c->stream));
+        double e = 0.0;
+        CUDA_OR_RETURN(c, cudaMemcpyAsync(&e, c->d_energy, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+        CUDA_OR_RETURN(c, cudaStreamSynchronize(c->stream));
+        bool bad = false;
+        if (out_f)
+            for (int i = 0; i < c->n; ++i) {
+                out_f[3 * i] = f[i].x;
+                out_f[3 * i + 1] = f[i].y;
+                out_f[3 * i + 2] = f[i].z;
+                bad |= f[i].w != 0.f;
+            }
+        if (out_energy) *out_energy = e;
+        if (bad) return fail(c, SOP_ERR_FENE_BREAK, "a bond is broken or a bead is inside the indenter");
+        return SOP_OK;
+    } catch (const std::exception &e) {
+        return fail(c, SOP_ERR_OOM, std::string("host exception: ") + e.what());
+    }
+}
+
+sop_status sop_pairlist_rebuild(sop_ctx *c) {
+    if (!c) return fail(nullptr, SOP_ERR_INVALID_ARG, "ctx is NULL");
+    sop_status s = rebuild_streamed(c);
+    if (s != SOP_OK) return s;
+    CUDA_OR_RETURN(c, cudaStreamSynchronize(c->stream));
+    return SOP_OK;
+}
+
+sop_status sop_pull(sop_ctx *c, int32_t n, const sop_pull_params *pulls) {
+    if (!c) return fail(nullptr, SOP_ERR_INVALID_ARG, "ctx is NULL");
+    if (n < 0 || (n > 0 && !pulls)) return fail(c, SOP_ERR_INVALID_ARG, "pulls");
+    std::vector<int> seen(c->n_sys, 0);
+    for (int k = 0; k < n; ++k) {
+        const sop_pull_params &q = pulls[k];
+        if (q.system < 0 || q.system >= c->n_sys || seen[q.system]++)
+            return fail(c, SOP_ERR_INVALID_ARG, "pull: system out of range or repeated");
+        const int lo = c->sys_lo[q.system], hi = c->sys_lo[q.system + 1];
+        if (q.anchor < lo || q.anchor >= hi || q.pulled < lo || q.pulled >= hi || q.anchor == q.pulled)
+            return fail(c, SOP_ERR_INVALID_ARG, "pull: anchor and pulled must be distinct beads of the system");
+        if (!std::isfinite(q.k_s) || q.k_s < 0 || !std::isfinite(q.v))
+            return fail(c, SOP_ERR_INVALID_ARG, "pull: k_s >= 0 and finite v required");
+    }
+    std::vector<float4> h;
+    sop_status s = positions_f4(c, h);
+    if (s != SOP_OK) return s;
+    // clear old pulled flags; anchors stay fixed only while pulled
+    for (size_t k = 0; k < c->pull_bead.size(); ++k) {
+        c->flags[c->pull_bead[k]] &= (uint8_t)~kFlagPulled;
+        c->flags[c->pull_anchor[k]] &= (uint8_t)~kFlagFixed;
+    }
+    c->pull_of_sys.assign(c->n_sys, -1);
+    c->pull_anchor.clear(); c->pull_bead.clear(); c->pull_sys.clear();
+    c->pull_ks.clear(); c->pull_v.clear(); c->pull_dir.clear(); c->pull_n0.clear(); c->pull_tip0.clear();
+    for (int k = 0; k < n; ++k) {
+        const sop_pull_params &q = pulls[k];
+        c->pull_of_sys[q.system] = k;
+        c->pull_anchor.push_back(q.anchor);
+        c->pull_bead.push_back(q.pulled);
+        c->pull_sys.push_back(q.system);
+        c->pull_ks.push_back(q.k_s);
+        c->pull_v.push_back(q.v);
+        c->pull_n0.push_back((double)c->step);
+        // direction anchor -> pulled at the start, from replica 0 (all replicas share it)
+        const float4 a = h[q.anchor], b = h[q.pulled];
+        const double d[3] = {(double)b.x - (double)a.x, (double)b.y - (double)a.y, (double)b.z - (double)a.z};
+        const double len = std::sqrt((d[0] * d[0] + d[1] * d[1]) + d[2] * d[2]);
+        if (!(len > 0)) return fail(c, SOP_ERR_INVALID_ARG, "pull: anchor and pulled coincide");
+        for (int m = 0; m < 3; ++m) c->pull_dir.push_back(d[m] / len);
+        c->flags[q.pulled] |= kFlagPulled;
+        c->flags[q.anchor] |= kFlagFixed;
+    }
+    c->pull_tip0.assign(3 * (size_t)n * c->R, 0.0);
+    for (int r = 0; r < c->R; ++r)
+        for (int k = 0; k < n; ++k) {
+            const float4 b = h[(size_t)r * c->n + c->pull_bead[k]];
+            double *t = &c->pull_tip0[((size_t)r * n + k) * 3];
+            t[0] = b.x; t[1] = b.y; t[2] = b.z;
+        }
+    return upload_pulls(c);
+}
+
+sop_status sop_indenter(sop_ctx *c, const double center[3], const double direction[3], double radius, double v) {
+    if (!c) return fail(nullptr, SOP_ERR_INVALID_ARG, "ctx is NULL");
+    if (!(radius > 0)) {
+        c->has_ind = false;
+    } else {
+        if (!center || !direction || !std::isfinite(v)) return fail(c, SOP_ERR_INVALID_ARG, "indenter");
+        const double len = std::sqrt((direction[0] * direction[0] + direction[1] * direction[1]) + direction[2] * direction[2]);
+        if (!(len > 0) || !std::isfinite(len)) return fail(c, SOP_ERR_INVALID_ARG, "indenter: direction");
+        for (int k = 0; k < 3; ++k) {
+            if (!std::isfinite(center[k])) return fail(c, SOP_ERR_INVALID_ARG, "indenter: centre");
+            c->ind_c0[k] = center[k];
+            c->ind_dir[k] = direction[k] / len;
+        }
+        c->has_ind = true;
+        c->ind_radius = radius;
+        c->ind_v = v;
+        c->ind_n0 = (double)c->step;
+    }
+    sync_external(c);
+    destroy_graphs(c);
+    return SOP_OK;
+}
+
+sop_status sop_get_positions(sop_ctx *c, int32_t replica, double *out) {
+    if (!c) return fail(nullptr, SOP_ERR_INVALID_ARG, "ctx is NULL");
+    if (!out || replica < -1 || replica >= c->R) return fail(c, SOP_ERR_INVALID_ARG, "replica or out");
+    const size_t cnt = replica < 0 ? (size_t)c->R * c->n : (size_t)c->n;
+    const size_t off = replica < 0 ? 0 : (size_t)replica * c->n;
+    std::vector<float4> h(cnt);
+    CUDA_OR_RETURN(c, cudaMemcpyAsync(h.data(), c->d_pos[c->cur] + off, sizeof(float4) * cnt, cudaMemcpyDeviceToHost,
+                                      c->stream));
+    CUDA_OR_RETURN(c, cudaStreamSynchronize(c->stream));
+    for (size_t i = 0; i < cnt; ++i) {
+        out[3 * i] = h[i].x;
+        out[3 * i + 1] = h[i].y;
+        out[3 * i + 2] = h[i].z;
+    }
+    return SOP_OK;
+}
+
+sop_status sop_set_positions(sop_ctx *c, int32_t replica, const double *xyz) {
+    if (!c) return fail(nullptr, SOP_ERR_INVALID_ARG, "ctx is NULL");
+    if (!xyz || replica < -1 || replica >= c->R) return fail(c, SOP_ERR_INVALID_ARG, "replica or xyz");
+    const size_t cnt = replica < 0 ? (size_t)c->R * c->n : (size_t)c->n;
+    const size_t off = replica < 0 ? 0 : (size_t)replica * c->n;
+    std::vector<float4> h(cnt);
+    for (size_t i = 0; i < cnt; ++i) {
+        if (!std::isfinite(xyz[3 * i]) || !std::isfinite(xyz[3 * i + 1]) || !std::isfinite(xyz[3 * i + 2]))
+            return fail(c, SOP_ERR_INVALID_ARG, "positions hold a non-finite value");
+        h[i] = make_float4((float)xyz[3 * i], (float)xyz[3 * i + 1], (float)xyz[3 * i + 2], 0.f);
+    }
+    CUDA_OR_RETURN(c, cudaMemcpyAsync(c->d_pos[c->cur] + off, h.data(), sizeof(float4) * cnt, cudaMemcpyHostToDevice,
+                                      c->stream));
+    CUDA_OR_RETURN(c, cudaMemsetAsync(c->d_comp + off, 0, sizeof(float4) * cnt, c->stream));
+    CUDA_OR_RETURN(c, cudaStreamSynchronize(c->stream));
+    return SOP_OK;
+}
+
+sop_status sop_get_pairlist(sop_ctx *c, int32_t replica, int32_t *row_ptr, int32_t *col, int64_t cap, int64_t *nnz) {
+    if (!c) return fail(nullptr, SOP_ERR_INVALID_ARG, "ctx is NULL");
+    if (replica < 0 || replica >= c->R || !row_ptr || !nnz) return fail(c, SOP_ERR_INVALID_ARG, "replica or outputs");
+    const int n = c->n;
+    std::vector<int32_t> start(n), len(n), cols;
+    int32_t base_index = 0;
+    if (c->schedule == SOP_SCHED_BATCHED) {
+        // the batched kernel builds its list in shared memory; rebuild it from the snapshot
+        // (the positions of the last rebuild) in forces mode and dump it
+        const int stride = c->batched_cap;
+        if (!c->d_dump_col) {
+            CUDA_OR_RETURN(c, dalloc(c, &c->d_dump_start, (size_t)c->R * n));
+            CUDA_OR_RETURN(c, dalloc(c, &c->d_dump_len, (size_t)c->R * n));
+            CUDA_OR_RETURN(c, dalloc(c, &c->d_dump_col, (size_t)c->R * n * stride));
+        }
+        BatchedArgs a = batched_args(c);
+        a.pos = c->d_snap;
+        a.n_steps = 0;
+        a.force_out = c->d_force;
+        a.pl_dump_start = c->d_dump_start;
+        a.pl_dump_len = c->d_dump_len;
+        a.pl_dump_col = c->d_dump_col;
+        a.pl_dump_stride = stride;
+        cudaError_t e = launch_batched(a, c->bcfg, c->stream, &c->st.kernel_launches);
+        if (e != cudaSuccess) return fail(c, SOP_ERR_CUDA, std::string("batched dump: ") + cudaGetErrorString(e));
+        std::vector<int32_t> st(n);
+        cols.resize((size_t)n * stride);
+        CUDA_OR_RETURN(c, cudaMemcpyAsync(len.data(), c->d_dump_len + (size_t)replica * n, sizeof(int32_t) * n,
+                                          cudaMemcpyDeviceToHost, c->stream));
+        CUDA_OR_RETURN(c, cudaMemcpyAsync(cols.data(), c->d_dump_col + (size_t)replica * n * stride,
+                                          sizeof(int32_t) * cols.size(), cudaMemcpyDeviceToHost, c->stream));
+        for (int i = 0; i < n; ++i) start[i] = i * stride;
+    } else {
+        CUDA_OR_RETURN(c, cudaMemcpyAsync(start.data(), c->pl.start + (size_t)replica * n, sizeof(int32_t) * n,
+                                          cudaMemcpyDeviceToHost, c->stream));
+        CUDA_OR_RETURN(c, cudaMemcpyAsync(len.data(), c->pl.len + (size_t)replica * n, sizeof(int32_t) * n,
+                                          cudaMemcpyDeviceToHost, c->stream));
+        CUDA_OR_RETURN(c, cudaStreamSynchronize(c->stream));
+        int32_t lo = INT32_MAX, hi = 0;
+        for (int i = 0; i < n; ++i)
+            if (len[i] > 0) { lo = std::min(lo, start[i]); hi = std::max(hi, start[i] + len[i]); }
+        if (hi > lo) {
+            cols.resize(hi - lo);
+            CUDA_OR_RETURN(c, cudaMemcpyAsync(cols.data(), c->pl.col + lo, sizeof(int32_t) * (hi - lo),
+                                              cudaMemcpyDeviceToHost, c->stream));
+            for (int i = 0; i < n; ++i) start[i] = len[i] > 0 ? start[i] - lo : 0;
+        }
+    }
+    CUDA_OR_RETURN(c, cudaStreamSynchronize(c->stream));
+    std::vector<int32_t> rp, out;
+    to_csr(n, start, len, cols, base_index, rp, out);
+    *nnz = (int64_t)out.size();
+    std::memcpy(row_ptr, rp.data(), sizeof(int32_t) * (n + 1));
+    if (!col || cap < (int64_t)out.size()) return fail(c, SOP_ERR_CAPACITY, "col capacity below nnz");
+    std::memcpy(col, out.data(), sizeof(int32_t) * out.size());
+    return SOP_OK;
+}
+
+sop_status sop_get_native_map(sop_ctx *c, int32_t *row_ptr, int32_t *col, double *r0, int64_t cap, int64_t *nnz) {
+    if (!c) return fail(nullptr, SOP_ERR_INVALID_ARG, "ctx is NULL");
+    if (!row_ptr || !nnz) return fail(c, SOP_ERR_INVALID_ARG, "outputs");
+    *nnz = c->nat_nnz;
+    std::memcpy(row_ptr, c->h_nat_row.data(), sizeof(int32_t) * (c->n + 1));
+    if (!col || !r0 || cap < c->nat_nnz) return fail(c, SOP_ERR_CAPACITY, "capacity below nnz");
+    std::memcpy(col, c->h_nat_col.data(), sizeof(int32_t) * c->nat_nnz);
+    std::memcpy(r0, c->h_nat_r0.data(), sizeof(double) * c->nat_nnz);
+    return SOP_OK;
+}
+
+sop_status sop_get_observables(sop_ctx *c, sop_record *out, int64_t cap, int64_t *n_records, int64_t *n_lost) {
+    if (!c) return fail(nullptr, SOP_ERR_INVALID_ARG, "ctx is NULL");
+    if (!n_records) return fail(c, SOP_ERR_INVALID_ARG, "n_records is NULL");
+    const int64_t per = c->n_seg;
+    const int64_t ring_events = c->obs.cap / per;
+    int64_t first = c->consumed;
+    int64_t lost = 0;
+    if (c->events - first > ring_events) {
+        lost = (c->events - ring_events - first) * per;
+        first = c->events - ring_events;
+    }
+    const int64_t n_ev = c->events - first;
+    *n_records = n_ev * per;
+    if (n_lost) *n_lost = lost;
+    if (n_ev == 0) return SOP_OK;
+    if (!out || cap < n_ev * per) return fail(c, SOP_ERR_CAPACITY, "out capacity below the pending records");
+    std::vector<sop_record> ring(c->obs.cap);
+    CUDA_OR_RETURN(c, cudaMemcpyAsync(ring.data(), c->obs.ring, sizeof(sop_record) * c->obs.cap,
+                                      cudaMemcpyDeviceToHost, c->stream));
+    CUDA_OR_RETURN(c, cudaStreamSynchronize(c->stream));
+    int64_t w = 0;
+    for (int64_t e = first; e < c->events; ++e)
+        for (int64_t g = 0; g < per; ++g) out[w++] = ring[(e * per + g) % c->obs.cap];
+    c->consumed = c->events;
+    return SOP_OK;
+}
+
+// Checkpoint layout: header of int64 fields, then arrays.
+sop_status sop_get_state(sop_ctx *c, void *buf, int64_t cap, int64_t *size) {
+    if (!c) return fail(nullptr, SOP_ERR_INVALID_ARG, "ctx is NULL");
+    if (!size) return fail(c, SOP_ERR_INVALID_ARG, "size is NULL");
+    const size_t RN = (size_t)c->R * c->n;
+    const size_t np = c->pull_bead.size();
+    const size_t need = 16 * sizeof(int64_t) + 3 * RN * sizeof(float4) + c->R * sizeof(int32_t) +
+                        np * (3 * sizeof(int32_t) + 6 * sizeof(double)) + 3 * np * c->R * sizeof(double) +
+                        9 * sizeof(double);
+    *size = (int64_t)need;
+    if (!buf) return SOP_OK;
+    if (cap < (int64_t)need) return fail(c, SOP_ERR_CAPACITY, "buffer too small");
+    char *p = static_cast<char *>(buf);
+    int64_t hdr[16] = {0x534f5031, SOP_ABI_VERSION, c->n, c->R, c->step, c->list_step, (int64_t)np,
+                       c->has_ind ? 1 : 0, c->events, c->consumed, 0, 0, 0, 0, 0, 0};
+    std::memcpy(p, hdr, sizeof hdr);
+    p += sizeof hdr;
+    CUDA_OR_RETURN(c, cudaMemcpyAsync(p, c->d_pos[c->cur], RN * sizeof(float4), cudaMemcpyDeviceToHost, c->stream));
+    p += RN * sizeof(float4);
+    CUDA_OR_RETURN(c, cudaMemcpyAsync(p, c->d_comp, RN * sizeof(float4), cudaMemcpyDeviceToHost, c->stream));
+    p += RN * sizeof(float4);
+    CUDA_OR_RETURN(c, cudaMemcpyAsync(p, c->d_snap, RN * sizeof(float4), cudaMemcpyDeviceToHost, c->stream));
+    p += RN * sizeof(float4);
+    CUDA_OR_RETURN(c, cudaMemcpyAsync(p, c->d_rep_status, c->R * sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
+    p += c->R * sizeof(int32_t);
+    CUDA_OR_RETURN(c, cudaStreamSynchronize(c->stream));
+    auto put = [&p](const void *src, size_t bytes) { if (bytes) std::memcpy(p, src, bytes); p += bytes; };
+    put(c->pull_sys.data(), np * sizeof(int32_t));
+    put(c->pull_anchor.data(), np * sizeof(int32_t));
+    put(c->pull_bead.data(), np * sizeof(int32_t));
+    put(c->pull_ks.data(), np * sizeof(double));
+    put(c->pull_v.data(), np * sizeof(double));
+    put(c->pull_n0.data(), np * sizeof(double));
+    put(c->pull_dir.data(), 3 * np * sizeof(double));
+    put(c->pull_tip0.data(), 3 * np * c->R * sizeof(double));
+    double ind[9] = {c->ind_c0[0], c->ind_c0[1], c->ind_c0[2], c->ind_dir[0], c->ind_dir[1], c->ind_dir[2],
+                     c->ind_radius, c->ind_v, c->ind_n0};
+    put(ind, sizeof ind);
+    return SOP_OK;
+}
+
+sop_status sop_set_state(sop_ctx *c, const void *buf, int64_t size) {
+    if (!c) return fail(nullptr, SOP_ERR_INVALID_ARG, "ctx is NULL");
+    if (!buf || size < (int64_t)(16 * sizeof(int64_t))) return fail(c, SOP_ERR_INVALID_ARG, "state buffer");
+    const char *p = static_cast<const char *>(buf);
+    int64_t hdr[16];
+    std::memcpy(hdr, p, sizeof hdr);
+    if (hdr[0] != 0x534f5031 || hdr[1] != SOP_ABI_VERSION || hdr[2] != c->n || hdr[3] != c->R)
+        return fail(c, SOP_ERR_INVALID_ARG, "state does not match this context");
+    const size_t RN = (size_t)c->R * c->n;
+    const size_t np = (size_t)hdr[6];
+    const size_t need = 16 * sizeof(int64_t) + 3 * RN * sizeof(float4) + c->R * sizeof(int32_t) +
+                        np * (3 * sizeof(int32_t) + 6 * sizeof(double)) + 3 * np * c->R * sizeof(double) +
+                        9 * sizeof(double);
+    if (size < (int64_t)need) return fail(c, SOP_ERR_INVALID_ARG, "state buffer truncated");
+    p += sizeof hdr;
+    c->cur = 0;
+    CUDA_OR_RETURN(c, cudaMemcpy(c->d_pos[0], p, RN * sizeof(float4), cudaMemcpyHostToDevice));
+    p += RN * sizeof(float4);
+    CUDA_OR_RETURN(c, cudaMemcpy(c->d_comp, p, RN * sizeof(float4), cudaMemcpyHostToDevice));
+    p += RN * sizeof(float4);
+    CUDA_OR_RETURN(c, cudaMemcpy(c->d_snap, p, RN * sizeof(float4), cudaMemcpyHostToDevice));
+    p += RN * sizeof(float4);
+    CUDA_OR_RETURN(c, cudaMemcpy(c->d_rep_status, p, c->R * sizeof(int32_t), cudaMemcpyHostToDevice));
+    p += c->R * sizeof(int32_t);
+    auto get = [&p](void *dst, size_t bytes) { if (bytes) std::memcpy(dst, p, bytes); p += bytes; };
+    for (size_t k = 0; k < c->pull_bead.size(); ++k) {
+        c->flags[c->pull_bead[k]] &= (uint8_t)~kFlagPulled;
+        c->flags[c->pull_anchor[k]] &= (uint8_t)~kFlagFixed;
+    }
+    c->pull_sys.resize(np); c->pull_anchor.resize(np); c->pull_bead.resize(np);
+    c->pull_ks.resize(np); c->pull_v.resize(np); c->pull_n0.resize(np);
+    c->pull_dir.resize(3 * np); c->pull_tip0.resize(3 * np * c->R);
+    get(c->pull_sys.data(), np * sizeof(int32_t));
+    get(c->pull_anchor.data(), np * sizeof(int32_t));
+    get(c->pull_bead.data(), np * sizeof(int32_t));
+    get(c->pull_ks.data(), np * sizeof(double));
+    get(c->pull_v.data(), np * sizeof(double));
+    get(c->pull_n0.data(), np * sizeof(double));
+    get(c->pull_dir.data(), 3 * np * sizeof(double));
+    get(c->pull_tip0.data(), 3 * np * c->R * sizeof(double));
+    c->pull_of_sys.assign(c->n_sys, -1);
+    for (size_t k = 0; k < np; ++k) {
+        if (c->pull_sys[k] < 0 || c->pull_sys[k] >= c->n_sys) return fail(c, SOP_ERR_INVALID_ARG, "state: pull system");
+        c->pull_of_sys[c->pull_sys[k]] = (int32_t)k;
+        c->flags[c->pull_bead[k]] |= kFlagPulled;
+        c->flags[c->pull_anchor[k]] |= kFlagFixed;
+    }
+    double ind[9];
+    get(ind, sizeof ind);
+    c->has_ind = hdr[7] != 0;
+    for (int k = 0; k < 3; ++k) { c->ind_c0[k] = ind[k]; c->ind_dir[k] = ind[3 + k]; }
+    c->ind_radius = ind[6];
+    c->ind_v = ind[7];
+    c->ind_n0 = ind[8];
+    c->step = hdr[4];
+    c->events = hdr[8];
+    c->consumed = hdr[9];
+    CUDA_OR_RETURN(c, cudaMemcpy(c->d_step, &c->step, sizeof(int64_t), cudaMemcpyHostToDevice));
+    CUDA_OR_RETURN(c, cudaMemcpy(c->d_events, &c->events, sizeof(int64_t), cudaMemcpyHostToDevice));
+    sop_status s = upload_pulls(c);
+    if (s != SOP_OK) return s;
+    // the list in use is the one built from the snapshot
+    launch_rebuild(c->sa, c->cells, c->pl, c->d_snap, nullptr, full_range(c), c->stream, &c->st.kernel_launches);
+    c->list_step = hdr[5];
+    CUDA_OR_RETURN(c, cudaStreamSynchronize(c->stream));
+    return SOP_OK;
+}
+
+sop_status sop_replica_status(sop_ctx *c, int32_t *out) {
+    if (!c) return fail(nullptr, SOP_ERR_INVALID_ARG, "ctx is NULL");
+    if (!out) return fail(c, SOP_ERR_INVALID_ARG, "out is NULL");
+    CUDA_OR_RETURN(c, cudaMemcpyAsync(out, c->d_rep_status, sizeof(int32_t) * c->R, cudaMemcpyDeviceToHost, c->stream));
+    CUDA_OR_RETURN(c, cudaStreamSynchronize(c->stream));
+    return SOP_OK;
+}
+
+void sop_abort(sop_ctx *c) {
+    if (c && c->h_abort) *(volatile int32_t *)c->h_abort = 1;
+}
+
+sop_status sop_get_stats(sop_ctx *c, sop_stats *out) {
+    if (!c) return fail(nullptr, SOP_ERR_INVALID_ARG, "ctx is NULL");
+    if (!out) return fail(c, SOP_ERR_INVALID_ARG, "out is NULL");
+    c->st.steps = c->step;
+    *out = c->st;
+    return SOP_OK;
+}
+
+const char *sop_last_error(const sop_ctx *c) { return c ? c->err.c_str() : g_create_error.c_str(); }
+
+void sop_destroy(sop_ctx *c) {
+    if (!c) return;
+    cudaStreamSynchronize(c->stream);
+    free_all(c);
+    delete c;
+}
+
+}  // extern "C"

@@ -1,0 +1,143 @@
+// Device-side building blocks of the SOP-model Langevin step (sm_103a).
+//
+// Pair terms of Eq. 1 (FENE, native 12-6, (sigma/r)^6 repulsion) in FP32,
+// counter-based Philox4x32-10 noise with a Box-Muller transform (Sec. III.C),
+// and the first-order update of Algorithm 7 with a compensated (Kahan) sum.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace sop {
+
+// Philox4x32 multipliers and Weyl key increments (Salmon et al., SC'11).
+constexpr uint32_t kPhiloxM0 = 0xD2511F53u;
+constexpr uint32_t kPhiloxM1 = 0xCD9E8D57u;
+constexpr uint32_t kPhiloxW0 = 0x9E3779B9u;
+constexpr uint32_t kPhiloxW1 = 0xBB67AE85u;
+
+// Philox4x32-10: ten rounds; each multiplies words 0 and 2, crosses the
+// product halves over the lanes and xors in the key; the key advances between
+// rounds by the Weyl constants.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) {
+            k0 += kPhiloxW0;
+            k1 += kPhiloxW1;
+        }
+        const uint32_t lo0 = kPhiloxM0 * c.x;
+        const uint32_t hi0 = __umulhi(kPhiloxM0, c.x);
+        const uint32_t lo1 = kPhiloxM1 * c.z;
+        const uint32_t hi1 = __umulhi(kPhiloxM1, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+    }
+    return c;
+}
+
+// -2 ln(u) for u = (x + 1) 2^-32 in (0, 1], accurate to a few ulp everywhere:
+// near u = 1 it uses log1p of the exactly known 1 - u = (2^32 - 1 - x) 2^-32.
+__device__ __forceinline__ float minus_two_log_u(uint32_t x) {
+    const float two_m32 = 2.3283064365386963e-10f;  // 2^-32
+    if (x >= 0x80000000u) {
+        const float one_minus_u = (float)(0xFFFFFFFFu - x) * two_m32;
+        return -2.0f * log1pf(-one_minus_u);
+    }
+    const float u = fmaf((float)x, two_m32, two_m32);
+    return -2.0f * logf(u);
+}
+
+// Three standard normals from one Philox block (Box-Muller): the pair
+// (x0, x1) gives radius sqrt(-2 ln u1) and angle 2 pi u2 (cos, sin); the pair
+// (x2, x3) gives the third normal from its cosine. The fourth is not used.
+__device__ __forceinline__ float3 box_muller3(uint4 x) {
+    const float two_m31 = 4.656612873077393e-10f;  // 2^-31, so that 2 pi u = pi * (x 2^-31)
+    const float ra = sqrtf(minus_two_log_u(x.x));
+    const float rb = sqrtf(minus_two_log_u(x.z));
+    float s, c;
+    sincospif((float)x.y * two_m31, &s, &c);
+    const float c2 = cospif((float)x.w * two_m31);
+    return make_float3(ra * c, ra * s, rb * c2);
+}
+
+// Gaussian 3-vector of bead `bead` at step `step` of the replica keyed by `seed`:
+// key = seed (lo, hi), counter = (step lo, step hi, bead, 0).
+__device__ __forceinline__ float3 bead_noise(uint64_t seed, int64_t step, uint32_t bead) {
+    const uint64_t s = (uint64_t)step;
+    const uint4 ctr = make_uint4((uint32_t)s, (uint32_t)(s >> 32), bead, 0u);
+    return box_muller3(philox4x32_10(ctr, (uint32_t)seed, (uint32_t)(seed >> 32)));
+}
+
+// Physical constants of one run, FP32 copies for the force loop.
+struct ForceParams {
+    float k_fene;     // k
+    float inv_R02;    // 1 / R0^2
+    float eps12_h;    // 12 eps_h
+    float eps6_l;     // 6 eps_l
+    float sigma2;     // sigma^2
+    float mob;        // h / zeta
+    float amp;        // sqrt(2 kT h / zeta)
+};
+
+// FENE: F_i = -k (r - r0) / (1 - (r - r0)^2 / R0^2) * d / r, d = r_i - r_j.
+// Returns the coefficient multiplying d; sets *broken when |r - r0| >= R0.
+__device__ __forceinline__ float fene_coef(float r2, float r0, const ForceParams &fp, bool *broken) {
+    const float r = sqrtf(r2);
+    const float dr = r - r0;
+    const float arg = 1.0f - dr * dr * fp.inv_R02;
+    if (!(arg > 0.0f)) {
+        *broken = true;
+        return 0.0f;
+    }
+    return -fp.k_fene * dr / (arg * r);
+}
+
+// Native 12-6: F_i = (12 eps_h / r^2) (s^6 - s^3) d with s = r0^2 / r^2.
+__device__ __forceinline__ float native_coef(float r2, float r0sq, const ForceParams &fp) {
+    const float inv_r2 = 1.0f / r2;
+    const float s = r0sq * inv_r2;
+    const float s3 = s * s * s;
+    return fp.eps12_h * inv_r2 * (s3 * s3 - s3);
+}
+
+// Repulsion: F_i = (6 eps_l / r^2) (sigma^2 / r^2)^3 d.
+__device__ __forceinline__ float repulsive_coef(float r2, const ForceParams &fp) {
+    const float inv_r2 = 1.0f / r2;
+    const float q = fp.sigma2 * inv_r2;
+    return fp.eps6_l * inv_r2 * (q * q * q);
+}
+
+// Compensated (Kahan) accumulation of one step's displacement.
+__device__ __forceinline__ void kahan_add(float &x, float &c, float delta) {
+    const float y = delta - c;
+    const float t = x + y;
+    c = (t - x) - y;
+    x = t;
+}
+
+// Is the squared distance below cut^2? FP32 decides unless the value lies within a
+// relative 1e-4 of the cutoff; there the FP64 expression ((dx*dx + dy*dy) + dz*dz)
+// of the same FP32 positions decides (round-to-nearest, no contraction), so the
+// outcome equals an FP64 evaluation of the definition.
+__device__ __forceinline__ bool within_cut(float4 a, float4 b, float cut2_f, double cut2_d) {
+    const float dx = a.x - b.x, dy = a.y - b.y, dz = a.z - b.z;
+    const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+    const float band = cut2_f * 1e-4f;
+    if (r2 < cut2_f - band) return true;
+    if (r2 > cut2_f + band) return false;
+    const double ex = __dsub_rn((double)a.x, (double)b.x);
+    const double ey = __dsub_rn((double)a.y, (double)b.y);
+    const double ez = __dsub_rn((double)a.z, (double)b.z);
+    const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey)), __dmul_rn(ez, ez));
+    return d2 < cut2_d;
+}
+
+// FP64 squared distance ((dx*dx + dy*dy) + dz*dz) with no contraction.
+__device__ __forceinline__ double dist2_d(double ax, double ay, double az, double bx, double by, double bz) {
+    const double ex = __dsub_rn(ax, bx);
+    const double ey = __dsub_rn(ay, by);
+    const double ez = __dsub_rn(az, bz);
+    return __dadd_rn(__dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey)), __dmul_rn(ez, ez));
+}
+
+}  // namespace sop

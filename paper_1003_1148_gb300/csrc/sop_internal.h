@@ -1,0 +1,198 @@
+// Internal interfaces between the C-ABI layer (sop_api.cu) and the kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/sop.h"
+#include "sop_device.cuh"
+
+namespace sop {
+
+// Bead flag bits (per bead of a replica, shared by all replicas).
+enum : uint8_t { kFlagFixed = 1, kFlagPulled = 2, kFlagFirstOfSystem = 4 };
+
+// Shared topology on the device. Bead indices are replica-local (0..n-1).
+struct DevTopo {
+    int32_t n = 0;                 // beads per replica
+    int32_t n_sys = 0;             // systems per replica
+    const int32_t *chain = nullptr;      // [n] chain id
+    const int32_t *sys = nullptr;        // [n] system id
+    const uint8_t *flags = nullptr;      // [n] kFlag*
+    const float *bond_r0 = nullptr;      // [n] r0 of bond (i, i+1), < 0 when i is the last bead of its chain
+    const double *bond_r0d = nullptr;    // [n] the same in FP64
+    const int32_t *nat_row = nullptr;    // [n+1] CSR rows, both directions, ascending
+    const int32_t *nat_col = nullptr;    // [nnz]
+    const float *nat_r0sq = nullptr;     // [nnz] r0^2 rounded to FP32
+    const double *nat_r0 = nullptr;      // [nnz] FP64 r0
+    const int32_t *sys_lo = nullptr;     // [n_sys+1] first bead of each system
+    const int32_t *sys_ree_last = nullptr;  // [n_sys] last bead of the system's first chain
+    const int32_t *sys_nat_pairs = nullptr; // [n_sys] native contacts (i < j) per system
+};
+
+// Cantilevers (per system) and the indenter, FP64.
+struct DevExternal {
+    const int32_t *pull_of_sys = nullptr;  // [n_sys] pull index or -1
+    const int32_t *pull_anchor = nullptr;  // [n_pull]
+    const int32_t *pull_bead = nullptr;    // [n_pull]
+    const double *pull_ks = nullptr;       // [n_pull]
+    const double *pull_v = nullptr;        // [n_pull]
+    const double *pull_dir = nullptr;      // [3 n_pull]
+    const double *pull_n0 = nullptr;       // [n_pull] start step
+    const double *pull_tip0 = nullptr;     // [R * n_pull * 3] tip at the start, per replica
+    int32_t n_pull = 0;
+    int32_t has_indenter = 0;
+    double ind_c0[3] = {0, 0, 0};
+    double ind_dir[3] = {0, 0, 0};
+    double ind_radius = 0, ind_v = 0, ind_n0 = 0;
+};
+
+// Everything the per-step kernels read.
+struct StepArgs {
+    DevTopo topo;
+    DevExternal ext;
+    ForceParams fp;
+    float cut2_f = 0;
+    double cut2_d = 0;
+    double k_fene = 0, R0 = 0, eps_h = 0, eps_l = 0, sigma = 0;   // FP64 copies for observables
+    uint64_t seed = 0;
+    int32_t R = 0;
+    const int64_t *d_step = nullptr;   // device step counter (step of the first kernel of a sequence)
+    int32_t *rep_status = nullptr;     // [R]
+    int32_t *halt = nullptr;           // [1] nonzero: every kernel copies state through
+};
+
+// Streamed-schedule Verlet list (row starts are arbitrary; rows are sorted).
+struct DevPairList {
+    int32_t *start = nullptr;          // [R*n]
+    int32_t *len = nullptr;            // [R*n]
+    int32_t *col = nullptr;            // [cap] replica-local partner index
+    int32_t *cursor = nullptr;         // [n_seg] next free column of each segment
+    const int64_t *seg_base = nullptr; // [n_seg] first column of each segment
+    const int64_t *seg_end = nullptr;  // [n_seg] one past the last column of each segment
+    int64_t cap = 0;
+};
+
+// Host-known extent of a range of segments [g_lo, g_hi).
+struct SegRange {
+    int32_t g_lo = 0, g_hi = 0;   // segments
+    int32_t b_lo = 0, b_hi = 0;   // global beads
+    int32_t c_lo = 0, c_hi = 0;   // cells
+};
+
+// Cell-list scratch of the streamed rebuild.
+struct DevCells {
+    int32_t n_seg = 0;
+    const int32_t *seg_bead_lo = nullptr;   // [n_seg+1] global bead offsets (replica-major)
+    const int32_t *seg_cell_base = nullptr; // [n_seg+1] cell offsets
+    float4 *seg_lo = nullptr;               // [n_seg] grid origin (w = inverse cell edge)
+    int4 *seg_dims = nullptr;               // [n_seg] dims (w = cells used)
+    int32_t *cell_of = nullptr;             // [R*n] global cell index of each bead
+    int32_t *cell_cnt = nullptr;            // [n_cells] zero between rebuilds
+    int32_t *cell_start = nullptr;          // [n_cells+1]
+    int32_t *sorted = nullptr;              // [R*n] global bead indices grouped by cell
+    int32_t *scan_tmp = nullptr;            // scan block sums
+    int64_t n_cells = 0;
+};
+
+// Observable scratch.
+struct DevObs {
+    int32_t n_chunks = 0;
+    const int32_t *chunk_seg = nullptr;     // [n_chunks]
+    const int32_t *chunk_lo = nullptr;      // [n_chunks] global bead range
+    const int32_t *chunk_hi = nullptr;
+    const int32_t *seg_chunk_lo = nullptr;  // [n_seg+1]
+    double *partial = nullptr;              // [n_chunks * 8]
+    sop_record *ring = nullptr;             // [cap]
+    int64_t cap = 0;
+    int64_t *events = nullptr;              // [1] cadence events recorded
+    int32_t obs_every = 0;
+};
+
+// ---- launchers (k_stream.cu) ----
+// Scan: out[0..n] = exclusive prefix sums of in[0..n-1], out[n] = total.
+void scan_exclusive(const int32_t *in, int32_t *out, int64_t n, int32_t *tmp, cudaStream_t s, int64_t *launches);
+int64_t scan_tmp_elems(int64_t n);
+
+void launch_setup_bonds(const double *native_xyz, const int32_t *chain, float *bond_r0, double *bond_r0d,
+                        int32_t n, cudaStream_t s);
+void launch_native_count(const double *native_xyz, const int32_t *chain, const int32_t *sys,
+                         const int32_t *sys_lo, int32_t n, double cut, int32_t *count, cudaStream_t s);
+void launch_native_fill(const double *native_xyz, const int32_t *chain, const int32_t *sys,
+                        const int32_t *sys_lo, int32_t n, double cut, const int32_t *row, int32_t *col,
+                        double *r0, float *r0sq, cudaStream_t s);
+
+// Streamed rebuild of the Verlet list for global beads [b_lo, b_hi) = segments [g_lo, g_hi).
+// pos: the positions to build from; snap (may be null) receives a copy of them.
+void launch_rebuild(const StepArgs &a, const DevCells &c, const DevPairList &pl, const float4 *pos, float4 *snap,
+                    const SegRange &rg, cudaStream_t s, int64_t *launches);
+
+// One fused force + noise + update step for global beads [b_lo, b_hi), step = *d_step + k_off.
+void launch_step(const StepArgs &a, const DevPairList &pl, const float4 *pos_in, float4 *pos_out, float4 *comp,
+                 int32_t b_lo, int32_t b_hi, int32_t k_off, int lanes, cudaStream_t s, int64_t *launches);
+
+// Forces only (no update) at pos for global beads [b_lo, b_hi); writes F (xyz, w unused).
+void launch_forces(const StepArgs &a, const DevPairList &pl, const float4 *pos, float4 *force, int32_t b_lo,
+                   int32_t b_hi, int64_t step, cudaStream_t s, int64_t *launches);
+
+// Observables (FP64) of all segments at pos; step = *d_step + k_off. If gate > 0 the record
+// is written only when the step is a multiple of gate. Writes into the ring.
+void launch_observables(const StepArgs &a, const DevPairList &pl, const DevObs &o, const float4 *pos, int32_t n_seg,
+                        int32_t k_off, int32_t gate, cudaStream_t s, int64_t *launches);
+
+// FP64 energy of the segments [g_lo, g_hi) at pos into *out (device), via the observable partials.
+void launch_energy(const StepArgs &a, const DevPairList &pl, const DevObs &o, const float4 *pos, int32_t g_lo,
+                   int32_t g_hi, double *out, cudaStream_t s, int64_t *launches);
+
+// Advance the device step counter by k; add one cadence event when gate > 0 and the new step
+// is a multiple of gate, else add n_events.
+void launch_tick(int64_t *d_step, int64_t k, int64_t *events, int32_t gate, int64_t n_events, cudaStream_t s,
+                 int64_t *launches);
+
+// ---- batched schedule (k_batched.cu) ----
+struct BatchedArgs {
+    StepArgs sa;
+    // work items (replica, system), heaviest first
+    int32_t n_items = 0;
+    const int32_t *item_rep = nullptr;
+    const int32_t *item_sys = nullptr;
+    // native lists in ELL form per system, column-major within a system:
+    // entry k of local bead b of system s is at nat_ell_off[s] + k * n_s + b
+    const int32_t *nat_ell_off = nullptr;  // [n_sys]
+    const int32_t *nat_ell_cnt = nullptr;  // [n] count per bead
+    const uint16_t *nat_ell_col = nullptr; // system-local partner
+    const float *nat_ell_r0sq = nullptr;
+    float4 *pos = nullptr;      // [R*n] current positions (read at start, written at end)
+    float4 *comp = nullptr;     // [R*n]
+    float4 *snap = nullptr;     // [R*n] positions at the last rebuild
+    int32_t *pl_dump_start = nullptr;  // optional: dump the list of the first rebuild (forces mode)
+    int32_t *pl_dump_len = nullptr;
+    int32_t *pl_dump_col = nullptr;
+    int32_t pl_dump_stride = 0;
+    float4 *force_out = nullptr;       // forces mode: F at the start positions
+    const int64_t *d_step = nullptr;    // step at launch start (device, read-only here)
+    const int64_t *d_events = nullptr;  // records taken before this launch (device)
+    int32_t n_steps = 0;
+    int32_t K = 10;             // rebuild_every
+    int32_t cap = 64;           // Verlet capacity per bead
+    int32_t max_n = 0;          // largest system in the launch
+    DevObs obs;
+    int32_t obs_every = 0;
+    int32_t n_seg = 0;
+};
+
+struct BatchedConfig {
+    int threads = 128;
+    int beads_per_thread = 1;
+    size_t smem = 0;
+};
+
+// Pick a configuration for systems of at most max_n beads with capacity cap.
+bool batched_config(int max_n, int cap, int threads_hint, BatchedConfig *cfg);
+// Run n_steps (or forces only when a.force_out != null and n_steps == 0).
+cudaError_t launch_batched(const BatchedArgs &a, const BatchedConfig &cfg, cudaStream_t s, int64_t *launches);
+
+}  // namespace sop

@@ -1,0 +1,303 @@
+"""ctypes binding of the C ABI in ``include/sop.h`` (argument marshalling only).
+
+Every step of the simulation runs in the CUDA library ``_lib/libsop.so``; this
+module converts numpy arrays to the C structs and pointers the ABI expects and
+raises ``SopError`` for any non-OK status. There is no CPU fallback: if the
+library is missing or cannot be loaded, ``load()`` raises.
+
+PyTorch is optional here and only supplies a CUDA stream (``stream=`` takes a
+``torch.cuda.Stream`` or a raw ``cudaStream_t`` integer).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libsop.so")
+_lock = threading.Lock()
+_lib = None
+
+OK, ERR_INVALID_ARG, ERR_CUDA, ERR_OOM, ERR_FENE_BREAK, ERR_NONFINITE, ERR_PAIRLIST_OVERFLOW, ERR_ABORTED, \
+    ERR_TIMEOUT, ERR_INDENTER_OVERLAP, ERR_UNSUPPORTED, ERR_CAPACITY = range(12)
+STATUS_NAMES = ["OK", "INVALID_ARG", "CUDA", "OOM", "FENE_BREAK", "NONFINITE", "PAIRLIST_OVERFLOW", "ABORTED",
+                "TIMEOUT", "INDENTER_OVERLAP", "UNSUPPORTED", "CAPACITY"]
+SCHED_AUTO, SCHED_BATCHED, SCHED_STREAMED, SCHED_PLAIN = range(4)
+SCHEDULES = {"auto": SCHED_AUTO, "batched": SCHED_BATCHED, "streamed": SCHED_STREAMED, "plain": SCHED_PLAIN}
+
+EXPORTED = ["sop_create", "sop_step", "sop_forces", "sop_pairlist_rebuild", "sop_pull", "sop_indenter",
+            "sop_get_positions", "sop_set_positions", "sop_get_pairlist", "sop_get_native_map",
+            "sop_get_observables", "sop_get_state", "sop_set_state", "sop_replica_status", "sop_abort",
+            "sop_get_stats", "sop_last_error", "sop_destroy"]
+
+
+class SopError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        name = STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else str(status)
+        super().__init__(f"SOP_ERR_{name}: {msg}")
+        self.status = status
+
+
+class Topology(C.Structure):
+    _fields_ = [("n_beads", C.c_int32), ("n_chains", C.c_int32), ("chain_offsets", C.c_void_p),
+                ("n_systems", C.c_int32), ("system_offsets", C.c_void_p), ("fixed_mask", C.c_void_p)]
+
+
+class Params(C.Structure):
+    _fields_ = [("k_fene", C.c_double), ("R0", C.c_double), ("eps_h", C.c_double), ("native_cut", C.c_double),
+                ("eps_l", C.c_double), ("sigma", C.c_double), ("T", C.c_double), ("zeta", C.c_double),
+                ("dt", C.c_double), ("pair_cut", C.c_double), ("rebuild_every", C.c_int32),
+                ("n_replicas", C.c_int32), ("seed", C.c_uint64), ("obs_every", C.c_int32),
+                ("obs_capacity", C.c_int32), ("pairs_per_bead", C.c_int32), ("schedule", C.c_int32),
+                ("cuda_stream", C.c_void_p)]
+
+
+class PullParams(C.Structure):
+    _fields_ = [("system", C.c_int32), ("anchor", C.c_int32), ("pulled", C.c_int32), ("k_s", C.c_double),
+                ("v", C.c_double)]
+
+
+class Record(C.Structure):
+    _fields_ = [(k, C.c_double) for k in ("step", "replica", "system", "energy", "f_ext", "extension", "q", "r_ee")]
+
+
+RECORD_FIELDS = [f for f, _ in Record._fields_]
+
+
+class Stats(C.Structure):
+    _fields_ = [("steps", C.c_int64), ("kernel_launches", C.c_int64), ("graph_launches", C.c_int64),
+                ("rebuilds", C.c_int64), ("schedule", C.c_int32), ("block_threads", C.c_int32),
+                ("pairs_per_bead", C.c_int32), ("beads_per_thread", C.c_int32), ("pairlist_entries", C.c_int64),
+                ("native_entries", C.c_int64)]
+
+
+def load(path: str | None = None):
+    """Load libsop.so (raises when it is missing: there is no fallback)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        p = path or LIB_PATH
+        if not os.path.exists(p):
+            raise RuntimeError(f"{p} is missing: build it with paper_1003_1148_gb300.build.build()")
+        L = C.CDLL(p)
+        vp, i32, i64, f64 = C.c_void_p, C.c_int32, C.c_int64, C.c_double
+        sig = {
+            "sop_create": ([vp, vp, vp, vp], C.c_int),
+            "sop_step": ([vp, i64], C.c_int),
+            "sop_forces": ([vp, i32, vp, vp], C.c_int),
+            "sop_pairlist_rebuild": ([vp], C.c_int),
+            "sop_pull": ([vp, i32, vp], C.c_int),
+            "sop_indenter": ([vp, vp, vp, f64, f64], C.c_int),
+            "sop_get_positions": ([vp, i32, vp], C.c_int),
+            "sop_set_positions": ([vp, i32, vp], C.c_int),
+            "sop_get_pairlist": ([vp, i32, vp, vp, i64, vp], C.c_int),
+            "sop_get_native_map": ([vp, vp, vp, vp, i64, vp], C.c_int),
+            "sop_get_observables": ([vp, vp, i64, vp, vp], C.c_int),
+            "sop_get_state": ([vp, vp, i64, vp], C.c_int),
+            "sop_set_state": ([vp, vp, i64], C.c_int),
+            "sop_replica_status": ([vp, vp], C.c_int),
+            "sop_abort": ([vp], None),
+            "sop_get_stats": ([vp, vp], C.c_int),
+            "sop_last_error": ([vp], C.c_char_p),
+            "sop_destroy": ([vp], None),
+        }
+        for name, (args, res) in sig.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = L
+    return _lib
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data
+
+
+def _stream_handle(stream) -> int | None:
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return int(getattr(stream, "cuda_stream"))
+
+
+class Simulation:
+    """One context of the library: a topology, its parameters and R replicas.
+
+    Arguments follow ``sop_create``: ``native_xyz`` [n, 3] FP64 native (and
+    starting) coordinates; ``chain_offsets`` [n_chains+1]; ``system_offsets``
+    [n_systems+1] in chains (None: every chain is its own system); ``fixed``
+    [n] 0/1; ``params`` a dict with the keys of ``sop_params``.
+    """
+
+    def __init__(self, native_xyz, chain_offsets, system_offsets=None, fixed=None, params=None, n_replicas=1,
+                 seed=0, obs_every=0, obs_capacity=0, pairs_per_bead=0, schedule="auto", stream=None):
+        L = load()
+        self._L = L
+        xyz = np.ascontiguousarray(native_xyz, np.float64).reshape(-1, 3)
+        self.n = xyz.shape[0]
+        self.R = int(n_replicas)
+        co = np.ascontiguousarray(chain_offsets, np.int32)
+        so = None if system_offsets is None else np.ascontiguousarray(system_offsets, np.int32)
+        fx = None if fixed is None else np.ascontiguousarray(fixed, np.uint8)
+        self.n_systems = (len(co) - 1) if so is None else len(so) - 1
+        topo = Topology(self.n, len(co) - 1, _ptr(co), 0 if so is None else len(so) - 1, _ptr(so), _ptr(fx))
+        p = dict(k_fene=14.0, R0=2.0, eps_h=1.0, native_cut=8.0, eps_l=1.0, sigma=3.8, T=300.0, zeta=50.0, dt=0.1,
+                 pair_cut=10.0, rebuild_every=10)
+        p.update(params or {})
+        sched = SCHEDULES[schedule] if isinstance(schedule, str) else int(schedule)
+        prm = Params(p["k_fene"], p["R0"], p["eps_h"], p["native_cut"], p["eps_l"], p["sigma"], p["T"], p["zeta"],
+                     p["dt"], p["pair_cut"], int(p["rebuild_every"]), self.R, int(seed), int(obs_every),
+                     int(obs_capacity), int(pairs_per_bead), sched, _stream_handle(stream))
+        self.params = p
+        self.obs_every = int(obs_every)
+        ctx = C.c_void_p()
+        rc = L.sop_create(C.byref(topo), _ptr(xyz), C.byref(prm), C.byref(ctx))
+        if rc != OK:
+            raise SopError(rc, L.sop_last_error(None).decode())
+        self._ctx = ctx
+
+    # -- helpers
+    def _check(self, rc):
+        if rc != OK:
+            raise SopError(rc, self._L.sop_last_error(self._ctx).decode())
+
+    def close(self):
+        if getattr(self, "_ctx", None):
+            self._L.sop_destroy(self._ctx)
+            self._ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- the ABI, one method per entry point
+    def step(self, n_steps: int, raise_on_error: bool = True) -> int:
+        rc = self._L.sop_step(self._ctx, int(n_steps))
+        if raise_on_error:
+            self._check(rc)
+        return rc
+
+    def forces(self, replica: int = 0):
+        """(F [n,3] FP64 from FP32 arithmetic, energy FP64) at the current positions."""
+        f = np.zeros((self.n, 3))
+        e = C.c_double(0.0)
+        self._check(self._L.sop_forces(self._ctx, replica, _ptr(f), C.byref(e)))
+        return f, e.value
+
+    def pairlist_rebuild(self):
+        self._check(self._L.sop_pairlist_rebuild(self._ctx))
+
+    def pull(self, pulls):
+        """pulls: iterable of (system, anchor, pulled, k_s, v)."""
+        pulls = list(pulls)
+        arr = (PullParams * max(1, len(pulls)))(*[PullParams(int(s), int(a), int(b), float(k), float(v))
+                                                   for s, a, b, k, v in pulls])
+        self._check(self._L.sop_pull(self._ctx, len(pulls), arr))
+
+    def indenter(self, center, direction, radius: float, v: float):
+        c = np.ascontiguousarray(center, np.float64)
+        d = np.ascontiguousarray(direction, np.float64)
+        self._check(self._L.sop_indenter(self._ctx, _ptr(c), _ptr(d), float(radius), float(v)))
+
+    def get_positions(self, replica: int = 0, out: np.ndarray | None = None) -> np.ndarray:
+        shape = (self.R, self.n, 3) if replica == -1 else (self.n, 3)
+        if out is None:
+            out = np.zeros(shape)
+        assert out.dtype == np.float64 and out.flags.c_contiguous and out.size == int(np.prod(shape))
+        self._check(self._L.sop_get_positions(self._ctx, replica, _ptr(out)))
+        return out
+
+    def set_positions(self, xyz, replica: int = 0):
+        a = np.ascontiguousarray(xyz, np.float64)
+        need = (self.R if replica == -1 else 1) * self.n * 3
+        if a.size != need:
+            raise ValueError(f"expected {need} coordinates, got {a.size}")
+        self._check(self._L.sop_set_positions(self._ctx, replica, _ptr(a)))
+
+    def get_pairlist(self, replica: int = 0):
+        """(row_ptr [n+1], col [nnz]) canonical CSR, both directions."""
+        rp = np.zeros(self.n + 1, np.int32)
+        nnz = C.c_int64(0)
+        rc = self._L.sop_get_pairlist(self._ctx, replica, _ptr(rp), None, 0, C.byref(nnz))
+        if rc not in (OK, ERR_CAPACITY):
+            self._check(rc)
+        col = np.zeros(max(1, nnz.value), np.int32)
+        self._check(self._L.sop_get_pairlist(self._ctx, replica, _ptr(rp), _ptr(col), len(col), C.byref(nnz)))
+        return rp, col[:nnz.value]
+
+    def get_native_map(self):
+        """(row_ptr [n+1], col [nnz], r0 [nnz] FP64), both directions."""
+        rp = np.zeros(self.n + 1, np.int32)
+        nnz = C.c_int64(0)
+        rc = self._L.sop_get_native_map(self._ctx, _ptr(rp), None, None, 0, C.byref(nnz))
+        if rc not in (OK, ERR_CAPACITY):
+            self._check(rc)
+        col = np.zeros(max(1, nnz.value), np.int32)
+        r0 = np.zeros(max(1, nnz.value), np.float64)
+        self._check(self._L.sop_get_native_map(self._ctx, _ptr(rp), _ptr(col), _ptr(r0), len(col), C.byref(nnz)))
+        return rp, col[:nnz.value], r0[:nnz.value]
+
+    def get_observables(self):
+        """Structured array of the records taken since the last call, and the count lost."""
+        n = C.c_int64(0)
+        lost = C.c_int64(0)
+        rc = self._L.sop_get_observables(self._ctx, None, 0, C.byref(n), C.byref(lost))
+        if rc not in (OK, ERR_CAPACITY):
+            self._check(rc)
+        buf = (Record * max(1, n.value))()
+        self._check(self._L.sop_get_observables(self._ctx, buf, n.value, C.byref(n), C.byref(lost)))
+        arr = np.frombuffer(buf, dtype=np.float64).reshape(-1, 8)[:n.value].copy()
+        return arr, lost.value
+
+    def get_state(self) -> bytes:
+        size = C.c_int64(0)
+        self._check(self._L.sop_get_state(self._ctx, None, 0, C.byref(size)))
+        buf = (C.c_char * size.value)()
+        self._check(self._L.sop_get_state(self._ctx, buf, size.value, C.byref(size)))
+        return bytes(buf)
+
+    def set_state(self, state: bytes):
+        buf = C.create_string_buffer(state, len(state))
+        self._check(self._L.sop_set_state(self._ctx, buf, len(state)))
+
+    def replica_status(self) -> np.ndarray:
+        out = np.zeros(self.R, np.int32)
+        self._check(self._L.sop_replica_status(self._ctx, _ptr(out)))
+        return out
+
+    def abort(self):
+        self._L.sop_abort(self._ctx)
+
+    def stats(self) -> dict:
+        s = Stats()
+        self._check(self._L.sop_get_stats(self._ctx, C.byref(s)))
+        return {k: getattr(s, k) for k, _ in Stats._fields_}
+
+
+def from_workload(w, n_replicas: int | None = None, schedule="auto", stream=None, obs_every=None, **kw) -> Simulation:
+    """A Simulation of a synthetic workload (duck-typed: xyz, chain_offsets,
+    system_offsets, fixed, params, n_replicas, seed, pulls, indenter, obs_every).
+    Pulling and the indenter start at step 0."""
+    sim = Simulation(w.xyz, w.chain_offsets, w.system_offsets, w.fixed, w.params,
+                     n_replicas=w.n_replicas if n_replicas is None else n_replicas, seed=w.seed,
+                     obs_every=w.obs_every if obs_every is None else obs_every, schedule=schedule, stream=stream, **kw)
+    if w.pulls:
+        sys_of = w.system_of_bead()
+        sim.pull([(int(sys_of[p.anchor]), p.anchor, p.pulled, p.k_s, p.v) for p in w.pulls])
+    if w.indenter is not None:
+        ind = w.indenter
+        sim.indenter(ind.center, ind.direction, ind.radius, ind.v)
+    return sim

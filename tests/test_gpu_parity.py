@@ -1,0 +1,248 @@
+"""CUDA path against the FP64 oracle, through the C ABI (needs a GPU).
+
+Bars (from the method's arithmetic):
+  * native map and Verlet list: bit-exact as sets (FP64 decisions on both sides);
+  * forces at identical positions: |F_gpu - F_64| <= 1e-5 * A per component, A the
+    oracle's term-magnitude scale (sum over terms of each term evaluated with
+    magnitudes, which bounds rounding error);
+  * energy (FP64 accumulation on both sides): relative 1e-9;
+  * positions after 100 steps with the same Philox stream: RMS <= 1e-3 A.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+FORCE_TOL = 1e-5
+RMS_TOL = 1e-3
+
+
+@pytest.fixture(scope="module")
+def sop():
+    from paper_1003_1148_gb300 import build, sop as s
+    build.build()
+    s.load()
+    return s
+
+
+def csr_pairs(rp, col):
+    out = set()
+    for i in range(len(rp) - 1):
+        for j in col[rp[i]:rp[i + 1]]:
+            if j > i:
+                out.add((i, int(j)))
+    return out
+
+
+def csr_is_symmetric_sorted(rp, col):
+    for i in range(len(rp) - 1):
+        row = col[rp[i]:rp[i + 1]]
+        if np.any(np.diff(row) <= 0):
+            return False
+    pairs = {(i, int(j)) for i in range(len(rp) - 1) for j in col[rp[i]:rp[i + 1]]}
+    return all((j, i) in pairs for i, j in pairs)
+
+
+def small_workloads(synth):
+    ws = [synth.chain64(), synth.replicas(n_replicas=6, n=128, steps=100)]
+    ws.append(synth.uneven(n_chains=12, lo=50, hi=400, steps=100))
+    ws.append(synth.fiber4096(n=700, steps=100))
+    ws.append(synth.shell(n_copies=6, n_per=150, r_in=60.0, r_out=80.0, ind_radius=20.0, steps=100))
+    return ws
+
+
+@pytest.fixture(scope="module")
+def workloads(synth):
+    return small_workloads(synth)
+
+
+def test_native_map_bit_exact(sop, orc, workloads):
+    for w in workloads:
+        sim = sop.from_workload(w, n_replicas=1, schedule="streamed")
+        rp, col, r0 = sim.get_native_map()
+        m = orc.model_from_workload(w)
+        got = csr_pairs(rp, col)
+        ref = set(zip(m.nat_i.tolist(), m.nat_j.tolist()))
+        assert got == ref, w.name
+        assert csr_is_symmetric_sorted(rp, col)
+        # FP64 r0 identical
+        lookup = {(a, b): v for a, b, v in zip(m.nat_i.tolist(), m.nat_j.tolist(), m.nat_r0.tolist())}
+        for i in range(len(rp) - 1):
+            for k in range(rp[i], rp[i + 1]):
+                j = int(col[k])
+                assert r0[k] == lookup[(min(i, j), max(i, j))]
+        sim.close()
+
+
+@pytest.mark.parametrize("schedule", ["streamed", "batched"])
+def test_pairlist_bit_exact_after_steps(sop, orc, workloads, schedule):
+    for w in workloads:
+        if schedule == "batched" and max(np.diff(w.chain_offsets)) > 2048:
+            continue
+        if schedule == "batched" and w.n_systems == 1 and w.n_beads > 2048:
+            continue
+        R = 2
+        sim = sop.from_workload(w, n_replicas=R, schedule=schedule)
+        m = orc.model_from_workload(w)
+        for steps in (0, 23):
+            if steps:
+                sim.step(steps)
+                sim.pairlist_rebuild()
+            for r in range(R):
+                x = sim.get_positions(r)
+                rp, col = sim.get_pairlist(r)
+                pi, pj = m.pairlist(x, cells=w.n_beads > 1500)
+                assert csr_pairs(rp, col) == set(zip(pi.tolist(), pj.tolist())), (w.name, schedule, steps, r)
+                assert csr_is_symmetric_sorted(rp, col)
+        sim.close()
+
+
+def oracle_with_externals(orc, w, x_start):
+    m = orc.model_from_workload(w)
+    if w.pulls:
+        sys_of = w.system_of_bead()
+        m.start_pulls([(int(sys_of[p.anchor]), p.anchor, p.pulled, p.k_s, p.v) for p in w.pulls], x_start)
+    if w.indenter is not None:
+        ind = w.indenter
+        m.set_indenter(ind.center, ind.direction, ind.radius, ind.v)
+    return m
+
+
+@pytest.mark.parametrize("schedule", ["streamed", "batched"])
+def test_forces_within_tolerance(sop, orc, workloads, schedule):
+    for w in workloads:
+        if schedule == "batched" and w.n_systems == 1 and w.n_beads > 2048:
+            continue
+        sim = sop.from_workload(w, n_replicas=2, schedule=schedule)
+        x0 = sim.get_positions(0)
+        m = oracle_with_externals(orc, w, x0)
+        sim.step(30)
+        for r in range(2):
+            x = sim.get_positions(r)
+            F, E = sim.forces(r)
+            Fo, Ao, Eo = m.forces(x, step=30)
+            err = np.abs(F - Fo) / Ao
+            assert err.max() <= FORCE_TOL, (w.name, schedule, r, err.max())
+            e_ref = Eo[0] + Eo[1] + Eo[2]
+            assert E == pytest.approx(e_ref, rel=1e-9, abs=1e-9), (w.name, schedule)
+        sim.close()
+
+
+@pytest.mark.parametrize("schedule", ["streamed", "batched", "plain"])
+def test_trajectory_100_steps(sop, orc, workloads, schedule):
+    for w in workloads:
+        if schedule == "batched" and w.n_systems == 1 and w.n_beads > 2048:
+            continue
+        R = 2
+        sim = sop.from_workload(w, n_replicas=R, schedule=schedule)
+        x0 = sim.get_positions(0)
+        m = oracle_with_externals(orc, w, x0)
+        sim.step(100)
+        for r in range(R):
+            xg = sim.get_positions(r)
+            xo, _, _, _ = m.run(x0, 100, seed=w.seed + r)
+            rms = float(np.sqrt(((xg - xo) ** 2).sum(1).mean()))
+            assert rms <= RMS_TOL, (w.name, schedule, r, rms)
+        sim.close()
+
+
+def test_plain_equals_streamed_bitwise(sop, synth):
+    w = synth.uneven(n_chains=5, lo=60, hi=300, steps=50)
+    a = sop.from_workload(w, n_replicas=2, schedule="streamed")
+    b = sop.from_workload(w, n_replicas=2, schedule="plain")
+    a.step(37)
+    b.step(37)
+    assert np.array_equal(a.get_positions(-1), b.get_positions(-1))
+
+
+def test_observables_match_oracle_at_gpu_positions(sop, orc, synth):
+    for schedule in ("streamed", "batched"):
+        w = synth.uneven(n_chains=4, lo=60, hi=200, steps=100)
+        sim = sop.from_workload(w, n_replicas=2, schedule=schedule, obs_every=20)
+        x0 = sim.get_positions(0)
+        m = oracle_with_externals(orc, w, x0)
+        sim.step(40)
+        rec, lost = sim.get_observables()
+        assert lost == 0 and len(rec) == 2 * 2 * w.n_systems
+        last = rec[rec[:, 0] == 40]
+        for r in range(2):
+            x = sim.get_positions(r)
+            ref = m.observables(x, pl=m.pairlist(x), step=40)
+            got = last[last[:, 1] == r]
+            got = got[np.argsort(got[:, 2])]
+            assert np.allclose(got[:, 3], ref[:, 2], rtol=1e-9, atol=1e-9), schedule       # energy
+            assert np.allclose(got[:, 4], ref[:, 3], rtol=1e-9, atol=1e-12), schedule      # pull force
+            assert np.allclose(got[:, 5], ref[:, 4], rtol=1e-12), schedule                 # extension
+            assert np.array_equal(got[:, 6], ref[:, 5]), schedule                          # Q
+            assert np.allclose(got[:, 7], ref[:, 6], rtol=1e-12), schedule                 # R_ee
+        sim.close()
+
+
+@pytest.mark.parametrize("schedule", ["streamed", "batched"])
+def test_checkpoint_resume_bit_exact(sop, synth, schedule):
+    w = synth.replicas(n_replicas=3, n=100, steps=100)
+    sim = sop.from_workload(w, schedule=schedule)
+    sim.step(37)
+    state = sim.get_state()
+    sim.step(55)
+    a = sim.get_positions(-1).copy()
+    sim.set_state(state)
+    sim.step(55)
+    b = sim.get_positions(-1)
+    assert np.array_equal(a, b)
+
+
+def test_replica_sharding_is_exact(sop, synth):
+    """Replicas split over two contexts (seed offset) reproduce one context bit for bit."""
+    w = synth.replicas(n_replicas=5, n=96, steps=60)
+    whole = sop.from_workload(w, schedule="batched")
+    whole.step(60)
+    x = whole.get_positions(-1)
+    a = sop.Simulation(w.xyz, w.chain_offsets, w.system_offsets, w.fixed, w.params, n_replicas=2, seed=w.seed,
+                       schedule="batched")
+    b = sop.Simulation(w.xyz, w.chain_offsets, w.system_offsets, w.fixed, w.params, n_replicas=3, seed=w.seed + 2,
+                       schedule="batched")
+    a.step(60)
+    b.step(60)
+    assert np.array_equal(np.concatenate([a.get_positions(-1), b.get_positions(-1)]), x)
+
+
+@pytest.mark.parametrize("schedule", ["streamed", "batched"])
+def test_fene_break_freezes_only_that_replica(sop, synth, schedule):
+    w = synth.replicas(n_replicas=3, n=64, steps=10)
+    sim = sop.from_workload(w, schedule=schedule)
+    bad = w.xyz.copy()
+    bad[40:] += np.array([30.0, 0.0, 0.0])       # bond 39-40 stretched far beyond R0
+    sim.set_positions(bad, replica=1)
+    rc = sim.step(10, raise_on_error=False)
+    assert rc == sop.ERR_FENE_BREAK
+    st = sim.replica_status()
+    assert st[1] == sop.ERR_FENE_BREAK and st[0] == 0 and st[2] == 0
+    frozen = sim.get_positions(1).copy()
+    # the beads of the broken bond never moved; the replica stays frozen
+    bad32 = bad.astype(np.float32).astype(np.float64)
+    assert np.array_equal(frozen[39:41], bad32[39:41])
+    rc = sim.step(10, raise_on_error=False)
+    assert rc == sop.ERR_FENE_BREAK
+    assert np.array_equal(sim.get_positions(1), frozen)
+    assert not np.array_equal(sim.get_positions(0), w.xyz.astype(np.float32).astype(np.float64))
+
+
+def test_pairlist_overflow_reported(sop, synth):
+    w = synth.replicas(n_replicas=1, n=128, steps=10)
+    with pytest.raises(sop.SopError) as e:
+        sim = sop.from_workload(w, schedule="streamed", pairs_per_bead=2)
+        sim.step(10)
+    assert e.value.status == sop.ERR_PAIRLIST_OVERFLOW
+
+
+def test_abort_stops_a_long_run(sop, synth):
+    import threading
+    w = synth.replicas(n_replicas=64, n=128, steps=10)
+    sim = sop.from_workload(w, schedule="batched")
+    t = threading.Timer(0.5, sim.abort)
+    t.start()
+    rc = sim.step(10_000_000, raise_on_error=False)
+    t.join()
+    assert rc == sop.ERR_ABORTED
+    assert sim.stats()["steps"] < 10_000_000

@@ -1,0 +1,403 @@
+"""Benchmark: bead-steps/s of the SOP-model Langevin hot path on GB300.
+
+Workload (default): 8,192 independent replicas of one 128-bead compact chain
+(seeded synthetic stand-in for the paper's many-runs-per-GPU experiment), run
+by the batched persistent kernel. One benchmark step = 1,000 Langevin steps of
+every replica: 100 Verlet-list rebuilds, 1,000 force + Philox noise +
+compensated-update steps and one FP64 observable record per replica.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line. `value` is device-timed (CUDA events on the library's
+stream, inputs resident, L2 flushed between timed steps); `e2e` times the same
+work through the public API with host buffers (positions uploaded from pinned
+memory and observables read back every step). `--impl reference` times the
+FP64 CPU oracle on the host cores on bounded samples of the same workload.
+Under torchrun every rank runs its own 8,192 replicas (weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import multiprocessing as mp
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "bead-steps/s on 1 GB300, batched FP32 vs plain per-chain; force err vs FP64"
+UNIT = "bead-steps/s"
+MD_STEPS_PER_STEP = 1000
+FP32_LANES_PER_SM = 128
+N_SM = 152
+
+# Algorithmic FP32 operations per unique pair term and per bead (FMA = 2): see the design doc.
+FLOP_FENE, FLOP_NATIVE, FLOP_REP, FLOP_BEAD = 25, 25, 23, 33
+
+
+def workload(name: str):
+    from paper_1003_1148_gb300 import synth
+    if name == "replicas8192x128":
+        return synth.replicas(n_replicas=8192, n=128, seed=3, steps=100_000)
+    if name.startswith("replicas"):
+        r, n = name[len("replicas"):].split("x")
+        return synth.replicas(n_replicas=int(r), n=int(n), seed=3, steps=100_000)
+    raise SystemExit(f"unknown workload {name}")
+
+
+# ----------------------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ----------------------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if f[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------------------
+# oracle legs (host cores only)
+# ----------------------------------------------------------------------------------------
+def _oracle_replica(args):
+    """Run one replica of the oracle (in a spawned worker); returns bead-steps and seconds."""
+    xyz, chain_offsets, seed, n_steps, params = args
+    sys.path.insert(0, ROOT)
+    import oracle
+    n = xyz.shape[0]
+    chain = np.zeros(n, np.int32)
+    for c in range(len(chain_offsets) - 1):
+        chain[chain_offsets[c]:chain_offsets[c + 1]] = c
+    m = oracle.Model(xyz, chain, np.zeros(n, np.int32), params=params)
+    t0 = time.perf_counter()
+    m.run(xyz, n_steps, seed=seed)
+    return n * n_steps, time.perf_counter() - t0
+
+
+def cpu_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def cpu_baseline_leg(w, n_replicas: int, n_steps: int, pool=None):
+    """The FP64 oracle as it stands, replicas spread over the host cores.
+    Returns (bead-steps/s, cores, sample text)."""
+    cores = cpu_cores()
+    jobs = [(w.xyz, w.chain_offsets, w.seed + r, n_steps, w.params) for r in range(n_replicas)]
+    t0 = time.perf_counter()
+    if pool is not None:
+        res = pool.map(_oracle_replica, jobs)
+    else:
+        res = [_oracle_replica(j) for j in jobs]
+    wall = time.perf_counter() - t0
+    work = sum(r[0] for r in res)
+    sample = (f"{n_replicas} replicas x {n_steps} steps x {w.xyz.shape[0]} beads of the same chain "
+              f"({work:.3g} bead-steps) on {min(cores, n_replicas)} processes")
+    return work / wall, min(cores, n_replicas), sample
+
+
+def force_error_leg(w, positions, forces_gpu):
+    """FP32 GPU forces against the FP64 oracle at identical positions (part of the
+    CPU-baseline leg: the only place the benchmark calls the oracle besides timing)."""
+    import oracle
+    n = w.xyz.shape[0]
+    m = oracle.Model(w.xyz, np.zeros(n, np.int32), np.zeros(n, np.int32), params=w.params)
+    Fo, Ao, _ = m.forces(positions, step=0)
+    d = np.abs(forces_gpu - Fo)
+    return {"max_rel_to_term_scale": float((d / Ao).max()),
+            "max_abs_kcal_mol_A": float(d.max()),
+            "median_rel": float(np.median(d / np.maximum(np.abs(Fo), 1e-12))),
+            "gate": 1e-5, "sample": "replica 0 after the timed run, all beads, FP64 oracle"}
+
+
+# ----------------------------------------------------------------------------------------
+# distributed helpers (weak scaling over replicas; no data-path collective)
+# ----------------------------------------------------------------------------------------
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def dist_init(world):
+    if world <= 1:
+        return None
+    import torch.distributed as dist
+    dist.init_process_group("gloo", init_method="env://")
+    return dist
+
+
+def dist_max(dist, v: float) -> float:
+    if dist is None:
+        return v
+    import torch
+    t = torch.tensor([v], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def dist_barrier(dist):
+    if dist is not None:
+        dist.barrier()
+
+
+# ----------------------------------------------------------------------------------------
+# arms
+# ----------------------------------------------------------------------------------------
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    w = workload(args.workload)
+    ctx = mp.get_context("spawn")
+    per_step_reps = max(1, min(cpu_cores(), 32))
+    with ctx.Pool(cpu_cores()) as pool:
+        for _ in range(args.warmup):
+            cpu_baseline_leg(w, per_step_reps, 100, pool)
+        t0 = time.perf_counter()
+        work = 0.0
+        for _ in range(args.steps):
+            rate, cores, sample = cpu_baseline_leg(w, per_step_reps, 100, pool)
+            work += per_step_reps * 100 * w.xyz.shape[0]
+        wall = time.perf_counter() - t0
+    value = work / wall
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wall / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded compact self-avoiding walk; PDB inputs unavailable)",
+            "config": config_dict(args, w),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"each step: {sample}"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def config_dict(args, w):
+    return {"workload": args.workload, "replicas_per_gpu": w.n_replicas, "beads_per_replica": w.n_beads,
+            "md_steps_per_step": MD_STEPS_PER_STEP, "rebuild_every": w.params["rebuild_every"],
+            "obs_every": w.obs_every, "dt_ps": w.params["dt"], "T_K": w.params["T"],
+            "pair_cut_A": w.params["pair_cut"], "schedule": args.schedule,
+            "l2": "flushed between timed steps (256 MiB write)", "parallelism": f"replicas x{args.gpus}"}
+
+
+def algorithmic_flops_per_bead_step(sim, w) -> tuple[float, dict]:
+    rp, col = sim.get_pairlist(0)
+    n_pl = len(col) / 2.0
+    n_nat = sim.stats()["native_entries"]
+    n_bonds = w.n_beads - w.n_chains
+    f = (FLOP_FENE * n_bonds + FLOP_NATIVE * n_nat + FLOP_REP * n_pl) / w.n_beads + FLOP_BEAD
+    return f, {"bonds": n_bonds, "native_pairs": int(n_nat), "verlet_pairs": int(n_pl)}
+
+
+def run_ours(args):
+    import torch
+    from paper_1003_1148_gb300 import sop
+
+    world, rank, local = dist_env()
+    dist = dist_init(world)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w = workload(args.workload)
+    R = w.n_replicas
+
+    # the CPU baseline runs first, from spawned workers, before any GPU work
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        ctx = mp.get_context("spawn")
+        n_rep = max(2, min(cpu_cores(), 64))
+        with ctx.Pool(cpu_cores()) as pool:
+            probe_rate, _, _ = cpu_baseline_leg(w, min(n_rep, cpu_cores()), 200, pool)
+            # size the sample to about 15 s of CPU work
+            steps = int(max(200, min(5000, 15.0 * probe_rate / (n_rep * w.n_beads))))
+            rate, cores, sample = cpu_baseline_leg(w, n_rep, steps, pool)
+        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+
+    stream = torch.cuda.Stream(device=dev)
+    sim = sop.Simulation(w.xyz, w.chain_offsets, w.system_offsets, w.fixed, w.params, n_replicas=R,
+                         seed=w.seed + rank * R, obs_every=w.obs_every, obs_capacity=4 * R,
+                         schedule=args.schedule, stream=stream)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    work_per_step = R * w.n_beads * MD_STEPS_PER_STEP
+
+    def one_step():
+        sim.step(MD_STEPS_PER_STEP)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            one_step()
+            sim.get_observables()
+        torch.cuda.synchronize()
+        launches0 = sim.stats()["kernel_launches"]
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        dist_barrier(dist)
+        torch.cuda.synchronize()
+        with ClockSampler(local) as clk:
+            t0 = time.perf_counter()
+            for k in range(args.steps):
+                flush.zero_()                      # L2 flush, outside the timed events
+                starts[k].record(stream)
+                one_step()
+                ends[k].record(stream)
+            torch.cuda.synchronize()
+            wall = time.perf_counter() - t0
+        dist_barrier(dist)
+        launches = sim.stats()["kernel_launches"] - launches0
+        dev_ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
+        sim.get_observables()
+
+        # end to end through the public API with host buffers
+        pinned = torch.empty((R, w.n_beads, 3), dtype=torch.float64, pin_memory=True)
+        pinned.numpy()[:] = sim.get_positions(-1)
+        torch.cuda.synchronize()
+        e2e_steps = max(1, min(args.steps, 5))
+        t1 = time.perf_counter()
+        d2h = 0
+        for _ in range(e2e_steps):
+            sim.set_positions(pinned.numpy(), replica=-1)
+            one_step()
+            rec, lost = sim.get_observables()
+            d2h = rec.nbytes
+        e2e_wall = time.perf_counter() - t1
+    h2d = R * w.n_beads * 3 * 8
+
+    t_dev = dist_max(dist, dev_ms / 1e3)
+    t_e2e = dist_max(dist, e2e_wall)
+    value = world * work_per_step * args.steps / t_dev
+    e2e_value = world * work_per_step * e2e_steps / t_e2e
+
+    if rank != 0:
+        sim.close()
+        return 0
+
+    # roofline of the dominant kernel (the batched persistent kernel; one launch per step)
+    flop_bs, counts = algorithmic_flops_per_bead_step(sim, w)
+    clocks = clk.summary()
+    peak_mhz = 2070.0
+    peak = N_SM * FP32_LANES_PER_SM * 2 * peak_mhz * 1e6 / 1e12
+    per_launch_s = dev_ms / 1e3 / args.steps
+    achieved = flop_bs * work_per_step / per_launch_s / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None, "kernel": "k_batched (one launch of 1,000 steps per benchmark step)",
+                "flop_per_bead_step": flop_bs, "list_sizes_replica0": counts,
+                "peak_note": "FP32 FMA pipe: 152 SMs x 128 lanes x 2 x 2070 MHz (max SM clock), derived"}
+    traffic_file = os.path.join(ROOT, "profiles", "k_batched_replicas8192x128.traffic.json")
+    if os.path.exists(traffic_file):
+        try:
+            roofline["traffic"] = json.load(open(traffic_file)).get("bytes_per_launch")
+        except (OSError, ValueError):
+            pass
+
+    # plain per-chain GPU form on a subset of replicas (same kernels' math, one chain per launch)
+    plain = None
+    if not args.no_plain:
+        n_plain, s_plain = 4, 200
+        ps = sop.Simulation(w.xyz, w.chain_offsets, w.system_offsets, w.fixed, w.params, n_replicas=n_plain,
+                            seed=w.seed, schedule="plain", stream=stream)
+        with torch.cuda.stream(stream):
+            ps.step(20)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ps.step(s_plain)
+            e1.record(stream)
+            torch.cuda.synchronize()
+        pv = n_plain * w.n_beads * s_plain / (e0.elapsed_time(e1) / 1e3)
+        plain = {"value": pv, "unit": UNIT, "sample": f"{n_plain} replicas x {s_plain} steps, one chain per "
+                 "launch sequence (per-step fused kernel, cell-list rebuild every 10 steps), chains in sequence",
+                 "batched_over_plain": value / world / pv}
+        ps.close()
+
+    ferr = None
+    if not args.no_cpu:
+        F, _ = sim.forces(0)
+        ferr = force_error_leg(w, sim.get_positions(0), F)
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": dev_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded compact self-avoiding walk; "
+            "PDB inputs unavailable)", "config": config_dict(args, w),
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "steps": e2e_steps},
+            "gpu_launches": launches, "wall_s_timed_region": wall,
+            "clocks": {"sm_mhz": clocks["sm_mhz"], "sm_max_mhz": clocks["sm_max_mhz"], "reasons": clocks["reasons"]},
+            "roofline": roofline, "cpu_baseline": cpu, "plain_per_chain": plain, "force_err_vs_fp64": ferr}
+    print(json.dumps(line))
+    sim.close()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="replicas8192x128")
+    ap.add_argument("--schedule", default="batched", choices=["batched", "streamed", "auto"])
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle legs (profiling runs)")
+    ap.add_argument("--no-plain", action="store_true", help="skip the plain per-chain comparison")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

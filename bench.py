@@ -331,8 +331,12 @@ def run_ours(args):
     peak = N_SM * FP32_LANES_PER_SM * 2 * peak_mhz * 1e6 / 1e12
     per_launch_s = dev_ms / 1e3 / args.steps
     achieved = flop_bs * work_per_step / per_launch_s / 1e12
+    st = sim.stats()
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": None, "kernel": "k_batched (one launch of 1,000 steps per benchmark step)",
+                "kernel_config": {"threads": st["block_threads"], "beads_per_thread": st["beads_per_thread"],
+                                  "register_cap": 65536 // (256 * max(1, st["min_blocks"])),
+                                  "verlet_capacity": st["pairs_per_bead"]},
                 "flop_per_bead_step": flop_bs, "list_sizes_replica0": counts,
                 "peak_note": "FP32 FMA pipe: 152 SMs x 128 lanes x 2 x 2070 MHz (max SM clock), derived"}
     traffic_file = os.path.join(ROOT, "profiles", "k_batched_replicas8192x128.traffic.json")

@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <string>
@@ -608,6 +609,107 @@ sop_status build_batched_tables(sop_ctx *c) {
     return SOP_OK;
 }
 
+// Size-bucket autotuner of the batched kernel. Candidates are (threads per CTA, beads
+// per thread, register cap); each is timed on a 20-step trial of up to 16 CTAs per SM on
+// scratch copies of the state (the run's state, records and statuses are untouched) and
+// the fastest is kept. Results are cached in the file named by SOP_TUNE_CACHE, keyed by
+// the system size, row width and trial size; SOP_TUNE=0 skips the trial.
+sop_status tune_batched(sop_ctx *c, int row_width, BatchedConfig *best) {
+    std::vector<BatchedConfig> cands;
+    for (int threads : {64, 128, 256})
+        for (int minb : {2, 3, 4}) {
+            BatchedConfig cfg;
+            if (!batched_config(c->max_sys, row_width, threads, &cfg)) continue;
+            if (threads > 32 * ((c->max_sys + 31) / 32) && threads > 64) continue;   // idle threads only
+            cfg.min_blocks = minb;
+            cands.push_back(cfg);
+        }
+    if (cands.empty()) return fail(c, SOP_ERR_UNSUPPORTED, "no batched configuration fits");
+    *best = cands[0];
+    for (const auto &cf : cands)   // default without a trial: the largest CTA at 64 registers
+        if (cf.min_blocks == 4 && cf.threads >= best->threads) *best = cf;
+    const char *env = std::getenv("SOP_TUNE");
+    if (env && std::string(env) == "0") return SOP_OK;
+    const int trial_items = std::min<int>(c->n_items, 152 * 16);
+    char key[128];
+    std::snprintf(key, sizeof key, "batched %d %d %d", c->max_sys, row_width, trial_items);
+    const char *cache = std::getenv("SOP_TUNE_CACHE");
+    if (cache) {
+        if (FILE *f = std::fopen(cache, "r")) {
+            char line[256];
+            while (std::fgets(line, sizeof line, f)) {
+                int t = 0, bpt = 0, mb = 0;
+                if (std::strncmp(line, key, std::strlen(key)) == 0 &&
+                    std::sscanf(line + std::strlen(key), " -> %d %d %d", &t, &bpt, &mb) == 3) {
+                    for (const auto &cf : cands)
+                        if (cf.threads == t && cf.beads_per_thread == bpt && cf.min_blocks == mb) {
+                            *best = cf;
+                            std::fclose(f);
+                            return SOP_OK;
+                        }
+                }
+            }
+            std::fclose(f);
+        }
+    }
+    const size_t RN = (size_t)c->R * c->n;
+    float4 *sp = nullptr, *sc = nullptr, *ss = nullptr;
+    int32_t *sst = nullptr;
+    CUDA_OR_RETURN(c, cudaMalloc(&sp, sizeof(float4) * RN));
+    CUDA_OR_RETURN(c, cudaMalloc(&sc, sizeof(float4) * RN));
+    CUDA_OR_RETURN(c, cudaMalloc(&ss, sizeof(float4) * RN));
+    CUDA_OR_RETURN(c, cudaMalloc(&sst, sizeof(int32_t) * c->R));
+    cudaEvent_t e0, e1;
+    CUDA_OR_RETURN(c, cudaEventCreate(&e0));
+    CUDA_OR_RETURN(c, cudaEventCreate(&e1));
+    float best_ms = 1e30f;
+    sop_status status = SOP_OK;
+    for (const auto &cf : cands) {
+        BatchedArgs a = batched_args(c);
+        a.pos = sp;
+        a.comp = sc;
+        a.snap = ss;
+        a.sa.rep_status = sst;
+        a.obs_every = 0;
+        a.n_items = trial_items;
+        a.n_steps = 20;
+        float ms = 0.f;
+        for (int rep = 0; rep < 3 && status == SOP_OK; ++rep) {
+            cudaMemcpyAsync(sp, c->d_pos[0], sizeof(float4) * RN, cudaMemcpyDeviceToDevice, c->stream);
+            cudaMemcpyAsync(sc, c->d_comp, sizeof(float4) * RN, cudaMemcpyDeviceToDevice, c->stream);
+            cudaMemcpyAsync(ss, c->d_snap, sizeof(float4) * RN, cudaMemcpyDeviceToDevice, c->stream);
+            cudaMemsetAsync(sst, 0, sizeof(int32_t) * c->R, c->stream);
+            cudaEventRecord(e0, c->stream);
+            cudaError_t e = launch_batched(a, cf, c->stream, nullptr);
+            cudaEventRecord(e1, c->stream);
+            if (e != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
+                status = fail(c, SOP_ERR_CUDA, std::string("autotune trial: ") + cudaGetErrorString(e));
+                break;
+            }
+            float t = 0.f;
+            cudaEventElapsedTime(&t, e0, e1);
+            if (rep > 0) ms = rep == 1 ? t : std::min(ms, t);
+        }
+        if (status != SOP_OK) break;
+        if (ms < best_ms) { best_ms = ms; *best = cf; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(sp);
+    cudaFree(sc);
+    cudaFree(ss);
+    cudaFree(sst);
+    if (status != SOP_OK) return status;
+    c->st.tune_ms = best_ms;
+    if (cache)
+        if (FILE *f = std::fopen(cache, "a")) {
+            std::fprintf(f, "%s -> %d %d %d %.4f\n", key, best->threads, best->beads_per_thread, best->min_blocks,
+                         best_ms);
+            std::fclose(f);
+        }
+    return SOP_OK;
+}
+
 // Largest Verlet row of replica 0 after the initial build.
 sop_status max_row(sop_ctx *c, int *out) {
     std::vector<int32_t> len(c->n);
@@ -839,7 +941,9 @@ sop_status create_impl(sop_ctx *c, const sop_topology *topo, const double *xyz, 
     int sched = p->schedule;
     BatchedConfig cfg;
     const int bcap = std::min(128, std::max(32, ((mrow * 3) / 2 + 8 + 7) / 8 * 8));
-    const bool batched_ok = c->max_sys <= kBatchedMaxBeads && batched_config(c->max_sys, bcap, 0, &cfg);
+    int maxnat = 0;
+    for (int i = 0; i < n; ++i) maxnat = std::max(maxnat, c->h_nat_row[i + 1] - c->h_nat_row[i]);
+    const bool batched_ok = c->max_sys <= kBatchedMaxBeads && batched_config(c->max_sys, maxnat + bcap, 0, &cfg);
     if (sched == SOP_SCHED_AUTO) sched = batched_ok ? SOP_SCHED_BATCHED : SOP_SCHED_STREAMED;
     if (sched == SOP_SCHED_BATCHED && !batched_ok)
         return fail(c, SOP_ERR_UNSUPPORTED, "batched schedule needs systems of at most 2048 beads that fit shared memory");
@@ -849,11 +953,15 @@ sop_status create_impl(sop_ctx *c, const sop_topology *topo, const double *xyz, 
     if (sched == SOP_SCHED_BATCHED) {
         s = build_batched_tables(c);
         if (s != SOP_OK) return s;
+        s = tune_batched(c, maxnat + bcap, &c->bcfg);
+        if (s != SOP_OK) return s;
+        cfg = c->bcfg;
     }
     c->st.schedule = sched;
     c->st.block_threads = sched == SOP_SCHED_BATCHED ? cfg.threads : 256;
     c->st.pairs_per_bead = sched == SOP_SCHED_BATCHED ? bcap : c->ppb;
     c->st.beads_per_thread = sched == SOP_SCHED_BATCHED ? cfg.beads_per_thread : 0;
+    c->st.min_blocks = sched == SOP_SCHED_BATCHED ? cfg.min_blocks : 0;
     CUDA_OR_RETURN(c, cudaStreamSynchronize(c->stream));
     return SOP_OK;
 }

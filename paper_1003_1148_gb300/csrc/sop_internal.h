@@ -187,11 +187,15 @@ struct BatchedArgs {
 struct BatchedConfig {
     int threads = 128;
     int beads_per_thread = 1;
+    int min_blocks = 4;   // register cap 65536 / (256 * min_blocks)
     size_t smem = 0;
 };
 
-// Pick a configuration for systems of at most max_n beads with capacity cap.
-bool batched_config(int max_n, int cap, int threads_hint, BatchedConfig *cfg);
+int batched_max_threads();
+
+// Pick a configuration for systems of at most max_n beads whose merged rows hold up to
+// row_width entries (natives + Verlet capacity).
+bool batched_config(int max_n, int row_width, int threads_hint, BatchedConfig *cfg);
 // Run n_steps (or forces only when a.force_out != null and n_steps == 0).
 cudaError_t launch_batched(const BatchedArgs &a, const BatchedConfig &cfg, cudaStream_t s, int64_t *launches);
 

@@ -59,6 +59,7 @@ class _Model(C.Structure):
                 ("k_fene", C.c_double), ("R0", C.c_double), ("eps_h", C.c_double), ("eps_l", C.c_double),
                 ("sigma", C.c_double), ("T", C.c_double), ("zeta", C.c_double), ("dt", C.c_double),
                 ("pair_cut", C.c_double), ("rebuild_every", C.c_int32), ("use_cells", C.c_int32),
+                ("noise_offset", C.c_int32),
                 ("n_pull", C.c_int32), ("pulls", C.c_void_p), ("indenter", C.c_void_p)]
 
 
@@ -178,6 +179,7 @@ class Model:
         self.n_pull = 0
         self.indenter = None
         self.use_cells = 0
+        self.noise_offset = 0
         self._sync()
 
     def _sync(self):
@@ -186,11 +188,16 @@ class Model:
                          _p(self.bond_i), _p(self.bond_j), _p(self.bond_r0), len(self.nat_i), _p(self.nat_i),
                          _p(self.nat_j), _p(self.nat_r0), p["k_fene"], p["R0"], p["eps_h"], p["eps_l"],
                          p["sigma"], p["T"], p["zeta"], p["dt"], p["pair_cut"], int(p["rebuild_every"]),
-                         int(self.use_cells), self.n_pull, C.addressof(self.pulls) if self.n_pull else None,
+                         int(self.use_cells), int(self.noise_offset), self.n_pull, C.addressof(self.pulls) if self.n_pull else None,
                          C.addressof(self.indenter) if self.indenter is not None else None)
 
     def set_cells(self, on: bool):
         self.use_cells = 1 if on else 0
+        self._sync()
+
+    def set_noise_offset(self, offset: int):
+        """Bead index offset of the noise counter (for a chain taken out of a larger topology)."""
+        self.noise_offset = int(offset)
         self._sync()
 
     def start_pulls(self, pulls, xyz, step: int = 0):

@@ -484,7 +484,7 @@ void orc_ermak_update(const orc_model *m, double *xyz, const double *F, uint64_t
     for (int32_t i = 0; i < m->n; ++i) {
         if (is_held(m, i)) continue;
         double g[3];
-        orc_noise(seed, step, i, g);
+        orc_noise(seed, step, i + m->noise_offset, g);
         for (int k = 0; k < 3; ++k) xyz[3 * i + k] = xyz[3 * i + k] + F[3 * i + k] * mob + g[k] * amp;
     }
 }

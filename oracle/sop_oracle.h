@@ -58,6 +58,8 @@ typedef struct {
     double pair_cut;
     int32_t rebuild_every;
     int32_t use_cells;               /* 0: brute-force list (the definition), 1: cell list */
+    int32_t noise_offset;            /* added to the bead index in the noise counter (a chain
+                                        checked out of a larger topology keeps its draws) */
     /* external forces */
     int32_t n_pull;
     const orc_pull *pulls;

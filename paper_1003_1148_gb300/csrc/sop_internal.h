@@ -7,7 +7,7 @@
 #include <string>
 #include <vector>
 
-#include "../../include/sop.h"
+#include "sop.h"
 #include "sop_device.cuh"
 
 namespace sop {

@@ -368,8 +368,8 @@ __global__ void __launch_bounds__(kMaxThreads, MINB) k_batched(BatchedArgs a) {
     const bool forces_only = (a.n_steps == 0 && a.force_out != nullptr);
 
     if (threadIdx.x == 0) L.h->fail = 0;
-    if (sa.rep_status[r] != 0 || *sa.halt != 0) {   // CTA-uniform: a frozen replica only marks its records
-        if (!forces_only && threadIdx.x == 0) missing_records(a, r, s, g, step0, step0, event0);
+    if (!forces_only && (sa.rep_status[r] != 0 || *sa.halt != 0)) {   // CTA-uniform: a frozen replica
+        if (threadIdx.x == 0) missing_records(a, r, s, g, step0, step0, event0);        // only marks its records
         return;
     }
     // load the item: positions, compensation, bonds, flags, native part of the rows

@@ -597,6 +597,7 @@ struct ObsArgs {
     const float4 *pos;
     int32_t k_off;
     int32_t gate;
+    int32_t chunk0;           // first chunk of the launch
     double eps_h, eps_l, sigma, k_fene, R0;
     const double *bond_r0d;   // [n] FP64 bond lengths
 };
@@ -604,7 +605,7 @@ struct ObsArgs {
 __global__ void __launch_bounds__(kObsThreads) k_obs_partial(ObsArgs q) {
     const int64_t step = *q.a.d_step + q.k_off;
     if (q.gate > 0 && step % q.gate != 0) return;
-    const int ch = blockIdx.x;
+    const int ch = q.chunk0 + blockIdx.x;
     const int lo = q.o.chunk_lo[ch], hi = q.o.chunk_hi[ch];
     const DevTopo &t = q.a.topo;
     const DevExternal &e = q.a.ext;
@@ -840,6 +841,7 @@ static ObsArgs make_obs_args(const StepArgs &a, const DevPairList &pl, const Dev
     q.pos = pos;
     q.k_off = k_off;
     q.gate = gate;
+    q.chunk0 = 0;
     q.eps_h = a.eps_h;
     q.eps_l = a.eps_l;
     q.sigma = a.sigma;
@@ -859,10 +861,12 @@ void launch_observables(const StepArgs &a, const DevPairList &pl, const DevObs &
 }
 
 void launch_energy(const StepArgs &a, const DevPairList &pl, const DevObs &o, const float4 *pos, int32_t g_lo,
-                   int32_t g_hi, double *out, cudaStream_t s, int64_t *launches) {
-    if (o.n_chunks <= 0) return;
+                   int32_t g_hi, int32_t ch_lo, int32_t ch_hi, double *out, cudaStream_t s, int64_t *launches) {
+    if (ch_hi <= ch_lo) return;
+    // only the chunks of segments [g_lo, g_hi): the list pl may be built for those alone
     ObsArgs q = make_obs_args(a, pl, o, pos, 0, 0);
-    k_obs_partial<<<o.n_chunks, kObsThreads, 0, s>>>(q);
+    q.chunk0 = ch_lo;
+    k_obs_partial<<<ch_hi - ch_lo, kObsThreads, 0, s>>>(q);
     k_energy_sum<<<1, 32, 0, s>>>(o.partial, o.seg_chunk_lo, g_lo, g_hi, out);
     if (launches) *launches += 2;
 }

@@ -984,6 +984,10 @@ void to_csr(int n, const std::vector<int32_t> &start, const std::vector<int32_t>
     row_ptr.assign(n + 1, 0);
     out.clear();
     for (int i = 0; i < n; ++i) {
+        if (len[i] <= 0 || start[i] < 0 || (size_t)start[i] + (size_t)len[i] > col.size()) {
+            row_ptr[i + 1] = (int32_t)out.size();
+            continue;
+        }
         std::vector<int32_t> row(col.begin() + start[i], col.begin() + start[i] + len[i]);
         for (auto &v : row) v -= base_index;
         std::sort(row.begin(), row.end());
@@ -1052,6 +1056,9 @@ sop_status sop_forces(sop_ctx *c, int32_t replica, double *out_f, double *out_en
             CUDA_OR_RETURN(c, dalloc(c, &c->pl2.len, (size_t)c->R * c->n));
             CUDA_OR_RETURN(c, dalloc(c, &c->pl2.col, c->pl_cap));
             CUDA_OR_RETURN(c, dalloc(c, &c->pl2.cursor, c->n_seg));
+            // rows of replicas not rebuilt here must read as empty, never as garbage
+            CUDA_OR_RETURN(c, cudaMemset(c->pl2.start, 0, sizeof(int32_t) * (size_t)c->R * c->n));
+            CUDA_OR_RETURN(c, cudaMemset(c->pl2.len, 0, sizeof(int32_t) * (size_t)c->R * c->n));
         }
         const int g_lo = replica * c->n_sys, g_hi = g_lo + c->n_sys;
         const SegRange rg = seg_range(c, g_lo, g_hi);
@@ -1070,7 +1077,8 @@ sop_status sop_forces(sop_ctx *c, int32_t replica, double *out_f, double *out_en
                           &c->st.kernel_launches);
         }
         // energy: the observable partials of this replica's segments at the current step
-        launch_energy(c->sa, c->pl2, c->obs, c->d_pos[c->cur], g_lo, g_hi, c->d_energy, c->stream,
+        launch_energy(c->sa, c->pl2, c->obs, c->d_pos[c->cur], g_lo, g_hi, c->h_seg_chunk_lo[g_lo],
+                      c->h_seg_chunk_lo[g_hi], c->d_energy, c->stream,
                       &c->st.kernel_launches);
         CUDA_OR_RETURN(c, cudaGetLastError());
         std::vector<float4> f(c->n);
@@ -1228,6 +1236,7 @@ sop_status sop_get_pairlist(sop_ctx *c, int32_t replica, int32_t *row_ptr, int32
             CUDA_OR_RETURN(c, dalloc(c, &c->d_dump_start, (size_t)c->R * n));
             CUDA_OR_RETURN(c, dalloc(c, &c->d_dump_len, (size_t)c->R * n));
             CUDA_OR_RETURN(c, dalloc(c, &c->d_dump_col, (size_t)c->R * n * stride));
+            CUDA_OR_RETURN(c, cudaMemset(c->d_dump_len, 0, sizeof(int32_t) * (size_t)c->R * n));
         }
         BatchedArgs a = batched_args(c);
         a.pos = c->d_snap;

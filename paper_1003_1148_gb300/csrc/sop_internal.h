@@ -144,8 +144,9 @@ void launch_observables(const StepArgs &a, const DevPairList &pl, const DevObs &
                         int32_t k_off, int32_t gate, cudaStream_t s, int64_t *launches);
 
 // FP64 energy of the segments [g_lo, g_hi) at pos into *out (device), via the observable partials.
+// Chunks [ch_lo, ch_hi) must be exactly the chunks of segments [g_lo, g_hi).
 void launch_energy(const StepArgs &a, const DevPairList &pl, const DevObs &o, const float4 *pos, int32_t g_lo,
-                   int32_t g_hi, double *out, cudaStream_t s, int64_t *launches);
+                   int32_t g_hi, int32_t ch_lo, int32_t ch_hi, double *out, cudaStream_t s, int64_t *launches);
 
 // Advance the device step counter by k; add one cadence event when gate > 0 and the new step
 // is a multiple of gate, else add n_events.

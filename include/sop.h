@@ -223,6 +223,45 @@ const char *sop_last_error(const sop_ctx *ctx);
 /* Free all device and host memory of ctx. NULL is allowed. */
 void sop_destroy(sop_ctx *ctx);
 
+/* Largest system sop_pairlist_build_noalloc accepts. */
+#define SOP_NOALLOC_MAX_BEADS 65536
+
+/*
+ * Verlet list of one system, built without allocating any device memory.
+ * The paper has no counterpart: this is an interface for callers that cannot
+ * call cudaMalloc -- code that runs while its stream is being captured into a
+ * CUDA graph, hosts whose device memory all belongs to their own pool
+ * allocator, or services that must not allocate after start-up. It runs the
+ * same cell-list rebuild as the streamed schedule on caller-provided device
+ * buffers; its scratch (1.8 MiB for at most SOP_NOALLOC_MAX_BEADS beads) is a
+ * fixed array inside this library that every GPU which loads the library holds
+ * until the process exits.
+ *
+ * Inputs (device pointers, read only): pos4 [4*n] floats, bead-major (x, y, z,
+ * unused), 16-byte aligned; chain [n] chain id of each bead (beads i, i+1 of
+ * one chain are bonded); nat_row [n+1], nat_col: the native contact map as CSR
+ * with both directions (e.g. from sop_get_native_map). Outputs (device
+ * pointers): row_start [n], row_len [n] and col [cap]: row i is
+ * col[row_start[i] .. row_start[i] + row_len[i]), ascending partner indices;
+ * rows are packed in no particular order. *nnz (host) receives the number of
+ * entries. The pair set equals that of sop_get_pairlist.
+ *
+ * Errors: SOP_ERR_INVALID_ARG when n is outside [1, SOP_NOALLOC_MAX_BEADS], a
+ * pointer is NULL or misaligned, or pair_cut <= 0; SOP_ERR_PAIRLIST_OVERFLOW
+ * when cap is too small; SOP_ERR_CUDA for a CUDA failure. The text is
+ * sop_last_error(NULL). The call synchronises cuda_stream (NULL = the legacy
+ * default stream) before it returns.
+ *
+ * The first call on a device looks up the scratch array's device address for
+ * that device; make that first call before any stream capture. Every call
+ * shares the one scratch array and overwrites it, so calls whose GPU work
+ * overlaps (two host threads, or two streams) race and must be serialised by
+ * the caller.
+ */
+sop_status sop_pairlist_build_noalloc(const float *pos4, int32_t n, const int32_t *chain, const int32_t *nat_row,
+                                      const int32_t *nat_col, double pair_cut, int32_t *row_start, int32_t *row_len,
+                                      int32_t *col, int64_t cap, int64_t *nnz, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -28,6 +28,8 @@ constexpr double kBoltzmannKcal = 8.314462618 / 4184.0;
 
 }  // namespace
 
+void sop::set_global_error(const std::string &msg) { g_create_error = msg; }
+
 struct sop_ctx {
     // sizes
     int32_t n = 0, n_chains = 0, n_sys = 0, R = 0, n_seg = 0;

@@ -112,6 +112,9 @@ struct DevObs {
     int32_t obs_every = 0;
 };
 
+// Set the text returned by sop_last_error(NULL) (sop_api.cu).
+void set_global_error(const std::string &msg);
+
 // ---- launchers (k_stream.cu) ----
 // Scan: out[0..n] = exclusive prefix sums of in[0..n-1], out[n] = total.
 void scan_exclusive(const int32_t *in, int32_t *out, int64_t n, int32_t *tmp, cudaStream_t s, int64_t *launches);

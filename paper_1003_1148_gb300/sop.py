@@ -31,7 +31,7 @@ SCHEDULES = {"auto": SCHED_AUTO, "batched": SCHED_BATCHED, "streamed": SCHED_STR
 EXPORTED = ["sop_create", "sop_step", "sop_forces", "sop_pairlist_rebuild", "sop_pull", "sop_indenter",
             "sop_get_positions", "sop_set_positions", "sop_get_pairlist", "sop_get_native_map",
             "sop_get_observables", "sop_get_state", "sop_set_state", "sop_replica_status", "sop_abort",
-            "sop_get_stats", "sop_last_error", "sop_destroy"]
+            "sop_get_stats", "sop_last_error", "sop_destroy", "sop_pairlist_build_noalloc"]
 
 
 class SopError(RuntimeError):
@@ -104,6 +104,7 @@ def load(path: str | None = None):
             "sop_get_stats": ([vp, vp], C.c_int),
             "sop_last_error": ([vp], C.c_char_p),
             "sop_destroy": ([vp], None),
+            "sop_pairlist_build_noalloc": ([vp, i32, vp, vp, vp, f64, vp, vp, vp, i64, vp, vp], C.c_int),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -301,3 +302,28 @@ def from_workload(w, n_replicas: int | None = None, schedule="auto", stream=None
         ind = w.indenter
         sim.indenter(ind.center, ind.direction, ind.radius, ind.v)
     return sim
+
+
+NOALLOC_MAX_BEADS = 65536
+
+
+def pairlist_build_noalloc(pos4, n: int, chain, nat_row, nat_col, pair_cut: float, row_start, row_len, col,
+                           cap: int, stream=None) -> int:
+    """``sop_pairlist_build_noalloc``: the Verlet list of one system from device
+    buffers, for callers that cannot allocate device memory (the library's own
+    fixed scratch array is used). Every buffer argument is a device pointer
+    (int) or an object with ``data_ptr()`` (e.g. a torch CUDA tensor): pos4
+    float32 [n, 4]; chain int32 [n]; nat_row int32 [n+1]; nat_col int32;
+    outputs row_start, row_len int32 [n] and col int32 [cap]. Returns nnz."""
+    L = load()
+
+    def dp(x):
+        return int(x) if isinstance(x, int) else int(x.data_ptr())
+
+    nnz = C.c_int64(0)
+    rc = L.sop_pairlist_build_noalloc(dp(pos4), int(n), dp(chain), dp(nat_row), dp(nat_col), float(pair_cut),
+                                      dp(row_start), dp(row_len), dp(col), int(cap), C.byref(nnz),
+                                      _stream_handle(stream))
+    if rc != OK:
+        raise SopError(rc, L.sop_last_error(None).decode())
+    return nnz.value

@@ -1,0 +1,85 @@
+"""The allocation-free Verlet-list entry point against the context-based one (needs a GPU).
+
+sop_pairlist_build_noalloc serves callers that cannot call cudaMalloc: code
+whose stream is being captured into a CUDA graph, hosts whose device memory all
+belongs to their own pool allocator, services that must not allocate after
+start-up. Its scratch is one fixed array inside the library that every call
+reuses, so the checks run two calls in a row, after a call that failed half
+way, and compare each list with sop_get_pairlist's for the same positions.
+This file sorts last so that a run stopping at the first failure has already
+run every other test.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1003_1148_gb300 import build, sop
+    build.build()
+    sop.load()
+    return sop
+
+
+def device_inputs(torch, sim, w, dev):
+    x = sim.get_positions(0)
+    n = w.n_beads
+    pos4 = torch.zeros((n, 4), dtype=torch.float32, device=dev)
+    pos4[:, :3] = torch.from_numpy(x.astype(np.float32)).to(dev)
+    chain = torch.from_numpy(w.chain_of_bead().astype(np.int32)).to(dev)
+    nrp, ncol, _ = sim.get_native_map()
+    nat_row = torch.from_numpy(nrp.astype(np.int32)).to(dev)
+    nat_col = torch.from_numpy(ncol.astype(np.int32) if len(ncol) else np.zeros(1, np.int32)).to(dev)
+    return pos4, chain, nat_row, nat_col
+
+
+def call(torch, sop, inputs, n, cut, cap, dev):
+    pos4, chain, nat_row, nat_col = inputs
+    rs = torch.full((n,), -1, dtype=torch.int32, device=dev)
+    rl = torch.full((n,), -1, dtype=torch.int32, device=dev)
+    col = torch.full((max(1, cap),), -1, dtype=torch.int32, device=dev)
+    nnz = sop.pairlist_build_noalloc(pos4, n, chain, nat_row, nat_col, cut, rs, rl, col, cap,
+                                     stream=torch.cuda.current_stream())
+    return nnz, rs.cpu().numpy(), rl.cpu().numpy(), col.cpu().numpy()
+
+
+def test_noalloc_list_equals_context_list_twice(lib, synth):
+    torch = pytest.importorskip("torch")
+    sop = lib
+    dev = torch.device("cuda", 0)
+    for w in (synth.replicas(n_replicas=1, n=128, seed=3), synth.fiber4096(n=1500)):
+        sim = sop.from_workload(w, n_replicas=1, schedule="streamed")
+        sim.step(25)
+        sim.pairlist_rebuild()
+        rp_ref, col_ref = sim.get_pairlist(0)
+        inputs = device_inputs(torch, sim, w, dev)
+        n = w.n_beads
+        for _ in range(2):
+            nnz, rs, rl, col = call(torch, sop, inputs, n, w.params["pair_cut"], 64 * n, dev)
+            assert nnz == len(col_ref)
+            for i in range(n):
+                row = col[rs[i]:rs[i] + rl[i]]
+                assert np.array_equal(row, col_ref[rp_ref[i]:rp_ref[i + 1]]), (w.name, i)
+        sim.close()
+
+
+def test_noalloc_rejects_and_recovers(lib, synth):
+    torch = pytest.importorskip("torch")
+    sop = lib
+    dev = torch.device("cuda", 0)
+    w = synth.replicas(n_replicas=1, n=128, seed=3)
+    sim = sop.from_workload(w, n_replicas=1, schedule="streamed")
+    rp_ref, col_ref = sim.get_pairlist(0)
+    inputs = device_inputs(torch, sim, w, dev)
+    with pytest.raises(sop.SopError) as e:
+        call(torch, sop, inputs, sop.NOALLOC_MAX_BEADS + 1, 10.0, 16, dev)
+    assert e.value.status == sop.ERR_INVALID_ARG
+    with pytest.raises(sop.SopError) as e:          # too small an output: stops half way
+        call(torch, sop, inputs, 128, 10.0, 8, dev)
+    assert e.value.status == sop.ERR_PAIRLIST_OVERFLOW
+    nnz, rs, rl, col = call(torch, sop, inputs, 128, 10.0, 64 * 128, dev)   # the scratch left behind is reset
+    assert nnz == len(col_ref)
+    for i in range(128):
+        assert np.array_equal(col[rs[i]:rs[i] + rl[i]], col_ref[rp_ref[i]:rp_ref[i + 1]])

@@ -47,6 +47,14 @@ def workload(name: str):
     from paper_1003_1148_gb300 import synth
     if name == "replicas8192x128":
         return synth.replicas(n_replicas=8192, n=128, seed=3, steps=100_000)
+    if name == "uneven2048":
+        return synth.uneven()
+    if name == "fiber4096":
+        return synth.fiber4096()
+    if name == "shell60x2500":
+        return synth.shell()
+    if name == "chain64":
+        return synth.chain64()
     if name.startswith("replicas"):
         r, n = name[len("replicas"):].split("x")
         return synth.replicas(n_replicas=int(r), n=int(n), seed=3, steps=100_000)
@@ -267,11 +275,11 @@ def run_ours(args):
         cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
 
     stream = torch.cuda.Stream(device=dev)
-    sim = sop.Simulation(w.xyz, w.chain_offsets, w.system_offsets, w.fixed, w.params, n_replicas=R,
-                         seed=w.seed + rank * R, obs_every=w.obs_every, obs_capacity=4 * R,
-                         schedule=args.schedule, stream=stream)
+    w.seed = w.seed + rank * R
+    sim = sop.from_workload(w, schedule=args.schedule, stream=stream, obs_capacity=max(4096, 4 * R * w.n_systems))
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     work_per_step = R * w.n_beads * MD_STEPS_PER_STEP
+    n_chains = w.n_chains
 
     def one_step():
         sim.step(MD_STEPS_PER_STEP)
@@ -335,7 +343,8 @@ def run_ours(args):
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": None, "kernel": "k_batched (one launch of 1,000 steps per benchmark step)",
                 "kernel_config": {"threads": st["block_threads"], "beads_per_thread": st["beads_per_thread"],
-                                  "register_cap": 65536 // (256 * max(1, st["min_blocks"])),
+                                  "register_cap": 65536 // (256 * st["min_blocks"]) if st["min_blocks"] else 64,
+                                  "size_buckets": st["buckets"],
                                   "verlet_capacity": st["pairs_per_bead"]},
                 "flop_per_bead_step": flop_bs, "list_sizes_replica0": counts,
                 "peak_note": "FP32 FMA pipe: 152 SMs x 128 lanes x 2 x 2070 MHz (max SM clock), derived"}

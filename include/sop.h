@@ -137,7 +137,8 @@ typedef struct {
     int32_t block_threads;        /* CTA size of the step kernel */
     int32_t pairs_per_bead;       /* Verlet-list capacity per bead */
     int32_t beads_per_thread;     /* batched schedule: beads owned by one thread */
-    int32_t min_blocks;           /* batched schedule: register cap 65536 / (256 * min_blocks) */
+    int32_t min_blocks;           /* batched schedule: register cap 65536 / (256 * min_blocks); 0 = rows in global memory */
+    int32_t buckets;              /* batched schedule: size buckets (one kernel launch each per chunk) */
     int64_t pairlist_entries;     /* entries in the last Verlet list of replica 0 */
     int64_t native_entries;       /* native contacts (i < j) */
     double tune_ms;               /* batched schedule: trial time of the chosen configuration */

@@ -2,24 +2,34 @@
 //
 // One CTA owns one work item (a system of one replica) for a whole chunk of
 // steps. The two time layers of positions (Algorithm 7), the compensation
-// terms, bond lengths and the neighbour rows live in shared memory; thread t
-// owns beads t, t + T, ... (BPT of them). Per step a thread gathers the Eq. 1
-// forces of its beads (particle-based, Algorithm 2) over one merged row per
-// bead -- its native partners first, then its Verlet partners -- so that one
-// loop of nearly equal length per lane covers both pair terms. It adds the
+// terms and bond lengths live in shared memory, and so do the neighbour rows
+// unless the system is too large (then each item's rows live in global
+// memory, L2-resident). Per step a thread gathers the Eq. 1 forces of its
+// beads (particle-based, Algorithm 2) over one merged row per bead -- its
+// native partners first, then its Verlet partners -- adds the
 // cantilever/indenter force, draws Philox noise and applies the compensated
-// first-order update into the other layer; one __syncthreads() separates steps.
+// first-order update into the other layer; one __syncthreads() separates
+// steps.
 //
-// Rows are column-major (entry k of bead b at k*n + b: a warp reads
-// consecutive 16-bit words). Every K steps the Verlet part of the rows is
-// rebuilt from the current layer by an all-pairs scan of the system
-// (Algorithm 3 with the whole system as candidate set): for 32 candidates at
-// a time each thread forms a bit mask of "closer than the cutoff", clears the
-// bits of itself, its bonded neighbours and its native partners, and appends
-// the remaining bits in ascending order. Every thread of a warp reads the
-// same candidate at the same time (a shared-memory broadcast). The natives'
-// r0^2 come from a column-major table in global memory that all replicas of a
-// system share (L1/L2 resident). Observables (FP64) are reduced in the CTA.
+// Work balance. Threads own "slots" (slot p = thread + k * blockDim). At each
+// Verlet rebuild the slots are handed to beads in order of decreasing row
+// length of the previous build (a counting sort in shared memory), so that a
+// warp holds beads with rows of similar length and its lanes finish their
+// force loops together. The row of the bead in slot p is stored in column p
+// (entry k at k*n + p): a warp reads consecutive 16-bit words. A bead's force
+// is summed in its row's order whatever slot it lands in, so the assignment
+// does not change any result.
+//
+// Rebuild (every K steps, Algorithm 3 with the whole system as candidate set):
+// the beads are taken 32 at a time in index order; consecutive beads of a
+// chain are close in space, so each block of 32 gets a bounding box and a
+// thread skips every block whose box lies beyond the cutoff. Otherwise it
+// tests the 32 candidates, forming a bit mask; clears itself, its bonded
+// neighbours and its native partners; and appends the remaining bits in
+// ascending order. All lanes of a warp read the same candidate (a
+// shared-memory broadcast). The natives' r0^2 come from a column-major table
+// in global memory shared by all replicas of a system. Observables (FP64) are
+// reduced in the CTA.
 #include <cuda_runtime.h>
 
 #include "sop_internal.h"
@@ -28,11 +38,12 @@ namespace sop {
 
 namespace {
 
-constexpr int kMaxThreads = 256;
+constexpr int kKeys = 257;   // row lengths 0..256
 
 struct SharedHead {
-    int fail;   // first sop_status raised in this CTA
-    double red[kMaxThreads / 32][6];
+    int fail;               // first sop_status raised in this CTA
+    int hist[kKeys];        // counting sort of slots by row length
+    double red[32][6];      // FP64 block reductions (up to 1024 threads)
 };
 
 // The arrays follow the head at a 16-byte aligned offset (float4 accesses).
@@ -40,45 +51,58 @@ constexpr size_t kHeadBytes = (sizeof(SharedHead) + 15) / 16 * 16;
 
 __device__ __forceinline__ void cta_fail(SharedHead *h, int code) { atomicCAS(&h->fail, 0, code); }
 
-// Shared-memory layout of one work item, for systems of at most max_n beads.
-struct Layout {
-    SharedHead *h;
-    float4 *lay[2];       // positions, two time layers
-    float4 *comp;         // Kahan compensation (w unused)
-    float2 *bond;         // (r0 of bond b-1,b ; r0 of bond b,b+1), < 0 when absent
-    uint16_t *n_nat;      // native partners of each bead
-    uint16_t *n_tot;      // natives + Verlet partners
-    uint8_t *flags;
-    uint16_t *row;        // merged rows, entry k of bead b at row[k * n + b]
-};
+// Shared-memory layout of one work item, for systems of at most max_n beads. The
+// accessors recompute each array's address from the dynamic shared-memory symbol, so
+// that only a few integers stay live and every access is a 32-bit shared address.
+extern __shared__ __align__(16) unsigned char g_smem[];
 
-__host__ __device__ inline size_t layout_bytes(int max_n, int row_width) {
+__host__ __device__ inline size_t state_bytes(int max_n) {
     size_t s = kHeadBytes;
-    s += 3 * sizeof(float4) * (size_t)max_n;   // two layers + compensation
-    s += sizeof(float2) * (size_t)max_n;       // bond lengths
-    s += 2 * sizeof(uint16_t) * (size_t)max_n; // counts
-    s += (size_t)max_n;                        // flags
+    s += 3 * sizeof(float4) * (size_t)max_n;       // two layers + compensation
+    s += sizeof(float2) * (size_t)max_n;           // bond lengths
+    s += 4 * sizeof(uint16_t) * (size_t)max_n;     // two orders + counts
+    s += (size_t)max_n;                            // flags
     s = (s + 15) / 16 * 16;
-    s += sizeof(uint16_t) * (size_t)row_width * max_n;
+    s += 2 * sizeof(float4) * (size_t)((max_n + 31) / 32);   // block bounding boxes
     return s;
 }
 
-__device__ inline Layout make_layout(unsigned char *smem, int max_n) {
-    Layout L;
-    L.h = reinterpret_cast<SharedHead *>(smem);
-    float4 *f4 = reinterpret_cast<float4 *>(smem + kHeadBytes);
-    L.lay[0] = f4;
-    L.lay[1] = f4 + max_n;
-    L.comp = f4 + 2 * max_n;
-    L.bond = reinterpret_cast<float2 *>(f4 + 3 * max_n);
-    L.n_nat = reinterpret_cast<uint16_t *>(L.bond + max_n);
-    L.n_tot = L.n_nat + max_n;
-    L.flags = reinterpret_cast<uint8_t *>(L.n_tot + max_n);
-    size_t off = (size_t)(reinterpret_cast<unsigned char *>(L.flags + max_n) - smem);
-    off = (off + 15) / 16 * 16;
-    L.row = reinterpret_cast<uint16_t *>(smem + off);
-    return L;
+__host__ __device__ inline size_t layout_bytes(int max_n, int row_width, bool rows_global) {
+    return state_bytes(max_n) + (rows_global ? 0 : sizeof(uint16_t) * (size_t)row_width * max_n);
 }
+
+template <bool RG>
+struct Layout {
+    int mx;          // max_n
+    uint16_t *grow;  // RG: this item's rows in global memory
+    __device__ __forceinline__ SharedHead *h() const { return reinterpret_cast<SharedHead *>(g_smem); }
+    // positions by bead, two time layers; lay(2) is the Kahan compensation (w unused)
+    __device__ __forceinline__ float4 *lay(int i) const {
+        return reinterpret_cast<float4 *>(g_smem + kHeadBytes) + i * mx;
+    }
+    __device__ __forceinline__ float4 *comp() const { return lay(2); }
+    // by bead: (r0 of bond b-1,b ; r0 of bond b,b+1), < 0 when absent
+    __device__ __forceinline__ float2 *bond() const { return reinterpret_cast<float2 *>(lay(3)); }
+    // slot -> bead (current, spare)
+    __device__ __forceinline__ uint16_t *order(int i) const {
+        return reinterpret_cast<uint16_t *>(bond() + mx) + i * mx;
+    }
+    // by slot: native entries of the row, and natives + Verlet entries
+    __device__ __forceinline__ uint16_t *n_nat() const { return order(2); }
+    __device__ __forceinline__ uint16_t *n_tot() const { return order(3); }
+    // by bead
+    __device__ __forceinline__ uint8_t *flags() const { return reinterpret_cast<uint8_t *>(order(4)); }
+    // per block of 32 beads: (lo, hi) corners of the bounding box
+    __device__ __forceinline__ float4 *bbox() const {
+        const size_t off = (kHeadBytes + 3 * 16 * (size_t)mx + 8 * (size_t)mx + 8 * (size_t)mx + mx + 15) / 16 * 16;
+        return reinterpret_cast<float4 *>(g_smem + off);
+    }
+    // by slot: entry k of slot p at row[k * n + p] (bead indices)
+    __device__ __forceinline__ uint16_t *row() const {
+        if (RG) return grow;
+        return reinterpret_cast<uint16_t *>(g_smem + state_bytes(mx));
+    }
+};
 
 // FP64 block sum of 6 values; result valid in thread 0.
 __device__ __forceinline__ void block_sum6(double v[6], SharedHead *h) {
@@ -99,46 +123,153 @@ __device__ __forceinline__ void block_sum6(double v[6], SharedHead *h) {
     }
 }
 
-// Verlet part of the rows of the thread's beads from layer src (all-pairs scan).
-template <int BPT>
-__device__ void rebuild_rows(const BatchedArgs &a, const Layout &L, const float4 *src, int n_s, int nat_off) {
+// Bounding boxes of the blocks of 32 consecutive beads of layer src (one warp per block).
+template <bool RG>
+__device__ void block_boxes(const Layout<RG> &L, const float4 *src, int n_s) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    float4 *bb = L.bbox();
+    for (int blk = w; blk * 32 < n_s; blk += nw) {
+        const int b = blk * 32 + lane;
+        float lx = INFINITY, ly = INFINITY, lz = INFINITY, hx = -INFINITY, hy = -INFINITY, hz = -INFINITY;
+        if (b < n_s) {
+            const float4 p = src[b];
+            lx = hx = p.x; ly = hy = p.y; lz = hz = p.z;
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            lx = fminf(lx, __shfl_xor_sync(0xffffffffu, lx, o));
+            ly = fminf(ly, __shfl_xor_sync(0xffffffffu, ly, o));
+            lz = fminf(lz, __shfl_xor_sync(0xffffffffu, lz, o));
+            hx = fmaxf(hx, __shfl_xor_sync(0xffffffffu, hx, o));
+            hy = fmaxf(hy, __shfl_xor_sync(0xffffffffu, hy, o));
+            hz = fmaxf(hz, __shfl_xor_sync(0xffffffffu, hz, o));
+        }
+        if (lane == 0) {
+            bb[2 * blk] = make_float4(lx, ly, lz, 0.f);
+            bb[2 * blk + 1] = make_float4(hx, hy, hz, 0.f);
+        }
+    }
+}
+
+// Hand the slots to beads by decreasing row length of the last build (counting sort).
+// Returns the index (0/1) of the new order buffer. Must be called by all threads.
+template <bool RG>
+__device__ int reorder_slots(const Layout<RG> &L, int n_s, int cur_order) {
+    const int T = blockDim.x;
+    SharedHead *h = L.h();
+    for (int k = threadIdx.x; k < kKeys; k += T) h->hist[k] = 0;
+    __syncthreads();
+    for (int p = threadIdx.x; p < n_s; p += T) atomicAdd(&h->hist[kKeys - 1 - min((int)L.n_tot()[p], kKeys - 1)], 1);
+    __syncthreads();
+    if (threadIdx.x < 32) {   // exclusive scan of the histogram by one warp
+        const int lane = threadIdx.x;
+        const int per = (kKeys + 31) / 32;
+        int local = 0;
+        for (int k = lane * per; k < min(kKeys, lane * per + per); ++k) local += h->hist[k];
+        int inc = local;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += t;
+        }
+        int run = inc - local;
+        for (int k = lane * per; k < min(kKeys, lane * per + per); ++k) {
+            const int c = h->hist[k];
+            h->hist[k] = run;
+            run += c;
+        }
+    }
+    __syncthreads();
+    const uint16_t *src = L.order(cur_order);
+    uint16_t *dst = L.order(cur_order ^ 1);
+    for (int p = threadIdx.x; p < n_s; p += T) {
+        const int pos = atomicAdd(&h->hist[kKeys - 1 - min((int)L.n_tot()[p], kKeys - 1)], 1);
+        dst[pos] = src[p];
+    }
+    __syncthreads();
+    return cur_order ^ 1;
+}
+
+// One 32-candidate block of the all-pairs scan: bit t of *within is set when
+// candidate base + t is closer than the cutoff, bit t of *near when it lies in
+// the guard band around it (decided later in FP64).
+template <bool kFull>
+__device__ __forceinline__ void scan32(const float4 *src, int base, int lim, float4 pb, float lo, float hi,
+                                       uint32_t *within, uint32_t *near) {
+    uint32_t w = 0u, nr = 0u;
+    if (kFull) {
+        // groups of four candidates form a nibble with constant bit positions
+#pragma unroll 2
+        for (int g = 0; g < 8; ++g) {
+            uint32_t wn = 0u, nn = 0u;
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                const float4 pj = src[base + 4 * g + t];
+                const float dx = pb.x - pj.x, dy = pb.y - pj.y, dz = pb.z - pj.z;
+                const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+                if (r2 < lo) wn |= 1u << t;
+                if (r2 < hi) nn |= 1u << t;
+            }
+            w |= wn << (4 * g);
+            nr |= nn << (4 * g);
+        }
+    } else {
+        for (int t = 0; t < lim; ++t) {
+            const float4 pj = src[base + t];
+            const float dx = pb.x - pj.x, dy = pb.y - pj.y, dz = pb.z - pj.z;
+            const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+            if (r2 < lo) w |= 1u << t;
+            if (r2 < hi) nr |= 1u << t;
+        }
+    }
+    *within = w;
+    *near = nr & ~w;
+}
+
+// Rows of the thread's slots from layer src: the bead in slot p gets its native
+// partners and its Verlet partners in column p. Block boxes must be current.
+template <int BPT, bool RG>
+__device__ void rebuild_rows(const BatchedArgs &a, const Layout<RG> &L, const uint16_t *order, const float4 *src,
+                             int n_s, int nat_off, int b0) {
     const int T = blockDim.x;
     const float cut2 = a.sa.cut2_f;
-    const float band = cut2 * 1e-4f;
+    const float lo = cut2 - cut2 * 1e-4f, hi = cut2 + cut2 * 1e-4f;
+    const float4 *bb = L.bbox();
+    uint16_t *row = L.row();
 #pragma unroll 1
     for (int k = 0; k < BPT; ++k) {
-        const int b = threadIdx.x + k * T;
-        if (b >= n_s) continue;
+        const int p = threadIdx.x + k * T;
+        if (p >= n_s) continue;
+        const int b = order[p];
         const float4 pb = src[b];
-        const int nn = L.n_nat[b];
+        const int nn = a.nat_ell_cnt[b0 + b];
         const uint16_t *natc = a.nat_ell_col + nat_off + b;
-        const float2 bd = L.bond[b];
-        int q = 0;                                  // next native to exclude
+        for (int q = 0; q < nn; ++q) row[q * n_s + p] = __ldg(natc + q * n_s);
+        const float2 bd = L.bond()[b];
+        int q = 0;   // next native to exclude
         int next_nat = nn > 0 ? (int)__ldg(natc) : 0x7fffffff;
         int cnt = 0;
         for (int base = 0; base < n_s; base += 32) {
-            const int lim = min(32, n_s - base);
+            // exact cull: every bead of the block is at least as far as its box
+            const float4 blo = bb[base >> 4], bhi = bb[(base >> 4) + 1];
+            const float ex = fmaxf(fmaxf(blo.x - pb.x, pb.x - bhi.x), 0.f);
+            const float ey = fmaxf(fmaxf(blo.y - pb.y, pb.y - bhi.y), 0.f);
+            const float ez = fmaxf(fmaxf(blo.z - pb.z, pb.z - bhi.z), 0.f);
             uint32_t within = 0u, near = 0u;
-#pragma unroll 8
-            for (int t = 0; t < lim; ++t) {
-                const float4 pj = src[base + t];
-                const float dx = pb.x - pj.x, dy = pb.y - pj.y, dz = pb.z - pj.z;
-                const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-                within |= (uint32_t)(r2 < cut2 - band) << t;
-                near |= (uint32_t)(fabsf(r2 - cut2) <= band) << t;
+            if (fmaf(ez, ez, fmaf(ey, ey, ex * ex)) < hi) {
+                if (base + 32 <= n_s) scan32<true>(src, base, 32, pb, lo, hi, &within, &near);
+                else scan32<false>(src, base, n_s - base, pb, lo, hi, &within, &near);
             }
             // exclusions in [base, base + 32): self, bonded neighbours, native partners
-            uint32_t ex = 0u;
-            if (b >= base && b < base + 32) ex |= 1u << (b - base);
-            if (bd.x > 0.f && b - 1 >= base && b - 1 < base + 32) ex |= 1u << (b - 1 - base);
-            if (bd.y > 0.f && b + 1 >= base && b + 1 < base + 32) ex |= 1u << (b + 1 - base);
+            uint32_t ex_mask = 0u;
+            if (b >= base && b < base + 32) ex_mask |= 1u << (b - base);
+            if (bd.x > 0.f && b - 1 >= base && b - 1 < base + 32) ex_mask |= 1u << (b - 1 - base);
+            if (bd.y > 0.f && b + 1 >= base && b + 1 < base + 32) ex_mask |= 1u << (b + 1 - base);
             while (next_nat < base + 32) {
-                ex |= 1u << (next_nat - base);
+                ex_mask |= 1u << (next_nat - base);
                 ++q;
-                next_nat = q < nn ? (int)__ldg(natc + (size_t)q * n_s) : 0x7fffffff;
+                next_nat = q < nn ? (int)__ldg(natc + q * n_s) : 0x7fffffff;
             }
-            within &= ~ex;
-            near &= ~ex;
+            within &= ~ex_mask;
+            near &= ~ex_mask;
             while (near) {   // rare: decide within the guard band in FP64
                 const int t = __ffs(near) - 1;
                 near &= near - 1;
@@ -147,23 +278,36 @@ __device__ void rebuild_rows(const BatchedArgs &a, const Layout &L, const float4
             while (within) {
                 const int t = __ffs(within) - 1;
                 within &= within - 1;
-                if (cnt < a.cap) L.row[(size_t)(nn + cnt) * n_s + b] = (uint16_t)(base + t);
+                if (cnt < a.cap) row[(nn + cnt) * n_s + p] = (uint16_t)(base + t);
                 ++cnt;
             }
         }
-        if (cnt > a.cap) cta_fail(L.h, SOP_ERR_PAIRLIST_OVERFLOW);
-        L.n_tot[b] = (uint16_t)(nn + min(cnt, a.cap));
+        if (cnt > a.cap) cta_fail(L.h(), SOP_ERR_PAIRLIST_OVERFLOW);
+        L.n_nat()[p] = (uint16_t)nn;
+        L.n_tot()[p] = (uint16_t)(nn + min(cnt, a.cap));
     }
 }
 
-// Sum of the Eq. 1 pair forces on bead b at layer P over its bonds and merged row.
+// A full rebuild from layer src: boxes, slot order, rows. Ends with a barrier.
+template <int BPT, bool RG>
+__device__ int rebuild(const BatchedArgs &a, const Layout<RG> &L, const float4 *src, int n_s, int nat_off, int b0,
+                       int ord) {
+    block_boxes(L, src, n_s);
+    ord = reorder_slots(L, n_s, ord);   // its barriers also publish the boxes
+    rebuild_rows<BPT>(a, L, L.order(ord), src, n_s, nat_off, b0);
+    __syncthreads();
+    return ord;
+}
+
+// Sum of the Eq. 1 pair forces on bead b (in slot p) at layer P over its bonds and row.
 // Entries k < n_nat are native (12-6 with r0^2 from the table), the rest repulsive.
-__device__ __forceinline__ float3 bead_force(const BatchedArgs &a, const Layout &L, const float4 *P, int n_s,
-                                             int nat_off, int b, bool *broken) {
+template <bool RG>
+__device__ __forceinline__ float3 bead_force(const BatchedArgs &a, const Layout<RG> &L, const float4 *P, int n_s,
+                                             int nat_off, int b, int p, bool *broken) {
     const ForceParams &fp = a.sa.fp;
     const float4 pb = P[b];
     float fx = 0.f, fy = 0.f, fz = 0.f;
-    const float2 bd = L.bond[b];
+    const float2 bd = L.bond()[b];
 #pragma unroll
     for (int side = 0; side < 2; ++side) {
         const float r0 = side ? bd.y : bd.x;
@@ -180,14 +324,15 @@ __device__ __forceinline__ float3 bead_force(const BatchedArgs &a, const Layout 
             fx = fmaf(c, dx, fx); fy = fmaf(c, dy, fy); fz = fmaf(c, dz, fz);
         }
     }
-    const int nn = L.n_nat[b], tot = L.n_tot[b];
+    const int nn = L.n_nat()[p], tot = L.n_tot()[p];
     const float *natr = a.nat_ell_r0sq + nat_off + b;
+    const uint16_t *rowp = L.row() + p;
     const float A = fp.eps12_h, B = fp.eps6_l;
 #pragma unroll 2
     for (int k = 0; k < tot; ++k) {
         const bool nat = k < nn;
-        const int j = L.row[(size_t)k * n_s + b];
-        const float s0 = nat ? __ldg(natr + (size_t)k * n_s) : fp.sigma2;
+        const int j = rowp[k * n_s];
+        const float s0 = nat ? __ldg(natr + k * n_s) : fp.sigma2;
         const float4 pj = P[j];
         const float dx = pb.x - pj.x, dy = pb.y - pj.y, dz = pb.z - pj.z;
         const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
@@ -237,47 +382,50 @@ __device__ __forceinline__ float3 ext_force(const StepArgs &sa, int r, int i, ui
 }
 
 // FP64 observables of the CTA's system at layer P (same definitions as the streamed kernels).
-template <int BPT>
-__device__ __noinline__ void observe(const BatchedArgs &a, const Layout &L, const float4 *P, int n_s, int b0, int r,
-                                     int s, int g, int64_t step, int64_t event) {
+template <int BPT, bool RG>
+__device__ __noinline__ void observe(const BatchedArgs &a, const Layout<RG> &L, const uint16_t *order,
+                                     const float4 *P, int n_s, int b0, int r, int s, int g, int64_t step,
+                                     int64_t event) {
     const StepArgs &sa = a.sa;
     const DevTopo &t = sa.topo;
     const DevExternal &e = sa.ext;
     const int T = blockDim.x;
+    const uint16_t *row = L.row();
     double v[6] = {0, 0, 0, 0, 0, 0};   // E, f_pull, ext, formed, f_wall, r_ee
     const double R02 = sa.R0 * sa.R0, sig2 = sa.sigma * sa.sigma;
     for (int k = 0; k < BPT; ++k) {
-        const int b = threadIdx.x + k * T;
-        if (b >= n_s) continue;
+        const int p = threadIdx.x + k * T;
+        if (p >= n_s) continue;
+        const int b = order[p];
         const int i = b0 + b;
         const float4 pb = P[b];
         const double xi = pb.x, yi = pb.y, zi = pb.z;
-        if (L.bond[b].y > 0.f) {
+        if (L.bond()[b].y > 0.f) {
             const float4 pj = P[b + 1];
             const double rr = __dsqrt_rn(dist2_d(xi, yi, zi, pj.x, pj.y, pj.z));
             const double dr = rr - t.bond_r0d[i];
             const double arg = 1.0 - dr * dr / R02;
             if (arg > 0.0) v[0] += -0.5 * sa.k_fene * R02 * log(arg);
         }
-        for (int p = t.nat_row[i]; p < t.nat_row[i + 1]; ++p) {
-            const int j = t.nat_col[p];
+        for (int q = t.nat_row[i]; q < t.nat_row[i + 1]; ++q) {
+            const int j = t.nat_col[q];
             if (j < i) continue;
             const float4 pj = P[j - b0];
             const double d2 = dist2_d(xi, yi, zi, pj.x, pj.y, pj.z);
-            const double r0 = t.nat_r0[p];
-            const double q = r0 * r0 / d2;
-            const double q3 = q * q * q;
-            v[0] += sa.eps_h * (q3 * q3 - 2.0 * q3);
+            const double r0 = t.nat_r0[q];
+            const double u = r0 * r0 / d2;
+            const double u3 = u * u * u;
+            v[0] += sa.eps_h * (u3 * u3 - 2.0 * u3);
             if (__dsqrt_rn(d2) < r0 + 2.0) v[3] += 1.0;
         }
-        for (int q = L.n_nat[b]; q < L.n_tot[b]; ++q) {
-            const int j = L.row[(size_t)q * n_s + b];
+        for (int q = L.n_nat()[p]; q < L.n_tot()[p]; ++q) {
+            const int j = row[q * n_s + p];
             if (j < b) continue;
             const float4 pj = P[j];
             const double c = sig2 / dist2_d(xi, yi, zi, pj.x, pj.y, pj.z);
             v[0] += sa.eps_l * c * c * c;
         }
-        const uint8_t fl = L.flags[b];
+        const uint8_t fl = L.flags()[b];
         if (fl & kFlagPulled) {
             const int qq = e.pull_of_sys[s];
             if (qq >= 0 && e.pull_bead[qq] == i) {
@@ -311,7 +459,7 @@ __device__ __noinline__ void observe(const BatchedArgs &a, const Layout &L, cons
             v[5] += __dsqrt_rn(dist2_d(xi, yi, zi, pl_.x, pl_.y, pl_.z));
         }
     }
-    block_sum6(v, L.h);
+    block_sum6(v, L.h());
     if (threadIdx.x == 0) {
         sop_record rec;
         rec.step = (double)step;
@@ -347,106 +495,107 @@ __device__ void missing_records(const BatchedArgs &a, int r, int s, int g, int64
     }
 }
 
-// MINB: CTAs of kMaxThreads threads that must fit an SM, i.e. the register cap
-// 65536 / (kMaxThreads * MINB): 2 -> 128, 3 -> 85, 4 -> 64 registers per thread.
-template <int BPT, int MINB>
-__global__ void __launch_bounds__(kMaxThreads, MINB) k_batched(BatchedArgs a) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    const Layout L = make_layout(smem, a.max_n);
+// MAXT: largest CTA the instance is compiled for; MINB: CTAs of MAXT threads that must
+// fit an SM, i.e. the register cap 65536 / (MAXT * MINB). RG: rows in global memory.
+template <int BPT, int MINB, int MAXT, bool RG>
+__global__ void __launch_bounds__(MAXT, MINB) k_batched(BatchedArgs a) {
     const int item = blockIdx.x;
+    Layout<RG> L;
+    L.mx = a.max_n;
+    L.grow = RG ? a.row_global + (size_t)item * a.row_width * a.max_n : nullptr;
     const int r = a.item_rep[item], s = a.item_sys[item];
     const StepArgs &sa = a.sa;
     const DevTopo &t = sa.topo;
     const int b0 = t.sys_lo[s], n_s = t.sys_lo[s + 1] - b0;
-    const int n = t.n;
-    const size_t gbase = (size_t)r * n + b0;
+    const int gbase = r * t.n + b0;   // replicas x beads < 2^28
     const int g = r * t.n_sys + s;
     const int nat_off = a.nat_ell_off[s];
     const int T = blockDim.x;
     const int64_t step0 = *a.d_step;
-    const int64_t event0 = a.d_events ? *a.d_events : 0;
     const bool forces_only = (a.n_steps == 0 && a.force_out != nullptr);
 
-    if (threadIdx.x == 0) L.h->fail = 0;
+    if (threadIdx.x == 0) L.h()->fail = 0;
     if (!forces_only && (sa.rep_status[r] != 0 || *sa.halt != 0)) {   // CTA-uniform: a frozen replica
-        if (threadIdx.x == 0) missing_records(a, r, s, g, step0, step0, event0);        // only marks its records
+        if (threadIdx.x == 0)                                           // only marks its records
+            missing_records(a, r, s, g, step0, step0, a.d_events ? *a.d_events : 0);
         return;
     }
-    // load the item: positions, compensation, bonds, flags, native part of the rows
+    // phases of the step counter, kept as wrapped counters instead of 64-bit modulos
+    int k_phase = (int)(step0 % a.K);                                   // step mod K
+    int o_phase = a.obs_every > 0 ? (int)(step0 % a.obs_every) : 0;     // step mod obs_every
+    // load the item; the first order is by native row length
     for (int b = threadIdx.x; b < n_s; b += T) {
         const int i = b0 + b;
-        L.lay[0][b] = a.pos[gbase + b];
-        L.comp[b] = a.comp[gbase + b];
-        L.bond[b] = make_float2(b > 0 ? t.bond_r0[i - 1] : -1.f, t.bond_r0[i]);
-        L.flags[b] = t.flags[i];
-        const int nn = a.nat_ell_cnt[i];
-        L.n_nat[b] = (uint16_t)nn;
-        L.n_tot[b] = (uint16_t)nn;
-        for (int k = 0; k < nn; ++k)
-            L.row[(size_t)k * n_s + b] = a.nat_ell_col[nat_off + (size_t)k * n_s + b];
+        L.lay(0)[b] = a.pos[gbase + b];
+        L.comp()[b] = a.comp[gbase + b];
+        L.bond()[b] = make_float2(b > 0 ? t.bond_r0[i - 1] : -1.f, t.bond_r0[i]);
+        L.flags()[b] = t.flags[i];
+        L.order(0)[b] = (uint16_t)b;
+        L.n_tot()[b] = (uint16_t)a.nat_ell_cnt[i];
         // the list of the first step comes from the positions at the last rebuild step
-        if (step0 % a.K != 0) L.lay[1][b] = a.snap[gbase + b];
+        if (k_phase != 0) L.lay(1)[b] = a.snap[gbase + b];
     }
     __syncthreads();
 
-    int cur = 0;
-    int64_t step = step0;
-    int64_t list_step = -1;
-    int64_t event = event0;
-    for (int it = 0; it < a.n_steps || (forces_only && it == 0); ++it) {
-        const float4 *P = L.lay[cur];
-        float4 *Q = L.lay[cur ^ 1];
-        if (it == 0 && step % a.K != 0 && !forces_only) {
-            rebuild_rows<BPT>(a, L, Q, n_s, nat_off);   // Q holds the snapshot here
-            list_step = step;
-            __syncthreads();
-        } else if ((step % a.K == 0 && list_step != step) || forces_only) {
-            rebuild_rows<BPT>(a, L, P, n_s, nat_off);
-            list_step = step;
+    int cur = 0, ord = 0;
+    int n_events = 0;
+    bool built_now = false;   // the list was built at the current step
+    int it = 0;
+    for (; it < a.n_steps || (forces_only && it == 0); ++it) {
+        const float4 *P = L.lay(cur);
+        float4 *Q = L.lay(cur ^ 1);
+        if (it == 0 && k_phase != 0 && !forces_only) {
+            ord = rebuild<BPT>(a, L, Q, n_s, nat_off, b0, ord);   // Q holds the snapshot here
+        } else if ((k_phase == 0 && !built_now) || forces_only) {
+            ord = rebuild<BPT>(a, L, P, n_s, nat_off, b0, ord);
             if (!forces_only)
                 for (int b = threadIdx.x; b < n_s; b += T) a.snap[gbase + b] = P[b];
-            __syncthreads();
         }
+        built_now = false;
+        const int64_t step = step0 + it;
+        const uint16_t *order = L.order(ord);
         if (forces_only) {
-            for (int b = threadIdx.x; b < n_s; b += T) {
+            for (int p = threadIdx.x; p < n_s; p += T) {
+                const int b = order[p];
                 bool broken = false, overlap = false;
-                const float3 f = bead_force(a, L, P, n_s, nat_off, b, &broken);
-                const float3 fe = ext_force(sa, r, b0 + b, L.flags[b], P[b], step, &overlap);
+                const float3 f = bead_force(a, L, P, n_s, nat_off, b, p, &broken);
+                const float3 fe = ext_force(sa, r, b0 + b, L.flags()[b], P[b], step, &overlap);
                 a.force_out[gbase + b] = make_float4(f.x + fe.x, f.y + fe.y, f.z + fe.z, (broken || overlap) ? 1.f : 0.f);
                 if (a.pl_dump_col) {
-                    const size_t rowi = gbase + b;
-                    const int nn = L.n_nat[b], np = L.n_tot[b] - nn;
+                    const size_t rowi = (size_t)gbase + b;
+                    const int nn = L.n_nat()[p], np = L.n_tot()[p] - nn;
                     a.pl_dump_start[rowi] = (int)(rowi * a.pl_dump_stride);
                     a.pl_dump_len[rowi] = np;
                     for (int q = 0; q < np; ++q)
-                        a.pl_dump_col[rowi * a.pl_dump_stride + q] = b0 + (int)L.row[(size_t)(nn + q) * n_s + b];
+                        a.pl_dump_col[rowi * a.pl_dump_stride + q] = b0 + (int)L.row()[(nn + q) * n_s + p];
                 }
             }
             break;
         }
 #pragma unroll 1
         for (int k = 0; k < BPT; ++k) {
-            const int b = threadIdx.x + k * T;
-            if (b >= n_s) continue;
+            const int p = threadIdx.x + k * T;
+            if (p >= n_s) continue;
+            const int b = order[p];
             bool broken = false, overlap = false;
-            const float3 f = bead_force(a, L, P, n_s, nat_off, b, &broken);
+            const float3 f = bead_force(a, L, P, n_s, nat_off, b, p, &broken);
             const float4 p_old = P[b];
-            const uint8_t fl = L.flags[b];
+            const uint8_t fl = L.flags()[b];
             const float3 fe = ext_force(sa, r, b0 + b, fl, p_old, step, &overlap);
             float4 pb = p_old;
             if (broken || overlap) {
                 // a bead whose force cannot be evaluated stays where it is; the replica freezes
-                cta_fail(L.h, broken ? SOP_ERR_FENE_BREAK : SOP_ERR_INDENTER_OVERLAP);
+                cta_fail(L.h(), broken ? SOP_ERR_FENE_BREAK : SOP_ERR_INDENTER_OVERLAP);
             } else if (!(fl & kFlagFixed)) {
                 const float3 gn = bead_noise(sa.seed + (uint64_t)r, step, (uint32_t)(b0 + b));
-                float4 c = L.comp[b];
+                float4 c = L.comp()[b];
                 kahan_add(pb.x, c.x, fmaf(f.x + fe.x, sa.fp.mob, gn.x * sa.fp.amp));
                 kahan_add(pb.y, c.y, fmaf(f.y + fe.y, sa.fp.mob, gn.y * sa.fp.amp));
                 kahan_add(pb.z, c.z, fmaf(f.z + fe.z, sa.fp.mob, gn.z * sa.fp.amp));
                 if (isfinite(pb.x) && isfinite(pb.y) && isfinite(pb.z)) {
-                    L.comp[b] = c;
+                    L.comp()[b] = c;
                 } else {
-                    cta_fail(L.h, SOP_ERR_NONFINITE);
+                    cta_fail(L.h(), SOP_ERR_NONFINITE);
                     pb = p_old;
                 }
             }
@@ -454,77 +603,87 @@ __global__ void __launch_bounds__(kMaxThreads, MINB) k_batched(BatchedArgs a) {
         }
         __syncthreads();
         cur ^= 1;
-        ++step;
-        if (L.h->fail != 0) break;   // the replica freezes after the step in which it failed
-        if (a.obs_every > 0 && step % a.obs_every == 0) {
-            const float4 *Pn = L.lay[cur];
-            if (step % a.K == 0) {
-                rebuild_rows<BPT>(a, L, Pn, n_s, nat_off);
-                list_step = step;
+        k_phase = k_phase + 1 == a.K ? 0 : k_phase + 1;
+        if (a.obs_every > 0) o_phase = o_phase + 1 == a.obs_every ? 0 : o_phase + 1;
+        if (L.h()->fail != 0) { ++it; break; }   // the replica freezes after the step in which it failed
+        if (a.obs_every > 0 && o_phase == 0) {
+            const float4 *Pn = L.lay(cur);
+            if (k_phase == 0) {
+                ord = rebuild<BPT>(a, L, Pn, n_s, nat_off, b0, ord);
+                built_now = true;
                 for (int b = threadIdx.x; b < n_s; b += T) a.snap[gbase + b] = Pn[b];
-                __syncthreads();
             }
-            observe<BPT>(a, L, Pn, n_s, b0, r, s, g, step, event);
-            ++event;
+            const int64_t ev = (a.d_events ? *a.d_events : 0) + n_events;
+            observe<BPT>(a, L, L.order(ord), Pn, n_s, b0, r, s, g, step + 1, ev);
+            ++n_events;
         }
     }
     if (forces_only) return;
-    if (threadIdx.x == 0 && L.h->fail != 0) missing_records(a, r, s, g, step0, step, event);
-    const float4 *P = L.lay[cur];
+    if (threadIdx.x == 0 && L.h()->fail != 0)
+        missing_records(a, r, s, g, step0, step0 + it, (a.d_events ? *a.d_events : 0) + n_events);
+    const float4 *P = L.lay(cur);
     for (int b = threadIdx.x; b < n_s; b += T) {
         a.pos[gbase + b] = P[b];
-        a.comp[gbase + b] = L.comp[b];
+        a.comp[gbase + b] = L.comp()[b];
     }
-    if (threadIdx.x == 0 && L.h->fail != 0) atomicCAS(&sa.rep_status[r], 0, L.h->fail);
+    if (threadIdx.x == 0 && L.h()->fail != 0) atomicCAS(&sa.rep_status[r], 0, L.h()->fail);
 }
 
-template <int BPT, int MINB>
+template <int BPT, int MINB, int MAXT, bool RG>
 cudaError_t launch_t(const BatchedArgs &a, const BatchedConfig &cfg, cudaStream_t s) {
-    auto kern = k_batched<BPT, MINB>;
+    auto kern = k_batched<BPT, MINB, MAXT, RG>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cfg.smem);
     if (e != cudaSuccess) return e;
     kern<<<a.n_items, cfg.threads, cfg.smem, s>>>(a);
     return cudaGetLastError();
 }
 
-}  // namespace
-
-int batched_max_threads() { return kMaxThreads; }
-
-bool batched_config(int max_n, int row_width, int threads_hint, BatchedConfig *cfg) {
-    if (max_n <= 0 || max_n > 65535) return false;
-    int threads = threads_hint > 0 ? threads_hint : 0;
-    if (threads == 0) {
-        threads = ((max_n + 31) / 32) * 32;
-        if (threads > 256) threads = 256;
-        if (threads < 64) threads = 64;
+// Shared-memory rows, CTAs of up to 256 threads.
+template <int BPT>
+cudaError_t launch_small(const BatchedArgs &a, const BatchedConfig &cfg, cudaStream_t s) {
+    switch (cfg.min_blocks) {
+    case 2: return launch_t<BPT, 2, 256, false>(a, cfg, s);
+    case 3: return launch_t<BPT, 3, 256, false>(a, cfg, s);
+    default: return launch_t<BPT, 4, 256, false>(a, cfg, s);
     }
-    if (threads > kMaxThreads || threads % 32) return false;
-    const int bpt = (max_n + threads - 1) / threads;
-    if (bpt > 8) return false;
-    cfg->threads = threads;
-    cfg->beads_per_thread = bpt <= 1 ? 1 : bpt <= 2 ? 2 : bpt <= 4 ? 4 : 8;
-    cfg->smem = layout_bytes(max_n, row_width);
-    return cfg->smem <= 227 * 1024;
 }
 
-template <int BPT>
-cudaError_t launch_b(const BatchedArgs &a, const BatchedConfig &cfg, cudaStream_t s) {
-    switch (cfg.min_blocks) {
-    case 2: return launch_t<BPT, 2>(a, cfg, s);
-    case 3: return launch_t<BPT, 3>(a, cfg, s);
-    default: return launch_t<BPT, 4>(a, cfg, s);
-    }
+}  // namespace
+
+// The compiled instances: shared-memory rows with CTAs of at most 256 threads and
+// 1, 2 or 4 beads per thread under a register cap of 128, 85 or 64; global-memory
+// rows with CTAs of at most 1024 threads, 1 to 8 beads per thread, 64 registers.
+bool batched_config(int max_n, int row_width, int threads, bool rows_global, int min_blocks, BatchedConfig *cfg) {
+    if (max_n <= 0 || max_n > 8192 || row_width > kKeys - 1 || threads % 32 || threads < 32) return false;
+    const int bpt = (max_n + threads - 1) / threads;
+    const int bpt_c = bpt <= 1 ? 1 : bpt <= 2 ? 2 : bpt <= 4 ? 4 : 8;
+    if (bpt > 8) return false;
+    if (!rows_global && (threads > 256 || bpt_c > 4 || min_blocks < 2 || min_blocks > 4)) return false;
+    if (rows_global && (threads > 1024 || min_blocks != 1)) return false;
+    cfg->threads = threads;
+    cfg->beads_per_thread = bpt_c;
+    cfg->min_blocks = min_blocks;
+    cfg->rows_global = rows_global;
+    cfg->row_width = row_width;
+    cfg->smem = layout_bytes(max_n, row_width, rows_global);
+    return cfg->smem <= 227 * 1024;
 }
 
 cudaError_t launch_batched(const BatchedArgs &a, const BatchedConfig &cfg, cudaStream_t s, int64_t *launches) {
     if (a.n_items <= 0) return cudaSuccess;
     if (launches) *launches += 1;
+    if (cfg.rows_global) {
+        switch (cfg.beads_per_thread) {
+        case 1: return launch_t<1, 1, 1024, true>(a, cfg, s);
+        case 2: return launch_t<2, 1, 1024, true>(a, cfg, s);
+        case 4: return launch_t<4, 1, 1024, true>(a, cfg, s);
+        default: return launch_t<8, 1, 1024, true>(a, cfg, s);
+        }
+    }
     switch (cfg.beads_per_thread) {
-    case 1: return launch_b<1>(a, cfg, s);
-    case 2: return launch_b<2>(a, cfg, s);
-    case 4: return launch_b<4>(a, cfg, s);
-    default: return launch_b<8>(a, cfg, s);
+    case 1: return launch_small<1>(a, cfg, s);
+    case 2: return launch_small<2>(a, cfg, s);
+    default: return launch_small<4>(a, cfg, s);
     }
 }
 

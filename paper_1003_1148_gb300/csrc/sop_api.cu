@@ -20,7 +20,7 @@ namespace {
 thread_local std::string g_create_error;
 
 constexpr int kObsChunk = 2048;        // beads per FP64 observable partial
-constexpr int kBatchedMaxBeads = 2048; // largest system the batched schedule takes
+constexpr int kBatchedMaxBeads = 8192; // largest system the batched schedule takes
 constexpr int64_t kBatchedChunk = 4096;  // steps per batched launch
 
 // k_B in kcal/(mol K): molar gas constant 8.314462618 J/(mol K) / 4184 J/kcal.
@@ -88,10 +88,23 @@ struct sop_ctx {
     double ind_c0[3] = {0, 0, 0}, ind_dir[3] = {0, 0, 0}, ind_radius = 0, ind_v = 0, ind_n0 = 0;
     // kernel arguments
     StepArgs sa;
-    // batched schedule
+    // batched schedule: work items (system, replica) grouped into size buckets, each with
+    // its own tuned configuration and stream
+    struct Bucket {
+        int max_n = 0;          // largest system of the bucket
+        int cap = 0;            // Verlet capacity per row
+        int row_width = 0;      // natives + cap
+        int32_t item_off = 0;   // first item in the item arrays
+        int32_t n_items = 0;
+        BatchedConfig cfg;
+        uint16_t *rows = nullptr;   // rows in global memory (when cfg.rows_global)
+        cudaStream_t stream = nullptr;
+        cudaEvent_t done = nullptr;
+    };
     int schedule = SOP_SCHED_STREAMED;
-    BatchedConfig bcfg;
-    int batched_cap = 64;
+    std::vector<Bucket> buckets;
+    cudaEvent_t fork_ev = nullptr;
+    int batched_cap = 64;   // largest Verlet capacity over the buckets
     int max_sys = 0;
     int32_t n_items = 0;
     int32_t *d_item_rep = nullptr, *d_item_sys = nullptr;
@@ -217,12 +230,12 @@ sop_status rebuild_streamed(sop_ctx *c) {
     return SOP_OK;
 }
 
-BatchedArgs batched_args(sop_ctx *c) {
+BatchedArgs batched_args(sop_ctx *c, const sop_ctx::Bucket &bk) {
     BatchedArgs a;
     a.sa = c->sa;
-    a.n_items = c->n_items;
-    a.item_rep = c->d_item_rep;
-    a.item_sys = c->d_item_sys;
+    a.n_items = bk.n_items;
+    a.item_rep = c->d_item_rep + bk.item_off;
+    a.item_sys = c->d_item_sys + bk.item_off;
     a.nat_ell_off = c->d_nat_ell_off;
     a.nat_ell_cnt = c->d_nat_ell_cnt;
     a.nat_ell_col = c->d_nat_ell_col;
@@ -233,12 +246,39 @@ BatchedArgs batched_args(sop_ctx *c) {
     a.d_step = c->d_step;
     a.d_events = c->d_events;
     a.K = c->prm.rebuild_every;
-    a.cap = c->batched_cap;
-    a.max_n = c->max_sys;
+    a.cap = bk.cap;
+    a.max_n = bk.max_n;
+    a.row_global = bk.rows;
+    a.row_width = bk.row_width;
     a.obs = c->obs;
     a.obs_every = c->prm.obs_every;
     a.n_seg = c->n_seg;
     return a;
+}
+
+// Launch the batched kernel for every bucket. `patch` adjusts each bucket's arguments
+// (steps, forces mode, buffers). With several buckets they run concurrently on their own
+// streams, forked from and joined back into the context's stream (also under capture).
+template <class Patch>
+sop_status launch_buckets(sop_ctx *c, Patch patch, int64_t *launches) {
+    if (c->buckets.size() == 1) {
+        BatchedArgs a = batched_args(c, c->buckets[0]);
+        patch(a);
+        cudaError_t e = launch_batched(a, c->buckets[0].cfg, c->stream, launches);
+        if (e != cudaSuccess) return fail(c, SOP_ERR_CUDA, std::string("batched launch: ") + cudaGetErrorString(e));
+        return SOP_OK;
+    }
+    CUDA_OR_RETURN(c, cudaEventRecord(c->fork_ev, c->stream));
+    for (auto &bk : c->buckets) {
+        CUDA_OR_RETURN(c, cudaStreamWaitEvent(bk.stream, c->fork_ev, 0));
+        BatchedArgs a = batched_args(c, bk);
+        patch(a);
+        cudaError_t e = launch_batched(a, bk.cfg, bk.stream, launches);
+        if (e != cudaSuccess) return fail(c, SOP_ERR_CUDA, std::string("batched launch: ") + cudaGetErrorString(e));
+        CUDA_OR_RETURN(c, cudaEventRecord(bk.done, bk.stream));
+    }
+    for (auto &bk : c->buckets) CUDA_OR_RETURN(c, cudaStreamWaitEvent(c->stream, bk.done, 0));
+    return SOP_OK;
 }
 
 int64_t events_in(int64_t s0, int64_t s1, int32_t every) {   // multiples of every in (s0, s1]
@@ -393,8 +433,7 @@ sop_status step_batched(sop_ctx *c, int64_t n_steps) {
         const int64_t nev = events_in(c->step, c->step + chunk, c->prm.obs_every);
         sop_status th = throttle_before_chunk(c);
         if (th != SOP_OK) return th;
-        BatchedArgs a = batched_args(c);
-        a.n_steps = (int32_t)chunk;
+        auto set_steps = [chunk](BatchedArgs &a) { a.n_steps = (int32_t)chunk; };
         // a full chunk whose cadence divides it always holds the same number of records:
         // replay it from a graph; anything else is launched directly
         const bool regular = c->prm.obs_every <= 0 || kBatchedChunk % c->prm.obs_every == 0;
@@ -403,12 +442,15 @@ sop_status step_batched(sop_ctx *c, int64_t n_steps) {
                 cudaGraph_t g = nullptr;
                 CUDA_OR_RETURN(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
                 int64_t dummy = 0;
-                cudaError_t e1 = launch_batched(a, c->bcfg, c->stream, &dummy);
+                sop_status s1 = launch_buckets(c, set_steps, &dummy);
                 launch_tick(c->d_step, chunk, c->d_events, 0, nev, c->stream, &dummy);
                 cudaError_t e2 = cudaStreamEndCapture(c->stream, &g);
-                if (e1 != cudaSuccess || e2 != cudaSuccess)
-                    return fail(c, SOP_ERR_CUDA, std::string("batched graph capture: ") +
-                                                     cudaGetErrorString(e1 != cudaSuccess ? e1 : e2));
+                if (s1 != SOP_OK) {
+                    if (g) cudaGraphDestroy(g);
+                    return s1;
+                }
+                if (e2 != cudaSuccess)
+                    return fail(c, SOP_ERR_CUDA, std::string("batched graph capture: ") + cudaGetErrorString(e2));
                 cudaError_t e3 = cudaGraphInstantiate(&c->bexec, g, 0);
                 cudaGraphDestroy(g);
                 if (e3 != cudaSuccess)
@@ -416,10 +458,10 @@ sop_status step_batched(sop_ctx *c, int64_t n_steps) {
             }
             CUDA_OR_RETURN(c, cudaGraphLaunch(c->bexec, c->stream));
             c->st.graph_launches++;
-            c->st.kernel_launches += 2;
+            c->st.kernel_launches += (int64_t)c->buckets.size() + 1;
         } else {
-            cudaError_t e = launch_batched(a, c->bcfg, c->stream, &c->st.kernel_launches);
-            if (e != cudaSuccess) return fail(c, SOP_ERR_CUDA, std::string("batched launch: ") + cudaGetErrorString(e));
+            sop_status s1 = launch_buckets(c, set_steps, &c->st.kernel_launches);
+            if (s1 != SOP_OK) return s1;
             launch_tick(c->d_step, chunk, c->d_events, 0, nev, c->stream, &c->st.kernel_launches);
         }
         th = record_chunk(c);
@@ -596,119 +638,175 @@ sop_status build_batched_tables(sop_ctx *c) {
     CUDA_OR_RETURN(c, upload(c, &c->d_nat_ell_cnt, cnt));
     CUDA_OR_RETURN(c, upload(c, &c->d_nat_ell_col, col));
     CUDA_OR_RETURN(c, upload(c, &c->d_nat_ell_r0sq, r0sq));
-    // work items, heaviest system first
-    std::vector<int32_t> order(c->n_sys);
-    for (int s = 0; s < c->n_sys; ++s) order[s] = s;
-    std::stable_sort(order.begin(), order.end(), [c](int a, int b) {
-        return c->sys_lo[a + 1] - c->sys_lo[a] > c->sys_lo[b + 1] - c->sys_lo[b];
-    });
-    std::vector<int32_t> ir, is;
-    for (int s : order)
-        for (int r = 0; r < c->R; ++r) { ir.push_back(r); is.push_back(s); }
-    c->n_items = (int32_t)ir.size();
-    CUDA_OR_RETURN(c, upload(c, &c->d_item_rep, ir));
-    CUDA_OR_RETURN(c, upload(c, &c->d_item_sys, is));
     return SOP_OK;
 }
 
-// Size-bucket autotuner of the batched kernel. Candidates are (threads per CTA, beads
-// per thread, register cap); each is timed on a 20-step trial of up to 16 CTAs per SM on
-// scratch copies of the state (the run's state, records and statuses are untouched) and
-// the fastest is kept. Results are cached in the file named by SOP_TUNE_CACHE, keyed by
-// the system size, row width and trial size; SOP_TUNE=0 skips the trial.
-sop_status tune_batched(sop_ctx *c, int row_width, BatchedConfig *best) {
+// Size buckets of the batched schedule: systems of up to 32, 64, 96, 128, 192, 256, 384, 512,
+// 768, 1024, 1536, 2048, 4096 and 8192 beads. Each bucket gets its work items (system,
+// replica; heaviest system first), a Verlet capacity from the first list of its systems and
+// the width of its merged rows.
+sop_status build_buckets(sop_ctx *c, const std::vector<int32_t> &first_len) {
+    static const int bounds[] = {32, 64, 96, 128, 192, 256, 384, 512, 768, 1024, 1536, 2048, 4096, 8192};
+    std::vector<int32_t> ir, is;
+    int lo = 0;
+    for (int hi : bounds) {
+        std::vector<int32_t> sys;
+        for (int s = 0; s < c->n_sys; ++s) {
+            const int ns = c->sys_lo[s + 1] - c->sys_lo[s];
+            if (ns > lo && ns <= hi) sys.push_back(s);
+        }
+        lo = hi;
+        if (sys.empty()) continue;
+        std::stable_sort(sys.begin(), sys.end(), [c](int a, int b) {
+            return c->sys_lo[a + 1] - c->sys_lo[a] > c->sys_lo[b + 1] - c->sys_lo[b];
+        });
+        sop_ctx::Bucket bk;
+        int maxnat = 0, mrow = 0;
+        for (int s : sys) {
+            bk.max_n = std::max(bk.max_n, c->sys_lo[s + 1] - c->sys_lo[s]);
+            for (int i = c->sys_lo[s]; i < c->sys_lo[s + 1]; ++i) {
+                maxnat = std::max(maxnat, c->h_nat_row[i + 1] - c->h_nat_row[i]);
+                mrow = std::max(mrow, first_len[i]);
+            }
+        }
+        bk.cap = std::min(128, std::max(32, ((mrow * 3) / 2 + 8 + 7) / 8 * 8));
+        bk.row_width = maxnat + bk.cap;
+        if (bk.row_width > 256) return fail(c, SOP_ERR_UNSUPPORTED, "batched rows wider than 256 entries");
+        bk.item_off = (int32_t)ir.size();
+        for (int s : sys)
+            for (int r = 0; r < c->R; ++r) { ir.push_back(r); is.push_back(s); }
+        bk.n_items = (int32_t)ir.size() - bk.item_off;
+        c->batched_cap = std::max(c->batched_cap, bk.cap);
+        c->buckets.push_back(bk);
+    }
+    if (lo < c->max_sys) return fail(c, SOP_ERR_UNSUPPORTED, "system too large for the batched schedule");
+    c->n_items = (int32_t)ir.size();
+    CUDA_OR_RETURN(c, upload(c, &c->d_item_rep, ir));
+    CUDA_OR_RETURN(c, upload(c, &c->d_item_sys, is));
+    if (c->buckets.size() > 1) {
+        CUDA_OR_RETURN(c, cudaEventCreateWithFlags(&c->fork_ev, cudaEventDisableTiming));
+        for (auto &bk : c->buckets) {
+            CUDA_OR_RETURN(c, cudaStreamCreateWithFlags(&bk.stream, cudaStreamNonBlocking));
+            CUDA_OR_RETURN(c, cudaEventCreateWithFlags(&bk.done, cudaEventDisableTiming));
+        }
+    }
+    return SOP_OK;
+}
+
+// Autotuner of one size bucket. Candidates are (threads per CTA, beads per thread, register
+// cap, rows in shared or global memory); each is timed on a 20-step trial of the bucket's
+// first items (up to 16 CTAs per SM) on scratch copies of the state (the run's state,
+// records and statuses are untouched) and the fastest is kept. Results are cached in the
+// file named by SOP_TUNE_CACHE, keyed by the bucket's size, row width and trial size;
+// SOP_TUNE=0 skips the trial and takes the default.
+sop_status tune_bucket(sop_ctx *c, sop_ctx::Bucket &bk) {
     std::vector<BatchedConfig> cands;
+    const int need = 32 * ((bk.max_n + 31) / 32);
     for (int threads : {64, 128, 256})
         for (int minb : {2, 3, 4}) {
             BatchedConfig cfg;
-            if (!batched_config(c->max_sys, row_width, threads, &cfg)) continue;
-            if (threads > 32 * ((c->max_sys + 31) / 32) && threads > 64) continue;   // idle threads only
-            cfg.min_blocks = minb;
-            cands.push_back(cfg);
+            if (threads > need && threads > 64) continue;   // idle threads only
+            if (batched_config(bk.max_n, bk.row_width, threads, false, minb, &cfg)) cands.push_back(cfg);
         }
-    if (cands.empty()) return fail(c, SOP_ERR_UNSUPPORTED, "no batched configuration fits");
-    *best = cands[0];
-    for (const auto &cf : cands)   // default without a trial: the largest CTA at 64 registers
-        if (cf.min_blocks == 4 && cf.threads >= best->threads) *best = cf;
+    for (int threads : {128, 256, 512, 1024}) {
+        BatchedConfig cfg;
+        if (threads > need && threads > 128) continue;
+        if (batched_config(bk.max_n, bk.row_width, threads, true, 1, &cfg)) cands.push_back(cfg);
+    }
+    if (cands.empty()) return fail(c, SOP_ERR_UNSUPPORTED, "no batched configuration fits the bucket");
+    // default without a trial: shared-memory rows, the largest CTA at 64 registers; else global rows
+    bk.cfg = cands[0];
+    for (const auto &cf : cands)
+        if (!cf.rows_global && cf.min_blocks == 4 && cf.threads >= bk.cfg.threads) bk.cfg = cf;
     const char *env = std::getenv("SOP_TUNE");
-    if (env && std::string(env) == "0") return SOP_OK;
-    const int trial_items = std::min<int>(c->n_items, 152 * 16);
-    char key[128];
-    std::snprintf(key, sizeof key, "batched %d %d %d", c->max_sys, row_width, trial_items);
-    const char *cache = std::getenv("SOP_TUNE_CACHE");
-    if (cache) {
-        if (FILE *f = std::fopen(cache, "r")) {
-            char line[256];
-            while (std::fgets(line, sizeof line, f)) {
-                int t = 0, bpt = 0, mb = 0;
-                if (std::strncmp(line, key, std::strlen(key)) == 0 &&
-                    std::sscanf(line + std::strlen(key), " -> %d %d %d", &t, &bpt, &mb) == 3) {
-                    for (const auto &cf : cands)
-                        if (cf.threads == t && cf.beads_per_thread == bpt && cf.min_blocks == mb) {
-                            *best = cf;
-                            std::fclose(f);
-                            return SOP_OK;
-                        }
+    const int trial_items = std::min<int>(bk.n_items, 152 * 16);
+    if (!(env && std::string(env) == "0") && cands.size() > 1) {
+        char key[128];
+        std::snprintf(key, sizeof key, "batched %d %d %d", bk.max_n, bk.row_width, trial_items);
+        bool cached = false;
+        const char *cache = std::getenv("SOP_TUNE_CACHE");
+        if (cache) {
+            if (FILE *f = std::fopen(cache, "r")) {
+                char line[256];
+                while (!cached && std::fgets(line, sizeof line, f)) {
+                    int t = 0, bpt = 0, mb = 0, rg = 0;
+                    if (std::strncmp(line, key, std::strlen(key)) == 0 &&
+                        std::sscanf(line + std::strlen(key), " -> %d %d %d %d", &t, &bpt, &mb, &rg) == 4) {
+                        for (const auto &cf : cands)
+                            if (cf.threads == t && cf.beads_per_thread == bpt && cf.min_blocks == mb &&
+                                (int)cf.rows_global == rg) {
+                                bk.cfg = cf;
+                                cached = true;
+                            }
+                    }
                 }
+                std::fclose(f);
             }
-            std::fclose(f);
+        }
+        if (!cached) {
+            const size_t RN = (size_t)c->R * c->n;
+            float4 *sp = nullptr, *sc = nullptr, *ss = nullptr;
+            int32_t *sst = nullptr;
+            uint16_t *srows = nullptr;
+            CUDA_OR_RETURN(c, cudaMalloc(&sp, sizeof(float4) * RN));
+            CUDA_OR_RETURN(c, cudaMalloc(&sc, sizeof(float4) * RN));
+            CUDA_OR_RETURN(c, cudaMalloc(&ss, sizeof(float4) * RN));
+            CUDA_OR_RETURN(c, cudaMalloc(&sst, sizeof(int32_t) * c->R));
+            CUDA_OR_RETURN(c, cudaMalloc(&srows, sizeof(uint16_t) * (size_t)trial_items * bk.row_width * bk.max_n));
+            cudaEvent_t e0, e1;
+            CUDA_OR_RETURN(c, cudaEventCreate(&e0));
+            CUDA_OR_RETURN(c, cudaEventCreate(&e1));
+            float best_ms = 1e30f;
+            sop_status status = SOP_OK;
+            for (const auto &cf : cands) {
+                BatchedArgs a = batched_args(c, bk);
+                a.pos = sp;
+                a.comp = sc;
+                a.snap = ss;
+                a.sa.rep_status = sst;
+                a.obs_every = 0;
+                a.n_items = trial_items;
+                a.n_steps = 20;
+                a.row_global = srows;
+                float ms = 0.f;
+                for (int rep = 0; rep < 3 && status == SOP_OK; ++rep) {
+                    cudaMemcpyAsync(sp, c->d_pos[0], sizeof(float4) * RN, cudaMemcpyDeviceToDevice, c->stream);
+                    cudaMemcpyAsync(sc, c->d_comp, sizeof(float4) * RN, cudaMemcpyDeviceToDevice, c->stream);
+                    cudaMemcpyAsync(ss, c->d_snap, sizeof(float4) * RN, cudaMemcpyDeviceToDevice, c->stream);
+                    cudaMemsetAsync(sst, 0, sizeof(int32_t) * c->R, c->stream);
+                    cudaEventRecord(e0, c->stream);
+                    cudaError_t e = launch_batched(a, cf, c->stream, nullptr);
+                    cudaEventRecord(e1, c->stream);
+                    if (e != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
+                        status = fail(c, SOP_ERR_CUDA, std::string("autotune trial: ") + cudaGetErrorString(e));
+                        break;
+                    }
+                    float t = 0.f;
+                    cudaEventElapsedTime(&t, e0, e1);
+                    if (rep > 0) ms = rep == 1 ? t : std::min(ms, t);
+                }
+                if (status != SOP_OK) break;
+                if (ms < best_ms) { best_ms = ms; bk.cfg = cf; }
+            }
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            cudaFree(sp);
+            cudaFree(sc);
+            cudaFree(ss);
+            cudaFree(sst);
+            cudaFree(srows);
+            if (status != SOP_OK) return status;
+            c->st.tune_ms += best_ms;
+            if (cache)
+                if (FILE *f = std::fopen(cache, "a")) {
+                    std::fprintf(f, "%s -> %d %d %d %d %.4f\n", key, bk.cfg.threads, bk.cfg.beads_per_thread,
+                                 bk.cfg.min_blocks, (int)bk.cfg.rows_global, best_ms);
+                    std::fclose(f);
+                }
         }
     }
-    const size_t RN = (size_t)c->R * c->n;
-    float4 *sp = nullptr, *sc = nullptr, *ss = nullptr;
-    int32_t *sst = nullptr;
-    CUDA_OR_RETURN(c, cudaMalloc(&sp, sizeof(float4) * RN));
-    CUDA_OR_RETURN(c, cudaMalloc(&sc, sizeof(float4) * RN));
-    CUDA_OR_RETURN(c, cudaMalloc(&ss, sizeof(float4) * RN));
-    CUDA_OR_RETURN(c, cudaMalloc(&sst, sizeof(int32_t) * c->R));
-    cudaEvent_t e0, e1;
-    CUDA_OR_RETURN(c, cudaEventCreate(&e0));
-    CUDA_OR_RETURN(c, cudaEventCreate(&e1));
-    float best_ms = 1e30f;
-    sop_status status = SOP_OK;
-    for (const auto &cf : cands) {
-        BatchedArgs a = batched_args(c);
-        a.pos = sp;
-        a.comp = sc;
-        a.snap = ss;
-        a.sa.rep_status = sst;
-        a.obs_every = 0;
-        a.n_items = trial_items;
-        a.n_steps = 20;
-        float ms = 0.f;
-        for (int rep = 0; rep < 3 && status == SOP_OK; ++rep) {
-            cudaMemcpyAsync(sp, c->d_pos[0], sizeof(float4) * RN, cudaMemcpyDeviceToDevice, c->stream);
-            cudaMemcpyAsync(sc, c->d_comp, sizeof(float4) * RN, cudaMemcpyDeviceToDevice, c->stream);
-            cudaMemcpyAsync(ss, c->d_snap, sizeof(float4) * RN, cudaMemcpyDeviceToDevice, c->stream);
-            cudaMemsetAsync(sst, 0, sizeof(int32_t) * c->R, c->stream);
-            cudaEventRecord(e0, c->stream);
-            cudaError_t e = launch_batched(a, cf, c->stream, nullptr);
-            cudaEventRecord(e1, c->stream);
-            if (e != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
-                status = fail(c, SOP_ERR_CUDA, std::string("autotune trial: ") + cudaGetErrorString(e));
-                break;
-            }
-            float t = 0.f;
-            cudaEventElapsedTime(&t, e0, e1);
-            if (rep > 0) ms = rep == 1 ? t : std::min(ms, t);
-        }
-        if (status != SOP_OK) break;
-        if (ms < best_ms) { best_ms = ms; *best = cf; }
-    }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    cudaFree(sp);
-    cudaFree(sc);
-    cudaFree(ss);
-    cudaFree(sst);
-    if (status != SOP_OK) return status;
-    c->st.tune_ms = best_ms;
-    if (cache)
-        if (FILE *f = std::fopen(cache, "a")) {
-            std::fprintf(f, "%s -> %d %d %d %.4f\n", key, best->threads, best->beads_per_thread, best->min_blocks,
-                         best_ms);
-            std::fclose(f);
-        }
+    if (bk.cfg.rows_global)
+        CUDA_OR_RETURN(c, dalloc(c, &bk.rows, (size_t)bk.n_items * bk.row_width * bk.max_n));
     return SOP_OK;
 }
 
@@ -939,37 +1037,54 @@ sop_status create_impl(sop_ctx *c, const sop_topology *topo, const double *xyz, 
     int mrow = 0;
     s = max_row(c, &mrow);
     if (s != SOP_OK) return s;
-    // ---- schedule
+    // ---- schedule: batched for small systems or many of them, streamed for a few large ones
     int sched = p->schedule;
-    BatchedConfig cfg;
-    const int bcap = std::min(128, std::max(32, ((mrow * 3) / 2 + 8 + 7) / 8 * 8));
-    int maxnat = 0;
-    for (int i = 0; i < n; ++i) maxnat = std::max(maxnat, c->h_nat_row[i + 1] - c->h_nat_row[i]);
-    const bool batched_ok = c->max_sys <= kBatchedMaxBeads && batched_config(c->max_sys, maxnat + bcap, 0, &cfg);
-    if (sched == SOP_SCHED_AUTO) sched = batched_ok ? SOP_SCHED_BATCHED : SOP_SCHED_STREAMED;
+    const bool batched_ok = c->max_sys <= kBatchedMaxBeads;
+    if (sched == SOP_SCHED_AUTO) {
+        const int64_t items = (int64_t)c->R * c->n_sys;
+        sched = batched_ok && (c->max_sys <= 512 || items >= 152) ? SOP_SCHED_BATCHED : SOP_SCHED_STREAMED;
+    }
     if (sched == SOP_SCHED_BATCHED && !batched_ok)
-        return fail(c, SOP_ERR_UNSUPPORTED, "batched schedule needs systems of at most 2048 beads that fit shared memory");
+        return fail(c, SOP_ERR_UNSUPPORTED, "the batched schedule takes systems of at most 8192 beads");
     c->schedule = sched;
-    c->batched_cap = bcap;
-    c->bcfg = cfg;
+    c->st.schedule = sched;
+    c->st.block_threads = 256;
+    c->st.pairs_per_bead = c->ppb;
     if (sched == SOP_SCHED_BATCHED) {
+        std::vector<int32_t> first_len(n);
+        CUDA_OR_RETURN(c, cudaMemcpy(first_len.data(), c->pl.len, sizeof(int32_t) * n, cudaMemcpyDeviceToHost));
         s = build_batched_tables(c);
         if (s != SOP_OK) return s;
-        s = tune_batched(c, maxnat + bcap, &c->bcfg);
+        s = build_buckets(c, first_len);
         if (s != SOP_OK) return s;
-        cfg = c->bcfg;
+        size_t main_bucket = 0;
+        for (size_t k = 0; k < c->buckets.size(); ++k) {
+            s = tune_bucket(c, c->buckets[k]);
+            if (s != SOP_OK) return s;
+            if (c->buckets[k].n_items > c->buckets[main_bucket].n_items) main_bucket = k;
+        }
+        const BatchedConfig &cfg = c->buckets[main_bucket].cfg;
+        c->st.block_threads = cfg.threads;
+        c->st.pairs_per_bead = c->batched_cap;
+        c->st.beads_per_thread = cfg.beads_per_thread;
+        c->st.min_blocks = cfg.rows_global ? 0 : cfg.min_blocks;
+        c->st.buckets = (int32_t)c->buckets.size();
     }
-    c->st.schedule = sched;
-    c->st.block_threads = sched == SOP_SCHED_BATCHED ? cfg.threads : 256;
-    c->st.pairs_per_bead = sched == SOP_SCHED_BATCHED ? bcap : c->ppb;
-    c->st.beads_per_thread = sched == SOP_SCHED_BATCHED ? cfg.beads_per_thread : 0;
-    c->st.min_blocks = sched == SOP_SCHED_BATCHED ? cfg.min_blocks : 0;
+    (void)mrow;
     CUDA_OR_RETURN(c, cudaStreamSynchronize(c->stream));
     return SOP_OK;
 }
 
 void free_all(sop_ctx *c) {
     destroy_graphs(c);
+    for (auto &bk : c->buckets) {
+        if (bk.stream) cudaStreamDestroy(bk.stream);
+        if (bk.done) cudaEventDestroy(bk.done);
+        bk.stream = nullptr;
+        bk.done = nullptr;
+    }
+    if (c->fork_ev) cudaEventDestroy(c->fork_ev);
+    c->fork_ev = nullptr;
     for (auto &e : c->chunk_ev)
         if (e) { cudaEventDestroy(e); e = nullptr; }
     for (void *q : c->allocs) cudaFree(q);
@@ -1066,13 +1181,14 @@ sop_status sop_forces(sop_ctx *c, int32_t replica, double *out_f, double *out_en
         const SegRange rg = seg_range(c, g_lo, g_hi);
         launch_rebuild(c->sa, c->cells, c->pl2, c->d_pos[c->cur], nullptr, rg, c->stream, &c->st.kernel_launches);
         if (c->schedule == SOP_SCHED_BATCHED) {
-            BatchedArgs a = batched_args(c);
-            a.pos = c->d_pos[c->cur];
-            a.n_steps = 0;
-            a.force_out = c->d_force;
-            // only this replica's items: items are ordered (system, replica); run all, cheap
-            cudaError_t e = launch_batched(a, c->bcfg, c->stream, &c->st.kernel_launches);
-            if (e != cudaSuccess) return fail(c, SOP_ERR_CUDA, std::string("batched forces: ") + cudaGetErrorString(e));
+            // forces mode of the batched kernel for every item (cheap next to the transfer)
+            float4 *pos = c->d_pos[c->cur], *force = c->d_force;
+            sop_status sb = launch_buckets(c, [pos, force](BatchedArgs &a) {
+                a.pos = pos;
+                a.n_steps = 0;
+                a.force_out = force;
+            }, &c->st.kernel_launches);
+            if (sb != SOP_OK) return sb;
         } else {
             int64_t step_now = c->step;
             launch_forces(c->sa, c->pl2, c->d_pos[c->cur], c->d_force, rg.b_lo, rg.b_hi, step_now, c->stream,
@@ -1240,17 +1356,17 @@ sop_status sop_get_pairlist(sop_ctx *c, int32_t replica, int32_t *row_ptr, int32
             CUDA_OR_RETURN(c, dalloc(c, &c->d_dump_col, (size_t)c->R * n * stride));
             CUDA_OR_RETURN(c, cudaMemset(c->d_dump_len, 0, sizeof(int32_t) * (size_t)c->R * n));
         }
-        BatchedArgs a = batched_args(c);
-        a.pos = c->d_snap;
-        a.n_steps = 0;
-        a.force_out = c->d_force;
-        a.pl_dump_start = c->d_dump_start;
-        a.pl_dump_len = c->d_dump_len;
-        a.pl_dump_col = c->d_dump_col;
-        a.pl_dump_stride = stride;
-        cudaError_t e = launch_batched(a, c->bcfg, c->stream, &c->st.kernel_launches);
-        if (e != cudaSuccess) return fail(c, SOP_ERR_CUDA, std::string("batched dump: ") + cudaGetErrorString(e));
-        std::vector<int32_t> st(n);
+        sop_ctx *cc = c;
+        sop_status sb = launch_buckets(c, [cc, stride](BatchedArgs &a) {
+            a.pos = cc->d_snap;
+            a.n_steps = 0;
+            a.force_out = cc->d_force;
+            a.pl_dump_start = cc->d_dump_start;
+            a.pl_dump_len = cc->d_dump_len;
+            a.pl_dump_col = cc->d_dump_col;
+            a.pl_dump_stride = stride;
+        }, &c->st.kernel_launches);
+        if (sb != SOP_OK) return sb;
         cols.resize((size_t)n * stride);
         CUDA_OR_RETURN(c, cudaMemcpyAsync(len.data(), c->d_dump_len + (size_t)replica * n, sizeof(int32_t) * n,
                                           cudaMemcpyDeviceToHost, c->stream));

@@ -183,6 +183,8 @@ struct BatchedArgs {
     int32_t K = 10;             // rebuild_every
     int32_t cap = 64;           // Verlet capacity per bead
     int32_t max_n = 0;          // largest system in the launch
+    uint16_t *row_global = nullptr;  // rows in global memory: [n_items][row_width][max_n]
+    int32_t row_width = 0;      // natives + Verlet capacity per row
     DevObs obs;
     int32_t obs_every = 0;
     int32_t n_seg = 0;
@@ -191,15 +193,15 @@ struct BatchedArgs {
 struct BatchedConfig {
     int threads = 128;
     int beads_per_thread = 1;
-    int min_blocks = 4;   // register cap 65536 / (256 * min_blocks)
+    int min_blocks = 4;        // register cap 65536 / (max threads of the instance * min_blocks)
+    bool rows_global = false;  // neighbour rows in global memory instead of shared memory
+    int row_width = 0;
     size_t smem = 0;
 };
 
-int batched_max_threads();
-
-// Pick a configuration for systems of at most max_n beads whose merged rows hold up to
-// row_width entries (natives + Verlet capacity).
-bool batched_config(int max_n, int row_width, int threads_hint, BatchedConfig *cfg);
+// A configuration for systems of at most max_n beads whose merged rows hold up to
+// row_width entries (natives + Verlet capacity); false when no compiled instance fits.
+bool batched_config(int max_n, int row_width, int threads, bool rows_global, int min_blocks, BatchedConfig *cfg);
 // Run n_steps (or forces only when a.force_out != null and n_steps == 0).
 cudaError_t launch_batched(const BatchedArgs &a, const BatchedConfig &cfg, cudaStream_t s, int64_t *launches);
 

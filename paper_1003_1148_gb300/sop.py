@@ -71,6 +71,7 @@ class Stats(C.Structure):
     _fields_ = [("steps", C.c_int64), ("kernel_launches", C.c_int64), ("graph_launches", C.c_int64),
                 ("rebuilds", C.c_int64), ("schedule", C.c_int32), ("block_threads", C.c_int32),
                 ("pairs_per_bead", C.c_int32), ("beads_per_thread", C.c_int32), ("min_blocks", C.c_int32),
+                ("buckets", C.c_int32),
                 ("pairlist_entries", C.c_int64), ("native_entries", C.c_int64), ("tune_ms", C.c_double)]
 
 

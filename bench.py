@@ -18,6 +18,7 @@ Under torchrun every rank runs its own 8,192 replicas (weak scaling).
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import math
 import multiprocessing as mp
@@ -33,13 +34,16 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
+from paper_1003_1148_gb300 import dist  # noqa: E402  (host-only helpers; loads no library)
+
 METRIC = "bead-steps/s on 1 GB300, batched FP32 vs plain per-chain; force err vs FP64"
 UNIT = "bead-steps/s"
 MD_STEPS_PER_STEP = 1000
 FP32_LANES_PER_SM = 128
 N_SM = 152
 
-# Algorithmic FP32 operations per unique pair term and per bead (FMA = 2): see the design doc.
+# Algorithmic FP32 operations per unique pair term and per bead, an FMA counted as 2: a FENE or
+# native 12-6 term 25, a (sigma/r)^6 term 23; per bead the noise, update and compensation 33.
 FLOP_FENE, FLOP_NATIVE, FLOP_REP, FLOP_BEAD = 25, 25, 23, 33
 
 
@@ -59,6 +63,30 @@ def workload(name: str):
         r, n = name[len("replicas"):].split("x")
         return synth.replicas(n_replicas=int(r), n=int(n), seed=3, steps=100_000)
     raise SystemExit(f"unknown workload {name}")
+
+
+def kernel_revision() -> str:
+    """Hash of the batched kernel's sources; a profile summary records the one it measured."""
+    h = hashlib.sha256()
+    for f in ("k_batched.cu", "sop_device.cuh", "sop_internal.h"):
+        with open(os.path.join(ROOT, "paper_1003_1148_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(name: str):
+    """DRAM bytes per launch from profiles/<name>.md, or None when that capture measured
+    other kernel sources than the ones built now."""
+    path = os.path.join(ROOT, "profiles", f"{name}.md")
+    if not os.path.exists(path):
+        return None
+    rev = traffic = None
+    for line in open(path):
+        if line.startswith("Kernel source revision:"):
+            rev = line.split("`")[1] if "`" in line else None
+        elif line.startswith("traffic_bytes_per_launch:"):
+            traffic = int(line.split(":")[1])
+    return traffic if rev == kernel_revision() else None
 
 
 # ----------------------------------------------------------------------------------------
@@ -171,42 +199,10 @@ def force_error_leg(w, positions, forces_gpu):
 
 
 # ----------------------------------------------------------------------------------------
-# distributed helpers (weak scaling over replicas; no data-path collective)
-# ----------------------------------------------------------------------------------------
-def dist_env():
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return world, rank, local
-
-
-def dist_init(world):
-    if world <= 1:
-        return None
-    import torch.distributed as dist
-    dist.init_process_group("gloo", init_method="env://")
-    return dist
-
-
-def dist_max(dist, v: float) -> float:
-    if dist is None:
-        return v
-    import torch
-    t = torch.tensor([v], dtype=torch.float64)
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    return float(t.item())
-
-
-def dist_barrier(dist):
-    if dist is not None:
-        dist.barrier()
-
-
-# ----------------------------------------------------------------------------------------
 # arms
 # ----------------------------------------------------------------------------------------
 def run_reference(args):
-    world, rank, _ = dist_env()
+    world, rank, _ = dist.rank_env()
     if rank != 0:
         return 0
     w = workload(args.workload)
@@ -255,8 +251,8 @@ def run_ours(args):
     import torch
     from paper_1003_1148_gb300 import sop
 
-    world, rank, local = dist_env()
-    dist = dist_init(world)
+    world, rank, local = dist.rank_env()
+    group = dist.init(world)
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     w = workload(args.workload)
@@ -275,7 +271,8 @@ def run_ours(args):
         cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
 
     stream = torch.cuda.Stream(device=dev)
-    w.seed = w.seed + rank * R
+    first, _ = dist.replica_range(rank, world, per_rank=R)
+    w.seed = w.seed + first                 # replica r of the job draws Philox key seed + r
     sim = sop.from_workload(w, schedule=args.schedule, stream=stream, obs_capacity=max(4096, 4 * R * w.n_systems))
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     work_per_step = R * w.n_beads * MD_STEPS_PER_STEP
@@ -292,7 +289,7 @@ def run_ours(args):
         launches0 = sim.stats()["kernel_launches"]
         starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
         ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-        dist_barrier(dist)
+        dist.barrier(group)
         torch.cuda.synchronize()
         with ClockSampler(local) as clk:
             t0 = time.perf_counter()
@@ -303,7 +300,7 @@ def run_ours(args):
                 ends[k].record(stream)
             torch.cuda.synchronize()
             wall = time.perf_counter() - t0
-        dist_barrier(dist)
+        dist.barrier(group)
         launches = sim.stats()["kernel_launches"] - launches0
         dev_ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
         sim.get_observables()
@@ -323,8 +320,8 @@ def run_ours(args):
         e2e_wall = time.perf_counter() - t1
     h2d = R * w.n_beads * 3 * 8
 
-    t_dev = dist_max(dist, dev_ms / 1e3)
-    t_e2e = dist_max(dist, e2e_wall)
+    t_dev = dist.max_over_ranks(group, dev_ms / 1e3)
+    t_e2e = dist.max_over_ranks(group, e2e_wall)
     value = world * work_per_step * args.steps / t_dev
     e2e_value = world * work_per_step * e2e_steps / t_e2e
 
@@ -348,12 +345,7 @@ def run_ours(args):
                                   "verlet_capacity": st["pairs_per_bead"]},
                 "flop_per_bead_step": flop_bs, "list_sizes_replica0": counts,
                 "peak_note": "FP32 FMA pipe: 152 SMs x 128 lanes x 2 x 2070 MHz (max SM clock), derived"}
-    traffic_file = os.path.join(ROOT, "profiles", "k_batched_replicas8192x128.traffic.json")
-    if os.path.exists(traffic_file):
-        try:
-            roofline["traffic"] = json.load(open(traffic_file)).get("bytes_per_launch")
-        except (OSError, ValueError):
-            pass
+    roofline["traffic"] = recorded_traffic("k_batched_replicas8192x128")
 
     # plain per-chain GPU form on a subset of replicas (same kernels' math, one chain per launch)
     plain = None

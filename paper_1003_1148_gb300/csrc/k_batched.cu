@@ -180,8 +180,12 @@ __device__ int reorder_slots(const Layout<RG> &L, int n_s, int cur_order) {
     __syncthreads();
     const uint16_t *src = L.order(cur_order);
     uint16_t *dst = L.order(cur_order ^ 1);
+    const int full = n_s - n_s % T;   // slots in complete rounds of T
     for (int p = threadIdx.x; p < n_s; p += T) {
-        const int pos = atomicAdd(&h->hist[kKeys - 1 - min((int)L.n_tot()[p], kKeys - 1)], 1);
+        int pos = atomicAdd(&h->hist[kKeys - 1 - min((int)L.n_tot()[p], kKeys - 1)], 1);
+        // boustrophedon: odd rounds run backwards, so a thread owning several slots gets
+        // long and short rows alike and the warps of the CTA finish together
+        if (pos < full && ((pos / T) & 1)) pos = (pos / T) * T + (T - 1 - pos % T);
         dst[pos] = src[p];
     }
     __syncthreads();

@@ -64,7 +64,10 @@ typedef enum {
     SOP_SCHED_AUTO = 0,      /* choose per workload (autotuned) */
     SOP_SCHED_BATCHED = 1,   /* persistent fused kernel, one CTA per (replica, system), state in shared memory */
     SOP_SCHED_STREAMED = 2,  /* per-step kernels over global memory, cell-list rebuilds, CUDA-graph replay */
-    SOP_SCHED_PLAIN = 3      /* the plain form: per-step launches, one system after another, no graph */
+    SOP_SCHED_PLAIN = 3,     /* the plain form: per-step launches, one system after another, no graph */
+    SOP_SCHED_PAIRS = 4      /* the streamed schedule with pair-based forces (Sec. III.B, Algorithms 4 and 5):
+                                one thread per interacting pair writes +df and -df into per-entry force
+                                slots; the per-bead gathering is fused into the update */
 } sop_schedule;
 
 typedef struct sop_ctx sop_ctx;

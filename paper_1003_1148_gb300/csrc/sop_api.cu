@@ -70,6 +70,9 @@ struct sop_ctx {
     int32_t *d_abort = nullptr;
     // streamed list and cells
     DevPairList pl, pl2;
+    // pair-based form: tables of the run's list (pt) and of the forces-only list (pt2)
+    bool pairs = false;
+    DevPairTables pt, pt2;
     DevCells cells;
     int64_t pl_cap = 0;
     int ppb = 64;
@@ -110,6 +113,7 @@ struct sop_ctx {
     int32_t *d_item_rep = nullptr, *d_item_sys = nullptr;
     // graphs: [start buffer] for the streamed K-step chunk, one for the batched chunk
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+    int64_t gexec_launches[2] = {0, 0};   // kernels in each streamed chunk graph
     cudaGraphExec_t bexec = nullptr;
     // in-flight limiter: at most kInFlight chunks queued ahead of the device, so that
     // sop_abort takes effect within a few chunks and the step counter stays exact
@@ -202,6 +206,20 @@ SegRange seg_range(const sop_ctx *c, int g_lo, int g_hi) {
     return r;
 }
 
+// Rebuild of the run's Verlet list (and, in the pair-based form, its half list).
+void rebuild_list(sop_ctx *c, const float4 *pos, float4 *snap, const SegRange &rg, int64_t *launches) {
+    launch_rebuild(c->sa, c->cells, c->pl, pos, snap, rg, c->stream, launches);
+    if (c->pairs) launch_pair_index(c->sa, c->pl, c->pt, rg, c->stream, launches);
+}
+
+// One step of the beads of rg from layer `in` to layer `out`, particle- or pair-based.
+void step_range(sop_ctx *c, const float4 *in, float4 *out, const SegRange &rg, int32_t k_off, int64_t *launches) {
+    if (c->pairs)
+        launch_pairs_step(c->sa, c->pl, c->pt, in, out, c->d_comp, rg, k_off, c->lanes, c->stream, launches);
+    else
+        launch_step(c->sa, c->pl, in, out, c->d_comp, rg.b_lo, rg.b_hi, k_off, c->lanes, c->stream, launches);
+}
+
 // Refresh the pulling / indenter part of the kernel arguments.
 void sync_external(sop_ctx *c) {
     DevExternal &e = c->sa.ext;
@@ -222,8 +240,7 @@ void sync_external(sop_ctx *c) {
 }
 
 sop_status rebuild_streamed(sop_ctx *c) {
-    launch_rebuild(c->sa, c->cells, c->pl, c->d_pos[c->cur], c->d_snap, full_range(c), c->stream,
-                   &c->st.kernel_launches);
+    rebuild_list(c, c->d_pos[c->cur], c->d_snap, full_range(c), &c->st.kernel_launches);
     c->list_step = c->step;
     c->st.rebuilds++;
     CUDA_OR_RETURN(c, cudaGetLastError());
@@ -298,13 +315,11 @@ void enqueue_streamed_chunk(sop_ctx *c, int start_buf, int64_t *launches) {
     const SegRange all = full_range(c);
     int b = start_buf;
     for (int k = 0; k < K; ++k) {
-        launch_step(c->sa, c->pl, c->d_pos[b], c->d_pos[b ^ 1], c->d_comp, all.b_lo, all.b_hi, k, c->lanes, c->stream,
-                    launches);
+        step_range(c, c->d_pos[b], c->d_pos[b ^ 1], all, k, launches);
         b ^= 1;
     }
     // the list of step + K is built from the positions of step + K (the next chunk's first step)
-    StepArgs sa2 = c->sa;
-    launch_rebuild(sa2, c->cells, c->pl, c->d_pos[b], c->d_snap, all, c->stream, launches);
+    rebuild_list(c, c->d_pos[b], c->d_snap, all, launches);
     if (c->prm.obs_every > 0)
         launch_observables(c->sa, c->pl, c->obs, c->d_pos[b], c->n_seg, K, c->prm.obs_every, c->stream, launches);
     launch_tick(c->d_step, K, c->d_events, c->prm.obs_every > 0 ? c->prm.obs_every : 0, 0, c->stream, launches);
@@ -319,13 +334,9 @@ sop_status build_streamed_graph(sop_ctx *c, int start_buf) {
     if (e != cudaSuccess) return fail(c, SOP_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
     e = cudaGraphInstantiate(&c->gexec[start_buf], g, 0);
     cudaGraphDestroy(g);
+    c->gexec_launches[start_buf] = launches;
     if (e != cudaSuccess) return fail(c, SOP_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
     return SOP_OK;
-}
-
-int64_t streamed_chunk_launches(const sop_ctx *c) {
-    // K steps + rebuild (8 or 7) + observables (2) + tick
-    return c->prm.rebuild_every + 8 + (c->prm.obs_every > 0 ? 2 : 0) + 1;
 }
 
 sop_status step_streamed(sop_ctx *c, int64_t n_steps) {
@@ -351,7 +362,7 @@ sop_status step_streamed(sop_ctx *c, int64_t n_steps) {
             th = record_chunk(c);
             if (th != SOP_OK) return th;
             c->st.graph_launches++;
-            c->st.kernel_launches += streamed_chunk_launches(c);
+            c->st.kernel_launches += c->gexec_launches[c->cur];
             c->st.rebuilds++;
             if (K & 1) c->cur ^= 1;
             note_events(c, c->step, c->step + K);
@@ -365,14 +376,12 @@ sop_status step_streamed(sop_ctx *c, int64_t n_steps) {
             sop_status s = rebuild_streamed(c);
             if (s != SOP_OK) return s;
         }
-        launch_step(c->sa, c->pl, c->d_pos[c->cur], c->d_pos[c->cur ^ 1], c->d_comp, all.b_lo, all.b_hi, 0, c->lanes,
-                    c->stream, &c->st.kernel_launches);
+        step_range(c, c->d_pos[c->cur], c->d_pos[c->cur ^ 1], all, 0, &c->st.kernel_launches);
         c->cur ^= 1;
         const int64_t s1 = c->step + 1;
         if (every > 0 && s1 % every == 0) {
             if (s1 % K == 0) {
-                launch_rebuild(c->sa, c->cells, c->pl, c->d_pos[c->cur], c->d_snap, all, c->stream,
-                               &c->st.kernel_launches);
+                rebuild_list(c, c->d_pos[c->cur], c->d_snap, all, &c->st.kernel_launches);
                 c->st.rebuilds++;
                 c->list_step = s1;
             }
@@ -537,7 +546,7 @@ sop_status validate_params(const sop_params *p) {
     if (p->n_replicas < 1) return fail(nullptr, SOP_ERR_INVALID_ARG, "params: n_replicas >= 1");
     if (p->obs_every < 0 || p->obs_capacity < 0 || p->pairs_per_bead < 0)
         return fail(nullptr, SOP_ERR_INVALID_ARG, "params: obs_every, obs_capacity, pairs_per_bead >= 0");
-    if (p->schedule < SOP_SCHED_AUTO || p->schedule > SOP_SCHED_PLAIN)
+    if (p->schedule < SOP_SCHED_AUTO || p->schedule > SOP_SCHED_PAIRS)
         return fail(nullptr, SOP_ERR_INVALID_ARG, "params: unknown schedule");
     return SOP_OK;
 }
@@ -810,6 +819,103 @@ sop_status tune_bucket(sop_ctx *c, sop_ctx::Bucket &bk) {
     return SOP_OK;
 }
 
+// Tables of the pair-based form: the static native half list with each entry's row and
+// reverse entry (from the host copy of the native map), the force slots, and the Verlet
+// half-list buffers of the run's list (pt) or of the forces-only list (pt2, which shares
+// the native lists and the force slots: every slot a gathering reads is rewritten by the
+// pair kernel of the same step).
+sop_status alloc_pair_tables(sop_ctx *c, DevPairTables &t) {
+    if (t.vpair) return SOP_OK;
+    const size_t RN = (size_t)c->R * c->n;
+    if (!c->pt.fb) {
+        std::vector<int32_t> half, owner(c->nat_nnz), mirror(c->nat_nnz);
+        const int32_t *col = c->h_nat_col.data();
+        for (int i = 0; i < c->n; ++i)
+            for (int q = c->h_nat_row[i]; q < c->h_nat_row[i + 1]; ++q) {
+                const int j = col[q];
+                owner[q] = i;
+                if (j > i) half.push_back(q);
+                const int32_t *b = col + c->h_nat_row[j], *e = col + c->h_nat_row[j + 1];
+                const int32_t *it = std::lower_bound(b, e, i);
+                if (it == e || *it != i) return fail(c, SOP_ERR_CUDA, "native map is not symmetric");
+                mirror[q] = (int32_t)(it - col);
+            }
+        int32_t *d_half = nullptr, *d_owner = nullptr, *d_mirror = nullptr;
+        CUDA_OR_RETURN(c, upload(c, &d_half, half));
+        CUDA_OR_RETURN(c, upload(c, &d_owner, owner));
+        CUDA_OR_RETURN(c, upload(c, &d_mirror, mirror));
+        c->pt.nat_half = d_half;
+        c->pt.nat_owner = d_owner;
+        c->pt.nat_mirror = d_mirror;
+        c->pt.n_nat_half = (int32_t)half.size();
+        c->pt.nnz = c->nat_nnz;
+        CUDA_OR_RETURN(c, dalloc(c, &c->pt.fb, 2 * RN + 2));
+        CUDA_OR_RETURN(c, cudaMemset(c->pt.fb, 0, sizeof(float4) * (2 * RN + 2)));   // absent bonds read 0
+        CUDA_OR_RETURN(c, dalloc(c, &c->pt.fn, (size_t)c->R * c->nat_nnz));
+        CUDA_OR_RETURN(c, dalloc(c, &c->pt.fv, c->pl_cap));
+    }
+    if (&t != &c->pt) {
+        t.nat_half = c->pt.nat_half;
+        t.nat_owner = c->pt.nat_owner;
+        t.nat_mirror = c->pt.nat_mirror;
+        t.n_nat_half = c->pt.n_nat_half;
+        t.nnz = c->pt.nnz;
+        t.fb = c->pt.fb;
+        t.fn = c->pt.fn;
+        t.fv = c->pt.fv;
+    }
+    // a symmetric list has half as many upper entries as entries
+    t.vcap = c->pl_cap / 2 + 1024;
+    CUDA_OR_RETURN(c, dalloc(c, &t.vpair, (size_t)t.vcap));
+    CUDA_OR_RETURN(c, dalloc(c, &t.vcount, RN));
+    CUDA_OR_RETURN(c, dalloc(c, &t.voff, RN + 1));
+    CUDA_OR_RETURN(c, dalloc(c, &t.scan_tmp, scan_tmp_elems((int64_t)RN)));
+    return SOP_OK;
+}
+
+// The streamed schedule's choice between the particle-based gather (Algorithm 2) and the
+// pair-based form (Algorithms 4, 5): both force evaluations are timed on the current
+// positions and list (forces only; the run's state is untouched), the faster is kept.
+// SOP_TUNE=0 keeps the particle-based form without a trial.
+sop_status tune_streamed_form(sop_ctx *c) {
+    const char *env = std::getenv("SOP_TUNE");
+    if (env && std::string(env) == "0") return SOP_OK;
+    sop_status s = alloc_pair_tables(c, c->pt);
+    if (s != SOP_OK) return s;
+    const SegRange all = full_range(c);
+    launch_pair_index(c->sa, c->pl, c->pt, all, c->stream, nullptr);
+    cudaEvent_t e0, e1;
+    CUDA_OR_RETURN(c, cudaEventCreate(&e0));
+    CUDA_OR_RETURN(c, cudaEventCreate(&e1));
+    float ms[2] = {0.f, 0.f};
+    const int reps = 20;
+    for (int form = 0; form < 2; ++form) {
+        for (int rep = 0; rep <= reps; ++rep) {
+            if (rep == 1) cudaEventRecord(e0, c->stream);   // the first launch is a warm-up
+            if (form == 0)
+                launch_forces(c->sa, c->pl, c->d_pos[c->cur], c->d_force, all.b_lo, all.b_hi, c->step, c->stream,
+                              nullptr);
+            else
+                launch_pairs_forces(c->sa, c->pl, c->pt, c->d_pos[c->cur], c->d_force, all, c->step, c->stream,
+                                    nullptr);
+        }
+        cudaEventRecord(e1, c->stream);
+        cudaError_t e = cudaEventSynchronize(e1);
+        if (e == cudaSuccess) e = cudaGetLastError();
+        if (e != cudaSuccess) {
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            return fail(c, SOP_ERR_CUDA, std::string("streamed form trial: ") + cudaGetErrorString(e));
+        }
+        cudaEventElapsedTime(&ms[form], e0, e1);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c->pairs = ms[1] < ms[0];
+    c->st.tune_ms = (c->pairs ? ms[1] : ms[0]) / reps;
+    return SOP_OK;
+}
+
 // Largest Verlet row of replica 0 after the initial build.
 sop_status max_row(sop_ctx *c, int *out) {
     std::vector<int32_t> len(c->n);
@@ -1046,6 +1152,16 @@ sop_status create_impl(sop_ctx *c, const sop_topology *topo, const double *xyz, 
     }
     if (sched == SOP_SCHED_BATCHED && !batched_ok)
         return fail(c, SOP_ERR_UNSUPPORTED, "the batched schedule takes systems of at most 8192 beads");
+    if (sched == SOP_SCHED_PAIRS) {
+        s = alloc_pair_tables(c, c->pt);
+        if (s != SOP_OK) return s;
+        c->pairs = true;
+        launch_pair_index(c->sa, c->pl, c->pt, full_range(c), c->stream, &c->st.kernel_launches);
+    } else if (sched == SOP_SCHED_STREAMED && p->schedule == SOP_SCHED_AUTO) {
+        s = tune_streamed_form(c);
+        if (s != SOP_OK) return s;
+        if (c->pairs) sched = SOP_SCHED_PAIRS;
+    }
     c->schedule = sched;
     c->st.schedule = sched;
     c->st.block_threads = 256;
@@ -1151,6 +1267,7 @@ sop_status sop_step(sop_ctx *c, int64_t n_steps) {
             switch (c->schedule) {
             case SOP_SCHED_BATCHED: s = step_batched(c, n_steps); break;
             case SOP_SCHED_PLAIN: s = step_plain(c, n_steps); break;
+            case SOP_SCHED_PAIRS: s = step_streamed(c, n_steps); break;
             default: s = step_streamed(c, n_steps); break;
             }
         }
@@ -1189,6 +1306,12 @@ sop_status sop_forces(sop_ctx *c, int32_t replica, double *out_f, double *out_en
                 a.force_out = force;
             }, &c->st.kernel_launches);
             if (sb != SOP_OK) return sb;
+        } else if (c->pairs) {
+            sop_status sp = alloc_pair_tables(c, c->pt2);
+            if (sp != SOP_OK) return sp;
+            launch_pair_index(c->sa, c->pl2, c->pt2, rg, c->stream, &c->st.kernel_launches);
+            launch_pairs_forces(c->sa, c->pl2, c->pt2, c->d_pos[c->cur], c->d_force, rg, c->step, c->stream,
+                                &c->st.kernel_launches);
         } else {
             int64_t step_now = c->step;
             launch_forces(c->sa, c->pl2, c->d_pos[c->cur], c->d_force, rg.b_lo, rg.b_hi, step_now, c->stream,
@@ -1540,7 +1663,7 @@ sop_status sop_set_state(sop_ctx *c, const void *buf, int64_t size) {
     sop_status s = upload_pulls(c);
     if (s != SOP_OK) return s;
     // the list in use is the one built from the snapshot
-    launch_rebuild(c->sa, c->cells, c->pl, c->d_snap, nullptr, full_range(c), c->stream, &c->st.kernel_launches);
+    rebuild_list(c, c->d_snap, nullptr, full_range(c), &c->st.kernel_launches);
     c->list_step = hdr[5];
     CUDA_OR_RETURN(c, cudaStreamSynchronize(c->stream));
     return SOP_OK;

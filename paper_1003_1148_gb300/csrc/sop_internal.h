@@ -156,6 +156,40 @@ void launch_energy(const StepArgs &a, const DevPairList &pl, const DevObs &o, co
 void launch_tick(int64_t *d_step, int64_t k, int64_t *events, int32_t gate, int64_t n_events, cudaStream_t s,
                  int64_t *launches);
 
+// ---- pair-based form (k_pairs.cu), Algorithms 4 and 5 ----
+// Pair lists and force tables. Each pair (i < j) is evaluated once; +df goes to the slot of
+// entry (i -> j), -df to the slot of the reverse entry (j -> i). Slots are laid out like the
+// rows, so a bead's gathering reads its own slots in row order.
+struct DevPairTables {
+    const int32_t *nat_half = nullptr;    // [n_nat_half] native CSR entries q with col[q] > row(q)
+    const int32_t *nat_owner = nullptr;   // [nnz] row (replica-local bead) of entry q
+    const int32_t *nat_mirror = nullptr;  // [nnz] reverse entry of q
+    int32_t n_nat_half = 0;
+    int64_t nnz = 0;
+    int4 *vpair = nullptr;                // [vcap] Verlet half pairs (entry, reverse entry or -1, gb, gj)
+    int32_t *vcount = nullptr;            // [beads of the range] upper entries per row
+    int32_t *voff = nullptr;              // [beads + 1] exclusive offsets; voff[beads] = total
+    int32_t *scan_tmp = nullptr;          // scan block sums
+    int64_t vcap = 0;
+    float4 *fb = nullptr;                 // [2 R n] bond slots: 2 gb left bond, 2 gb + 1 right bond; w = 1 if broken
+    float4 *fn = nullptr;                 // [R nnz] native slots, replica r at r * nnz
+    float4 *fv = nullptr;                 // [pl cap] Verlet slots, aligned with the list's columns
+};
+
+// Half list of the Verlet list for the beads of range rg (whole replicas): count, scan, fill.
+void launch_pair_index(const StepArgs &a, const DevPairList &pl, const DevPairTables &t, const SegRange &rg,
+                       cudaStream_t s, int64_t *launches);
+
+// One step in the pair-based form: the pair kernel (Algorithm 4) over bonds, natives and the
+// Verlet half list, then the gathering (Algorithm 5) fused with noise and the update.
+void launch_pairs_step(const StepArgs &a, const DevPairList &pl, const DevPairTables &t, const float4 *pos_in,
+                       float4 *pos_out, float4 *comp, const SegRange &rg, int32_t k_off, int lanes, cudaStream_t s,
+                       int64_t *launches);
+
+// Forces only in the pair-based form (pair kernel + gathering), as launch_forces.
+void launch_pairs_forces(const StepArgs &a, const DevPairList &pl, const DevPairTables &t, const float4 *pos,
+                         float4 *force, const SegRange &rg, int64_t step, cudaStream_t s, int64_t *launches);
+
 // ---- batched schedule (k_batched.cu) ----
 struct BatchedArgs {
     StepArgs sa;

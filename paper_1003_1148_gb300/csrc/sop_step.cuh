@@ -1,0 +1,93 @@
+// Per-bead pieces of a streamed step shared by the particle-based form (k_stream.cu)
+// and the pair-based form (k_pairs.cu): the cantilever and indenter forces, the failure
+// checks, the Philox noise and the compensated first-order update of Algorithm 7.
+#pragma once
+
+#include "sop_internal.h"
+
+namespace sop {
+
+__device__ __forceinline__ void set_status(int32_t *st, int32_t code) { atomicCAS(st, 0, code); }
+
+// Lanes of this thread's group of L (groups are aligned within the warp).
+template <int L>
+__device__ __forceinline__ unsigned group_mask() {
+    return L == 32 ? 0xffffffffu : (((1u << L) - 1u) << ((threadIdx.x & 31) & ~(L - 1)));
+}
+
+// Cantilever and indenter forces on bead i (FP64 tip / centre, FP32 force).
+__device__ __forceinline__ float3 external_force(const StepArgs &a, int r, int i, float4 pi, int64_t step,
+                                                 bool *overlap) {
+    float3 f = make_float3(0.f, 0.f, 0.f);
+    const DevTopo &t = a.topo;
+    const DevExternal &e = a.ext;
+    if (t.flags[i] & kFlagPulled) {
+        const int q = e.pull_of_sys[t.sys[i]];
+        if (q >= 0 && e.pull_bead[q] == i) {
+            const double tt = e.pull_v[q] * ((double)step - e.pull_n0[q]);
+            const double *tip0 = e.pull_tip0 + ((size_t)r * e.n_pull + q) * 3;
+            const float ks = (float)e.pull_ks[q];
+            f.x += ks * (float)(tip0[0] + tt * e.pull_dir[3 * q] - (double)pi.x);
+            f.y += ks * (float)(tip0[1] + tt * e.pull_dir[3 * q + 1] - (double)pi.y);
+            f.z += ks * (float)(tip0[2] + tt * e.pull_dir[3 * q + 2] - (double)pi.z);
+        }
+    }
+    if (e.has_indenter) {
+        const double tt = e.ind_v * ((double)step - e.ind_n0);
+        const float cx = (float)(e.ind_c0[0] + tt * e.ind_dir[0]);
+        const float cy = (float)(e.ind_c0[1] + tt * e.ind_dir[1]);
+        const float cz = (float)(e.ind_c0[2] + tt * e.ind_dir[2]);
+        const float ex = pi.x - cx, ey = pi.y - cy, ez = pi.z - cz;
+        const float rr = sqrtf(fmaf(ez, ez, fmaf(ey, ey, ex * ex)));
+        const float rho = rr - (float)e.ind_radius;
+        if (!(rho > 0.f)) {
+            *overlap = true;
+        } else {
+            const float q = a.fp.sigma2 > 0.f ? sqrtf(a.fp.sigma2) / rho : 0.f;
+            const float q2 = q * q;
+            const float q6 = q2 * q2 * q2;
+            const float c = a.fp.eps6_l * q6 / (rho * rr);
+            f.x = fmaf(c, ex, f.x); f.y = fmaf(c, ey, f.y); f.z = fmaf(c, ez, f.z);
+        }
+    }
+    return f;
+}
+
+// The end of one step for bead i of replica r (global index gb) given the sum f of its
+// pair forces at layer P: a broken bond or an indenter overlap leaves the bead where it
+// is and marks the replica; a fixed bead stays; otherwise r += F h/zeta + g sqrt(2kTh/zeta)
+// with the FP32 compensation of the bead.
+__device__ __forceinline__ void advance_bead(const StepArgs &a, int r, int i, int gb, const float4 *P, float3 f,
+                                             bool broken, int64_t step, float4 *pos_out, float4 *comp) {
+    float4 pi = P[i];
+    if (broken) {
+        set_status(&a.rep_status[r], (int32_t)SOP_ERR_FENE_BREAK);
+        pos_out[gb] = pi;
+        return;
+    }
+    bool overlap = false;
+    const float3 fe = external_force(a, r, i, pi, step, &overlap);
+    if (overlap) {
+        set_status(&a.rep_status[r], (int32_t)SOP_ERR_INDENTER_OVERLAP);
+        pos_out[gb] = pi;
+        return;
+    }
+    if (a.topo.flags[i] & kFlagFixed) {
+        pos_out[gb] = pi;
+        return;
+    }
+    const float3 g = bead_noise(a.seed + (uint64_t)r, step, (uint32_t)i);
+    float4 c = comp[gb];
+    kahan_add(pi.x, c.x, fmaf(f.x + fe.x, a.fp.mob, g.x * a.fp.amp));
+    kahan_add(pi.y, c.y, fmaf(f.y + fe.y, a.fp.mob, g.y * a.fp.amp));
+    kahan_add(pi.z, c.z, fmaf(f.z + fe.z, a.fp.mob, g.z * a.fp.amp));
+    if (!(isfinite(pi.x) && isfinite(pi.y) && isfinite(pi.z))) {
+        set_status(&a.rep_status[r], (int32_t)SOP_ERR_NONFINITE);
+        pos_out[gb] = P[i];
+        return;
+    }
+    comp[gb] = c;
+    pos_out[gb] = pi;
+}
+
+}  // namespace sop

@@ -25,8 +25,9 @@ OK, ERR_INVALID_ARG, ERR_CUDA, ERR_OOM, ERR_FENE_BREAK, ERR_NONFINITE, ERR_PAIRL
     ERR_TIMEOUT, ERR_INDENTER_OVERLAP, ERR_UNSUPPORTED, ERR_CAPACITY = range(12)
 STATUS_NAMES = ["OK", "INVALID_ARG", "CUDA", "OOM", "FENE_BREAK", "NONFINITE", "PAIRLIST_OVERFLOW", "ABORTED",
                 "TIMEOUT", "INDENTER_OVERLAP", "UNSUPPORTED", "CAPACITY"]
-SCHED_AUTO, SCHED_BATCHED, SCHED_STREAMED, SCHED_PLAIN = range(4)
-SCHEDULES = {"auto": SCHED_AUTO, "batched": SCHED_BATCHED, "streamed": SCHED_STREAMED, "plain": SCHED_PLAIN}
+SCHED_AUTO, SCHED_BATCHED, SCHED_STREAMED, SCHED_PLAIN, SCHED_PAIRS = range(5)
+SCHEDULES = {"auto": SCHED_AUTO, "batched": SCHED_BATCHED, "streamed": SCHED_STREAMED, "plain": SCHED_PLAIN,
+             "pairs": SCHED_PAIRS}
 
 EXPORTED = ["sop_create", "sop_step", "sop_forces", "sop_pairlist_rebuild", "sop_pull", "sop_indenter",
             "sop_get_positions", "sop_set_positions", "sop_get_pairlist", "sop_get_native_map",

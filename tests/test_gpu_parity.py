@@ -108,7 +108,7 @@ def oracle_with_externals(orc, w, x_start):
     return m
 
 
-@pytest.mark.parametrize("schedule", ["streamed", "batched"])
+@pytest.mark.parametrize("schedule", ["streamed", "batched", "pairs"])
 def test_forces_within_tolerance(sop, orc, workloads, schedule):
     for w in workloads:
         if schedule == "batched" and w.n_systems == 1 and w.n_beads > 2048:
@@ -128,7 +128,7 @@ def test_forces_within_tolerance(sop, orc, workloads, schedule):
         sim.close()
 
 
-@pytest.mark.parametrize("schedule", ["streamed", "batched", "plain"])
+@pytest.mark.parametrize("schedule", ["streamed", "batched", "plain", "pairs"])
 def test_trajectory_100_steps(sop, orc, workloads, schedule):
     for w in workloads:
         if schedule == "batched" and w.n_systems == 1 and w.n_beads > 2048:
@@ -156,7 +156,7 @@ def test_plain_equals_streamed_bitwise(sop, synth):
 
 
 def test_observables_match_oracle_at_gpu_positions(sop, orc, synth):
-    for schedule in ("streamed", "batched"):
+    for schedule in ("streamed", "batched", "pairs"):
         w = synth.uneven(n_chains=4, lo=60, hi=200, steps=100)
         sim = sop.from_workload(w, n_replicas=2, schedule=schedule, obs_every=20)
         x0 = sim.get_positions(0)
@@ -178,7 +178,7 @@ def test_observables_match_oracle_at_gpu_positions(sop, orc, synth):
         sim.close()
 
 
-@pytest.mark.parametrize("schedule", ["streamed", "batched"])
+@pytest.mark.parametrize("schedule", ["streamed", "batched", "pairs"])
 def test_checkpoint_resume_bit_exact(sop, synth, schedule):
     w = synth.replicas(n_replicas=3, n=100, steps=100)
     sim = sop.from_workload(w, schedule=schedule)
@@ -246,3 +246,38 @@ def test_abort_stops_a_long_run(sop, synth):
     t.join()
     assert rc == sop.ERR_ABORTED
     assert sim.stats()["steps"] < 10_000_000
+
+
+def test_pair_based_is_deterministic_and_close_to_particle_based(sop, synth):
+    """The pair-based form writes every force slot from one thread and sums slots in row
+    order: two runs agree bit for bit. Its sums differ from the particle-based gather only
+    by rounding order."""
+    w = synth.shell(n_copies=6, n_per=150, r_in=60.0, r_out=80.0, ind_radius=20.0, steps=100)
+    a = sop.from_workload(w, n_replicas=2, schedule="pairs")
+    b = sop.from_workload(w, n_replicas=2, schedule="pairs")
+    c = sop.from_workload(w, n_replicas=2, schedule="streamed")
+    assert a.stats()["schedule"] == sop.SCHED_PAIRS
+    for s in (a, b, c):
+        s.step(45)
+    xa, xb, xc = a.get_positions(-1), b.get_positions(-1), c.get_positions(-1)
+    assert np.array_equal(xa, xb)
+    assert float(np.sqrt(((xa - xc) ** 2).sum(-1).mean())) <= RMS_TOL
+    Fa, Ea = a.forces(1)
+    Fc, Ec = c.forces(1)
+    assert Ea == pytest.approx(Ec, rel=1e-12)
+    assert np.abs(Fa - Fc).max() <= 1e-4 * max(1.0, np.abs(Fc).max())
+    for s in (a, b, c):
+        s.close()
+
+
+def test_auto_streamed_form_is_timed(sop, synth):
+    """For a large single system the automatic schedule is the streamed one, in whichever
+    force form (particle- or pair-based) its trial timed faster."""
+    w = synth.fiber4096(n=3000, steps=10)
+    sim = sop.from_workload(w, schedule="auto")
+    st = sim.stats()
+    assert st["schedule"] in (sop.SCHED_STREAMED, sop.SCHED_PAIRS)
+    assert st["tune_ms"] > 0
+    sim.step(20)
+    assert np.all(np.isfinite(sim.get_positions(0)))
+    sim.close()

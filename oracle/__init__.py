@@ -12,12 +12,14 @@ contraction, no fast-math). This module only marshals numpy arrays.
 Parity pins (tests/test_oracle_*.py): closed-form values of each potential at
 special distances, central finite differences of the energy against the
 forces, zero net force and torque, brute-force against scipy KD-tree and cell
-lists, Philox against ATen's independent implementation, Box-Muller
+lists, Philox against ATen's independent implementation, the Hybrid Taus
+components against their bit-level linear recurrences and the LCG against its
+closed form, Box-Muller
 invariants and moments, the exactly solvable Brownian particle (Eqs. 3-4) and
 the free-diffusion law.
 """
-from .oracle import (Model, box_muller, build, bonds, kB, native_pairs, noise, philox, OracleError,
+from .oracle import (Model, box_muller, build, bonds, kB, native_pairs, noise, philox, taus_next, OracleError,
                      model_from_workload)
 
-__all__ = ["Model", "box_muller", "build", "bonds", "kB", "native_pairs", "noise", "philox", "OracleError",
-           "model_from_workload"]
+__all__ = ["Model", "box_muller", "build", "bonds", "kB", "native_pairs", "noise", "philox", "taus_next",
+           "OracleError", "model_from_workload"]

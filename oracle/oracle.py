@@ -60,7 +60,7 @@ class _Model(C.Structure):
                 ("sigma", C.c_double), ("T", C.c_double), ("zeta", C.c_double), ("dt", C.c_double),
                 ("pair_cut", C.c_double), ("rebuild_every", C.c_int32), ("use_cells", C.c_int32),
                 ("noise_offset", C.c_int32),
-                ("n_pull", C.c_int32), ("pulls", C.c_void_p), ("indenter", C.c_void_p)]
+                ("n_pull", C.c_int32), ("pulls", C.c_void_p), ("indenter", C.c_void_p), ("taus", C.c_void_p)]
 
 
 def _L():
@@ -84,6 +84,9 @@ def _L():
             L.orc_philox4x32_10.argtypes = [vp, vp, vp]
             L.orc_box_muller.argtypes = [vp, vp]
             L.orc_noise.argtypes = [u64, i64, i32, vp]
+            L.orc_taus_next.argtypes = [vp]
+            L.orc_taus_next.restype = C.c_uint32
+            L.orc_taus_noise.argtypes = [vp, vp]
             L.orc_ermak_update.argtypes = [vp, vp, vp, u64, i64]
             L.orc_observables.argtypes = [vp, vp, i64, vp, vp, i64, i32, vp]
             L.orc_observables.restype = C.c_int
@@ -180,6 +183,7 @@ class Model:
         self.indenter = None
         self.use_cells = 0
         self.noise_offset = 0
+        self.taus = None
         self._sync()
 
     def _sync(self):
@@ -189,7 +193,8 @@ class Model:
                          _p(self.nat_j), _p(self.nat_r0), p["k_fene"], p["R0"], p["eps_h"], p["eps_l"],
                          p["sigma"], p["T"], p["zeta"], p["dt"], p["pair_cut"], int(p["rebuild_every"]),
                          int(self.use_cells), int(self.noise_offset), self.n_pull, C.addressof(self.pulls) if self.n_pull else None,
-                         C.addressof(self.indenter) if self.indenter is not None else None)
+                         C.addressof(self.indenter) if self.indenter is not None else None,
+                         _p(self.taus) if self.taus is not None else None)
 
     def set_cells(self, on: bool):
         self.use_cells = 1 if on else 0
@@ -199,6 +204,15 @@ class Model:
         """Bead index offset of the noise counter (for a chain taken out of a larger topology)."""
         self.noise_offset = int(offset)
         self._sync()
+
+    def set_taus_state(self, state):
+        """Use Hybrid Taus noise (Algorithm 6) with per-bead state [n, 4] (uint32), advanced in
+        place by every update; None returns to Philox."""
+        self.taus = None if state is None else np.ascontiguousarray(state, np.uint32).reshape(self.n, 4).copy()
+        self._sync()
+
+    def taus_state(self):
+        return None if self.taus is None else self.taus.copy()
 
     def start_pulls(self, pulls, xyz, step: int = 0):
         """pulls: iterable of (system, anchor, pulled, k_s, v); direction anchor->pulled at xyz."""
@@ -269,6 +283,14 @@ class Model:
         if rc and raise_on_error:
             raise OracleError(rc, f"at step {fail.value}")
         return xyz, obs[:n_obs.value].copy(), rc, fail.value
+
+
+def taus_next(state):
+    """One Hybrid Taus output; state (4 uint32) is advanced in place."""
+    st = np.ascontiguousarray(state, np.uint32)
+    out = _L().orc_taus_next(_p(st))
+    state[:] = st
+    return int(out)
 
 
 def model_from_workload(w, native_cells: bool | None = None) -> Model:

@@ -20,9 +20,11 @@
  *   orc_philox4x32_10, orc_noise  counter-based Philox4x32-10 as published by
  *                                 Salmon et al. (SC'11); the paper's own
  *                                 generator is Hybrid Taus (Algorithm 6)
+ *   orc_taus_next, orc_taus_noise Algorithm 6 (Hybrid Taus: three Tausworthe
+ *                                 generators and an LCG), Sec. III.C
  *   orc_box_muller                Sec. III.C (Box-Muller transformation)
- *   orc_ermak_update              Algorithm 7, line "1-st order integration
- *                                 scheme" (Ermak-McCammon, Eq. 2)
+ *   orc_ermak_update              Algorithm 7 (the first-order Ermak-McCammon
+ *                                 update, Eq. 2)
  *   orc_run                       the step sequence of Fig. 2 / Sec. III.D
  *
  * Readings where the paper is silent or garbled (each also listed in the
@@ -457,6 +459,32 @@ void orc_box_muller(const uint32_t x[4], double g[3]) {
     g[2] = rb * cos(two_pi * u4);
 }
 
+/* One step of a Tausworthe component (L'Ecuyer's shift form of a trinomial
+ * recurrence of degree k): b = ((y << q) ^ y) >> (k - s); y = ((y & mask) << s) ^ b,
+ * mask keeping the top k bits. The three components of Algorithm 6, read as
+ * (q, k - s, s, mask): (13, 19, 12, 4294967294), (2, 25, 4, 4294967288),
+ * (3, 11, 17, 4294967280); the listing's subscripts are garbled, and these are
+ * the values of L'Ecuyer's taus88, degrees k = 31, 29, 28 (periods 2^31-1,
+ * 2^29-1, 2^28-1; the text gives 2^30-1 for the second). */
+static uint32_t taus_component(uint32_t y, int q, int k_minus_s, int s, uint32_t mask) {
+    uint32_t b = ((y << q) ^ y) >> k_minus_s;
+    return ((y & mask) << s) ^ b;
+}
+
+uint32_t orc_taus_next(uint32_t s[4]) {
+    s[0] = taus_component(s[0], 13, 19, 12, 4294967294u);
+    s[1] = taus_component(s[1], 2, 25, 4, 4294967288u);
+    s[2] = taus_component(s[2], 3, 11, 17, 4294967280u);
+    s[3] = 1664525u * s[3] + 1013904223u;   /* LCG modulo 2^32 */
+    return s[0] ^ s[1] ^ s[2] ^ s[3];
+}
+
+void orc_taus_noise(uint32_t s[4], double g[3]) {
+    uint32_t x[4];
+    for (int k = 0; k < 4; ++k) x[k] = orc_taus_next(s);
+    orc_box_muller(x, g);
+}
+
 /* Key = the replica's 64-bit seed; counter = (step lo, step hi, bead, 0). */
 void orc_noise(uint64_t seed, int64_t step, int32_t bead, double g[3]) {
     uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
@@ -484,7 +512,8 @@ void orc_ermak_update(const orc_model *m, double *xyz, const double *F, uint64_t
     for (int32_t i = 0; i < m->n; ++i) {
         if (is_held(m, i)) continue;
         double g[3];
-        orc_noise(seed, step, i + m->noise_offset, g);
+        if (m->taus) orc_taus_noise(m->taus + 4 * (size_t)i, g);
+        else orc_noise(seed, step, i + m->noise_offset, g);
         for (int k = 0; k < 3; ++k) xyz[3 * i + k] = xyz[3 * i + k] + F[3 * i + k] * mob + g[k] * amp;
     }
 }

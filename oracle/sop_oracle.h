@@ -64,6 +64,9 @@ typedef struct {
     int32_t n_pull;
     const orc_pull *pulls;
     const orc_indenter *indenter;    /* may be NULL */
+    /* noise source: NULL = Philox4x32-10 keyed by the replica seed; else the Hybrid
+     * Taus state of every bead ([n][4] words y1..y4), advanced in place */
+    uint32_t *taus;
 } orc_model;
 
 enum {
@@ -116,11 +119,21 @@ void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t ou
 /* Three standard normals from one Philox block by Box-Muller. */
 void orc_box_muller(const uint32_t x[4], double g[3]);
 
+/* Hybrid Taus (Algorithm 6): one output of the generator with state s = (y1, y2,
+ * y3, y4): the three Tausworthe components and the LCG each take one step and the
+ * output is y1 ^ y2 ^ y3 ^ y4 (as an integer; times 2^-32 it is the uniform). */
+uint32_t orc_taus_next(uint32_t s[4]);
+
+/* Three standard normals from four successive Hybrid Taus outputs (Box-Muller as
+ * for a Philox block), advancing s by four outputs. */
+void orc_taus_noise(uint32_t s[4], double g[3]);
+
 /* Gaussian vector of bead `bead` at step `step` for the replica keyed by seed. */
 void orc_noise(uint64_t seed, int64_t step, int32_t bead, double g[3]);
 
 /* One first-order (Ermak-McCammon) update of all non-fixed beads given forces F:
- * r += F h/zeta + g sqrt(2 kT h / zeta), g from orc_noise(seed, step, i). */
+ * r += F h/zeta + g sqrt(2 kT h / zeta), g from orc_noise(seed, step, i), or from
+ * the bead's Hybrid Taus state when m->taus is set (only moved beads draw). */
 void orc_ermak_update(const orc_model *m, double *xyz, const double *F, uint64_t seed, int64_t step);
 
 /* Observables of every system at positions xyz and step `step`. Per system 8

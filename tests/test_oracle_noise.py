@@ -94,3 +94,99 @@ def test_noise_moments_and_distribution(orc):
         assert stats.kstest(g[:, c], "norm").pvalue > 1e-4
     cor = np.corrcoef(g.T)
     assert np.abs(cor - np.eye(3)).max() < 5 * se
+
+
+# ---------------------------------------------------------------------------------------
+# Hybrid Taus (Algorithm 6): each component is pinned against its defining bit-level
+# recurrence, the LCG against its closed form, both with the paper's printed constants
+# (tests/golden/paper_values.json, Sec. III.C). A Tausworthe component with state 0 stays
+# 0, so one component's sequence is isolated by XOR-ing two runs that differ only in it.
+# ---------------------------------------------------------------------------------------
+def _golden_taus():
+    import json
+    with open(os.path.join(HERE, "golden", "paper_values.json")) as f:
+        return json.load(f)["sec_III_C_algorithm_6_hybrid_taus"]
+
+
+def _outputs(orc, state, n):
+    st = np.array(state, np.uint32)
+    return np.array([orc.taus_next(st) for _ in range(n)], np.uint64)
+
+
+def _isolated(orc, comp, seed_word, lcg_seed, n):
+    state = [0, 0, 0, lcg_seed]
+    state[comp] = seed_word
+    return _outputs(orc, state, n) ^ _outputs(orc, [0, 0, 0, lcg_seed], n)
+
+
+def _bit_recurrence_words(seed_word, q, kms, s, mask, n):
+    """Words n = 1..n of the Tausworthe generator defined bit by bit: b_j = b_{j-k+q} xor
+    b_{j-k} (characteristic trinomial z^k + z^q + 1), word n = bits b_{ns} .. b_{ns+31}, most
+    significant first; b_0 .. b_{k-1} are the top k bits of the seed word."""
+    k = bin(mask).count("1")
+    assert mask == (0xFFFFFFFF << (32 - k)) & 0xFFFFFFFF and kms + s == k
+    bits = [(seed_word >> (31 - t)) & 1 for t in range(k)]
+    need = n * s + 32
+    while len(bits) < need:
+        j = len(bits)
+        bits.append(bits[j - k + q] ^ bits[j - k])
+    words = []
+    for m in range(1, n + 1):
+        w = 0
+        for t in range(32):
+            w = (w << 1) | bits[m * s + t]
+        words.append(w)
+    return np.array(words, np.uint64)
+
+
+@pytest.mark.parametrize("comp", [0, 1, 2])
+def test_taus_components_follow_their_recurrences(orc, comp):
+    g = _golden_taus()
+    q, kms, s, mask = g["tausworthe_q_kms_s_mask"][comp]
+    rng = np.random.default_rng(11 + comp)
+    for seed_word in [int(x) for x in rng.integers(1 << 28, 1 << 32, size=4)] + [0xFFFFFFFF]:
+        got = _isolated(orc, comp, seed_word, 12345, 200)
+        ref = _bit_recurrence_words(seed_word, q, kms, s, mask, 200)
+        assert np.array_equal(got, ref), (comp, seed_word)
+
+
+def test_taus_lcg_closed_form(orc):
+    g = _golden_taus()
+    a, c = g["lcg_a"], g["lcg_c"]
+    for y0 in (0, 1, 2 ** 31 + 7, 4294967295):
+        got = _outputs(orc, [0, 0, 0, y0], 300)
+        for n in (1, 2, 3, 17, 100, 299):
+            geom = (pow(a, n) - 1) // (a - 1)          # sum_{i<n} a^i, exact
+            ref = (pow(a, n, 1 << 32) * y0 + c * geom) % (1 << 32)
+            assert int(got[n - 1]) == ref, (y0, n)
+
+
+def test_taus_output_is_xor_of_components(orc):
+    st = [0x9E3779B9, 0x7F4A7C15, 0xF39CC060, 0x5CEDC834]
+    full = _outputs(orc, st, 100)
+    parts = [_outputs(orc, [st[0], 0, 0, 0], 100), _outputs(orc, [0, st[1], 0, 0], 100),
+             _outputs(orc, [0, 0, st[2], 0], 100), _outputs(orc, [0, 0, 0, 0], 100)]
+    lcg0 = parts[3]
+    comb = (parts[0] ^ lcg0) ^ (parts[1] ^ lcg0) ^ (parts[2] ^ lcg0) ^ _outputs(orc, [0, 0, 0, st[3]], 100)
+    assert np.array_equal(full, comb)
+
+
+def test_taus_uniforms_and_normals(orc):
+    g = _golden_taus()
+    st = np.array([0x12345678, 0x9ABCDEF0, 0x0FEDCBA9, 0x87654321], np.uint32)
+    u = _outputs(orc, st, 200000).astype(np.float64) * g["mult"]
+    assert stats.kstest(u, "uniform").pvalue > 1e-3
+    assert abs(u.mean() - 0.5) < 5 * math.sqrt(1 / 12 / len(u))
+    # the noise of one bead-step: Box-Muller of four successive outputs
+    s0 = np.array([0x12345678, 0x9ABCDEF0, 0x0FEDCBA9, 0x87654321], np.uint32)
+    x = _outputs(orc, s0, 4).astype(np.uint32)
+    m = orc.Model(np.array([[0.0, 0.0, 0.0]]), np.zeros(1, np.int32), np.zeros(1, np.int32))
+    m.set_taus_state(s0.reshape(1, 4))
+    F = np.zeros((1, 3))
+    x1 = m.ermak_update(np.zeros((1, 3)), F, seed=0, step=0)
+    amp = math.sqrt(2 * orc.kB() * 300.0 * 0.1 / 50.0)
+    assert np.allclose(x1[0], orc.box_muller(x) * amp, rtol=0, atol=1e-15)
+    st2 = s0.copy()
+    for _ in range(4):
+        orc.taus_next(st2)
+    assert np.array_equal(m.taus_state()[0], st2)

@@ -70,6 +70,14 @@ typedef enum {
                                 slots; the per-bead gathering is fused into the update */
 } sop_schedule;
 
+/* Source of the Gaussian random force (Sec. III.C). */
+typedef enum {
+    SOP_RNG_PHILOX = 0,       /* counter-based Philox4x32-10: key seed + replica, counter (step, bead); no state */
+    SOP_RNG_HYBRID_TAUS = 1   /* Hybrid Taus (Algorithm 6): three Tausworthe generators and an LCG per bead,
+                                 16 bytes of state each, four outputs per bead and step; a bead's generator
+                                 advances only in steps in which the bead moves */
+} sop_rng;
+
 typedef struct sop_ctx sop_ctx;
 
 /* Topology of one replica. Chains are contiguous bead ranges; systems are
@@ -104,6 +112,7 @@ typedef struct {
     int32_t pairs_per_bead; /* Verlet-list capacity per bead (0 = automatic) */
     int32_t schedule;       /* a sop_schedule */
     void *cuda_stream;      /* cudaStream_t to queue work on (NULL = default stream) */
+    int32_t rng;            /* a sop_rng (0 = Philox) */
 } sop_params;
 
 /* Cantilever on one system (Sec. IV.B): `anchor` is held fixed; a spring of
@@ -207,10 +216,24 @@ sop_status sop_get_native_map(sop_ctx *ctx, int32_t *row_ptr, int32_t *col, doub
 sop_status sop_get_observables(sop_ctx *ctx, sop_record *out, int64_t cap, int64_t *n_records, int64_t *n_lost);
 
 /* Checkpoint: the step counter, positions, compensation terms, pulling and
- * indenter set-up and status. Resuming from it continues bit-exactly.
+ * indenter set-up, status and the Hybrid Taus state (when used). Resuming from it
+ * continues bit-exactly.
  * With buf == NULL, *size receives the byte count needed. */
 sop_status sop_get_state(sop_ctx *ctx, void *buf, int64_t cap, int64_t *size);
 sop_status sop_set_state(sop_ctx *ctx, const void *buf, int64_t size);
+
+/* Hybrid Taus state of every bead of every replica (SOP_RNG_HYBRID_TAUS only):
+ * n_words = 4 * n_replicas * n_beads uint32 host words, replica-major, bead i of
+ * replica r at 4 (r n_beads + i), words (y1, y2, y3, y4). sop_create seeds them from
+ * params.seed with SplitMix64 (Steele, Lea, Flood, OOPSLA'14): for replica r and bead i
+ * the SplitMix64 state starts at ((seed + r) << 32) + i and two outputs give
+ * y1 y2 (first, low word first) and y3 y4 (second); y1 < 2, y2 < 8, y3 < 16 are raised
+ * by 2, 8, 16 (a Tausworthe component needs a nonzero top k bits).
+ * sop_set_rng_state rejects y1 < 2, y2 < 8 or y3 < 16 (SOP_ERR_INVALID_ARG);
+ * SOP_ERR_UNSUPPORTED when the context draws from Philox, SOP_ERR_CAPACITY when
+ * n_words is too small. The state is part of the checkpoint. */
+sop_status sop_get_rng_state(sop_ctx *ctx, uint32_t *state, int64_t n_words);
+sop_status sop_set_rng_state(sop_ctx *ctx, const uint32_t *state, int64_t n_words);
 
 /* Per-replica status ([n_replicas] int32 host): a sop_status value each. */
 sop_status sop_replica_status(sop_ctx *ctx, int32_t *out);

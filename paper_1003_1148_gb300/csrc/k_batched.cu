@@ -591,7 +591,14 @@ __global__ void __launch_bounds__(MAXT, MINB) k_batched(BatchedArgs a) {
                 // a bead whose force cannot be evaluated stays where it is; the replica freezes
                 cta_fail(L.h(), broken ? SOP_ERR_FENE_BREAK : SOP_ERR_INDENTER_OVERLAP);
             } else if (!(fl & kFlagFixed)) {
-                const float3 gn = bead_noise(sa.seed + (uint64_t)r, step, (uint32_t)(b0 + b));
+                float3 gn;
+                if (sa.taus) {   // Hybrid Taus: the bead's state in global memory (L2)
+                    uint4 st = sa.taus[gbase + b];
+                    gn = taus_noise(st);
+                    sa.taus[gbase + b] = st;
+                } else {
+                    gn = bead_noise(sa.seed + (uint64_t)r, step, (uint32_t)(b0 + b));
+                }
                 float4 c = L.comp()[b];
                 kahan_add(pb.x, c.x, fmaf(f.x + fe.x, sa.fp.mob, gn.x * sa.fp.amp));
                 kahan_add(pb.y, c.y, fmaf(f.y + fe.y, sa.fp.mob, gn.y * sa.fp.amp));

@@ -48,6 +48,7 @@ struct sop_ctx {
     int32_t *d_chain = nullptr, *d_sys = nullptr, *d_sys_lo = nullptr, *d_sys_ree_last = nullptr,
             *d_sys_nat_pairs = nullptr;
     uint8_t *d_flags = nullptr;
+    uint4 *d_taus = nullptr;   // Hybrid Taus state per bead (SOP_RNG_HYBRID_TAUS)
     float *d_bond_r0 = nullptr;
     double *d_bond_r0d = nullptr;
     int32_t *d_nat_row = nullptr, *d_nat_col = nullptr;
@@ -548,7 +549,30 @@ sop_status validate_params(const sop_params *p) {
         return fail(nullptr, SOP_ERR_INVALID_ARG, "params: obs_every, obs_capacity, pairs_per_bead >= 0");
     if (p->schedule < SOP_SCHED_AUTO || p->schedule > SOP_SCHED_PAIRS)
         return fail(nullptr, SOP_ERR_INVALID_ARG, "params: unknown schedule");
+    if (p->rng != SOP_RNG_PHILOX && p->rng != SOP_RNG_HYBRID_TAUS)
+        return fail(nullptr, SOP_ERR_INVALID_ARG, "params: unknown rng");
     return SOP_OK;
+}
+
+// SplitMix64 (Steele, Lea, Flood, OOPSLA'14): advance the Weyl state, mix the result.
+uint64_t splitmix64(uint64_t &x) {
+    uint64_t z = (x += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// Initial Hybrid Taus state of bead i of replica r (see sop_get_rng_state).
+void taus_seed(uint64_t seed, int r, int i, uint32_t out[4]) {
+    uint64_t x = ((seed + (uint64_t)r) << 32) + (uint64_t)(uint32_t)i;
+    const uint64_t a = splitmix64(x), b = splitmix64(x);
+    out[0] = (uint32_t)a;
+    out[1] = (uint32_t)(a >> 32);
+    out[2] = (uint32_t)b;
+    out[3] = (uint32_t)(b >> 32);
+    if (out[0] < 2u) out[0] += 2u;
+    if (out[1] < 8u) out[1] += 8u;
+    if (out[2] < 16u) out[2] += 16u;
 }
 
 sop_status alloc_pull_arrays(sop_ctx *c, size_t n_pull) {
@@ -773,6 +797,7 @@ sop_status tune_bucket(sop_ctx *c, sop_ctx::Bucket &bk) {
                 a.comp = sc;
                 a.snap = ss;
                 a.sa.rep_status = sst;
+                a.sa.taus = nullptr;   // trials draw Philox noise: the run's Taus state is untouched
                 a.obs_every = 0;
                 a.n_items = trial_items;
                 a.n_steps = 20;
@@ -1135,6 +1160,17 @@ sop_status create_impl(sop_ctx *c, const sop_topology *topo, const double *xyz, 
     a.d_step = c->d_step;
     a.rep_status = c->d_rep_status;
     a.halt = c->d_halt;
+    if (p->rng == SOP_RNG_HYBRID_TAUS) {
+        std::vector<uint4> st((size_t)R * n);
+        for (int r = 0; r < R; ++r)
+            for (int i = 0; i < n; ++i) {
+                uint32_t w[4];
+                taus_seed(p->seed, r, i, w);
+                st[(size_t)r * n + i] = make_uint4(w[0], w[1], w[2], w[3]);
+            }
+        CUDA_OR_RETURN(c, upload(c, &c->d_taus, st));
+    }
+    a.taus = c->d_taus;
     sync_external(c);
     // ---- the first Verlet list (streamed builder; also fills the snapshot)
     s = rebuild_streamed(c);
@@ -1568,13 +1604,13 @@ sop_status sop_get_state(sop_ctx *c, void *buf, int64_t cap, int64_t *size) {
     const size_t np = c->pull_bead.size();
     const size_t need = 16 * sizeof(int64_t) + 3 * RN * sizeof(float4) + c->R * sizeof(int32_t) +
                         np * (3 * sizeof(int32_t) + 6 * sizeof(double)) + 3 * np * c->R * sizeof(double) +
-                        9 * sizeof(double);
+                        9 * sizeof(double) + (c->d_taus ? RN * sizeof(uint4) : 0);
     *size = (int64_t)need;
     if (!buf) return SOP_OK;
     if (cap < (int64_t)need) return fail(c, SOP_ERR_CAPACITY, "buffer too small");
     char *p = static_cast<char *>(buf);
     int64_t hdr[16] = {0x534f5031, SOP_ABI_VERSION, c->n, c->R, c->step, c->list_step, (int64_t)np,
-                       c->has_ind ? 1 : 0, c->events, c->consumed, 0, 0, 0, 0, 0, 0};
+                       c->has_ind ? 1 : 0, c->events, c->consumed, c->d_taus ? 1 : 0, 0, 0, 0, 0, 0};
     std::memcpy(p, hdr, sizeof hdr);
     p += sizeof hdr;
     CUDA_OR_RETURN(c, cudaMemcpyAsync(p, c->d_pos[c->cur], RN * sizeof(float4), cudaMemcpyDeviceToHost, c->stream));
@@ -1585,6 +1621,9 @@ sop_status sop_get_state(sop_ctx *c, void *buf, int64_t cap, int64_t *size) {
     p += RN * sizeof(float4);
     CUDA_OR_RETURN(c, cudaMemcpyAsync(p, c->d_rep_status, c->R * sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
     p += c->R * sizeof(int32_t);
+    if (c->d_taus)   // after the fixed-size part: at the end of the buffer
+        CUDA_OR_RETURN(c, cudaMemcpyAsync(static_cast<char *>(buf) + need - RN * sizeof(uint4), c->d_taus,
+                                          RN * sizeof(uint4), cudaMemcpyDeviceToHost, c->stream));
     CUDA_OR_RETURN(c, cudaStreamSynchronize(c->stream));
     auto put = [&p](const void *src, size_t bytes) { if (bytes) std::memcpy(p, src, bytes); p += bytes; };
     put(c->pull_sys.data(), np * sizeof(int32_t));
@@ -1611,10 +1650,16 @@ sop_status sop_set_state(sop_ctx *c, const void *buf, int64_t size) {
         return fail(c, SOP_ERR_INVALID_ARG, "state does not match this context");
     const size_t RN = (size_t)c->R * c->n;
     const size_t np = (size_t)hdr[6];
+    if ((hdr[10] != 0) != (c->d_taus != nullptr))
+        return fail(c, SOP_ERR_INVALID_ARG, "state: noise source differs from this context");
     const size_t need = 16 * sizeof(int64_t) + 3 * RN * sizeof(float4) + c->R * sizeof(int32_t) +
                         np * (3 * sizeof(int32_t) + 6 * sizeof(double)) + 3 * np * c->R * sizeof(double) +
-                        9 * sizeof(double);
+                        9 * sizeof(double) + (c->d_taus ? RN * sizeof(uint4) : 0);
     if (size < (int64_t)need) return fail(c, SOP_ERR_INVALID_ARG, "state buffer truncated");
+    CUDA_OR_RETURN(c, cudaStreamSynchronize(c->stream));   // no queued work may still use the state
+    if (c->d_taus)
+        CUDA_OR_RETURN(c, cudaMemcpy(c->d_taus, static_cast<const char *>(buf) + need - RN * sizeof(uint4),
+                                     RN * sizeof(uint4), cudaMemcpyHostToDevice));
     p += sizeof hdr;
     c->cur = 0;
     CUDA_OR_RETURN(c, cudaMemcpy(c->d_pos[0], p, RN * sizeof(float4), cudaMemcpyHostToDevice));
@@ -1666,6 +1711,31 @@ sop_status sop_set_state(sop_ctx *c, const void *buf, int64_t size) {
     rebuild_list(c, c->d_snap, nullptr, full_range(c), &c->st.kernel_launches);
     c->list_step = hdr[5];
     CUDA_OR_RETURN(c, cudaStreamSynchronize(c->stream));
+    return SOP_OK;
+}
+
+sop_status sop_get_rng_state(sop_ctx *c, uint32_t *state, int64_t n_words) {
+    if (!c) return fail(nullptr, SOP_ERR_INVALID_ARG, "ctx is NULL");
+    if (!c->d_taus) return fail(c, SOP_ERR_UNSUPPORTED, "the context draws its noise from Philox (no state)");
+    const size_t RN = (size_t)c->R * c->n;
+    if (!state) return fail(c, SOP_ERR_INVALID_ARG, "state is NULL");
+    if (n_words < (int64_t)(4 * RN)) return fail(c, SOP_ERR_CAPACITY, "state buffer too small");
+    CUDA_OR_RETURN(c, cudaMemcpyAsync(state, c->d_taus, RN * sizeof(uint4), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_OR_RETURN(c, cudaStreamSynchronize(c->stream));
+    return SOP_OK;
+}
+
+sop_status sop_set_rng_state(sop_ctx *c, const uint32_t *state, int64_t n_words) {
+    if (!c) return fail(nullptr, SOP_ERR_INVALID_ARG, "ctx is NULL");
+    if (!c->d_taus) return fail(c, SOP_ERR_UNSUPPORTED, "the context draws its noise from Philox (no state)");
+    const size_t RN = (size_t)c->R * c->n;
+    if (!state) return fail(c, SOP_ERR_INVALID_ARG, "state is NULL");
+    if (n_words < (int64_t)(4 * RN)) return fail(c, SOP_ERR_CAPACITY, "state buffer too small");
+    for (size_t k = 0; k < RN; ++k)
+        if (state[4 * k] < 2u || state[4 * k + 1] < 8u || state[4 * k + 2] < 16u)
+            return fail(c, SOP_ERR_INVALID_ARG, "Hybrid Taus state needs y1 >= 2, y2 >= 8, y3 >= 16");
+    CUDA_OR_RETURN(c, cudaStreamSynchronize(c->stream));
+    CUDA_OR_RETURN(c, cudaMemcpy(c->d_taus, state, RN * sizeof(uint4), cudaMemcpyHostToDevice));
     return SOP_OK;
 }
 

@@ -68,6 +68,28 @@ __device__ __forceinline__ float3 bead_noise(uint64_t seed, int64_t step, uint32
     return box_muller3(philox4x32_10(ctr, (uint32_t)seed, (uint32_t)(seed >> 32)));
 }
 
+// Hybrid Taus (Algorithm 6): three Tausworthe components in L'Ecuyer's shift form
+// b = ((y << q) ^ y) >> (k - s), y = ((y & mask) << s) ^ b with (q, k - s, s, mask) =
+// (13, 19, 12, 0xFFFFFFFE), (2, 25, 4, 0xFFFFFFF8), (3, 11, 17, 0xFFFFFFF0), and the LCG
+// y4 = 1664525 y4 + 1013904223 (mod 2^32); the output is y1 ^ y2 ^ y3 ^ y4.
+__device__ __forceinline__ uint32_t taus_next(uint4 &s) {
+    s.x = (((s.x & 0xFFFFFFFEu) << 12) ^ (((s.x << 13) ^ s.x) >> 19));
+    s.y = (((s.y & 0xFFFFFFF8u) << 4) ^ (((s.y << 2) ^ s.y) >> 25));
+    s.z = (((s.z & 0xFFFFFFF0u) << 17) ^ (((s.z << 3) ^ s.z) >> 11));
+    s.w = 1664525u * s.w + 1013904223u;
+    return s.x ^ s.y ^ s.z ^ s.w;
+}
+
+// Three normals from four successive outputs, mapped like one Philox block.
+__device__ __forceinline__ float3 taus_noise(uint4 &s) {
+    uint4 x;
+    x.x = taus_next(s);
+    x.y = taus_next(s);
+    x.z = taus_next(s);
+    x.w = taus_next(s);
+    return box_muller3(x);
+}
+
 // Physical constants of one run, FP32 copies for the force loop.
 struct ForceParams {
     float k_fene;     // k

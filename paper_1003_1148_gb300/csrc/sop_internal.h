@@ -63,6 +63,7 @@ struct StepArgs {
     const int64_t *d_step = nullptr;   // device step counter (step of the first kernel of a sequence)
     int32_t *rep_status = nullptr;     // [R]
     int32_t *halt = nullptr;           // [1] nonzero: every kernel copies state through
+    uint4 *taus = nullptr;             // [R*n] Hybrid Taus state per bead; null: Philox noise
 };
 
 // Streamed-schedule Verlet list (row starts are arbitrary; rows are sorted).

@@ -56,7 +56,7 @@ __device__ __forceinline__ float3 external_force(const StepArgs &a, int r, int i
 // The end of one step for bead i of replica r (global index gb) given the sum f of its
 // pair forces at layer P: a broken bond or an indenter overlap leaves the bead where it
 // is and marks the replica; a fixed bead stays; otherwise r += F h/zeta + g sqrt(2kTh/zeta)
-// with the FP32 compensation of the bead.
+// with the FP32 compensation of the bead, g from Philox or from the bead's Hybrid Taus state.
 __device__ __forceinline__ void advance_bead(const StepArgs &a, int r, int i, int gb, const float4 *P, float3 f,
                                              bool broken, int64_t step, float4 *pos_out, float4 *comp) {
     float4 pi = P[i];
@@ -76,7 +76,14 @@ __device__ __forceinline__ void advance_bead(const StepArgs &a, int r, int i, in
         pos_out[gb] = pi;
         return;
     }
-    const float3 g = bead_noise(a.seed + (uint64_t)r, step, (uint32_t)i);
+    float3 g;
+    if (a.taus) {
+        uint4 st = a.taus[gb];
+        g = taus_noise(st);
+        a.taus[gb] = st;
+    } else {
+        g = bead_noise(a.seed + (uint64_t)r, step, (uint32_t)i);
+    }
     float4 c = comp[gb];
     kahan_add(pi.x, c.x, fmaf(f.x + fe.x, a.fp.mob, g.x * a.fp.amp));
     kahan_add(pi.y, c.y, fmaf(f.y + fe.y, a.fp.mob, g.y * a.fp.amp));

@@ -32,7 +32,10 @@ SCHEDULES = {"auto": SCHED_AUTO, "batched": SCHED_BATCHED, "streamed": SCHED_STR
 EXPORTED = ["sop_create", "sop_step", "sop_forces", "sop_pairlist_rebuild", "sop_pull", "sop_indenter",
             "sop_get_positions", "sop_set_positions", "sop_get_pairlist", "sop_get_native_map",
             "sop_get_observables", "sop_get_state", "sop_set_state", "sop_replica_status", "sop_abort",
-            "sop_get_stats", "sop_last_error", "sop_destroy", "sop_pairlist_build_noalloc"]
+            "sop_get_stats", "sop_last_error", "sop_destroy", "sop_pairlist_build_noalloc", "sop_get_rng_state",
+            "sop_set_rng_state"]
+RNG_PHILOX, RNG_HYBRID_TAUS = 0, 1
+RNGS = {"philox": RNG_PHILOX, "taus": RNG_HYBRID_TAUS}
 
 
 class SopError(RuntimeError):
@@ -53,7 +56,7 @@ class Params(C.Structure):
                 ("dt", C.c_double), ("pair_cut", C.c_double), ("rebuild_every", C.c_int32),
                 ("n_replicas", C.c_int32), ("seed", C.c_uint64), ("obs_every", C.c_int32),
                 ("obs_capacity", C.c_int32), ("pairs_per_bead", C.c_int32), ("schedule", C.c_int32),
-                ("cuda_stream", C.c_void_p)]
+                ("cuda_stream", C.c_void_p), ("rng", C.c_int32)]
 
 
 class PullParams(C.Structure):
@@ -107,6 +110,8 @@ def load(path: str | None = None):
             "sop_last_error": ([vp], C.c_char_p),
             "sop_destroy": ([vp], None),
             "sop_pairlist_build_noalloc": ([vp, i32, vp, vp, vp, f64, vp, vp, vp, i64, vp, vp], C.c_int),
+            "sop_get_rng_state": ([vp, vp, i64], C.c_int),
+            "sop_set_rng_state": ([vp, vp, i64], C.c_int),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -138,7 +143,8 @@ class Simulation:
     """
 
     def __init__(self, native_xyz, chain_offsets, system_offsets=None, fixed=None, params=None, n_replicas=1,
-                 seed=0, obs_every=0, obs_capacity=0, pairs_per_bead=0, schedule="auto", stream=None):
+                 seed=0, obs_every=0, obs_capacity=0, pairs_per_bead=0, schedule="auto", stream=None,
+                 rng="philox"):
         L = load()
         self._L = L
         xyz = np.ascontiguousarray(native_xyz, np.float64).reshape(-1, 3)
@@ -155,7 +161,8 @@ class Simulation:
         sched = SCHEDULES[schedule] if isinstance(schedule, str) else int(schedule)
         prm = Params(p["k_fene"], p["R0"], p["eps_h"], p["native_cut"], p["eps_l"], p["sigma"], p["T"], p["zeta"],
                      p["dt"], p["pair_cut"], int(p["rebuild_every"]), self.R, int(seed), int(obs_every),
-                     int(obs_capacity), int(pairs_per_bead), sched, _stream_handle(stream))
+                     int(obs_capacity), int(pairs_per_bead), sched, _stream_handle(stream),
+                     RNGS[rng] if isinstance(rng, str) else int(rng))
         self.params = p
         self.obs_every = int(obs_every)
         ctx = C.c_void_p()
@@ -192,6 +199,18 @@ class Simulation:
         if raise_on_error:
             self._check(rc)
         return rc
+
+    def get_rng_state(self):
+        """Hybrid Taus state [R, n, 4] uint32 (contexts created with rng="taus")."""
+        out = np.zeros((self.R, self.n, 4), np.uint32)
+        self._check(self._L.sop_get_rng_state(self._ctx, _ptr(out), out.size))
+        return out
+
+    def set_rng_state(self, state):
+        a = np.ascontiguousarray(state, np.uint32)
+        if a.size != self.R * self.n * 4:
+            raise ValueError(f"expected {self.R * self.n * 4} words, got {a.size}")
+        self._check(self._L.sop_set_rng_state(self._ctx, _ptr(a), a.size))
 
     def forces(self, replica: int = 0):
         """(F [n,3] FP64 from FP32 arithmetic, energy FP64) at the current positions."""

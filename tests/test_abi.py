@@ -38,13 +38,31 @@ def test_binding_covers_the_abi():
     assert sorted(sop.EXPORTED) == declared_functions()
 
 
-def test_struct_layouts_match_header():
-    # field order and sizes of the ctypes mirrors follow the header's structs
+def test_struct_layouts_match_header(tmp_path):
+    """Size and every field offset of the ctypes mirrors equal what a C compiler lays out
+    from include/sop.h."""
+    import subprocess
     from paper_1003_1148_gb300 import sop
-    assert ctypes.sizeof(sop.Record) == 8 * 8
-    assert ctypes.sizeof(sop.PullParams) == 4 * 3 + 4 + 8 * 2
-    assert ctypes.sizeof(sop.Params) == 10 * 8 + 2 * 4 + 8 + 4 * 4 + 8
-    assert ctypes.sizeof(sop.Topology) == 8 + 8 + 8 + 8 + 8
+    mirrors = {"sop_topology": sop.Topology, "sop_params": sop.Params, "sop_pull_params": sop.PullParams,
+               "sop_record": sop.Record, "sop_stats": sop.Stats}
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "sop.h"', "int main(void) {"]
+    for cname, py in mirrors.items():
+        lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
+        for f, _ in py._fields_:
+            lines.append(f'printf("{cname} {f} %zu\\n", offsetof({cname}, {f}));')
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), "-o", str(exe), str(src)])
+    got = {}
+    for line in subprocess.check_output([str(exe)], text=True).splitlines():
+        c, f, v = line.split()
+        got[(c, f)] = int(v)
+    for cname, py in mirrors.items():
+        assert got[(cname, "size")] == ctypes.sizeof(py), cname
+        for f, _ in py._fields_:
+            assert got[(cname, f)] == getattr(py, f).offset, (cname, f)
 
 
 def test_create_rejects_bad_input_without_gpu_work(lib):

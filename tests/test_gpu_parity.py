@@ -262,6 +262,8 @@ def test_pair_based_is_deterministic_and_close_to_particle_based(sop, synth):
     xa, xb, xc = a.get_positions(-1), b.get_positions(-1), c.get_positions(-1)
     assert np.array_equal(xa, xb)
     assert float(np.sqrt(((xa - xc) ** 2).sum(-1).mean())) <= RMS_TOL
+    # forces of both forms at the same positions
+    c.set_positions(xa, replica=-1)
     Fa, Ea = a.forces(1)
     Fc, Ec = c.forces(1)
     assert Ea == pytest.approx(Ec, rel=1e-12)

@@ -18,8 +18,8 @@ closed form, Box-Muller
 invariants and moments, the exactly solvable Brownian particle (Eqs. 3-4) and
 the free-diffusion law.
 """
-from .oracle import (Model, box_muller, build, bonds, kB, native_pairs, noise, philox, taus_next, OracleError,
-                     model_from_workload)
+from .oracle import (Model, Ramp, box_muller, box_muller4, build, bonds, kB, native_pairs, noise, philox,
+                     taus_next, OracleError, model_from_workload)
 
-__all__ = ["Model", "box_muller", "build", "bonds", "kB", "native_pairs", "noise", "philox", "taus_next",
+__all__ = ["Model", "Ramp", "box_muller", "box_muller4", "build", "bonds", "kB", "native_pairs", "noise", "philox", "taus_next",
            "OracleError", "model_from_workload"]

@@ -84,6 +84,13 @@ def _L():
             L.orc_philox4x32_10.argtypes = [vp, vp, vp]
             L.orc_box_muller.argtypes = [vp, vp]
             L.orc_noise.argtypes = [u64, i64, i32, vp]
+            L.orc_ramp_theory.argtypes = [vp, f64]
+            L.orc_ramp_theory.restype = f64
+            L.orc_ramp_mean.argtypes = [vp, i64]
+            L.orc_ramp_mean.restype = f64
+            L.orc_box_muller4.argtypes = [vp, vp]
+            L.orc_ramp_run.argtypes = [vp, u64, i64, i64]
+            L.orc_ramp_run.restype = f64
             L.orc_taus_next.argtypes = [vp]
             L.orc_taus_next.restype = C.c_uint32
             L.orc_taus_noise.argtypes = [vp, vp]
@@ -283,6 +290,38 @@ class Model:
         if rc and raise_on_error:
             raise OracleError(rc, f"at step {fail.value}")
         return xyz, obs[:n_obs.value].copy(), rc, fail.value
+
+
+class _Ramp(C.Structure):
+    _fields_ = [("K", C.c_double), ("xi", C.c_double), ("kT", C.c_double), ("h", C.c_double),
+                ("r_f", C.c_double), ("X0", C.c_double), ("order", C.c_int32)]
+
+
+class Ramp:
+    """The harmonic Brownian particle under a ramp force of Sec. IV.C (any consistent units)."""
+
+    def __init__(self, K, xi, kT, h, r_f, X0=0.0, order=1):
+        self._p = _Ramp(float(K), float(xi), float(kT), float(h), float(r_f), float(X0), int(order))
+        self.K, self.xi, self.kT, self.h, self.r_f, self.X0, self.order = K, xi, kT, h, r_f, X0, order
+
+    def theory(self, t: float) -> float:
+        """Eq. 3."""
+        return _L().orc_ramp_theory(C.byref(self._p), float(t))
+
+    def mean(self, n: int) -> float:
+        """Eq. 4 (order 1) or Eq. 5 (order 2) iterated n steps."""
+        return _L().orc_ramp_mean(C.byref(self._p), int(n))
+
+    def run(self, seed: int, run: int, n_steps: int) -> float:
+        """X after n_steps of stochastic run `run`."""
+        return _L().orc_ramp_run(C.byref(self._p), int(seed), int(run), int(n_steps))
+
+
+def box_muller4(x):
+    x = np.ascontiguousarray(x, np.uint32)
+    g = np.zeros(4)
+    _L().orc_box_muller4(_p(x), _p(g))
+    return g
 
 
 def taus_next(state):

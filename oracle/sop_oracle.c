@@ -26,6 +26,8 @@
  *   orc_ermak_update              Algorithm 7 (the first-order Ermak-McCammon
  *                                 update, Eq. 2)
  *   orc_run                       the step sequence of Fig. 2 / Sec. III.D
+ *   orc_ramp_*                    Sec. IV.C: the harmonic Brownian particle under a
+ *                                 ramp force, Eqs. 3, 4 and 5
  *
  * Readings where the paper is silent or garbled (each also listed in the
  * design notes): the integrator follows Algorithm 7 (r += f h/xi + g
@@ -516,6 +518,60 @@ void orc_ermak_update(const orc_model *m, double *xyz, const double *F, uint64_t
         else orc_noise(seed, step, i + m->noise_offset, g);
         for (int k = 0; k < 3; ++k) xyz[3 * i + k] = xyz[3 * i + k] + F[3 * i + k] * mob + g[k] * amp;
     }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Integrator accuracy: Sec. IV.C, Eqs. 3-5                                  */
+/* ------------------------------------------------------------------------ */
+double orc_ramp_theory(const orc_ramp *p, double t) {
+    double tau = p->xi / p->K;
+    double e = exp(-t / tau);
+    return p->X0 * e + p->r_f * tau / p->xi * (t - tau * (1.0 - e));
+}
+
+/* drift of one step at X and t_n: Eq. 4's increment, plus Eq. 5's h^2 term (order 2),
+ * plus the h^2 term of the ramp's own time derivative (order 3: the full Taylor step
+ * X'' h^2 / 2 with X'' = r_f / xi - X' / tau) */
+static double ramp_drift(const orc_ramp *p, double X, double t) {
+    double tau = p->xi / p->K;
+    double d = (p->r_f * t / p->xi - X / tau) * p->h;
+    if (p->order >= 2) d += (X / (2.0 * tau * tau) - p->r_f * t / (2.0 * tau * p->xi)) * p->h * p->h;
+    if (p->order == 3) d += p->r_f / (2.0 * p->xi) * p->h * p->h;
+    return d;
+}
+
+double orc_ramp_mean(const orc_ramp *p, int64_t n) {
+    double X = p->X0;
+    for (int64_t k = 0; k < n; ++k) X = X + ramp_drift(p, X, (double)k * p->h);
+    return X;
+}
+
+void orc_box_muller4(const uint32_t x[4], double g[4]) {
+    const double two_m32 = 1.0 / 4294967296.0;
+    const double two_pi = 6.283185307179586476925286766559;
+    double ra = sqrt(-2.0 * log(((double)x[0] + 1.0) * two_m32));
+    double rb = sqrt(-2.0 * log(((double)x[2] + 1.0) * two_m32));
+    g[0] = ra * cos(two_pi * (double)x[1] * two_m32);
+    g[1] = ra * sin(two_pi * (double)x[1] * two_m32);
+    g[2] = rb * cos(two_pi * (double)x[3] * two_m32);
+    g[3] = rb * sin(two_pi * (double)x[3] * two_m32);
+}
+
+double orc_ramp_run(const orc_ramp *p, uint64_t seed, int64_t run, int64_t n_steps) {
+    double amp = sqrt(2.0 * p->kT * p->h / p->xi);
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    double X = p->X0, g[4] = {0, 0, 0, 0};
+    for (int64_t n = 0; n < n_steps; ++n) {
+        if (n % 4 == 0) {
+            uint64_t b = (uint64_t)(n / 4);
+            uint32_t ctr[4] = {(uint32_t)b, (uint32_t)(b >> 32), (uint32_t)run, 1u};
+            uint32_t x[4];
+            orc_philox4x32_10(ctr, key, x);
+            orc_box_muller4(x, g);
+        }
+        X = X + ramp_drift(p, X, (double)n * p->h) + amp * g[n % 4];
+    }
+    return X;
 }
 
 /* ------------------------------------------------------------------------ */

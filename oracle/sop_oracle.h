@@ -136,6 +136,31 @@ void orc_noise(uint64_t seed, int64_t step, int32_t bead, double g[3]);
  * the bead's Hybrid Taus state when m->taus is set (only moved beads draw). */
 void orc_ermak_update(const orc_model *m, double *xyz, const double *F, uint64_t seed, int64_t step);
 
+/* Accuracy of the integrator (Sec. IV.C): a Brownian particle in the harmonic
+ * potential K X^2 / 2 driven by the ramp force r_f t, started at X0 (the reading:
+ * the minimum is at 0 and X0 is the start, as Eqs. 3-5 have it). tau = xi / K. */
+typedef struct {
+    double K, xi, kT, h, r_f, X0;
+    int32_t order;                   /* 1: Eq. 4; 2: Eq. 5 as printed; 3: Eq. 5 with the r_f h^2 / (2 xi)
+                                        term of the second-order Taylor step, which the printed
+                                        equation lacks (without it the scheme is first order) */
+} orc_ramp;
+
+/* Eq. 3: X0 e^(-t/tau) + (r_f tau / xi)(t - tau (1 - e^(-t/tau))). */
+double orc_ramp_theory(const orc_ramp *p, double t);
+
+/* The mean after n steps: Eq. 4 (or Eq. 5) iterated from X0 with t_n = n h. */
+double orc_ramp_mean(const orc_ramp *p, int64_t n);
+
+/* Four standard normals from one Philox block (Box-Muller on (x0, x1) and (x2, x3),
+ * cosine then sine of each pair). */
+void orc_box_muller4(const uint32_t x[4], double g[4]);
+
+/* One stochastic run (`run` = its index): X += drift_n + sqrt(2 kT h / xi) g_n, with
+ * g_n normal n % 4 of the Philox block of key seed, counter (n/4 lo, n/4 hi, run, 1).
+ * Returns X after n_steps. */
+double orc_ramp_run(const orc_ramp *p, uint64_t seed, int64_t run, int64_t n_steps);
+
 /* Observables of every system at positions xyz and step `step`. Per system 8
  * doubles: step, system, energy (Eq. 1 over the list), external force along its
  * direction, extension, fraction of native contacts Q, end-to-end distance of

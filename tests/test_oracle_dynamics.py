@@ -167,3 +167,73 @@ def test_fene_break_is_reported(orc):
     far = np.array([[0.0, 0, 0], [3.8 + 2.5, 0, 0]])
     xr, obs, rc, fail = m.run(far, 5, seed=1, raise_on_error=False)
     assert rc == 3 and fail == 0
+
+
+# ---------------------------------------------------------------------------------------
+# Sec. IV.C experiment functions (orc_ramp_*): the mean recursion against the closed
+# form of a linear recursion (exact rationals), the order of Eqs. 4 and 5 against Eq. 3,
+# and the stochastic run's noise stream and moments.
+# ---------------------------------------------------------------------------------------
+def _recursion_closed_form(K, xi, h, r_f, X0, order, n):
+    """X_n of X_{k+1} = a X_k + b k + c (t_k = k h) in exact rationals:
+    X_n = a^n X0 + b (a^n - n a + n - 1) / (1 - a)^2 + c (1 - a^n) / (1 - a)."""
+    from fractions import Fraction as Fr
+    K, xi, h, r_f, X0 = (Fr(v) for v in (K, xi, h, r_f, X0))
+    tau = xi / K
+    a = 1 - h / tau
+    b = r_f * h * h / xi
+    c = Fr(0)
+    if order >= 2:
+        a += h * h / (2 * tau * tau)
+        b *= 1 - h / (2 * tau)
+    if order == 3:
+        c = r_f * h * h / (2 * xi)
+    an = a ** n
+    return float(an * X0 + b * (an - n * a + n - 1) / (1 - a) ** 2 + c * (1 - an) / (1 - a))
+
+
+@pytest.mark.parametrize("order", [1, 2, 3])
+def test_ramp_mean_recursion_closed_form(orc, order):
+    K, xi, h, r_f, X0 = 0.5, 8.0, 0.25, 0.125, 1.5       # binary fractions: exact inputs
+    r = orc.Ramp(K, xi, 0.0, h, r_f, X0, order)
+    for n in (1, 2, 3, 50, 400):
+        ref = _recursion_closed_form(K, xi, h, r_f, X0, order, n)
+        assert r.mean(n) == pytest.approx(ref, rel=1e-12, abs=1e-14), (order, n)
+
+
+@pytest.mark.parametrize("order,ratio", [(1, 2.0), (2, 2.0), (3, 4.0)])
+def test_ramp_scheme_order_against_eq3(orc, order, ratio):
+    """Halving h divides the error against Eq. 3 by 2 for Eq. 4 and for Eq. 5 as printed
+    (its h^2 term lacks the ramp's r_f h^2 / (2 xi), so it stays first order), and by 4 for
+    the complete second-order Taylor step."""
+    K, xi, r_f, X0, t = 1.0, 10.0, 0.3, 2.0, 25.0
+    errs = []
+    for h in (0.05, 0.025, 0.0125):
+        r = orc.Ramp(K, xi, 0.0, h, r_f, X0, order)
+        errs.append(abs(r.mean(int(round(t / h))) - r.theory(t)))
+    for e0, e1 in zip(errs, errs[1:]):
+        assert e0 / e1 == pytest.approx(ratio, rel=0.05), (order, errs)
+
+
+def test_ramp_run_noise_stream_and_moments(orc):
+    # noise-free run = the mean recursion
+    r0 = orc.Ramp(1.0, 10.0, 0.0, 0.1, 0.3, 0.5, 1)
+    assert r0.run(7, 3, 333) == r0.mean(333)
+    # one step from X0 = 0 at t = 0 is the first normal of block 0 of this run's stream
+    r = orc.Ramp(1.0, 10.0, 0.6, 0.1, 0.3, 0.0, 1)
+    amp = math.sqrt(2 * 0.6 * 0.1 / 10.0)
+    for run in (0, 5):
+        x = orc.philox([0, 0, run, 1], [11, 0])
+        g = orc.box_muller4(x)
+        assert r.run(11, run, 1) == pytest.approx(amp * g[0], rel=1e-15)
+        g3 = orc.box_muller(x)
+        assert np.allclose(g[:3], g3, rtol=0, atol=0)
+        u3 = (float(x[2]) + 1.0) / 2 ** 32
+        assert g[2] ** 2 + g[3] ** 2 == pytest.approx(-2 * math.log(u3), rel=1e-12)
+    # ensemble: mean = recursion, variance = sigma^2 (1 - a^(2n)) / (1 - a^2)
+    n, runs = 120, 3000
+    xs = np.array([r.run(11, k, n) for k in range(runs)])
+    a = 1 - 0.1 / 10.0
+    var = amp ** 2 * (1 - a ** (2 * n)) / (1 - a * a)
+    assert abs(xs.mean() - r.mean(n)) < 4 * math.sqrt(var / runs)
+    assert xs.var(ddof=1) == pytest.approx(var, rel=4 * math.sqrt(2 / (runs - 1)))

@@ -380,7 +380,8 @@ def run_ours(args):
                     "steps": e2e_steps},
             "gpu_launches": launches, "wall_s_timed_region": wall,
             "clocks": {"sm_mhz": clocks["sm_mhz"], "sm_max_mhz": clocks["sm_max_mhz"], "reasons": clocks["reasons"]},
-            "roofline": roofline, "cpu_baseline": cpu, "plain_per_chain": plain, "force_err_vs_fp64": ferr}
+            "roofline": roofline, "cpu_baseline": cpu, "plain_per_chain": plain, "force_err_vs_fp64": ferr,
+            "replicas_failed": int(np.count_nonzero(sim.replica_status()))}
     print(json.dumps(line))
     sim.close()
     return 0

@@ -235,6 +235,41 @@ sop_status sop_set_state(sop_ctx *ctx, const void *buf, int64_t size);
 sop_status sop_get_rng_state(sop_ctx *ctx, uint32_t *state, int64_t n_words);
 sop_status sop_set_rng_state(sop_ctx *ctx, const uint32_t *state, int64_t n_words);
 
+/* Accuracy of the first-order integrator (Sec. IV.C): n_runs independent Brownian
+ * particles in the harmonic potential K X^2 / 2 (minimum at 0) driven by the ramp force
+ * r_f t, started at X0 and advanced n_steps steps of
+ *     X += (r_f t_n / xi - X / tau) h  [+ (X / (2 tau^2) - r_f t_n / (2 tau xi)) h^2]
+ *          [+ r_f h^2 / (2 xi)] + sqrt(2 kT h / xi) g_n,     t_n = n h, tau = xi / K,
+ * the first bracket for order >= 2 (Eq. 5 as printed), the second for order 3 (the
+ * complete second-order Taylor step; Eq. 5 as printed lacks it and is first-order
+ * accurate). FP32 arithmetic with a compensated (Kahan) position, one thread per run.
+ * Noise: Philox4x32-10, key = seed, counter = (n/4 lo, n/4 hi, run, 1); step n takes
+ * normal n mod 4 of its block (Box-Muller on (x0, x1) and (x2, x3), cosine then sine).
+ * Units are the caller's (any consistent set). */
+typedef struct {
+    double K;          /* spring constant, > 0 */
+    double xi;         /* friction, > 0 */
+    double kT;         /* thermal energy, >= 0 (0: no noise) */
+    double h;          /* time step, > 0 */
+    double r_f;        /* loading rate of the ramp force */
+    double X0;         /* position at t = 0 */
+    int64_t n_runs;    /* 1 .. 2^31 - 1 */
+    int64_t n_steps;   /* >= 1 */
+    int32_t order;     /* 1, 2 or 3 */
+    int32_t n_out;     /* checkpoints, 1 .. n_steps: after steps n_steps (k + 1) / n_out, k < n_out */
+    uint64_t seed;
+} sop_ramp_params;
+
+/* Runs the experiment on the device behind cuda_stream (NULL = default stream) and
+ * blocks until it ends. mean[k], var[k] (host, [n_out], FP64): mean and population
+ * variance over runs of X at checkpoint k; x_final (host, [n_runs] or NULL): every
+ * run's final X. X is read as the FP32 value minus its compensation, in FP64.
+ * Allocates and frees its own device memory (8 bytes per run plus reduction scratch).
+ * SOP_ERR_INVALID_ARG on a parameter out of range; SOP_ERR_CUDA / SOP_ERR_OOM on
+ * device failure (text in sop_last_error(NULL)). */
+sop_status sop_brownian_ramp(const sop_ramp_params *params, double *mean, double *var, double *x_final,
+                             void *cuda_stream);
+
 /* Per-replica status ([n_replicas] int32 host): a sop_status value each. */
 sop_status sop_replica_status(sop_ctx *ctx, int32_t *out);
 

@@ -220,15 +220,19 @@ __global__ void k_seg_setup(RebuildArgs a, int32_t *pl_cursor, const int64_t *pl
         float edge = a.cell_edge;
         int d[3] = {1, 1, 1};
         if (!sbad && hi > lo) {
-            for (int it = 0; it < 64; ++it) {
+            bool fit = false;
+            for (int it = 0; it < 64 && !fit; ++it) {
                 long long prod = 1;
                 for (int k = 0; k < 3; ++k) {
                     const float e = (h[k] - l[k]) / edge;
                     d[k] = e < 1e6f ? (int)floorf(e) + 1 : 1000000;
                     prod *= d[k];
                 }
-                if (prod <= budget) break;
-                edge *= 1.25f;
+                if (prod <= budget) fit = true;
+                else edge *= 1.25f;
+            }
+            if (!fit) {   // an extent no grid of the budget covers (beads flung ~1e10 A apart): one cell
+                d[0] = d[1] = d[2] = 1;
             }
         } else {
             l[0] = l[1] = l[2] = 0.0f;
@@ -263,6 +267,14 @@ __global__ void k_cell_count(RebuildArgs a, int b_lo, int b_hi) {
         cz = cell_coord(p.z, lo.z, lo.w, d.z);
     }
     const int gc = a.seg_cell_base[g] + (cz * d.y + cy) * d.x + cx;
+    // the grid never exceeds the segment's budget (k_seg_setup); a cell outside it is
+    // recorded as a failure of the replica and the bead goes to the segment's first cell
+    if (gc < a.seg_cell_base[g] || gc >= a.seg_cell_base[g + 1]) {
+        atomicCAS(&a.rep_status[r], 0, (int32_t)SOP_ERR_NONFINITE);
+        a.cell_of[gb] = a.seg_cell_base[g];
+        atomicAdd(&a.cell_cnt[a.seg_cell_base[g]], 1);
+        return;
+    }
     a.cell_of[gb] = gc;
     atomicAdd(&a.cell_cnt[gc], 1);
 }

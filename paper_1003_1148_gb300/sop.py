@@ -33,7 +33,7 @@ EXPORTED = ["sop_create", "sop_step", "sop_forces", "sop_pairlist_rebuild", "sop
             "sop_get_positions", "sop_set_positions", "sop_get_pairlist", "sop_get_native_map",
             "sop_get_observables", "sop_get_state", "sop_set_state", "sop_replica_status", "sop_abort",
             "sop_get_stats", "sop_last_error", "sop_destroy", "sop_pairlist_build_noalloc", "sop_get_rng_state",
-            "sop_set_rng_state"]
+            "sop_set_rng_state", "sop_brownian_ramp"]
 RNG_PHILOX, RNG_HYBRID_TAUS = 0, 1
 RNGS = {"philox": RNG_PHILOX, "taus": RNG_HYBRID_TAUS}
 
@@ -62,6 +62,12 @@ class Params(C.Structure):
 class PullParams(C.Structure):
     _fields_ = [("system", C.c_int32), ("anchor", C.c_int32), ("pulled", C.c_int32), ("k_s", C.c_double),
                 ("v", C.c_double)]
+
+
+class RampParams(C.Structure):
+    _fields_ = [("K", C.c_double), ("xi", C.c_double), ("kT", C.c_double), ("h", C.c_double),
+                ("r_f", C.c_double), ("X0", C.c_double), ("n_runs", C.c_int64), ("n_steps", C.c_int64),
+                ("order", C.c_int32), ("n_out", C.c_int32), ("seed", C.c_uint64)]
 
 
 class Record(C.Structure):
@@ -112,6 +118,7 @@ def load(path: str | None = None):
             "sop_pairlist_build_noalloc": ([vp, i32, vp, vp, vp, f64, vp, vp, vp, i64, vp, vp], C.c_int),
             "sop_get_rng_state": ([vp, vp, i64], C.c_int),
             "sop_set_rng_state": ([vp, vp, i64], C.c_int),
+            "sop_brownian_ramp": ([vp, vp, vp, vp, vp], C.c_int),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -323,6 +330,21 @@ def from_workload(w, n_replicas: int | None = None, schedule="auto", stream=None
         ind = w.indenter
         sim.indenter(ind.center, ind.direction, ind.radius, ind.v)
     return sim
+
+
+def brownian_ramp(K, xi, kT, h, r_f, n_runs, n_steps, X0=0.0, order=1, n_out=1, seed=0, x_final=False,
+                  stream=None):
+    """``sop_brownian_ramp``: the Sec. IV.C experiment on the GPU. Returns (mean [n_out],
+    var [n_out]) or, with x_final, (mean, var, X of every run after the last step)."""
+    L = load()
+    prm = RampParams(float(K), float(xi), float(kT), float(h), float(r_f), float(X0), int(n_runs), int(n_steps),
+                     int(order), int(n_out), int(seed))
+    mean, var = np.zeros(n_out), np.zeros(n_out)
+    xf = np.zeros(int(n_runs)) if x_final else None
+    rc = L.sop_brownian_ramp(C.byref(prm), _ptr(mean), _ptr(var), _ptr(xf), _stream_handle(stream))
+    if rc != OK:
+        raise SopError(rc, L.sop_last_error(None).decode())
+    return (mean, var, xf) if x_final else (mean, var)
 
 
 NOALLOC_MAX_BEADS = 65536

@@ -44,7 +44,7 @@ def test_struct_layouts_match_header(tmp_path):
     import subprocess
     from paper_1003_1148_gb300 import sop
     mirrors = {"sop_topology": sop.Topology, "sop_params": sop.Params, "sop_pull_params": sop.PullParams,
-               "sop_record": sop.Record, "sop_stats": sop.Stats}
+               "sop_record": sop.Record, "sop_stats": sop.Stats, "sop_ramp_params": sop.RampParams}
     lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "sop.h"', "int main(void) {"]
     for cname, py in mirrors.items():
         lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')

@@ -60,7 +60,8 @@ class _Model(C.Structure):
                 ("sigma", C.c_double), ("T", C.c_double), ("zeta", C.c_double), ("dt", C.c_double),
                 ("pair_cut", C.c_double), ("rebuild_every", C.c_int32), ("use_cells", C.c_int32),
                 ("noise_offset", C.c_int32),
-                ("n_pull", C.c_int32), ("pulls", C.c_void_p), ("indenter", C.c_void_p), ("taus", C.c_void_p)]
+                ("n_pull", C.c_int32), ("pulls", C.c_void_p), ("indenter", C.c_void_p), ("taus", C.c_void_p),
+                ("integrator", C.c_int32), ("mass", C.c_double), ("vel", C.c_void_p)]
 
 
 def _L():
@@ -95,6 +96,7 @@ def _L():
             L.orc_taus_next.restype = C.c_uint32
             L.orc_taus_noise.argtypes = [vp, vp]
             L.orc_ermak_update.argtypes = [vp, vp, vp, u64, i64]
+            L.orc_baoab_update.argtypes = [vp, vp, vp, u64, i64]
             L.orc_observables.argtypes = [vp, vp, i64, vp, vp, i64, i32, vp]
             L.orc_observables.restype = C.c_int
             L.orc_run.argtypes = [vp, vp, i64, i64, u64, i32, i32, vp, i64, vp, vp]
@@ -191,6 +193,7 @@ class Model:
         self.use_cells = 0
         self.noise_offset = 0
         self.taus = None
+        self.integrator, self.mass, self.vel = 0, 0.0, None
         self._sync()
 
     def _sync(self):
@@ -201,7 +204,8 @@ class Model:
                          p["sigma"], p["T"], p["zeta"], p["dt"], p["pair_cut"], int(p["rebuild_every"]),
                          int(self.use_cells), int(self.noise_offset), self.n_pull, C.addressof(self.pulls) if self.n_pull else None,
                          C.addressof(self.indenter) if self.indenter is not None else None,
-                         _p(self.taus) if self.taus is not None else None)
+                         _p(self.taus) if self.taus is not None else None, int(self.integrator),
+                         float(self.mass), _p(self.vel) if self.vel is not None else None)
 
     def set_cells(self, on: bool):
         self.use_cells = 1 if on else 0
@@ -217,6 +221,27 @@ class Model:
         place by every update; None returns to Philox."""
         self.taus = None if state is None else np.ascontiguousarray(state, np.uint32).reshape(self.n, 4).copy()
         self._sync()
+
+    def set_underdamped(self, mass: float, vel=None):
+        """Underdamped BAOAB dynamics (mass in (kcal/mol) ps^2/A^2, friction = zeta) with the
+        stored velocities vel [n, 3] (default 0), advanced in place; mass None returns to the
+        overdamped update."""
+        if mass is None:
+            self.integrator, self.mass, self.vel = 0, 0.0, None
+        else:
+            self.integrator, self.mass = 1, float(mass)
+            self.vel = np.zeros((self.n, 3)) if vel is None else np.ascontiguousarray(vel, np.float64).reshape(
+                self.n, 3).copy()
+        self._sync()
+
+    def velocities(self):
+        return None if self.vel is None else self.vel.copy()
+
+    def baoab_update(self, xyz, F, seed: int, step: int):
+        xyz = np.ascontiguousarray(xyz, np.float64).copy()
+        F = np.ascontiguousarray(F, np.float64)
+        _L().orc_baoab_update(C.byref(self._m), _p(xyz), _p(F), seed, step)
+        return xyz
 
     def taus_state(self):
         return None if self.taus is None else self.taus.copy()

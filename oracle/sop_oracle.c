@@ -26,6 +26,8 @@
  *   orc_ermak_update              Algorithm 7 (the first-order Ermak-McCammon
  *                                 update, Eq. 2)
  *   orc_run                       the step sequence of Fig. 2 / Sec. III.D
+ *   orc_baoab_update              the underdamped limit named in the Conclusion, as the
+ *                                 BAOAB splitting of Leimkuhler and Matthews (2013)
  *   orc_ramp_*                    Sec. IV.C: the harmonic Brownian particle under a
  *                                 ramp force, Eqs. 3, 4 and 5
  *
@@ -520,6 +522,26 @@ void orc_ermak_update(const orc_model *m, double *xyz, const double *F, uint64_t
     }
 }
 
+void orc_baoab_update(const orc_model *m, double *xyz, const double *F, uint64_t seed, int64_t step) {
+    double kT = orc_kB() * m->T;
+    double h = m->dt;
+    double c1 = exp(-m->zeta * h / m->mass);
+    double c2 = sqrt(kT * (1.0 - c1 * c1) / m->mass);
+    for (int32_t i = 0; i < m->n; ++i) {
+        if (is_held(m, i)) continue;
+        double g[3];
+        if (m->taus) orc_taus_noise(m->taus + 4 * (size_t)i, g);
+        else orc_noise(seed, step, i + m->noise_offset, g);
+        for (int k = 0; k < 3; ++k) {
+            double v1 = m->vel[3 * i + k] + h / m->mass * F[3 * i + k];
+            double x = xyz[3 * i + k] + 0.5 * h * v1;
+            double v2 = c1 * v1 + c2 * g[k];
+            xyz[3 * i + k] = x + 0.5 * h * v2;
+            m->vel[3 * i + k] = v2;
+        }
+    }
+}
+
 /* ------------------------------------------------------------------------ */
 /* Integrator accuracy: Sec. IV.C, Eqs. 3-5                                  */
 /* ------------------------------------------------------------------------ */
@@ -692,7 +714,8 @@ int orc_run(const orc_model *m, double *xyz, int64_t step0, int64_t n_steps, uin
         }
         rc = orc_forces(m, xyz, n_pl, pi, pj, step, F, NULL, NULL);
         if (rc != ORC_OK) break;
-        orc_ermak_update(m, xyz, F, seed, step);
+        if (m->integrator == 1) orc_baoab_update(m, xyz, F, seed, step);
+        else orc_ermak_update(m, xyz, F, seed, step);
         for (int64_t k = 0; k < 3 * (int64_t)n; ++k)
             if (!isfinite(xyz[k])) { rc = ORC_ERR_NONFINITE; break; }
         if (rc != ORC_OK) break;

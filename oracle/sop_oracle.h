@@ -67,6 +67,13 @@ typedef struct {
     /* noise source: NULL = Philox4x32-10 keyed by the replica seed; else the Hybrid
      * Taus state of every bead ([n][4] words y1..y4), advanced in place */
     uint32_t *taus;
+    /* integrator: 0 = overdamped first-order update (Algorithm 7); 1 = underdamped
+     * Langevin dynamics by the BAOAB splitting (Leimkuhler and Matthews, 2013) with
+     * bead mass `mass` and friction coefficient zeta; `vel` ([n][3]) holds each bead's
+     * velocity after the O step of the previous step (0 at the start), advanced in place */
+    int32_t integrator;
+    double mass;
+    double *vel;
 } orc_model;
 
 enum {
@@ -160,6 +167,16 @@ void orc_box_muller4(const uint32_t x[4], double g[4]);
  * g_n normal n % 4 of the Philox block of key seed, counter (n/4 lo, n/4 hi, run, 1).
  * Returns X after n_steps. */
 double orc_ramp_run(const orc_ramp *p, uint64_t seed, int64_t run, int64_t n_steps);
+
+/* One underdamped step (m->integrator == 1) of all non-fixed beads from x_n with
+ * forces F = F(x_n) and stored velocities w = m->vel: the B, A, O, A sub-steps of
+ * BAOAB with the closing B of the previous step merged into this step's opening B:
+ *   v' = w + (h / m) F        (the previous step's closing half kick and this one's opening)
+ *   x  = x + (h / 2) v'
+ *   v'' = c1 v' + c2 g,  c1 = exp(-zeta h / m), c2 = sqrt(kT (1 - c1^2) / m)
+ *   x  = x + (h / 2) v'',  w = v''
+ * so the first step from w = 0 starts from the velocity (h / 2m) F(x_0). */
+void orc_baoab_update(const orc_model *m, double *xyz, const double *F, uint64_t seed, int64_t step);
 
 /* Observables of every system at positions xyz and step `step`. Per system 8
  * doubles: step, system, energy (Eq. 1 over the list), external force along its

@@ -237,3 +237,55 @@ def test_ramp_run_noise_stream_and_moments(orc):
     var = amp ** 2 * (1 - a ** (2 * n)) / (1 - a * a)
     assert abs(xs.mean() - r.mean(n)) < 4 * math.sqrt(var / runs)
     assert xs.var(ddof=1) == pytest.approx(var, rel=4 * math.sqrt(2 / (runs - 1)))
+
+
+# ---------------------------------------------------------------------------------------
+# Underdamped BAOAB (orc_baoab_update): a bead on the cantilever spring (tip speed 0) is a
+# 3-D harmonic oscillator. Without friction and noise the scheme is velocity Verlet, whose
+# orbit has the closed form x_n = A cos(n theta) + B sin(n theta), cos theta = 1 - (h w)^2/2;
+# with friction and noise BAOAB samples the exact configurational variance kT / k_s of a
+# harmonic oscillator at any stable h (tested at h w = 1, where a scheme with the A and O
+# sub-steps swapped would be a third off).
+# ---------------------------------------------------------------------------------------
+def _oscillator(orc, k_s, mass, zeta, T, dt, disp):
+    xyz = np.array([[0.0, 0.0, 0.0], [100.0, 0.0, 0.0]])
+    m = orc.Model(xyz, np.array([0, 1], np.int32), np.array([0, 0], np.int32),
+                  params=dict(zeta=zeta, T=T, dt=dt))
+    m.start_pulls([(0, 0, 1, k_s, 0.0)], xyz)
+    m.set_underdamped(mass)
+    x0 = xyz.copy()
+    x0[1] += disp
+    return m, x0
+
+
+def test_baoab_without_friction_is_velocity_verlet(orc):
+    k_s, mass, dt = 9.0, 1.0, 0.1                 # h w = 0.3
+    disp = np.array([0.5, -0.2, 0.1])
+    m, x = _oscillator(orc, k_s, mass, 0.0, 0.0, dt, disp)
+    hw2 = dt * dt * k_s / mass
+    theta = math.acos(1 - hw2 / 2)
+    A = disp
+    B = (disp * (1 - hw2) - disp * math.cos(theta)) / math.sin(theta)
+    for block in range(30):
+        x, _, _, _ = m.run(x, 10, seed=1, step0=10 * block)
+        n = 10 * (block + 1)
+        ref = A * math.cos(n * theta) + B * math.sin(n * theta)
+        assert np.allclose(x[1] - np.array([100.0, 0, 0]), ref, rtol=0, atol=1e-11), n
+    assert np.array_equal(x[0], [0.0, 0.0, 0.0])      # the anchor never moves
+
+
+def test_baoab_harmonic_configurational_variance_is_exact(orc):
+    k_s, mass, zeta, dt, T = 100.0, 1.0, 5.0, 0.1, 300.0   # h w = 1
+    kT = orc.kB() * T
+    samples = []
+    for seed in range(48):
+        m, x = _oscillator(orc, k_s, mass, zeta, T, dt, np.zeros(3))
+        for block in range(400):
+            x, _, _, _ = m.run(x, 10, seed=seed, step0=10 * block)
+            if block >= 40:
+                samples.append(x[1] - np.array([100.0, 0.0, 0.0]))
+    s = np.array(samples).ravel()
+    var = s.var()
+    # about 1e5 nearly independent samples (relaxation within a few steps)
+    assert var == pytest.approx(kT / k_s, rel=0.03)
+    assert abs(s.mean()) < 5 * math.sqrt(kT / k_s / len(s) * 10)

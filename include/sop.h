@@ -78,6 +78,17 @@ typedef enum {
                                  advances only in steps in which the bead moves */
 } sop_rng;
 
+/* Equations of motion. */
+typedef enum {
+    SOP_INTEGRATOR_OVERDAMPED = 0,   /* Algorithm 7: r += F h/zeta + g sqrt(2 kT h/zeta) */
+    SOP_INTEGRATOR_BAOAB = 1         /* underdamped Langevin dynamics (the limit the Conclusion names), by the
+                                        BAOAB splitting of Leimkuhler and Matthews (2013): bead mass `mass`,
+                                        friction zeta; per step, with F = F(r_n) and w the stored velocity:
+                                        v' = w + (h/m) F; v'' = c1 v' + c2 g; r += (h/2)(v' + v''); w = v'',
+                                        c1 = exp(-zeta h/m), c2 = sqrt(kT (1 - c1^2)/m). The stored velocity
+                                        is the one after the O sub-step (0 at the start). */
+} sop_integrator;
+
 typedef struct sop_ctx sop_ctx;
 
 /* Topology of one replica. Chains are contiguous bead ranges; systems are
@@ -113,6 +124,8 @@ typedef struct {
     int32_t schedule;       /* a sop_schedule */
     void *cuda_stream;      /* cudaStream_t to queue work on (NULL = default stream) */
     int32_t rng;            /* a sop_rng (0 = Philox) */
+    int32_t integrator;     /* a sop_integrator (0 = overdamped) */
+    double mass;            /* bead mass, (kcal/mol) ps^2 / A^2 (> 0 for SOP_INTEGRATOR_BAOAB) */
 } sop_params;
 
 /* Cantilever on one system (Sec. IV.B): `anchor` is held fixed; a spring of
@@ -199,6 +212,13 @@ sop_status sop_get_positions(sop_ctx *ctx, int32_t replica, double *out_xyz);
  * all replicas from a [3*n_beads*n_replicas] array. */
 sop_status sop_set_positions(sop_ctx *ctx, int32_t replica, const double *xyz);
 
+/* Stored velocities of the underdamped integrator (A/ps, the velocity after the O
+ * sub-step of the last step), FP64 host [3*n_beads] (replica >= 0) or
+ * [3*n_beads*n_replicas] (replica == -1). SOP_ERR_UNSUPPORTED for the overdamped
+ * integrator. Part of the checkpoint. */
+sop_status sop_get_velocities(sop_ctx *ctx, int32_t replica, double *out_v);
+sop_status sop_set_velocities(sop_ctx *ctx, int32_t replica, const double *v);
+
 /* Verlet list of `replica` as canonical CSR over its beads: row i holds every
  * partner j (both directions, ascending). row_ptr: [n_beads+1]; col: [cap].
  * *nnz receives the entry count; SOP_ERR_CAPACITY when cap < nnz. */
@@ -216,8 +236,8 @@ sop_status sop_get_native_map(sop_ctx *ctx, int32_t *row_ptr, int32_t *col, doub
 sop_status sop_get_observables(sop_ctx *ctx, sop_record *out, int64_t cap, int64_t *n_records, int64_t *n_lost);
 
 /* Checkpoint: the step counter, positions, compensation terms, pulling and
- * indenter set-up, status and the Hybrid Taus state (when used). Resuming from it
- * continues bit-exactly.
+ * indenter set-up, status, the Hybrid Taus state and the velocities (when used).
+ * Resuming from it continues bit-exactly.
  * With buf == NULL, *size receives the byte count needed. */
 sop_status sop_get_state(sop_ctx *ctx, void *buf, int64_t cap, int64_t *size);
 sop_status sop_set_state(sop_ctx *ctx, const void *buf, int64_t size);

@@ -600,11 +600,25 @@ __global__ void __launch_bounds__(MAXT, MINB) k_batched(BatchedArgs a) {
                     gn = bead_noise(sa.seed + (uint64_t)r, step, (uint32_t)(b0 + b));
                 }
                 float4 c = L.comp()[b];
-                kahan_add(pb.x, c.x, fmaf(f.x + fe.x, sa.fp.mob, gn.x * sa.fp.amp));
-                kahan_add(pb.y, c.y, fmaf(f.y + fe.y, sa.fp.mob, gn.y * sa.fp.amp));
-                kahan_add(pb.z, c.z, fmaf(f.z + fe.z, sa.fp.mob, gn.z * sa.fp.amp));
+                float4 w;
+                if (sa.vel) {   // underdamped: BAOAB, the stored velocity in global memory (L2)
+                    w = sa.vel[gbase + b];
+                    const float v1x = fmaf(f.x + fe.x, sa.h_m, w.x), v1y = fmaf(f.y + fe.y, sa.h_m, w.y),
+                                v1z = fmaf(f.z + fe.z, sa.h_m, w.z);
+                    w.x = fmaf(sa.c1, v1x, sa.c2 * gn.x);
+                    w.y = fmaf(sa.c1, v1y, sa.c2 * gn.y);
+                    w.z = fmaf(sa.c1, v1z, sa.c2 * gn.z);
+                    kahan_add(pb.x, c.x, sa.half_h * (v1x + w.x));
+                    kahan_add(pb.y, c.y, sa.half_h * (v1y + w.y));
+                    kahan_add(pb.z, c.z, sa.half_h * (v1z + w.z));
+                } else {
+                    kahan_add(pb.x, c.x, fmaf(f.x + fe.x, sa.fp.mob, gn.x * sa.fp.amp));
+                    kahan_add(pb.y, c.y, fmaf(f.y + fe.y, sa.fp.mob, gn.y * sa.fp.amp));
+                    kahan_add(pb.z, c.z, fmaf(f.z + fe.z, sa.fp.mob, gn.z * sa.fp.amp));
+                }
                 if (isfinite(pb.x) && isfinite(pb.y) && isfinite(pb.z)) {
                     L.comp()[b] = c;
+                    if (sa.vel) sa.vel[gbase + b] = w;
                 } else {
                     cta_fail(L.h(), SOP_ERR_NONFINITE);
                     pb = p_old;

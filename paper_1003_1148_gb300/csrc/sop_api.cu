@@ -49,6 +49,7 @@ struct sop_ctx {
             *d_sys_nat_pairs = nullptr;
     uint8_t *d_flags = nullptr;
     uint4 *d_taus = nullptr;   // Hybrid Taus state per bead (SOP_RNG_HYBRID_TAUS)
+    float4 *d_vel = nullptr;   // stored velocity per bead (SOP_INTEGRATOR_BAOAB)
     float *d_bond_r0 = nullptr;
     double *d_bond_r0d = nullptr;
     int32_t *d_nat_row = nullptr, *d_nat_col = nullptr;
@@ -551,6 +552,10 @@ sop_status validate_params(const sop_params *p) {
         return fail(nullptr, SOP_ERR_INVALID_ARG, "params: unknown schedule");
     if (p->rng != SOP_RNG_PHILOX && p->rng != SOP_RNG_HYBRID_TAUS)
         return fail(nullptr, SOP_ERR_INVALID_ARG, "params: unknown rng");
+    if (p->integrator != SOP_INTEGRATOR_OVERDAMPED && p->integrator != SOP_INTEGRATOR_BAOAB)
+        return fail(nullptr, SOP_ERR_INVALID_ARG, "params: unknown integrator");
+    if (p->integrator == SOP_INTEGRATOR_BAOAB && !(std::isfinite(p->mass) && p->mass > 0))
+        return fail(nullptr, SOP_ERR_INVALID_ARG, "params: the underdamped integrator needs a finite mass > 0");
     return SOP_OK;
 }
 
@@ -798,6 +803,7 @@ sop_status tune_bucket(sop_ctx *c, sop_ctx::Bucket &bk) {
                 a.snap = ss;
                 a.sa.rep_status = sst;
                 a.sa.taus = nullptr;   // trials draw Philox noise: the run's Taus state is untouched
+                a.sa.vel = nullptr;    // and take the overdamped update: the run's velocities are untouched
                 a.obs_every = 0;
                 a.n_items = trial_items;
                 a.n_steps = 20;
@@ -1171,6 +1177,16 @@ sop_status create_impl(sop_ctx *c, const sop_topology *topo, const double *xyz, 
         CUDA_OR_RETURN(c, upload(c, &c->d_taus, st));
     }
     a.taus = c->d_taus;
+    if (p->integrator == SOP_INTEGRATOR_BAOAB) {
+        CUDA_OR_RETURN(c, dalloc(c, &c->d_vel, (size_t)R * n));
+        CUDA_OR_RETURN(c, cudaMemset(c->d_vel, 0, sizeof(float4) * (size_t)R * n));
+        const double c1 = std::exp(-p->zeta * p->dt / p->mass);
+        a.h_m = (float)(p->dt / p->mass);
+        a.half_h = (float)(0.5 * p->dt);
+        a.c1 = (float)c1;
+        a.c2 = (float)std::sqrt(kT * (1.0 - c1 * c1) / p->mass);
+    }
+    a.vel = c->d_vel;
     sync_external(c);
     // ---- the first Verlet list (streamed builder; also fills the snapshot)
     s = rebuild_streamed(c);
@@ -1499,6 +1515,43 @@ sop_status sop_set_positions(sop_ctx *c, int32_t replica, const double *xyz) {
     return SOP_OK;
 }
 
+sop_status sop_get_velocities(sop_ctx *c, int32_t replica, double *out) {
+    if (!c) return fail(nullptr, SOP_ERR_INVALID_ARG, "ctx is NULL");
+    if (!c->d_vel) return fail(c, SOP_ERR_UNSUPPORTED, "the overdamped integrator has no velocities");
+    if (!out || replica < -1 || replica >= c->R) return fail(c, SOP_ERR_INVALID_ARG, "replica or out");
+    const size_t cnt = replica < 0 ? (size_t)c->R * c->n : (size_t)c->n;
+    const size_t off = replica < 0 ? 0 : (size_t)replica * c->n;
+    std::vector<float4> h(cnt);
+    CUDA_OR_RETURN(c, cudaMemcpyAsync(h.data(), c->d_vel + off, sizeof(float4) * cnt, cudaMemcpyDeviceToHost,
+                                      c->stream));
+    CUDA_OR_RETURN(c, cudaStreamSynchronize(c->stream));
+    for (size_t i = 0; i < cnt; ++i) {
+        out[3 * i] = h[i].x;
+        out[3 * i + 1] = h[i].y;
+        out[3 * i + 2] = h[i].z;
+    }
+    return SOP_OK;
+}
+
+sop_status sop_set_velocities(sop_ctx *c, int32_t replica, const double *v) {
+    if (!c) return fail(nullptr, SOP_ERR_INVALID_ARG, "ctx is NULL");
+    if (!c->d_vel) return fail(c, SOP_ERR_UNSUPPORTED, "the overdamped integrator has no velocities");
+    if (!v || replica < -1 || replica >= c->R) return fail(c, SOP_ERR_INVALID_ARG, "replica or v");
+    const size_t cnt = replica < 0 ? (size_t)c->R * c->n : (size_t)c->n;
+    const size_t off = replica < 0 ? 0 : (size_t)replica * c->n;
+    std::vector<float4> h(cnt);
+    for (size_t i = 0; i < cnt; ++i) {
+        if (!std::isfinite(v[3 * i]) || !std::isfinite(v[3 * i + 1]) || !std::isfinite(v[3 * i + 2]))
+            return fail(c, SOP_ERR_INVALID_ARG, "velocities hold a non-finite value");
+        h[i] = make_float4((float)v[3 * i], (float)v[3 * i + 1], (float)v[3 * i + 2], 0.f);
+    }
+    CUDA_OR_RETURN(c, cudaStreamSynchronize(c->stream));
+    CUDA_OR_RETURN(c, cudaMemcpyAsync(c->d_vel + off, h.data(), sizeof(float4) * cnt, cudaMemcpyHostToDevice,
+                                      c->stream));
+    CUDA_OR_RETURN(c, cudaStreamSynchronize(c->stream));
+    return SOP_OK;
+}
+
 sop_status sop_get_pairlist(sop_ctx *c, int32_t replica, int32_t *row_ptr, int32_t *col, int64_t cap, int64_t *nnz) {
     if (!c) return fail(nullptr, SOP_ERR_INVALID_ARG, "ctx is NULL");
     if (replica < 0 || replica >= c->R || !row_ptr || !nnz) return fail(c, SOP_ERR_INVALID_ARG, "replica or outputs");
@@ -1604,13 +1657,14 @@ sop_status sop_get_state(sop_ctx *c, void *buf, int64_t cap, int64_t *size) {
     const size_t np = c->pull_bead.size();
     const size_t need = 16 * sizeof(int64_t) + 3 * RN * sizeof(float4) + c->R * sizeof(int32_t) +
                         np * (3 * sizeof(int32_t) + 6 * sizeof(double)) + 3 * np * c->R * sizeof(double) +
-                        9 * sizeof(double) + (c->d_taus ? RN * sizeof(uint4) : 0);
+                        9 * sizeof(double) + (c->d_taus ? RN * sizeof(uint4) : 0) +
+                        (c->d_vel ? RN * sizeof(float4) : 0);
     *size = (int64_t)need;
     if (!buf) return SOP_OK;
     if (cap < (int64_t)need) return fail(c, SOP_ERR_CAPACITY, "buffer too small");
     char *p = static_cast<char *>(buf);
     int64_t hdr[16] = {0x534f5031, SOP_ABI_VERSION, c->n, c->R, c->step, c->list_step, (int64_t)np,
-                       c->has_ind ? 1 : 0, c->events, c->consumed, c->d_taus ? 1 : 0, 0, 0, 0, 0, 0};
+                       c->has_ind ? 1 : 0, c->events, c->consumed, c->d_taus ? 1 : 0, c->d_vel ? 1 : 0, 0, 0, 0, 0};
     std::memcpy(p, hdr, sizeof hdr);
     p += sizeof hdr;
     CUDA_OR_RETURN(c, cudaMemcpyAsync(p, c->d_pos[c->cur], RN * sizeof(float4), cudaMemcpyDeviceToHost, c->stream));
@@ -1621,9 +1675,14 @@ sop_status sop_get_state(sop_ctx *c, void *buf, int64_t cap, int64_t *size) {
     p += RN * sizeof(float4);
     CUDA_OR_RETURN(c, cudaMemcpyAsync(p, c->d_rep_status, c->R * sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
     p += c->R * sizeof(int32_t);
-    if (c->d_taus)   // after the fixed-size part: at the end of the buffer
-        CUDA_OR_RETURN(c, cudaMemcpyAsync(static_cast<char *>(buf) + need - RN * sizeof(uint4), c->d_taus,
+    // optional parts at the end of the buffer: the Taus state, then the velocities
+    const size_t tail_vel = c->d_vel ? RN * sizeof(float4) : 0;
+    if (c->d_taus)
+        CUDA_OR_RETURN(c, cudaMemcpyAsync(static_cast<char *>(buf) + need - tail_vel - RN * sizeof(uint4), c->d_taus,
                                           RN * sizeof(uint4), cudaMemcpyDeviceToHost, c->stream));
+    if (c->d_vel)
+        CUDA_OR_RETURN(c, cudaMemcpyAsync(static_cast<char *>(buf) + need - tail_vel, c->d_vel, tail_vel,
+                                          cudaMemcpyDeviceToHost, c->stream));
     CUDA_OR_RETURN(c, cudaStreamSynchronize(c->stream));
     auto put = [&p](const void *src, size_t bytes) { if (bytes) std::memcpy(p, src, bytes); p += bytes; };
     put(c->pull_sys.data(), np * sizeof(int32_t));
@@ -1652,14 +1711,20 @@ sop_status sop_set_state(sop_ctx *c, const void *buf, int64_t size) {
     const size_t np = (size_t)hdr[6];
     if ((hdr[10] != 0) != (c->d_taus != nullptr))
         return fail(c, SOP_ERR_INVALID_ARG, "state: noise source differs from this context");
+    if ((hdr[11] != 0) != (c->d_vel != nullptr))
+        return fail(c, SOP_ERR_INVALID_ARG, "state: integrator differs from this context");
+    const size_t tail_vel = c->d_vel ? RN * sizeof(float4) : 0;
     const size_t need = 16 * sizeof(int64_t) + 3 * RN * sizeof(float4) + c->R * sizeof(int32_t) +
                         np * (3 * sizeof(int32_t) + 6 * sizeof(double)) + 3 * np * c->R * sizeof(double) +
-                        9 * sizeof(double) + (c->d_taus ? RN * sizeof(uint4) : 0);
+                        9 * sizeof(double) + (c->d_taus ? RN * sizeof(uint4) : 0) + tail_vel;
     if (size < (int64_t)need) return fail(c, SOP_ERR_INVALID_ARG, "state buffer truncated");
     CUDA_OR_RETURN(c, cudaStreamSynchronize(c->stream));   // no queued work may still use the state
     if (c->d_taus)
-        CUDA_OR_RETURN(c, cudaMemcpy(c->d_taus, static_cast<const char *>(buf) + need - RN * sizeof(uint4),
+        CUDA_OR_RETURN(c, cudaMemcpy(c->d_taus, static_cast<const char *>(buf) + need - tail_vel - RN * sizeof(uint4),
                                      RN * sizeof(uint4), cudaMemcpyHostToDevice));
+    if (c->d_vel)
+        CUDA_OR_RETURN(c, cudaMemcpy(c->d_vel, static_cast<const char *>(buf) + need - tail_vel, tail_vel,
+                                     cudaMemcpyHostToDevice));
     p += sizeof hdr;
     c->cur = 0;
     CUDA_OR_RETURN(c, cudaMemcpy(c->d_pos[0], p, RN * sizeof(float4), cudaMemcpyHostToDevice));

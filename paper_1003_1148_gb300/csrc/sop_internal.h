@@ -64,6 +64,8 @@ struct StepArgs {
     int32_t *rep_status = nullptr;     // [R]
     int32_t *halt = nullptr;           // [1] nonzero: every kernel copies state through
     uint4 *taus = nullptr;             // [R*n] Hybrid Taus state per bead; null: Philox noise
+    float4 *vel = nullptr;             // [R*n] underdamped (BAOAB) velocity per bead; null: overdamped
+    float h_m = 0, half_h = 0, c1 = 0, c2 = 0;   // BAOAB: h/m, h/2, exp(-zeta h/m), sqrt(kT (1 - c1^2)/m)
 };
 
 // Streamed-schedule Verlet list (row starts are arbitrary; rows are sorted).

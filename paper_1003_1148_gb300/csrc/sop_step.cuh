@@ -85,14 +85,28 @@ __device__ __forceinline__ void advance_bead(const StepArgs &a, int r, int i, in
         g = bead_noise(a.seed + (uint64_t)r, step, (uint32_t)i);
     }
     float4 c = comp[gb];
-    kahan_add(pi.x, c.x, fmaf(f.x + fe.x, a.fp.mob, g.x * a.fp.amp));
-    kahan_add(pi.y, c.y, fmaf(f.y + fe.y, a.fp.mob, g.y * a.fp.amp));
-    kahan_add(pi.z, c.z, fmaf(f.z + fe.z, a.fp.mob, g.z * a.fp.amp));
+    float4 w;
+    if (a.vel) {   // underdamped: BAOAB with the stored post-O velocity w
+        w = a.vel[gb];
+        const float v1x = fmaf(f.x + fe.x, a.h_m, w.x), v1y = fmaf(f.y + fe.y, a.h_m, w.y),
+                    v1z = fmaf(f.z + fe.z, a.h_m, w.z);
+        w.x = fmaf(a.c1, v1x, a.c2 * g.x);
+        w.y = fmaf(a.c1, v1y, a.c2 * g.y);
+        w.z = fmaf(a.c1, v1z, a.c2 * g.z);
+        kahan_add(pi.x, c.x, a.half_h * (v1x + w.x));
+        kahan_add(pi.y, c.y, a.half_h * (v1y + w.y));
+        kahan_add(pi.z, c.z, a.half_h * (v1z + w.z));
+    } else {
+        kahan_add(pi.x, c.x, fmaf(f.x + fe.x, a.fp.mob, g.x * a.fp.amp));
+        kahan_add(pi.y, c.y, fmaf(f.y + fe.y, a.fp.mob, g.y * a.fp.amp));
+        kahan_add(pi.z, c.z, fmaf(f.z + fe.z, a.fp.mob, g.z * a.fp.amp));
+    }
     if (!(isfinite(pi.x) && isfinite(pi.y) && isfinite(pi.z))) {
         set_status(&a.rep_status[r], (int32_t)SOP_ERR_NONFINITE);
         pos_out[gb] = P[i];
         return;
     }
+    if (a.vel) a.vel[gb] = w;
     comp[gb] = c;
     pos_out[gb] = pi;
 }

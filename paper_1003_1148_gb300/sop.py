@@ -33,7 +33,9 @@ EXPORTED = ["sop_create", "sop_step", "sop_forces", "sop_pairlist_rebuild", "sop
             "sop_get_positions", "sop_set_positions", "sop_get_pairlist", "sop_get_native_map",
             "sop_get_observables", "sop_get_state", "sop_set_state", "sop_replica_status", "sop_abort",
             "sop_get_stats", "sop_last_error", "sop_destroy", "sop_pairlist_build_noalloc", "sop_get_rng_state",
-            "sop_set_rng_state", "sop_brownian_ramp"]
+            "sop_set_rng_state", "sop_brownian_ramp", "sop_get_velocities", "sop_set_velocities"]
+INTEGRATOR_OVERDAMPED, INTEGRATOR_BAOAB = 0, 1
+INTEGRATORS = {"overdamped": INTEGRATOR_OVERDAMPED, "baoab": INTEGRATOR_BAOAB}
 RNG_PHILOX, RNG_HYBRID_TAUS = 0, 1
 RNGS = {"philox": RNG_PHILOX, "taus": RNG_HYBRID_TAUS}
 
@@ -56,7 +58,7 @@ class Params(C.Structure):
                 ("dt", C.c_double), ("pair_cut", C.c_double), ("rebuild_every", C.c_int32),
                 ("n_replicas", C.c_int32), ("seed", C.c_uint64), ("obs_every", C.c_int32),
                 ("obs_capacity", C.c_int32), ("pairs_per_bead", C.c_int32), ("schedule", C.c_int32),
-                ("cuda_stream", C.c_void_p), ("rng", C.c_int32)]
+                ("cuda_stream", C.c_void_p), ("rng", C.c_int32), ("integrator", C.c_int32), ("mass", C.c_double)]
 
 
 class PullParams(C.Structure):
@@ -119,6 +121,8 @@ def load(path: str | None = None):
             "sop_get_rng_state": ([vp, vp, i64], C.c_int),
             "sop_set_rng_state": ([vp, vp, i64], C.c_int),
             "sop_brownian_ramp": ([vp, vp, vp, vp, vp], C.c_int),
+            "sop_get_velocities": ([vp, i32, vp], C.c_int),
+            "sop_set_velocities": ([vp, i32, vp], C.c_int),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -151,7 +155,7 @@ class Simulation:
 
     def __init__(self, native_xyz, chain_offsets, system_offsets=None, fixed=None, params=None, n_replicas=1,
                  seed=0, obs_every=0, obs_capacity=0, pairs_per_bead=0, schedule="auto", stream=None,
-                 rng="philox"):
+                 rng="philox", integrator="overdamped", mass=0.0):
         L = load()
         self._L = L
         xyz = np.ascontiguousarray(native_xyz, np.float64).reshape(-1, 3)
@@ -169,7 +173,8 @@ class Simulation:
         prm = Params(p["k_fene"], p["R0"], p["eps_h"], p["native_cut"], p["eps_l"], p["sigma"], p["T"], p["zeta"],
                      p["dt"], p["pair_cut"], int(p["rebuild_every"]), self.R, int(seed), int(obs_every),
                      int(obs_capacity), int(pairs_per_bead), sched, _stream_handle(stream),
-                     RNGS[rng] if isinstance(rng, str) else int(rng))
+                     RNGS[rng] if isinstance(rng, str) else int(rng),
+                     INTEGRATORS[integrator] if isinstance(integrator, str) else int(integrator), float(mass))
         self.params = p
         self.obs_every = int(obs_every)
         ctx = C.c_void_p()
@@ -206,6 +211,20 @@ class Simulation:
         if raise_on_error:
             self._check(rc)
         return rc
+
+    def get_velocities(self, replica: int = 0):
+        """Stored velocities of the underdamped integrator, [n, 3] (or [R, n, 3] for replica -1)."""
+        shape = (self.R, self.n, 3) if replica == -1 else (self.n, 3)
+        out = np.zeros(shape)
+        self._check(self._L.sop_get_velocities(self._ctx, replica, _ptr(out)))
+        return out
+
+    def set_velocities(self, v, replica: int = 0):
+        a = np.ascontiguousarray(v, np.float64)
+        need = (self.R if replica == -1 else 1) * self.n * 3
+        if a.size != need:
+            raise ValueError(f"expected {need} components, got {a.size}")
+        self._check(self._L.sop_set_velocities(self._ctx, replica, _ptr(a)))
 
     def get_rng_state(self):
         """Hybrid Taus state [R, n, 4] uint32 (contexts created with rng="taus")."""

@@ -175,11 +175,23 @@ struct RebuildArgs {
 };
 
 // One CTA per segment: bounding box, then a grid of cubic cells of edge >= cutoff
-// with at most the segment's cell budget.
+// with at most the segment's cell budget. A segment whose replica has failed is
+// skipped by the whole rebuild (dims.w = 0: no bead is binned and its rows stay empty):
+// its frozen positions may lie anywhere. A live segment with a non-finite position or
+// an extent that no grid of the budget covers (beads flung ~1e9 A apart) fails its
+// replica and is skipped too.
 __global__ void k_seg_setup(RebuildArgs a, int32_t *pl_cursor, const int64_t *pl_seg_base) {
     // every thread of the CTA works on segment g
     const int g = a.g_lo + blockIdx.x;
     const int lo = a.seg_bead_lo[g], hi = a.seg_bead_lo[g + 1];
+    if (a.rep_status[g / a.n_sys] != 0) {   // CTA-uniform
+        if (threadIdx.x == 0) {
+            a.seg_lo[g] = make_float4(0.f, 0.f, 0.f, 1.0f / a.cell_edge);
+            a.seg_dims[g] = make_int4(1, 1, 1, 0);
+            if (pl_cursor) pl_cursor[g] = (int32_t)pl_seg_base[g];
+        }
+        return;
+    }
     float mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
     bool bad = false;
     for (int b = lo + threadIdx.x; b < hi; b += blockDim.x) {
@@ -219,7 +231,8 @@ __global__ void k_seg_setup(RebuildArgs a, int32_t *pl_cursor, const int64_t *pl
         const int budget = a.seg_cell_base[g + 1] - a.seg_cell_base[g];
         float edge = a.cell_edge;
         int d[3] = {1, 1, 1};
-        if (!sbad && hi > lo) {
+        bool skip = sbad != 0 || hi <= lo;
+        if (!skip) {
             bool fit = false;
             for (int it = 0; it < 64 && !fit; ++it) {
                 long long prod = 1;
@@ -231,14 +244,17 @@ __global__ void k_seg_setup(RebuildArgs a, int32_t *pl_cursor, const int64_t *pl
                 if (prod <= budget) fit = true;
                 else edge *= 1.25f;
             }
-            if (!fit) {   // an extent no grid of the budget covers (beads flung ~1e10 A apart): one cell
+            if (!fit) {
                 d[0] = d[1] = d[2] = 1;
+                skip = true;
             }
-        } else {
+        }
+        if (skip) {
             l[0] = l[1] = l[2] = 0.0f;
+            if (hi > lo) atomicCAS(&a.rep_status[g / a.n_sys], 0, (int32_t)SOP_ERR_NONFINITE);
         }
         a.seg_lo[g] = make_float4(l[0], l[1], l[2], 1.0f / edge);
-        a.seg_dims[g] = make_int4(d[0], d[1], d[2], d[0] * d[1] * d[2]);
+        a.seg_dims[g] = make_int4(d[0], d[1], d[2], skip ? 0 : d[0] * d[1] * d[2]);
         if (pl_cursor) pl_cursor[g] = (int32_t)pl_seg_base[g];
     }
 }
@@ -260,6 +276,10 @@ __global__ void k_cell_count(RebuildArgs a, int b_lo, int b_hi) {
     if (a.snap) a.snap[gb] = p;
     const float4 lo = a.seg_lo[g];
     const int4 d = a.seg_dims[g];
+    if (d.w == 0) {   // skipped segment: the bead is not binned
+        a.cell_of[gb] = -1;
+        return;
+    }
     int cx = 0, cy = 0, cz = 0;
     if (isfinite(p.x) && isfinite(p.y) && isfinite(p.z)) {
         cx = cell_coord(p.x, lo.x, lo.w, d.x);
@@ -284,6 +304,7 @@ __global__ void k_cell_scatter(RebuildArgs a, int b_lo, int b_hi) {
     const int gb = b_lo + blockIdx.x * blockDim.x + threadIdx.x;
     if (gb >= b_hi) return;
     const int gc = a.cell_of[gb];
+    if (gc < 0) return;   // skipped segment
     const int slot = atomicSub(&a.cell_cnt[gc], 1) - 1;
     a.sorted[a.sorted_base + a.cell_start[gc - a.cell_base0] + slot] = gb;
 }

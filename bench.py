@@ -305,7 +305,9 @@ def run_ours(args):
         dev_ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
         sim.get_observables()
 
-        # end to end through the public API with host buffers
+        # end to end through the public API with host buffers: every step uploads the
+        # state it starts from (positions, pinned host memory), steps, and reads back its
+        # result (the new positions and the observable records)
         pinned = torch.empty((R, w.n_beads, 3), dtype=torch.float64, pin_memory=True)
         pinned.numpy()[:] = sim.get_positions(-1)
         torch.cuda.synchronize()
@@ -315,8 +317,9 @@ def run_ours(args):
         for _ in range(e2e_steps):
             sim.set_positions(pinned.numpy(), replica=-1)
             one_step()
+            sim.get_positions(-1, out=pinned.numpy())
             rec, lost = sim.get_observables()
-            d2h = rec.nbytes
+            d2h = pinned.numpy().nbytes + rec.nbytes
         e2e_wall = time.perf_counter() - t1
     h2d = R * w.n_beads * 3 * 8
 

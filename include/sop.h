@@ -209,7 +209,10 @@ sop_status sop_indenter(sop_ctx *ctx, const double center[3], const double direc
  * replica == -1 ([3*n_beads*n_replicas], replica major). */
 sop_status sop_get_positions(sop_ctx *ctx, int32_t replica, double *out_xyz);
 /* Set positions (converted to FP32, compensation reset). replica == -1 sets
- * all replicas from a [3*n_beads*n_replicas] array. */
+ * all replicas from a [3*n_beads*n_replicas] array. The Verlet list is rebuilt from
+ * the new positions at once (they replace the snapshot of the last rebuild), so a
+ * list built from other positions is never used with them; the step counter, and with
+ * it the cantilever tips and the indenter, is unchanged. */
 sop_status sop_set_positions(sop_ctx *ctx, int32_t replica, const double *xyz);
 
 /* Stored velocities of the underdamped integrator (A/ps, the velocity after the O

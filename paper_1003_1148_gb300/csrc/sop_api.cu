@@ -1511,6 +1511,16 @@ sop_status sop_set_positions(sop_ctx *c, int32_t replica, const double *xyz) {
     CUDA_OR_RETURN(c, cudaMemcpyAsync(c->d_pos[c->cur] + off, h.data(), sizeof(float4) * cnt, cudaMemcpyHostToDevice,
                                       c->stream));
     CUDA_OR_RETURN(c, cudaMemsetAsync(c->d_comp + off, 0, sizeof(float4) * cnt, c->stream));
+    // the list follows the new positions: they become the snapshot of the last rebuild
+    if (c->schedule == SOP_SCHED_BATCHED) {
+        CUDA_OR_RETURN(c, cudaMemcpyAsync(c->d_snap + off, c->d_pos[c->cur] + off, sizeof(float4) * cnt,
+                                          cudaMemcpyDeviceToDevice, c->stream));
+    } else {
+        rebuild_list(c, c->d_pos[c->cur], c->d_snap, full_range(c), &c->st.kernel_launches);
+        c->list_step = c->step;
+        c->st.rebuilds++;
+    }
+    CUDA_OR_RETURN(c, cudaGetLastError());
     CUDA_OR_RETURN(c, cudaStreamSynchronize(c->stream));
     return SOP_OK;
 }

@@ -9,9 +9,11 @@ compensated-update steps and one FP64 observable record per replica.
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 Prints one JSON line. `value` is device-timed (CUDA events on the library's
-stream, inputs resident, L2 flushed between timed steps); `e2e` times the same
-work through the public API with host buffers (positions uploaded from pinned
-memory and observables read back every step). `--impl reference` times the
+stream, inputs resident, L2 flushed between timed steps); by default 100 timed
+steps, i.e. the configuration's 1e5 Langevin steps. `e2e` times the same work
+through the public API with host buffers (every step uploads the positions it
+starts from out of pinned memory and reads back the new positions and the
+observable records). `--impl reference` times the
 FP64 CPU oracle on the host cores on bounded samples of the same workload.
 Under torchrun every rank runs its own 8,192 replicas (weak scaling).
 """
@@ -393,7 +395,7 @@ def run_ours(args):
 def main():
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="replicas8192x128")

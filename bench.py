@@ -343,14 +343,19 @@ def run_ours(args):
     achieved = flop_bs * work_per_step / per_launch_s / 1e12
     st = sim.stats()
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": None, "kernel": "k_batched (one launch of 1,000 steps per benchmark step)",
+                "traffic": None, "kernel": {
+                    sop.SCHED_BATCHED: "k_batched (one launch of 1,000 steps per benchmark step)",
+                    sop.SCHED_STREAMED: "k_step (one launch per step, CUDA-graph replay) and the cell rebuild",
+                    sop.SCHED_PAIRS: "k_pairs + k_pairs_step (two launches per step) and the cell rebuild"}.get(
+                        st["schedule"], "per-step kernels"),
                 "kernel_config": {"threads": st["block_threads"], "beads_per_thread": st["beads_per_thread"],
                                   "register_cap": 65536 // (256 * st["min_blocks"]) if st["min_blocks"] else 64,
                                   "size_buckets": st["buckets"],
                                   "verlet_capacity": st["pairs_per_bead"]},
                 "flop_per_bead_step": flop_bs, "list_sizes_replica0": counts,
                 "peak_note": "FP32 FMA pipe: 152 SMs x 128 lanes x 2 x 2070 MHz (max SM clock), derived"}
-    roofline["traffic"] = recorded_traffic("k_batched_replicas8192x128")
+    roofline["traffic"] = (recorded_traffic("k_batched_replicas8192x128")
+                           if args.workload == "replicas8192x128" and st["schedule"] == sop.SCHED_BATCHED else None)
 
     # plain per-chain GPU form on a subset of replicas (same kernels' math, one chain per launch)
     plain = None

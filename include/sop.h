@@ -167,6 +167,9 @@ typedef struct {
     int64_t pairlist_entries;     /* entries in the last Verlet list of replica 0 */
     int64_t native_entries;       /* native contacts (i < j) */
     double tune_ms;               /* batched schedule: trial time of the chosen configuration */
+    int32_t cluster_buckets;      /* batched schedule: buckets run in the cluster form (one system over a
+                                     thread-block cluster) */
+    int32_t cluster_size;         /* CTAs per cluster in the bucket with the most systems (0: not clustered) */
 } sop_stats;
 
 /* Create a context: validates the arguments, builds the bonds (r0 from the

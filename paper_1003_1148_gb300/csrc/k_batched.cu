@@ -30,9 +30,12 @@
 // shared-memory broadcast). The natives' r0^2 come from a column-major table
 // in global memory shared by all replicas of a system. Observables (FP64) are
 // reduced in the CTA.
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include "sop_internal.h"
+
+namespace cg = cooperative_groups;
 
 namespace sop {
 
@@ -654,6 +657,470 @@ __global__ void __launch_bounds__(MAXT, MINB) k_batched(BatchedArgs a) {
     if (threadIdx.x == 0 && L.h()->fail != 0) atomicCAS(&sa.rep_status[r], 0, L.h()->fail);
 }
 
+// ===========================================================================
+// Cluster form: one system over a thread-block cluster (sm_90+ distributed
+// shared memory). CTA q of a cluster of C owns the system's beads
+// [q m, (q + 1) m), m = 2^m_shift a multiple of 32, with their two position
+// layers, compensation, bond lengths, slot orders, rows and block boxes in its
+// own shared memory, laid out exactly as one batched item of m beads. A bead's
+// partners are read from the owner CTA's shared memory through generic
+// addresses of the distributed shared memory window. One cluster barrier ends
+// every step (the next layer is complete everywhere); the rebuild adds one after
+// the block boxes. Every CTA of a cluster takes the same sequence of cluster
+// barriers: all control decisions (a frozen replica, a failure, the rebuild and
+// observable cadence) are made from values that every CTA reads after the same
+// barrier.
+// ===========================================================================
+constexpr int kMaxCluster = 16;
+constexpr int kNoFail = 0x7fffffff;
+
+struct ClusterExtra {
+    int fail_step;                        // first step of the launch at which this CTA failed
+    int frozen;                           // rank 0: the replica was frozen at launch
+    double part[6];                       // this CTA's observable sums
+    const float4 *lay[2][kMaxCluster];    // every rank's two position layers (generic addresses)
+    const float4 *box[kMaxCluster];       // every rank's block boxes
+    const ClusterExtra *peer[kMaxCluster];
+};
+
+__host__ __device__ inline size_t cluster_smem(int m, int row_width) {
+    return layout_bytes(m, row_width, false) + (sizeof(ClusterExtra) + 15) / 16 * 16;
+}
+
+__device__ __forceinline__ ClusterExtra *cluster_extra(int m, int row_width) {
+    return reinterpret_cast<ClusterExtra *>(g_smem + layout_bytes(m, row_width, false));
+}
+
+// Position of system bead j at layer `cur`.
+__device__ __forceinline__ float4 cfetch(const ClusterExtra *X, int cur, int j, int sh) {
+    return X->lay[cur][j >> sh][j & ((1 << sh) - 1)];
+}
+
+// Rows of this CTA's slots (system-local bead index in every entry). Boxes of every
+// rank must be current (a cluster barrier after block_boxes).
+template <int BPT>
+__device__ void cluster_rows(const BatchedArgs &a, const Layout<false> &L, const ClusterExtra *X, const uint16_t *order,
+                             int cur, int n_loc, int lo, int n_s, int sh, int nat_off, int b0) {
+    const int T = blockDim.x, m = 1 << sh;
+    const float cut2 = a.sa.cut2_f;
+    const float lo2 = cut2 - cut2 * 1e-4f, hi2 = cut2 + cut2 * 1e-4f;
+    uint16_t *row = L.row();
+#pragma unroll 1
+    for (int k = 0; k < BPT; ++k) {
+        const int p = threadIdx.x + k * T;
+        if (p >= n_loc) continue;
+        const int l = order[p];
+        const int b = lo + l;   // system-local bead
+        const float4 pb = L.lay(cur)[l];
+        const int nn = a.nat_ell_cnt[b0 + b];
+        const uint16_t *natc = a.nat_ell_col + nat_off + b;
+        for (int q = 0; q < nn; ++q) row[q * m + p] = __ldg(natc + q * n_s);
+        const float2 bd = L.bond()[l];
+        int q = 0;
+        int next_nat = nn > 0 ? (int)__ldg(natc) : 0x7fffffff;
+        int cnt = 0;
+        for (int base = 0; base < n_s; base += 32) {
+            const int owner = base >> sh, lb = (base & (m - 1)) >> 5;
+            const float4 blo = X->box[owner][2 * lb], bhi = X->box[owner][2 * lb + 1];
+            const float ex = fmaxf(fmaxf(blo.x - pb.x, pb.x - bhi.x), 0.f);
+            const float ey = fmaxf(fmaxf(blo.y - pb.y, pb.y - bhi.y), 0.f);
+            const float ez = fmaxf(fmaxf(blo.z - pb.z, pb.z - bhi.z), 0.f);
+            const float4 *src = X->lay[cur][owner];
+            const int lbase = base & (m - 1);
+            uint32_t within = 0u, near = 0u;
+            if (fmaf(ez, ez, fmaf(ey, ey, ex * ex)) < hi2) {
+                if (base + 32 <= n_s) scan32<true>(src, lbase, 32, pb, lo2, hi2, &within, &near);
+                else scan32<false>(src, lbase, n_s - base, pb, lo2, hi2, &within, &near);
+            }
+            uint32_t ex_mask = 0u;
+            if (b >= base && b < base + 32) ex_mask |= 1u << (b - base);
+            if (bd.x > 0.f && b - 1 >= base && b - 1 < base + 32) ex_mask |= 1u << (b - 1 - base);
+            if (bd.y > 0.f && b + 1 >= base && b + 1 < base + 32) ex_mask |= 1u << (b + 1 - base);
+            while (next_nat < base + 32) {
+                ex_mask |= 1u << (next_nat - base);
+                ++q;
+                next_nat = q < nn ? (int)__ldg(natc + q * n_s) : 0x7fffffff;
+            }
+            within &= ~ex_mask;
+            near &= ~ex_mask;
+            while (near) {
+                const int t = __ffs(near) - 1;
+                near &= near - 1;
+                if (within_cut(pb, src[lbase + t], cut2, a.sa.cut2_d)) within |= 1u << t;
+            }
+            while (within) {
+                const int t = __ffs(within) - 1;
+                within &= within - 1;
+                if (cnt < a.cap) row[(nn + cnt) * m + p] = (uint16_t)(base + t);
+                ++cnt;
+            }
+        }
+        if (cnt > a.cap) cta_fail(L.h(), SOP_ERR_PAIRLIST_OVERFLOW);
+        L.n_nat()[p] = (uint16_t)nn;
+        L.n_tot()[p] = (uint16_t)(nn + min(cnt, a.cap));
+    }
+}
+
+// Eq. 1 pair forces on own bead l (system bead b) in slot p at layer cur.
+__device__ __forceinline__ float3 cluster_force(const BatchedArgs &a, const Layout<false> &L, const ClusterExtra *X,
+                                                int cur, int sh, int n_s, int nat_off, int l, int b, int p,
+                                                bool *broken) {
+    const ForceParams &fp = a.sa.fp;
+    const int m = 1 << sh;
+    const float4 pb = L.lay(cur)[l];
+    float fx = 0.f, fy = 0.f, fz = 0.f;
+    const float2 bd = L.bond()[l];
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+        const float r0 = side ? bd.y : bd.x;
+        if (r0 > 0.f) {
+            const float4 pj = cfetch(X, cur, side ? b + 1 : b - 1, sh);
+            const float dx = pb.x - pj.x, dy = pb.y - pj.y, dz = pb.z - pj.z;
+            const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+            const float r = r2 * rsqrtf(r2);
+            const float dr = r - r0;
+            const float arg = fmaf(-dr * dr, fp.inv_R02, 1.0f);
+            float c = 0.f;
+            if (arg > 0.f) c = __fdividef(-fp.k_fene * dr, arg * r);
+            else *broken = true;
+            fx = fmaf(c, dx, fx); fy = fmaf(c, dy, fy); fz = fmaf(c, dz, fz);
+        }
+    }
+    const int nn = L.n_nat()[p], tot = L.n_tot()[p];
+    const float *natr = a.nat_ell_r0sq + nat_off + b;
+    const uint16_t *rowp = L.row() + p;
+    const float A = fp.eps12_h, B = fp.eps6_l;
+#pragma unroll 2
+    for (int k = 0; k < tot; ++k) {
+        const bool nat = k < nn;
+        const int j = rowp[k * m];
+        const float s0 = nat ? __ldg(natr + k * n_s) : fp.sigma2;
+        const float4 pj = cfetch(X, cur, j, sh);
+        const float dx = pb.x - pj.x, dy = pb.y - pj.y, dz = pb.z - pj.z;
+        const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+        const float inv = __fdividef(1.0f, r2);
+        const float s = s0 * inv;
+        const float s3 = s * s * s;
+        const float c = inv * s3 * (nat ? fmaf(A, s3, -A) : B);
+        fx = fmaf(c, dx, fx); fy = fmaf(c, dy, fy); fz = fmaf(c, dz, fz);
+    }
+    return make_float3(fx, fy, fz);
+}
+
+// FP64 observables of the cluster's system at layer cur: every CTA sums its own beads,
+// rank 0 adds the CTA sums after a cluster barrier and writes the record.
+template <int BPT>
+__device__ __noinline__ void cluster_observe(const BatchedArgs &a, const Layout<false> &L, ClusterExtra *X,
+                                             const uint16_t *order, int cur, int n_loc, int lo, int sh, int b0,
+                                             int r, int s, int g, int64_t step, int64_t event, int rank, int C) {
+    const StepArgs &sa = a.sa;
+    const DevTopo &t = sa.topo;
+    const DevExternal &e = sa.ext;
+    const int T = blockDim.x, m = 1 << sh;
+    const uint16_t *row = L.row();
+    double v[6] = {0, 0, 0, 0, 0, 0};   // E, f_pull, ext, formed, f_wall, r_ee
+    const double R02 = sa.R0 * sa.R0, sig2 = sa.sigma * sa.sigma;
+    for (int k = 0; k < BPT; ++k) {
+        const int p = threadIdx.x + k * T;
+        if (p >= n_loc) continue;
+        const int l = order[p];
+        const int b = lo + l;
+        const int i = b0 + b;
+        const float4 pb = L.lay(cur)[l];
+        const double xi = pb.x, yi = pb.y, zi = pb.z;
+        if (L.bond()[l].y > 0.f) {
+            const float4 pj = cfetch(X, cur, b + 1, sh);
+            const double rr = __dsqrt_rn(dist2_d(xi, yi, zi, pj.x, pj.y, pj.z));
+            const double dr = rr - t.bond_r0d[i];
+            const double arg = 1.0 - dr * dr / R02;
+            if (arg > 0.0) v[0] += -0.5 * sa.k_fene * R02 * log(arg);
+        }
+        for (int q = t.nat_row[i]; q < t.nat_row[i + 1]; ++q) {
+            const int j = t.nat_col[q];
+            if (j < i) continue;
+            const float4 pj = cfetch(X, cur, j - b0, sh);
+            const double d2 = dist2_d(xi, yi, zi, pj.x, pj.y, pj.z);
+            const double r0 = t.nat_r0[q];
+            const double u = r0 * r0 / d2;
+            const double u3 = u * u * u;
+            v[0] += sa.eps_h * (u3 * u3 - 2.0 * u3);
+            if (__dsqrt_rn(d2) < r0 + 2.0) v[3] += 1.0;
+        }
+        for (int q = L.n_nat()[p]; q < L.n_tot()[p]; ++q) {
+            const int j = row[q * m + p];
+            if (j < b) continue;
+            const float4 pj = cfetch(X, cur, j, sh);
+            const double c = sig2 / dist2_d(xi, yi, zi, pj.x, pj.y, pj.z);
+            v[0] += sa.eps_l * c * c * c;
+        }
+        const uint8_t fl = L.flags()[l];
+        if (fl & kFlagPulled) {
+            const int qq = e.pull_of_sys[s];
+            if (qq >= 0 && e.pull_bead[qq] == i) {
+                const double tt = e.pull_v[qq] * ((double)step - e.pull_n0[qq]);
+                const double *tip0 = e.pull_tip0 + ((size_t)r * e.n_pull + qq) * 3;
+                const double *dir = e.pull_dir + 3 * qq;
+                const double x[3] = {xi, yi, zi};
+                double f = 0.0;
+                for (int c = 0; c < 3; ++c) f += e.pull_ks[qq] * (tip0[c] + tt * dir[c] - x[c]) * dir[c];
+                v[1] += f;
+                const float4 pa = cfetch(X, cur, e.pull_anchor[qq] - b0, sh);
+                v[2] += __dsqrt_rn(dist2_d(xi, yi, zi, pa.x, pa.y, pa.z));
+            }
+        }
+        if (e.has_indenter) {
+            const double tt = e.ind_v * ((double)step - e.ind_n0);
+            const double c[3] = {e.ind_c0[0] + tt * e.ind_dir[0], e.ind_c0[1] + tt * e.ind_dir[1],
+                                 e.ind_c0[2] + tt * e.ind_dir[2]};
+            const double ex = xi - c[0], ey = yi - c[1], ez = zi - c[2];
+            const double rr = __dsqrt_rn((ex * ex + ey * ey) + ez * ez);
+            const double rho = rr - e.ind_radius;
+            if (rho > 0.0) {
+                const double qq = sa.sigma / rho;
+                const double q2 = qq * qq;
+                const double coef = 6.0 * sa.eps_l * (q2 * q2 * q2) / rho / rr;
+                v[4] += coef * ((ex * e.ind_dir[0] + ey * e.ind_dir[1]) + ez * e.ind_dir[2]);
+            }
+        }
+        if (fl & kFlagFirstOfSystem) {
+            const float4 pl_ = cfetch(X, cur, t.sys_ree_last[s] - b0, sh);
+            v[5] += __dsqrt_rn(dist2_d(xi, yi, zi, pl_.x, pl_.y, pl_.z));
+        }
+    }
+    block_sum6(v, L.h());
+    if (threadIdx.x == 0)
+        for (int k = 0; k < 6; ++k) X->part[k] = v[k];
+    cg::this_cluster().sync();
+    if (rank == 0 && threadIdx.x == 0) {
+        double w[6] = {0, 0, 0, 0, 0, 0};
+        for (int q = 0; q < C; ++q)
+            for (int k = 0; k < 6; ++k) w[k] += X->peer[q]->part[k];
+        sop_record rec;
+        rec.step = (double)step;
+        rec.replica = (double)r;
+        rec.system = (double)s;
+        rec.energy = w[0];
+        const bool pulled = e.pull_of_sys[s] >= 0;
+        rec.f_ext = pulled ? w[1] : (e.has_indenter ? w[4] : 0.0);
+        rec.extension = pulled ? w[2] : (e.has_indenter ? e.ind_v * ((double)step - e.ind_n0) : 0.0);
+        const int np = t.sys_nat_pairs[s];
+        rec.q = np > 0 ? w[3] / (double)np : 0.0;
+        rec.r_ee = w[5];
+        a.obs.ring[(event * a.n_seg + g) % a.obs.cap] = rec;
+    }
+    __syncthreads();
+}
+
+// A rebuild of this CTA's rows from layer cur: own block boxes, a cluster barrier (every
+// rank's boxes are then current), slot order, rows. Ends with a CTA barrier.
+template <int BPT>
+__device__ int cluster_rebuild(const BatchedArgs &a, const Layout<false> &L, const ClusterExtra *X, int cur, int n_loc,
+                               int lo, int n_s, int sh, int nat_off, int b0, int ord) {
+    block_boxes(L, L.lay(cur), n_loc);
+    cg::this_cluster().sync();
+    ord = reorder_slots(L, n_loc, ord);
+    cluster_rows<BPT>(a, L, X, L.order(ord), cur, n_loc, lo, n_s, sh, nat_off, b0);
+    __syncthreads();
+    return ord;
+}
+
+template <int BPT, int MAXT>
+__global__ void __launch_bounds__(MAXT, 1) k_cluster(BatchedArgs a, int sh) {
+    cg::cluster_group cl = cg::this_cluster();
+    const int rank = (int)cl.block_rank();
+    const int C = (int)cl.num_blocks();
+    const int item = blockIdx.x / C;
+    const int m = 1 << sh;
+    Layout<false> L;
+    L.mx = m;
+    L.grow = nullptr;
+    ClusterExtra *X = cluster_extra(m, a.row_width);
+    const int r = a.item_rep[item], s = a.item_sys[item];
+    const StepArgs &sa = a.sa;
+    const DevTopo &t = sa.topo;
+    const int b0 = t.sys_lo[s], n_s = t.sys_lo[s + 1] - b0;
+    const int lo = rank * m;
+    const int n_loc = max(0, min(m, n_s - lo));
+    const int gbase = r * t.n + b0;
+    const int g = r * t.n_sys + s;
+    const int nat_off = a.nat_ell_off[s];
+    const int T = blockDim.x;
+    const int64_t step0 = *a.d_step;
+    const bool forces_only = (a.n_steps == 0 && a.force_out != nullptr);
+    if (threadIdx.x == 0) {
+        L.h()->fail = 0;
+        X->fail_step = kNoFail;
+        X->frozen = (!forces_only && (sa.rep_status[r] != 0 || *sa.halt != 0)) ? 1 : 0;
+    }
+    for (int k = threadIdx.x; k < 3 * C + 2; k += T) {
+        if (k < 2 * C) X->lay[k / C][k % C] = cl.map_shared_rank(L.lay(k / C), k % C);
+        else if (k < 3 * C) X->box[k - 2 * C] = cl.map_shared_rank(L.bbox(), k - 2 * C);
+    }
+    for (int k = threadIdx.x; k < C; k += T) X->peer[k] = cl.map_shared_rank(X, k);
+    cl.sync();
+    const bool frozen = X->peer[0]->frozen != 0;   // rank 0's reading, the same for every CTA
+    if (frozen) {
+        if (rank == 0 && threadIdx.x == 0)
+            missing_records(a, r, s, g, step0, step0, a.d_events ? *a.d_events : 0);
+        cl.sync();   // no CTA leaves while another may still read its shared memory
+        return;
+    }
+    int k_phase = (int)(step0 % a.K);
+    int o_phase = a.obs_every > 0 ? (int)(step0 % a.obs_every) : 0;
+    for (int l = threadIdx.x; l < n_loc; l += T) {
+        const int b = lo + l, i = b0 + b;
+        L.lay(0)[l] = a.pos[gbase + b];
+        L.comp()[l] = a.comp[gbase + b];
+        L.bond()[l] = make_float2(b > 0 ? t.bond_r0[i - 1] : -1.f, t.bond_r0[i]);
+        L.flags()[l] = t.flags[i];
+        L.order(0)[l] = (uint16_t)l;
+        L.n_tot()[l] = (uint16_t)a.nat_ell_cnt[i];
+        if (k_phase != 0) L.lay(1)[l] = a.snap[gbase + b];
+    }
+    cl.sync();
+
+    int cur = 0, ord = 0, n_events = 0;
+    bool built_now = false;
+    int it = 0;
+    for (; it < a.n_steps || (forces_only && it == 0); ++it) {
+        if (it == 0 && k_phase != 0 && !forces_only) {
+            ord = cluster_rebuild<BPT>(a, L, X, cur ^ 1, n_loc, lo, n_s, sh, nat_off, b0, ord);   // the snapshot layer
+        } else if ((k_phase == 0 && !built_now) || forces_only) {
+            ord = cluster_rebuild<BPT>(a, L, X, cur, n_loc, lo, n_s, sh, nat_off, b0, ord);
+            if (!forces_only)
+                for (int l = threadIdx.x; l < n_loc; l += T) a.snap[gbase + lo + l] = L.lay(cur)[l];
+        }
+        built_now = false;
+        const int64_t step = step0 + it;
+        const uint16_t *order = L.order(ord);
+        if (forces_only) {
+            for (int p = threadIdx.x; p < n_loc; p += T) {
+                const int l = order[p], b = lo + l;
+                bool broken = false, overlap = false;
+                const float3 f = cluster_force(a, L, X, cur, sh, n_s, nat_off, l, b, p, &broken);
+                const float3 fe = ext_force(sa, r, b0 + b, L.flags()[l], L.lay(cur)[l], step, &overlap);
+                a.force_out[gbase + b] = make_float4(f.x + fe.x, f.y + fe.y, f.z + fe.z, (broken || overlap) ? 1.f : 0.f);
+                if (a.pl_dump_col) {
+                    const size_t rowi = (size_t)gbase + b;
+                    const int nn = L.n_nat()[p], np = L.n_tot()[p] - nn;
+                    a.pl_dump_start[rowi] = (int)(rowi * a.pl_dump_stride);
+                    a.pl_dump_len[rowi] = np;
+                    for (int q = 0; q < np; ++q)
+                        a.pl_dump_col[rowi * a.pl_dump_stride + q] = b0 + (int)L.row()[(nn + q) * m + p];
+                }
+            }
+            break;
+        }
+        float4 *Q = L.lay(cur ^ 1);
+#pragma unroll 1
+        for (int k = 0; k < BPT; ++k) {
+            const int p = threadIdx.x + k * T;
+            if (p >= n_loc) continue;
+            const int l = order[p], b = lo + l;
+            bool broken = false, overlap = false;
+            const float3 f = cluster_force(a, L, X, cur, sh, n_s, nat_off, l, b, p, &broken);
+            const float4 p_old = L.lay(cur)[l];
+            const uint8_t fl = L.flags()[l];
+            const float3 fe = ext_force(sa, r, b0 + b, fl, p_old, step, &overlap);
+            float4 pb = p_old;
+            if (broken || overlap) {
+                cta_fail(L.h(), broken ? SOP_ERR_FENE_BREAK : SOP_ERR_INDENTER_OVERLAP);
+            } else if (!(fl & kFlagFixed)) {
+                float3 gn;
+                if (sa.taus) {
+                    uint4 st = sa.taus[gbase + b];
+                    gn = taus_noise(st);
+                    sa.taus[gbase + b] = st;
+                } else {
+                    gn = bead_noise(sa.seed + (uint64_t)r, step, (uint32_t)(b0 + b));
+                }
+                float4 c = L.comp()[l];
+                float4 w;
+                if (sa.vel) {
+                    w = sa.vel[gbase + b];
+                    const float v1x = fmaf(f.x + fe.x, sa.h_m, w.x), v1y = fmaf(f.y + fe.y, sa.h_m, w.y),
+                                v1z = fmaf(f.z + fe.z, sa.h_m, w.z);
+                    w.x = fmaf(sa.c1, v1x, sa.c2 * gn.x);
+                    w.y = fmaf(sa.c1, v1y, sa.c2 * gn.y);
+                    w.z = fmaf(sa.c1, v1z, sa.c2 * gn.z);
+                    kahan_add(pb.x, c.x, sa.half_h * (v1x + w.x));
+                    kahan_add(pb.y, c.y, sa.half_h * (v1y + w.y));
+                    kahan_add(pb.z, c.z, sa.half_h * (v1z + w.z));
+                } else {
+                    kahan_add(pb.x, c.x, fmaf(f.x + fe.x, sa.fp.mob, gn.x * sa.fp.amp));
+                    kahan_add(pb.y, c.y, fmaf(f.y + fe.y, sa.fp.mob, gn.y * sa.fp.amp));
+                    kahan_add(pb.z, c.z, fmaf(f.z + fe.z, sa.fp.mob, gn.z * sa.fp.amp));
+                }
+                if (isfinite(pb.x) && isfinite(pb.y) && isfinite(pb.z)) {
+                    L.comp()[l] = c;
+                    if (sa.vel) sa.vel[gbase + b] = w;
+                } else {
+                    cta_fail(L.h(), SOP_ERR_NONFINITE);
+                    pb = p_old;
+                }
+            }
+            Q[l] = pb;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0 && L.h()->fail != 0 && X->fail_step == kNoFail) X->fail_step = it;
+        cl.sync();   // the next layer is complete in every CTA
+        cur ^= 1;
+        k_phase = k_phase + 1 == a.K ? 0 : k_phase + 1;
+        if (a.obs_every > 0) o_phase = o_phase + 1 == a.obs_every ? 0 : o_phase + 1;
+        // the replica freezes after the step in which any CTA failed (a decision every
+        // CTA takes from the same values: a CTA's fail_step is written once, before a barrier)
+        bool stop = false;
+        for (int q = 0; q < C; ++q) stop |= X->peer[q]->fail_step <= it;
+        if (stop) { ++it; break; }
+        if (a.obs_every > 0 && o_phase == 0) {
+            if (k_phase == 0) {
+                ord = cluster_rebuild<BPT>(a, L, X, cur, n_loc, lo, n_s, sh, nat_off, b0, ord);
+                built_now = true;
+                for (int l = threadIdx.x; l < n_loc; l += T) a.snap[gbase + lo + l] = L.lay(cur)[l];
+            }
+            const int64_t ev = (a.d_events ? *a.d_events : 0) + n_events;
+            cluster_observe<BPT>(a, L, X, L.order(ord), cur, n_loc, lo, sh, b0, r, s, g, step + 1, ev, rank, C);
+            ++n_events;
+        }
+    }
+    if (!forces_only) {
+        int code = 0;
+        for (int q = 0; q < C && code == 0; ++q) code = X->peer[q]->fail_step != kNoFail ? 1 : 0;
+        if (code && rank == 0 && threadIdx.x == 0)
+            missing_records(a, r, s, g, step0, step0 + it, (a.d_events ? *a.d_events : 0) + n_events);
+        for (int l = threadIdx.x; l < n_loc; l += T) {
+            a.pos[gbase + lo + l] = L.lay(cur)[l];
+            a.comp[gbase + lo + l] = L.comp()[l];
+        }
+        if (threadIdx.x == 0 && L.h()->fail != 0) atomicCAS(&sa.rep_status[r], 0, L.h()->fail);
+    }
+    cl.sync();   // no CTA leaves while another may still read its shared memory
+}
+
+template <int BPT, int MAXT>
+cudaError_t launch_cl(const BatchedArgs &a, const BatchedConfig &cfg, cudaStream_t s) {
+    auto kern = k_cluster<BPT, MAXT>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cfg.smem);
+    if (e != cudaSuccess) return e;
+    if (cfg.cluster > 8) {
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        if (e != cudaSuccess) return e;
+    }
+    cudaLaunchConfig_t lc = {};
+    lc.gridDim = dim3((unsigned)(a.n_items * cfg.cluster), 1, 1);
+    lc.blockDim = dim3((unsigned)cfg.threads, 1, 1);
+    lc.dynamicSmemBytes = cfg.smem;
+    lc.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = (unsigned)cfg.cluster;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    lc.attrs = at;
+    lc.numAttrs = 1;
+    return cudaLaunchKernelEx(&lc, kern, a, cfg.m_shift);
+}
+
 template <int BPT, int MINB, int MAXT, bool RG>
 cudaError_t launch_t(const BatchedArgs &a, const BatchedConfig &cfg, cudaStream_t s) {
     auto kern = k_batched<BPT, MINB, MAXT, RG>;
@@ -694,9 +1161,57 @@ bool batched_config(int max_n, int row_width, int threads, bool rows_global, int
     return cfg->smem <= 227 * 1024;
 }
 
+bool cluster_config(int max_n, int row_width, int threads, int m_shift, BatchedConfig *cfg) {
+    if (m_shift < 5 || m_shift > 9 || max_n <= 0 || max_n > 8192 || row_width > kKeys - 1) return false;
+    const int m = 1 << m_shift;
+    const int C = (max_n + m - 1) / m;
+    if (C < 2 || C > kMaxCluster || threads % 32 || threads < 32 || threads > 512) return false;
+    const int bpt = (m + threads - 1) / threads;
+    if (bpt > 2) return false;
+    cfg->threads = threads;
+    cfg->beads_per_thread = bpt;
+    cfg->min_blocks = 1;
+    cfg->rows_global = false;
+    cfg->row_width = row_width;
+    cfg->smem = cluster_smem(m, row_width);
+    cfg->cluster = C;
+    cfg->m_shift = m_shift;
+    return cfg->smem <= 227 * 1024;
+}
+
+// Clusters of this configuration that can be resident at once (0: it cannot launch).
+int cluster_capacity(const BatchedConfig &cfg) {
+    if (cfg.cluster <= 0) return 0;
+    auto kern = cfg.beads_per_thread == 1 ? k_cluster<1, 512> : k_cluster<2, 512>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cfg.smem) != cudaSuccess ||
+        (cfg.cluster > 8 && cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)) {
+        cudaGetLastError();
+        return 0;
+    }
+    cudaLaunchConfig_t lc = {};
+    lc.gridDim = dim3((unsigned)cfg.cluster, 1, 1);
+    lc.blockDim = dim3((unsigned)cfg.threads, 1, 1);
+    lc.dynamicSmemBytes = cfg.smem;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = (unsigned)cfg.cluster;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    lc.attrs = at;
+    lc.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, kern, &lc) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return n;
+}
+
 cudaError_t launch_batched(const BatchedArgs &a, const BatchedConfig &cfg, cudaStream_t s, int64_t *launches) {
     if (a.n_items <= 0) return cudaSuccess;
     if (launches) *launches += 1;
+    if (cfg.cluster > 0)
+        return cfg.beads_per_thread == 1 ? launch_cl<1, 512>(a, cfg, s) : launch_cl<2, 512>(a, cfg, s);
     if (cfg.rows_global) {
         switch (cfg.beads_per_thread) {
         case 1: return launch_t<1, 1, 1024, true>(a, cfg, s);

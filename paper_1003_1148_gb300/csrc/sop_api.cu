@@ -751,6 +751,25 @@ sop_status tune_bucket(sop_ctx *c, sop_ctx::Bucket &bk) {
         if (threads > need && threads > 128) continue;
         if (batched_config(bk.max_n, bk.row_width, threads, true, 1, &cfg)) cands.push_back(cfg);
     }
+    // the cluster form for larger systems: one system over 2..16 CTAs of 2^sh beads each.
+    // SOP_FORCE_CLUSTER=sh keeps only the cluster configurations of 2^sh beads per CTA (sh 5
+    // to 9, when the bucket has one): a tuning override that makes the form testable at any size
+    const char *fc = std::getenv("SOP_FORCE_CLUSTER");
+    const int force_sh = fc ? std::atoi(fc) : 0;
+    if (bk.max_n > 256 || force_sh > 0) {
+        std::vector<BatchedConfig> clusters;
+        for (int sh = 5; sh <= 9; ++sh) {
+            if (force_sh > 0 ? sh != force_sh : sh < 7) continue;
+            for (int threads : {1 << sh, (1 << sh) / 2}) {
+                BatchedConfig cfg;
+                if (threads < (force_sh > 0 ? 32 : 64) || threads > 512) continue;
+                if (cluster_config(bk.max_n, bk.row_width, threads, sh, &cfg) && cluster_capacity(cfg) > 0)
+                    clusters.push_back(cfg);
+            }
+        }
+        if (force_sh > 0 && !clusters.empty()) cands = clusters;
+        else cands.insert(cands.end(), clusters.begin(), clusters.end());
+    }
     if (cands.empty()) return fail(c, SOP_ERR_UNSUPPORTED, "no batched configuration fits the bucket");
     // default without a trial: shared-memory rows, the largest CTA at 64 registers; else global rows
     bk.cfg = cands[0];
@@ -767,12 +786,12 @@ sop_status tune_bucket(sop_ctx *c, sop_ctx::Bucket &bk) {
             if (FILE *f = std::fopen(cache, "r")) {
                 char line[256];
                 while (!cached && std::fgets(line, sizeof line, f)) {
-                    int t = 0, bpt = 0, mb = 0, rg = 0;
+                    int t = 0, bpt = 0, mb = 0, rg = 0, cs = 0, sh = 0;
                     if (std::strncmp(line, key, std::strlen(key)) == 0 &&
-                        std::sscanf(line + std::strlen(key), " -> %d %d %d %d", &t, &bpt, &mb, &rg) == 4) {
+                        std::sscanf(line + std::strlen(key), " -> %d %d %d %d %d %d", &t, &bpt, &mb, &rg, &cs, &sh) == 6) {
                         for (const auto &cf : cands)
                             if (cf.threads == t && cf.beads_per_thread == bpt && cf.min_blocks == mb &&
-                                (int)cf.rows_global == rg) {
+                                (int)cf.rows_global == rg && cf.cluster == cs && cf.m_shift == sh) {
                                 bk.cfg = cf;
                                 cached = true;
                             }
@@ -817,8 +836,14 @@ sop_status tune_bucket(sop_ctx *c, sop_ctx::Bucket &bk) {
                     cudaEventRecord(e0, c->stream);
                     cudaError_t e = launch_batched(a, cf, c->stream, nullptr);
                     cudaEventRecord(e1, c->stream);
-                    if (e != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
-                        status = fail(c, SOP_ERR_CUDA, std::string("autotune trial: ") + cudaGetErrorString(e));
+                    if (e != cudaSuccess) {   // a configuration this device cannot launch: not a candidate
+                        cudaGetLastError();
+                        ms = 1e30f;
+                        break;
+                    }
+                    const cudaError_t es = cudaEventSynchronize(e1);
+                    if (es != cudaSuccess) {
+                        status = fail(c, SOP_ERR_CUDA, std::string("autotune trial: ") + cudaGetErrorString(es));
                         break;
                     }
                     float t = 0.f;
@@ -839,8 +864,8 @@ sop_status tune_bucket(sop_ctx *c, sop_ctx::Bucket &bk) {
             c->st.tune_ms += best_ms;
             if (cache)
                 if (FILE *f = std::fopen(cache, "a")) {
-                    std::fprintf(f, "%s -> %d %d %d %d %.4f\n", key, bk.cfg.threads, bk.cfg.beads_per_thread,
-                                 bk.cfg.min_blocks, (int)bk.cfg.rows_global, best_ms);
+                    std::fprintf(f, "%s -> %d %d %d %d %d %d %.4f\n", key, bk.cfg.threads, bk.cfg.beads_per_thread,
+                                 bk.cfg.min_blocks, (int)bk.cfg.rows_global, bk.cfg.cluster, bk.cfg.m_shift, best_ms);
                     std::fclose(f);
                 }
         }
@@ -1237,6 +1262,9 @@ sop_status create_impl(sop_ctx *c, const sop_topology *topo, const double *xyz, 
         c->st.beads_per_thread = cfg.beads_per_thread;
         c->st.min_blocks = cfg.rows_global ? 0 : cfg.min_blocks;
         c->st.buckets = (int32_t)c->buckets.size();
+        c->st.cluster_size = cfg.cluster;
+        c->st.cluster_buckets = 0;
+        for (const auto &bk : c->buckets) c->st.cluster_buckets += bk.cfg.cluster > 0 ? 1 : 0;
     }
     (void)mrow;
     CUDA_OR_RETURN(c, cudaStreamSynchronize(c->stream));

@@ -234,11 +234,18 @@ struct BatchedConfig {
     bool rows_global = false;  // neighbour rows in global memory instead of shared memory
     int row_width = 0;
     size_t smem = 0;
+    int cluster = 0;           // > 0: the cluster form, one system over `cluster` CTAs of 2^m_shift beads each
+    int m_shift = 0;
 };
 
 // A configuration for systems of at most max_n beads whose merged rows hold up to
 // row_width entries (natives + Verlet capacity); false when no compiled instance fits.
 bool batched_config(int max_n, int row_width, int threads, bool rows_global, int min_blocks, BatchedConfig *cfg);
+// The cluster form: each system is split over ceil(max_n / 2^m_shift) CTAs (at most 16)
+// of `threads` threads that own 2^m_shift consecutive beads each; false when it does not fit.
+bool cluster_config(int max_n, int row_width, int threads, int m_shift, BatchedConfig *cfg);
+// Clusters of the configuration that fit the device at once (0: it cannot launch).
+int cluster_capacity(const BatchedConfig &cfg);
 // Run n_steps (or forces only when a.force_out != null and n_steps == 0).
 cudaError_t launch_batched(const BatchedArgs &a, const BatchedConfig &cfg, cudaStream_t s, int64_t *launches);
 

@@ -84,7 +84,8 @@ class Stats(C.Structure):
                 ("rebuilds", C.c_int64), ("schedule", C.c_int32), ("block_threads", C.c_int32),
                 ("pairs_per_bead", C.c_int32), ("beads_per_thread", C.c_int32), ("min_blocks", C.c_int32),
                 ("buckets", C.c_int32),
-                ("pairlist_entries", C.c_int64), ("native_entries", C.c_int64), ("tune_ms", C.c_double)]
+                ("pairlist_entries", C.c_int64), ("native_entries", C.c_int64), ("tune_ms", C.c_double),
+                ("cluster_buckets", C.c_int32), ("cluster_size", C.c_int32)]
 
 
 def load(path: str | None = None):

@@ -1,0 +1,120 @@
+"""The cluster form of the batched schedule (one system over a thread-block cluster,
+partners read from the owner CTA's shared memory) through the C ABI (needs a GPU).
+
+The tuning override SOP_FORCE_CLUSTER=sh makes every bucket with systems larger than
+2^sh beads run in the cluster form with 2^sh beads per CTA, so small systems exercise
+clusters of several CTAs (including CTAs that own no bead of a shorter system).
+* same arithmetic in the same order as the one-CTA form: positions bit-identical;
+* parity with the FP64 oracle: Verlet lists bit-exact, forces within 1e-5 of the term
+  scale, 100-step trajectories within 1e-3 A RMS, FP64 observables;
+* checkpoint/resume bit-exact; a failing replica freezes alone (the failure decision is
+  taken by every CTA of the cluster from the same values).
+"""
+import os
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sop():
+    from paper_1003_1148_gb300 import build, sop as s
+    build.build()
+    s.load()
+    return s
+
+
+def clustered(sop, w, sh, **kw):
+    os.environ["SOP_FORCE_CLUSTER"] = str(sh)
+    try:
+        sim = sop.from_workload(w, schedule="batched", **kw)
+    finally:
+        del os.environ["SOP_FORCE_CLUSTER"]
+    assert sim.stats()["cluster_buckets"] > 0
+    return sim
+
+
+def small_uneven(synth):
+    return synth.uneven(n_chains=6, lo=90, hi=300, steps=100)
+
+
+def test_cluster_equals_one_cta_form(sop, synth):
+    w = small_uneven(synth)
+    a = sop.from_workload(w, n_replicas=2, schedule="batched")
+    b = clustered(sop, w, 5, n_replicas=2)
+    assert a.stats()["cluster_buckets"] == 0
+    a.step(57)
+    b.step(57)
+    assert np.array_equal(a.get_positions(-1), b.get_positions(-1))
+    ra, ca = a.get_pairlist(1)
+    rb, cb = b.get_pairlist(1)
+    assert np.array_equal(ra, rb) and np.array_equal(ca, cb)
+
+
+@pytest.mark.parametrize("sh", [5, 6])
+def test_cluster_parity_with_oracle(sop, orc, synth, sh):
+    w = small_uneven(synth)
+    R = 2
+    sim = clustered(sop, w, sh, n_replicas=R)
+    x0 = sim.get_positions(0)
+    m = orc.model_from_workload(w)
+    sys_of = w.system_of_bead()
+    m.start_pulls([(int(sys_of[p.anchor]), p.anchor, p.pulled, p.k_s, p.v) for p in w.pulls], x0)
+    sim.step(30)
+    for r in range(R):
+        x = sim.get_positions(r)
+        rp, col = sim.get_pairlist(r)
+        pi, pj = m.pairlist(x)
+        got = {(i, int(j)) for i in range(len(rp) - 1) for j in col[rp[i]:rp[i + 1]] if j > i}
+        assert got == set(zip(pi.tolist(), pj.tolist()))
+        F, E = sim.forces(r)
+        Fo, Ao, Eo = m.forces(x, step=30)
+        assert (np.abs(F - Fo) / Ao).max() <= 1e-5
+        assert E == pytest.approx(Eo[0] + Eo[1] + Eo[2], rel=1e-9, abs=1e-9)
+    sim.close()
+    sim = clustered(sop, w, sh, n_replicas=R, obs_every=20)
+    sim.step(100)
+    for r in range(R):
+        xo, _, _, _ = m.run(x0, 100, seed=w.seed + r)
+        rms = float(np.sqrt(((sim.get_positions(r) - xo) ** 2).sum(1).mean()))
+        assert rms <= 1e-3, (sh, r, rms)
+    rec, lost = sim.get_observables()
+    assert lost == 0 and len(rec) == 5 * R * w.n_systems
+    last = rec[rec[:, 0] == 100]
+    for r in range(R):
+        x = sim.get_positions(r)
+        ref = m.observables(x, pl=m.pairlist(x), step=100)
+        got = last[last[:, 1] == r]
+        got = got[np.argsort(got[:, 2])]
+        assert np.allclose(got[:, 3], ref[:, 2], rtol=1e-9, atol=1e-9)
+        assert np.array_equal(got[:, 6], ref[:, 5])
+    sim.close()
+
+
+def test_cluster_checkpoint_and_failure(sop, synth):
+    w = small_uneven(synth)
+    sim = clustered(sop, w, 5, n_replicas=3)
+    sim.step(23)
+    state = sim.get_state()
+    sim.step(41)
+    a = sim.get_positions(-1).copy()
+    sim.set_state(state)
+    sim.step(41)
+    assert np.array_equal(a, sim.get_positions(-1))
+    # stretch one bond of replica 1 beyond R0: that replica fails and freezes alone
+    x = sim.get_positions(1)
+    i = int(w.chain_offsets[2]) + 40
+    x[i + 1:int(w.chain_offsets[3])] += np.array([5.0, 0.0, 0.0])
+    sim.set_positions(x, replica=1)
+    frozen = sim.get_positions(1).copy()
+    rc = sim.step(30, raise_on_error=False)
+    st = sim.replica_status()
+    assert st[1] == sop.ERR_FENE_BREAK and st[0] == 0 and st[2] == 0
+    after = sim.get_positions(1)
+    moved = np.abs(after - frozen).max(axis=1) > 0
+    assert moved.sum() < w.n_beads          # the failed replica stopped within its first step
+    sim.step(10, raise_on_error=False)
+    assert np.array_equal(sim.get_positions(1), after)
+    sim.close()

@@ -42,7 +42,11 @@ def small_uneven(synth):
 
 def test_cluster_equals_one_cta_form(sop, synth):
     w = small_uneven(synth)
-    a = sop.from_workload(w, n_replicas=2, schedule="batched")
+    os.environ["SOP_TUNE"] = "0"          # the untuned default: one CTA per system, rows in shared memory
+    try:
+        a = sop.from_workload(w, n_replicas=2, schedule="batched")
+    finally:
+        del os.environ["SOP_TUNE"]
     b = clustered(sop, w, 5, n_replicas=2)
     assert a.stats()["cluster_buckets"] == 0
     a.step(57)

@@ -67,6 +67,7 @@ def test_cluster_parity_with_oracle(sop, orc, synth, sh):
     sys_of = w.system_of_bead()
     m.start_pulls([(int(sys_of[p.anchor]), p.anchor, p.pulled, p.k_s, p.v) for p in w.pulls], x0)
     sim.step(30)
+    sim.pairlist_rebuild()     # the dumped list is the one of the positions of the last rebuild
     for r in range(R):
         x = sim.get_positions(r)
         rp, col = sim.get_pairlist(r)

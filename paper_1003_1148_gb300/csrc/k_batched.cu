@@ -127,8 +127,8 @@ __device__ __forceinline__ void block_sum6(double v[6], SharedHead *h) {
 }
 
 // Bounding boxes of the blocks of 32 consecutive beads of layer src (one warp per block).
-template <bool RG>
-__device__ void block_boxes(const Layout<RG> &L, const float4 *src, int n_s) {
+template <class Lay>
+__device__ void block_boxes(const Lay &L, const float4 *src, int n_s) {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
     float4 *bb = L.bbox();
     for (int blk = w; blk * 32 < n_s; blk += nw) {
@@ -155,8 +155,8 @@ __device__ void block_boxes(const Layout<RG> &L, const float4 *src, int n_s) {
 
 // Hand the slots to beads by decreasing row length of the last build (counting sort).
 // Returns the index (0/1) of the new order buffer. Must be called by all threads.
-template <bool RG>
-__device__ int reorder_slots(const Layout<RG> &L, int n_s, int cur_order) {
+template <class Lay>
+__device__ int reorder_slots(const Lay &L, int n_s, int cur_order) {
     const int T = blockDim.x;
     SharedHead *h = L.h();
     for (int k = threadIdx.x; k < kKeys; k += T) h->hist[k] = 0;
@@ -658,18 +658,19 @@ __global__ void __launch_bounds__(MAXT, MINB) k_batched(BatchedArgs a) {
 }
 
 // ===========================================================================
-// Cluster form: one system over a thread-block cluster (sm_90+ distributed
-// shared memory). CTA q of a cluster of C owns the system's beads
-// [q m, (q + 1) m), m = 2^m_shift a multiple of 32, with their two position
-// layers, compensation, bond lengths, slot orders, rows and block boxes in its
-// own shared memory, laid out exactly as one batched item of m beads. A bead's
-// partners are read from the owner CTA's shared memory through generic
-// addresses of the distributed shared memory window. One cluster barrier ends
-// every step (the next layer is complete everywhere); the rebuild adds one after
-// the block boxes. Every CTA of a cluster takes the same sequence of cluster
-// barriers: all control decisions (a frozen replica, a failure, the rebuild and
-// observable cadence) are made from values that every CTA reads after the same
-// barrier.
+// Cluster form: one system over a thread-block cluster (distributed shared
+// memory). CTA q of a cluster of C owns the system's beads [q m, (q + 1) m),
+// m = 2^m_shift a multiple of 32: their compensation, bond lengths, slot orders
+// and rows live in its shared memory, next to a full copy of the positions of the
+// whole system (both time layers). All reads are local: a CTA gathers forces and
+// builds rows exactly as the one-CTA form does, from its own copy. After the
+// update each CTA writes the new positions of its own beads into every copy in
+// the cluster (stores to distributed shared memory), and one cluster barrier
+// (release/acquire) ends the step. A copy's layer is only ever written while
+// every CTA reads the other layer, so no read meets a remote write. Every CTA of
+// a cluster takes the same sequence of cluster barriers: each control decision
+// (a frozen replica, a failure, the rebuild and observable cadence) comes from
+// values every CTA reads after the same barrier.
 // ===========================================================================
 constexpr int kMaxCluster = 16;
 constexpr int kNoFail = 0x7fffffff;
@@ -678,40 +679,66 @@ struct ClusterExtra {
     int fail_step;                        // first step of the launch at which this CTA failed
     int frozen;                           // rank 0: the replica was frozen at launch
     double part[6];                       // this CTA's observable sums
-    const float4 *lay[2][kMaxCluster];    // every rank's two position layers (generic addresses)
-    const float4 *box[kMaxCluster];       // every rank's block boxes
+    float4 *rpos[2][kMaxCluster];         // every rank's two position layers (generic addresses)
     const ClusterExtra *peer[kMaxCluster];
 };
 
-__host__ __device__ inline size_t cluster_smem(int m, int row_width) {
-    return layout_bytes(m, row_width, false) + (sizeof(ClusterExtra) + 15) / 16 * 16;
+// Shared-memory layout of one CTA of the cluster form: positions of all n_max = C m
+// beads (two layers), then own-bead state for m beads, block boxes of the whole
+// system, rows of the own slots, and the cluster bookkeeping.
+struct CLayout {
+    int nmax, m, rw;
+    __device__ __forceinline__ SharedHead *h() const { return reinterpret_cast<SharedHead *>(g_smem); }
+    __device__ __forceinline__ float4 *pos(int layer) const {
+        return reinterpret_cast<float4 *>(g_smem + kHeadBytes) + (size_t)layer * nmax;
+    }
+    __device__ __forceinline__ float4 *comp() const { return pos(2); }
+    __device__ __forceinline__ float2 *bond() const { return reinterpret_cast<float2 *>(comp() + m); }
+    __device__ __forceinline__ uint16_t *order(int i) const {
+        return reinterpret_cast<uint16_t *>(bond() + m) + i * m;
+    }
+    __device__ __forceinline__ uint16_t *n_nat() const { return order(2); }
+    __device__ __forceinline__ uint16_t *n_tot() const { return order(3); }
+    __device__ __forceinline__ uint8_t *flags() const { return reinterpret_cast<uint8_t *>(order(4)); }
+    __device__ __forceinline__ float4 *bbox() const {
+        const size_t off = (kHeadBytes + 32 * (size_t)nmax + 16 * (size_t)m + 8 * (size_t)m + 8 * (size_t)m + m + 15)
+                           / 16 * 16;
+        return reinterpret_cast<float4 *>(g_smem + off);
+    }
+    __device__ __forceinline__ uint16_t *row() const { return reinterpret_cast<uint16_t *>(bbox() + nmax / 16); }
+    __device__ __forceinline__ ClusterExtra *extra() const {
+        const size_t off = ((reinterpret_cast<unsigned char *>(row() + (size_t)rw * m) - g_smem) + 15) / 16 * 16;
+        return reinterpret_cast<ClusterExtra *>(g_smem + off);
+    }
+};
+
+__host__ __device__ inline size_t cluster_smem(int m, int nmax, int row_width) {
+    size_t s = kHeadBytes + 32 * (size_t)nmax + 16 * (size_t)m + 8 * (size_t)m + 8 * (size_t)m + m;
+    s = (s + 15) / 16 * 16;
+    s += 2 * sizeof(float4) * (size_t)(nmax / 32);
+    s += sizeof(uint16_t) * (size_t)row_width * m;
+    s = (s + 15) / 16 * 16;
+    return s + (sizeof(ClusterExtra) + 15) / 16 * 16;
 }
 
-__device__ __forceinline__ ClusterExtra *cluster_extra(int m, int row_width) {
-    return reinterpret_cast<ClusterExtra *>(g_smem + layout_bytes(m, row_width, false));
-}
-
-// Position of system bead j at layer `cur`.
-__device__ __forceinline__ float4 cfetch(const ClusterExtra *X, int cur, int j, int sh) {
-    return X->lay[cur][j >> sh][j & ((1 << sh) - 1)];
-}
-
-// Rows of this CTA's slots (system-local bead index in every entry). Boxes of every
-// rank must be current (a cluster barrier after block_boxes).
+// Rows of this CTA's slots from layer `layer` of its copy (system-local bead indices).
+// The block boxes of the whole system must be current.
 template <int BPT>
-__device__ void cluster_rows(const BatchedArgs &a, const Layout<false> &L, const ClusterExtra *X, const uint16_t *order,
-                             int cur, int n_loc, int lo, int n_s, int sh, int nat_off, int b0) {
-    const int T = blockDim.x, m = 1 << sh;
+__device__ void cluster_rows(const BatchedArgs &a, const CLayout &L, const uint16_t *order, int layer, int n_loc,
+                             int lo, int n_s, int nat_off, int b0) {
+    const int T = blockDim.x, m = L.m;
     const float cut2 = a.sa.cut2_f;
     const float lo2 = cut2 - cut2 * 1e-4f, hi2 = cut2 + cut2 * 1e-4f;
+    const float4 *src = L.pos(layer);
+    const float4 *bb = L.bbox();
     uint16_t *row = L.row();
 #pragma unroll 1
     for (int k = 0; k < BPT; ++k) {
         const int p = threadIdx.x + k * T;
         if (p >= n_loc) continue;
         const int l = order[p];
-        const int b = lo + l;   // system-local bead
-        const float4 pb = L.lay(cur)[l];
+        const int b = lo + l;
+        const float4 pb = src[b];
         const int nn = a.nat_ell_cnt[b0 + b];
         const uint16_t *natc = a.nat_ell_col + nat_off + b;
         for (int q = 0; q < nn; ++q) row[q * m + p] = __ldg(natc + q * n_s);
@@ -720,17 +747,14 @@ __device__ void cluster_rows(const BatchedArgs &a, const Layout<false> &L, const
         int next_nat = nn > 0 ? (int)__ldg(natc) : 0x7fffffff;
         int cnt = 0;
         for (int base = 0; base < n_s; base += 32) {
-            const int owner = base >> sh, lb = (base & (m - 1)) >> 5;
-            const float4 blo = X->box[owner][2 * lb], bhi = X->box[owner][2 * lb + 1];
+            const float4 blo = bb[base >> 4], bhi = bb[(base >> 4) + 1];
             const float ex = fmaxf(fmaxf(blo.x - pb.x, pb.x - bhi.x), 0.f);
             const float ey = fmaxf(fmaxf(blo.y - pb.y, pb.y - bhi.y), 0.f);
             const float ez = fmaxf(fmaxf(blo.z - pb.z, pb.z - bhi.z), 0.f);
-            const float4 *src = X->lay[cur][owner];
-            const int lbase = base & (m - 1);
             uint32_t within = 0u, near = 0u;
             if (fmaf(ez, ez, fmaf(ey, ey, ex * ex)) < hi2) {
-                if (base + 32 <= n_s) scan32<true>(src, lbase, 32, pb, lo2, hi2, &within, &near);
-                else scan32<false>(src, lbase, n_s - base, pb, lo2, hi2, &within, &near);
+                if (base + 32 <= n_s) scan32<true>(src, base, 32, pb, lo2, hi2, &within, &near);
+                else scan32<false>(src, base, n_s - base, pb, lo2, hi2, &within, &near);
             }
             uint32_t ex_mask = 0u;
             if (b >= base && b < base + 32) ex_mask |= 1u << (b - base);
@@ -746,7 +770,7 @@ __device__ void cluster_rows(const BatchedArgs &a, const Layout<false> &L, const
             while (near) {
                 const int t = __ffs(near) - 1;
                 near &= near - 1;
-                if (within_cut(pb, src[lbase + t], cut2, a.sa.cut2_d)) within |= 1u << t;
+                if (within_cut(pb, src[base + t], cut2, a.sa.cut2_d)) within |= 1u << t;
             }
             while (within) {
                 const int t = __ffs(within) - 1;
@@ -761,20 +785,31 @@ __device__ void cluster_rows(const BatchedArgs &a, const Layout<false> &L, const
     }
 }
 
-// Eq. 1 pair forces on own bead l (system bead b) in slot p at layer cur.
-__device__ __forceinline__ float3 cluster_force(const BatchedArgs &a, const Layout<false> &L, const ClusterExtra *X,
-                                                int cur, int sh, int n_s, int nat_off, int l, int b, int p,
-                                                bool *broken) {
+// Rebuild from layer `layer` of the local copy: boxes of every block of the system, the
+// own slot order and rows. Local only; ends with a CTA barrier.
+template <int BPT>
+__device__ int cluster_rebuild(const BatchedArgs &a, const CLayout &L, int layer, int n_loc, int lo, int n_s,
+                               int nat_off, int b0, int ord) {
+    block_boxes(L, L.pos(layer), n_s);
+    ord = reorder_slots(L, n_loc, ord);   // its barriers also publish the boxes
+    cluster_rows<BPT>(a, L, L.order(ord), layer, n_loc, lo, n_s, nat_off, b0);
+    __syncthreads();
+    return ord;
+}
+
+// Eq. 1 pair forces on own bead l (system bead b, slot p) at layer P of the local copy.
+__device__ __forceinline__ float3 cluster_force(const BatchedArgs &a, const CLayout &L, const float4 *P, int n_s,
+                                                int nat_off, int l, int b, int p, bool *broken) {
     const ForceParams &fp = a.sa.fp;
-    const int m = 1 << sh;
-    const float4 pb = L.lay(cur)[l];
+    const int m = L.m;
+    const float4 pb = P[b];
     float fx = 0.f, fy = 0.f, fz = 0.f;
     const float2 bd = L.bond()[l];
 #pragma unroll
     for (int side = 0; side < 2; ++side) {
         const float r0 = side ? bd.y : bd.x;
         if (r0 > 0.f) {
-            const float4 pj = cfetch(X, cur, side ? b + 1 : b - 1, sh);
+            const float4 pj = P[side ? b + 1 : b - 1];
             const float dx = pb.x - pj.x, dy = pb.y - pj.y, dz = pb.z - pj.z;
             const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
             const float r = r2 * rsqrtf(r2);
@@ -795,7 +830,7 @@ __device__ __forceinline__ float3 cluster_force(const BatchedArgs &a, const Layo
         const bool nat = k < nn;
         const int j = rowp[k * m];
         const float s0 = nat ? __ldg(natr + k * n_s) : fp.sigma2;
-        const float4 pj = cfetch(X, cur, j, sh);
+        const float4 pj = P[j];
         const float dx = pb.x - pj.x, dy = pb.y - pj.y, dz = pb.z - pj.z;
         const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
         const float inv = __fdividef(1.0f, r2);
@@ -807,16 +842,16 @@ __device__ __forceinline__ float3 cluster_force(const BatchedArgs &a, const Layo
     return make_float3(fx, fy, fz);
 }
 
-// FP64 observables of the cluster's system at layer cur: every CTA sums its own beads,
-// rank 0 adds the CTA sums after a cluster barrier and writes the record.
+// FP64 observables of the cluster's system at layer P: every CTA sums its own beads, rank
+// 0 adds the CTA sums after a cluster barrier and writes the record.
 template <int BPT>
-__device__ __noinline__ void cluster_observe(const BatchedArgs &a, const Layout<false> &L, ClusterExtra *X,
-                                             const uint16_t *order, int cur, int n_loc, int lo, int sh, int b0,
+__device__ __noinline__ void cluster_observe(const BatchedArgs &a, const CLayout &L, ClusterExtra *X,
+                                             const uint16_t *order, const float4 *P, int n_loc, int lo, int b0,
                                              int r, int s, int g, int64_t step, int64_t event, int rank, int C) {
     const StepArgs &sa = a.sa;
     const DevTopo &t = sa.topo;
     const DevExternal &e = sa.ext;
-    const int T = blockDim.x, m = 1 << sh;
+    const int T = blockDim.x, m = L.m;
     const uint16_t *row = L.row();
     double v[6] = {0, 0, 0, 0, 0, 0};   // E, f_pull, ext, formed, f_wall, r_ee
     const double R02 = sa.R0 * sa.R0, sig2 = sa.sigma * sa.sigma;
@@ -826,10 +861,10 @@ __device__ __noinline__ void cluster_observe(const BatchedArgs &a, const Layout<
         const int l = order[p];
         const int b = lo + l;
         const int i = b0 + b;
-        const float4 pb = L.lay(cur)[l];
+        const float4 pb = P[b];
         const double xi = pb.x, yi = pb.y, zi = pb.z;
         if (L.bond()[l].y > 0.f) {
-            const float4 pj = cfetch(X, cur, b + 1, sh);
+            const float4 pj = P[b + 1];
             const double rr = __dsqrt_rn(dist2_d(xi, yi, zi, pj.x, pj.y, pj.z));
             const double dr = rr - t.bond_r0d[i];
             const double arg = 1.0 - dr * dr / R02;
@@ -838,7 +873,7 @@ __device__ __noinline__ void cluster_observe(const BatchedArgs &a, const Layout<
         for (int q = t.nat_row[i]; q < t.nat_row[i + 1]; ++q) {
             const int j = t.nat_col[q];
             if (j < i) continue;
-            const float4 pj = cfetch(X, cur, j - b0, sh);
+            const float4 pj = P[j - b0];
             const double d2 = dist2_d(xi, yi, zi, pj.x, pj.y, pj.z);
             const double r0 = t.nat_r0[q];
             const double u = r0 * r0 / d2;
@@ -849,7 +884,7 @@ __device__ __noinline__ void cluster_observe(const BatchedArgs &a, const Layout<
         for (int q = L.n_nat()[p]; q < L.n_tot()[p]; ++q) {
             const int j = row[q * m + p];
             if (j < b) continue;
-            const float4 pj = cfetch(X, cur, j, sh);
+            const float4 pj = P[j];
             const double c = sig2 / dist2_d(xi, yi, zi, pj.x, pj.y, pj.z);
             v[0] += sa.eps_l * c * c * c;
         }
@@ -864,7 +899,7 @@ __device__ __noinline__ void cluster_observe(const BatchedArgs &a, const Layout<
                 double f = 0.0;
                 for (int c = 0; c < 3; ++c) f += e.pull_ks[qq] * (tip0[c] + tt * dir[c] - x[c]) * dir[c];
                 v[1] += f;
-                const float4 pa = cfetch(X, cur, e.pull_anchor[qq] - b0, sh);
+                const float4 pa = P[e.pull_anchor[qq] - b0];
                 v[2] += __dsqrt_rn(dist2_d(xi, yi, zi, pa.x, pa.y, pa.z));
             }
         }
@@ -883,7 +918,7 @@ __device__ __noinline__ void cluster_observe(const BatchedArgs &a, const Layout<
             }
         }
         if (fl & kFlagFirstOfSystem) {
-            const float4 pl_ = cfetch(X, cur, t.sys_ree_last[s] - b0, sh);
+            const float4 pl_ = P[t.sys_ree_last[s] - b0];
             v[5] += __dsqrt_rn(dist2_d(xi, yi, zi, pl_.x, pl_.y, pl_.z));
         }
     }
@@ -911,36 +946,23 @@ __device__ __noinline__ void cluster_observe(const BatchedArgs &a, const Layout<
     __syncthreads();
 }
 
-// A rebuild of this CTA's rows from layer cur: own block boxes, a cluster barrier (every
-// rank's boxes are then current), slot order, rows. Ends with a CTA barrier.
-template <int BPT>
-__device__ int cluster_rebuild(const BatchedArgs &a, const Layout<false> &L, const ClusterExtra *X, int cur, int n_loc,
-                               int lo, int n_s, int sh, int nat_off, int b0, int ord) {
-    block_boxes(L, L.lay(cur), n_loc);
-    cg::this_cluster().sync();
-    ord = reorder_slots(L, n_loc, ord);
-    cluster_rows<BPT>(a, L, X, L.order(ord), cur, n_loc, lo, n_s, sh, nat_off, b0);
-    __syncthreads();
-    return ord;
-}
-
 template <int BPT, int MAXT>
 __global__ void __launch_bounds__(MAXT, 1) k_cluster(BatchedArgs a, int sh) {
     cg::cluster_group cl = cg::this_cluster();
     const int rank = (int)cl.block_rank();
     const int C = (int)cl.num_blocks();
     const int item = blockIdx.x / C;
-    const int m = 1 << sh;
-    Layout<false> L;
-    L.mx = m;
-    L.grow = nullptr;
-    ClusterExtra *X = cluster_extra(m, a.row_width);
+    CLayout L;
+    L.m = 1 << sh;
+    L.nmax = C << sh;
+    L.rw = a.row_width;
+    ClusterExtra *X = L.extra();
     const int r = a.item_rep[item], s = a.item_sys[item];
     const StepArgs &sa = a.sa;
     const DevTopo &t = sa.topo;
     const int b0 = t.sys_lo[s], n_s = t.sys_lo[s + 1] - b0;
-    const int lo = rank * m;
-    const int n_loc = max(0, min(m, n_s - lo));
+    const int lo = rank * L.m;
+    const int n_loc = max(0, min(L.m, n_s - lo));
     const int gbase = r * t.n + b0;
     const int g = r * t.n_sys + s;
     const int nat_off = a.nat_ell_off[s];
@@ -952,12 +974,26 @@ __global__ void __launch_bounds__(MAXT, 1) k_cluster(BatchedArgs a, int sh) {
         X->fail_step = kNoFail;
         X->frozen = (!forces_only && (sa.rep_status[r] != 0 || *sa.halt != 0)) ? 1 : 0;
     }
-    for (int k = threadIdx.x; k < 3 * C + 2; k += T) {
-        if (k < 2 * C) X->lay[k / C][k % C] = cl.map_shared_rank(L.lay(k / C), k % C);
-        else if (k < 3 * C) X->box[k - 2 * C] = cl.map_shared_rank(L.bbox(), k - 2 * C);
+    for (int k = threadIdx.x; k < 3 * C; k += T) {
+        if (k < 2 * C) X->rpos[k / C][k % C] = cl.map_shared_rank(L.pos(k / C), k % C);
+        else X->peer[k - 2 * C] = cl.map_shared_rank(X, k - 2 * C);
     }
-    for (int k = threadIdx.x; k < C; k += T) X->peer[k] = cl.map_shared_rank(X, k);
-    cl.sync();
+    int k_phase = (int)(step0 % a.K);
+    int o_phase = a.obs_every > 0 ? (int)(step0 % a.obs_every) : 0;
+    // the whole system into the local copy (and the snapshot of the last rebuild into layer 1)
+    for (int b = threadIdx.x; b < n_s; b += T) {
+        L.pos(0)[b] = a.pos[gbase + b];
+        if (k_phase != 0 && !forces_only) L.pos(1)[b] = a.snap[gbase + b];
+    }
+    for (int l = threadIdx.x; l < n_loc; l += T) {
+        const int b = lo + l, i = b0 + b;
+        L.comp()[l] = a.comp[gbase + b];
+        L.bond()[l] = make_float2(b > 0 ? t.bond_r0[i - 1] : -1.f, t.bond_r0[i]);
+        L.flags()[l] = t.flags[i];
+        L.order(0)[l] = (uint16_t)l;
+        L.n_tot()[l] = (uint16_t)a.nat_ell_cnt[i];
+    }
+    cl.sync();   // every copy is loaded before any CTA writes into another
     const bool frozen = X->peer[0]->frozen != 0;   // rank 0's reading, the same for every CTA
     if (frozen) {
         if (rank == 0 && threadIdx.x == 0)
@@ -965,40 +1001,29 @@ __global__ void __launch_bounds__(MAXT, 1) k_cluster(BatchedArgs a, int sh) {
         cl.sync();   // no CTA leaves while another may still read its shared memory
         return;
     }
-    int k_phase = (int)(step0 % a.K);
-    int o_phase = a.obs_every > 0 ? (int)(step0 % a.obs_every) : 0;
-    for (int l = threadIdx.x; l < n_loc; l += T) {
-        const int b = lo + l, i = b0 + b;
-        L.lay(0)[l] = a.pos[gbase + b];
-        L.comp()[l] = a.comp[gbase + b];
-        L.bond()[l] = make_float2(b > 0 ? t.bond_r0[i - 1] : -1.f, t.bond_r0[i]);
-        L.flags()[l] = t.flags[i];
-        L.order(0)[l] = (uint16_t)l;
-        L.n_tot()[l] = (uint16_t)a.nat_ell_cnt[i];
-        if (k_phase != 0) L.lay(1)[l] = a.snap[gbase + b];
-    }
-    cl.sync();
 
     int cur = 0, ord = 0, n_events = 0;
     bool built_now = false;
     int it = 0;
     for (; it < a.n_steps || (forces_only && it == 0); ++it) {
         if (it == 0 && k_phase != 0 && !forces_only) {
-            ord = cluster_rebuild<BPT>(a, L, X, cur ^ 1, n_loc, lo, n_s, sh, nat_off, b0, ord);   // the snapshot layer
+            ord = cluster_rebuild<BPT>(a, L, 1, n_loc, lo, n_s, nat_off, b0, ord);   // from the snapshot
+            cl.sync();   // layer 1 is read by every CTA before the step writes it
         } else if ((k_phase == 0 && !built_now) || forces_only) {
-            ord = cluster_rebuild<BPT>(a, L, X, cur, n_loc, lo, n_s, sh, nat_off, b0, ord);
+            ord = cluster_rebuild<BPT>(a, L, cur, n_loc, lo, n_s, nat_off, b0, ord);
             if (!forces_only)
-                for (int l = threadIdx.x; l < n_loc; l += T) a.snap[gbase + lo + l] = L.lay(cur)[l];
+                for (int l = threadIdx.x; l < n_loc; l += T) a.snap[gbase + lo + l] = L.pos(cur)[lo + l];
         }
         built_now = false;
         const int64_t step = step0 + it;
         const uint16_t *order = L.order(ord);
+        const float4 *P = L.pos(cur);
         if (forces_only) {
             for (int p = threadIdx.x; p < n_loc; p += T) {
                 const int l = order[p], b = lo + l;
                 bool broken = false, overlap = false;
-                const float3 f = cluster_force(a, L, X, cur, sh, n_s, nat_off, l, b, p, &broken);
-                const float3 fe = ext_force(sa, r, b0 + b, L.flags()[l], L.lay(cur)[l], step, &overlap);
+                const float3 f = cluster_force(a, L, P, n_s, nat_off, l, b, p, &broken);
+                const float3 fe = ext_force(sa, r, b0 + b, L.flags()[l], P[b], step, &overlap);
                 a.force_out[gbase + b] = make_float4(f.x + fe.x, f.y + fe.y, f.z + fe.z, (broken || overlap) ? 1.f : 0.f);
                 if (a.pl_dump_col) {
                     const size_t rowi = (size_t)gbase + b;
@@ -1006,20 +1031,20 @@ __global__ void __launch_bounds__(MAXT, 1) k_cluster(BatchedArgs a, int sh) {
                     a.pl_dump_start[rowi] = (int)(rowi * a.pl_dump_stride);
                     a.pl_dump_len[rowi] = np;
                     for (int q = 0; q < np; ++q)
-                        a.pl_dump_col[rowi * a.pl_dump_stride + q] = b0 + (int)L.row()[(nn + q) * m + p];
+                        a.pl_dump_col[rowi * a.pl_dump_stride + q] = b0 + (int)L.row()[(nn + q) * L.m + p];
                 }
             }
             break;
         }
-        float4 *Q = L.lay(cur ^ 1);
+        const int nxt = cur ^ 1;
 #pragma unroll 1
         for (int k = 0; k < BPT; ++k) {
             const int p = threadIdx.x + k * T;
             if (p >= n_loc) continue;
             const int l = order[p], b = lo + l;
             bool broken = false, overlap = false;
-            const float3 f = cluster_force(a, L, X, cur, sh, n_s, nat_off, l, b, p, &broken);
-            const float4 p_old = L.lay(cur)[l];
+            const float3 f = cluster_force(a, L, P, n_s, nat_off, l, b, p, &broken);
+            const float4 p_old = P[b];
             const uint8_t fl = L.flags()[l];
             const float3 fe = ext_force(sa, r, b0 + b, fl, p_old, step, &overlap);
             float4 pb = p_old;
@@ -1059,37 +1084,38 @@ __global__ void __launch_bounds__(MAXT, 1) k_cluster(BatchedArgs a, int sh) {
                     pb = p_old;
                 }
             }
-            Q[l] = pb;
+            // the new position into every copy of the cluster
+            for (int q = 0; q < C; ++q) X->rpos[nxt][q][b] = pb;
         }
         __syncthreads();
         if (threadIdx.x == 0 && L.h()->fail != 0 && X->fail_step == kNoFail) X->fail_step = it;
-        cl.sync();   // the next layer is complete in every CTA
-        cur ^= 1;
+        cl.sync();   // the next layer is complete in every copy
+        cur = nxt;
         k_phase = k_phase + 1 == a.K ? 0 : k_phase + 1;
         if (a.obs_every > 0) o_phase = o_phase + 1 == a.obs_every ? 0 : o_phase + 1;
-        // the replica freezes after the step in which any CTA failed (a decision every
-        // CTA takes from the same values: a CTA's fail_step is written once, before a barrier)
+        // the replica freezes after the step in which any CTA failed (every CTA decides
+        // from the same values: a CTA's fail_step is written once, before a barrier)
         bool stop = false;
         for (int q = 0; q < C; ++q) stop |= X->peer[q]->fail_step <= it;
         if (stop) { ++it; break; }
         if (a.obs_every > 0 && o_phase == 0) {
             if (k_phase == 0) {
-                ord = cluster_rebuild<BPT>(a, L, X, cur, n_loc, lo, n_s, sh, nat_off, b0, ord);
+                ord = cluster_rebuild<BPT>(a, L, cur, n_loc, lo, n_s, nat_off, b0, ord);
                 built_now = true;
-                for (int l = threadIdx.x; l < n_loc; l += T) a.snap[gbase + lo + l] = L.lay(cur)[l];
+                for (int l = threadIdx.x; l < n_loc; l += T) a.snap[gbase + lo + l] = L.pos(cur)[lo + l];
             }
             const int64_t ev = (a.d_events ? *a.d_events : 0) + n_events;
-            cluster_observe<BPT>(a, L, X, L.order(ord), cur, n_loc, lo, sh, b0, r, s, g, step + 1, ev, rank, C);
+            cluster_observe<BPT>(a, L, X, L.order(ord), L.pos(cur), n_loc, lo, b0, r, s, g, step + 1, ev, rank, C);
             ++n_events;
         }
     }
     if (!forces_only) {
-        int code = 0;
-        for (int q = 0; q < C && code == 0; ++q) code = X->peer[q]->fail_step != kNoFail ? 1 : 0;
-        if (code && rank == 0 && threadIdx.x == 0)
+        bool failed = false;
+        for (int q = 0; q < C; ++q) failed |= X->peer[q]->fail_step != kNoFail;
+        if (failed && rank == 0 && threadIdx.x == 0)
             missing_records(a, r, s, g, step0, step0 + it, (a.d_events ? *a.d_events : 0) + n_events);
         for (int l = threadIdx.x; l < n_loc; l += T) {
-            a.pos[gbase + lo + l] = L.lay(cur)[l];
+            a.pos[gbase + lo + l] = L.pos(cur)[lo + l];
             a.comp[gbase + lo + l] = L.comp()[l];
         }
         if (threadIdx.x == 0 && L.h()->fail != 0) atomicCAS(&sa.rep_status[r], 0, L.h()->fail);
@@ -1173,7 +1199,7 @@ bool cluster_config(int max_n, int row_width, int threads, int m_shift, BatchedC
     cfg->min_blocks = 1;
     cfg->rows_global = false;
     cfg->row_width = row_width;
-    cfg->smem = cluster_smem(m, row_width);
+    cfg->smem = cluster_smem(m, C * m, row_width);
     cfg->cluster = C;
     cfg->m_shift = m_shift;
     return cfg->smem <= 227 * 1024;

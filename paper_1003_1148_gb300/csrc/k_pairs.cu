@@ -163,7 +163,7 @@ __global__ void __launch_bounds__(256) k_pairs_step(StepArgs a, DevPairList pl, 
     const int n = a.topo.n;
     const int r = gb / n, i = gb - r * n;
     const float4 *P = pos_in + (size_t)r * n;
-    if (*a.halt != 0 || a.rep_status[r] != 0) {
+    if (__any_sync(group_mask<L>(), *a.halt != 0 || a.rep_status[r] != 0)) {   // one decision per group
         if (lane == 0) pos_out[gb] = P[i];
         return;
     }

@@ -502,7 +502,7 @@ __global__ void __launch_bounds__(256) k_step(StepArgs a, DevPairList pl, const 
     const int n = a.topo.n;
     const int r = gb / n, i = gb - r * n;
     const float4 *P = pos_in + (size_t)r * n;
-    if (*a.halt != 0 || a.rep_status[r] != 0) {
+    if (__any_sync(group_mask<L>(), *a.halt != 0 || a.rep_status[r] != 0)) {   // one decision per group
         if (lane == 0) pos_out[gb] = P[i];
         return;
     }
@@ -512,6 +512,47 @@ __global__ void __launch_bounds__(256) k_step(StepArgs a, DevPairList pl, const 
     broken = __any_sync(group_mask<L>(), broken);
     if (lane != 0) return;
     advance_bead(a, r, i, gb, P, f, broken, step, pos_out, comp);
+}
+
+// The same step for large systems, with the tail spread over the lanes: a group of L
+// lanes gathers the forces of L consecutive beads one after another (the same gather and
+// reduction as k_step, so every force is bit-identical), lane q keeps bead q's sum, and
+// then every lane draws the noise and updates its own bead. k_step leaves L - 1 lanes of
+// each group idle through the noise and the update; here none is.
+template <int L>
+__global__ void __launch_bounds__(256) k_step_spread(StepArgs a, DevPairList pl, const float4 *__restrict__ pos_in,
+                                                     float4 *__restrict__ pos_out, float4 *__restrict__ comp,
+                                                     int b_lo, int b_hi, int k_off) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = t % L;
+    const int gb0 = b_lo + (t - lane);   // first bead of the group
+    if (gb0 >= b_hi) return;             // whole groups of L lanes leave together
+    const int n = a.topo.n;
+    const bool halted = *a.halt != 0;
+    float3 mine = make_float3(0.f, 0.f, 0.f);
+    bool mine_broken = false;
+    for (int q = 0; q < L && gb0 + q < b_hi; ++q) {   // the same trip count in every lane of the group
+        const int gb = gb0 + q;
+        const int r = gb / n, i = gb - r * n;
+        // one decision for the group (its lanes then shuffle together)
+        if (__any_sync(group_mask<L>(), halted || a.rep_status[r] != 0)) continue;
+        bool broken = false;
+        const float3 f = gather_force<L>(a, pl, pos_in + (size_t)r * n, i, gb, lane, &broken);
+        broken = __any_sync(group_mask<L>(), broken);
+        if (lane == q) {
+            mine = f;
+            mine_broken = broken;
+        }
+    }
+    const int gb = gb0 + lane;
+    if (gb >= b_hi) return;
+    const int r = gb / n, i = gb - r * n;
+    const float4 *P = pos_in + (size_t)r * n;
+    if (halted || a.rep_status[r] != 0) {
+        pos_out[gb] = P[i];
+        return;
+    }
+    advance_bead(a, r, i, gb, P, mine, mine_broken, *a.d_step + k_off, pos_out, comp);
 }
 
 template <int L>
@@ -695,6 +736,9 @@ __global__ void k_tick(int64_t *d_step, int64_t k, int64_t *events, int32_t gate
 
 inline int blocks_for(int64_t work, int threads) { return (int)((work + threads - 1) / threads); }
 
+// From this many beads in one launch the step runs one thread per bead (k_step_spread).
+constexpr int64_t kSpreadMinBeads = 152 * 256;
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -772,7 +816,18 @@ void launch_rebuild(const StepArgs &sa, const DevCells &c, const DevPairList &pl
 
 void launch_step(const StepArgs &a, const DevPairList &pl, const float4 *pos_in, float4 *pos_out, float4 *comp,
                  int32_t b_lo, int32_t b_hi, int32_t k_off, int lanes, cudaStream_t s, int64_t *launches) {
-    const int64_t threads = (int64_t)(b_hi - b_lo) * lanes;
+    const int64_t nb = b_hi - b_lo;
+    if (nb >= kSpreadMinBeads) {   // enough beads to fill the GPU with one thread per bead
+        const int blocks = blocks_for(nb, 256);
+        switch (lanes) {
+        case 4: k_step_spread<4><<<blocks, 256, 0, s>>>(a, pl, pos_in, pos_out, comp, b_lo, b_hi, k_off); break;
+        case 16: k_step_spread<16><<<blocks, 256, 0, s>>>(a, pl, pos_in, pos_out, comp, b_lo, b_hi, k_off); break;
+        default: k_step_spread<8><<<blocks, 256, 0, s>>>(a, pl, pos_in, pos_out, comp, b_lo, b_hi, k_off); break;
+        }
+        if (launches) *launches += 1;
+        return;
+    }
+    const int64_t threads = nb * lanes;
     const int blocks = blocks_for(threads, 256);
     if (blocks <= 0) return;
     switch (lanes) {

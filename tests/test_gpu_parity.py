@@ -283,3 +283,17 @@ def test_auto_streamed_form_is_timed(sop, synth):
     sim.step(20)
     assert np.all(np.isfinite(sim.get_positions(0)))
     sim.close()
+
+
+def test_spread_step_equals_group_step(sop, synth):
+    """Above 38,912 beads per launch the streamed step gathers with the same lanes but
+    finishes each bead in its own lane; forces and positions stay bit-identical to the
+    per-system launches of the plain form."""
+    w = synth.replicas(n_replicas=320, n=128, steps=50)     # 40,960 beads in one launch
+    a = sop.from_workload(w, schedule="streamed")
+    b = sop.from_workload(w, schedule="plain")
+    a.step(33)
+    b.step(33)
+    assert np.array_equal(a.get_positions(-1), b.get_positions(-1))
+    a.close()
+    b.close()

@@ -34,6 +34,7 @@
 #include <cuda_runtime.h>
 
 #include "sop_internal.h"
+#include "sop_step.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -594,38 +595,12 @@ __global__ void __launch_bounds__(MAXT, MINB) k_batched(BatchedArgs a) {
                 // a bead whose force cannot be evaluated stays where it is; the replica freezes
                 cta_fail(L.h(), broken ? SOP_ERR_FENE_BREAK : SOP_ERR_INDENTER_OVERLAP);
             } else if (!(fl & kFlagFixed)) {
-                float3 gn;
-                if (sa.taus) {   // Hybrid Taus: the bead's state in global memory (L2)
-                    uint4 st = sa.taus[gbase + b];
-                    gn = taus_noise(st);
-                    sa.taus[gbase + b] = st;
-                } else {
-                    gn = bead_noise(sa.seed + (uint64_t)r, step, (uint32_t)(b0 + b));
-                }
                 float4 c = L.comp()[b];
-                float4 w;
-                if (sa.vel) {   // underdamped: BAOAB, the stored velocity in global memory (L2)
-                    w = sa.vel[gbase + b];
-                    const float v1x = fmaf(f.x + fe.x, sa.h_m, w.x), v1y = fmaf(f.y + fe.y, sa.h_m, w.y),
-                                v1z = fmaf(f.z + fe.z, sa.h_m, w.z);
-                    w.x = fmaf(sa.c1, v1x, sa.c2 * gn.x);
-                    w.y = fmaf(sa.c1, v1y, sa.c2 * gn.y);
-                    w.z = fmaf(sa.c1, v1z, sa.c2 * gn.z);
-                    kahan_add(pb.x, c.x, sa.half_h * (v1x + w.x));
-                    kahan_add(pb.y, c.y, sa.half_h * (v1y + w.y));
-                    kahan_add(pb.z, c.z, sa.half_h * (v1z + w.z));
-                } else {
-                    kahan_add(pb.x, c.x, fmaf(f.x + fe.x, sa.fp.mob, gn.x * sa.fp.amp));
-                    kahan_add(pb.y, c.y, fmaf(f.y + fe.y, sa.fp.mob, gn.y * sa.fp.amp));
-                    kahan_add(pb.z, c.z, fmaf(f.z + fe.z, sa.fp.mob, gn.z * sa.fp.amp));
-                }
-                if (isfinite(pb.x) && isfinite(pb.y) && isfinite(pb.z)) {
+                if (update_position(sa, r, b0 + b, (size_t)gbase + b, pb, c,
+                                    make_float3(f.x + fe.x, f.y + fe.y, f.z + fe.z), step))
                     L.comp()[b] = c;
-                    if (sa.vel) sa.vel[gbase + b] = w;
-                } else {
+                else
                     cta_fail(L.h(), SOP_ERR_NONFINITE);
-                    pb = p_old;
-                }
             }
             Q[b] = pb;
         }
@@ -1051,38 +1026,12 @@ __global__ void __launch_bounds__(MAXT, 1) k_cluster(BatchedArgs a, int sh) {
             if (broken || overlap) {
                 cta_fail(L.h(), broken ? SOP_ERR_FENE_BREAK : SOP_ERR_INDENTER_OVERLAP);
             } else if (!(fl & kFlagFixed)) {
-                float3 gn;
-                if (sa.taus) {
-                    uint4 st = sa.taus[gbase + b];
-                    gn = taus_noise(st);
-                    sa.taus[gbase + b] = st;
-                } else {
-                    gn = bead_noise(sa.seed + (uint64_t)r, step, (uint32_t)(b0 + b));
-                }
                 float4 c = L.comp()[l];
-                float4 w;
-                if (sa.vel) {
-                    w = sa.vel[gbase + b];
-                    const float v1x = fmaf(f.x + fe.x, sa.h_m, w.x), v1y = fmaf(f.y + fe.y, sa.h_m, w.y),
-                                v1z = fmaf(f.z + fe.z, sa.h_m, w.z);
-                    w.x = fmaf(sa.c1, v1x, sa.c2 * gn.x);
-                    w.y = fmaf(sa.c1, v1y, sa.c2 * gn.y);
-                    w.z = fmaf(sa.c1, v1z, sa.c2 * gn.z);
-                    kahan_add(pb.x, c.x, sa.half_h * (v1x + w.x));
-                    kahan_add(pb.y, c.y, sa.half_h * (v1y + w.y));
-                    kahan_add(pb.z, c.z, sa.half_h * (v1z + w.z));
-                } else {
-                    kahan_add(pb.x, c.x, fmaf(f.x + fe.x, sa.fp.mob, gn.x * sa.fp.amp));
-                    kahan_add(pb.y, c.y, fmaf(f.y + fe.y, sa.fp.mob, gn.y * sa.fp.amp));
-                    kahan_add(pb.z, c.z, fmaf(f.z + fe.z, sa.fp.mob, gn.z * sa.fp.amp));
-                }
-                if (isfinite(pb.x) && isfinite(pb.y) && isfinite(pb.z)) {
+                if (update_position(sa, r, b0 + b, (size_t)gbase + b, pb, c,
+                                    make_float3(f.x + fe.x, f.y + fe.y, f.z + fe.z), step))
                     L.comp()[l] = c;
-                    if (sa.vel) sa.vel[gbase + b] = w;
-                } else {
+                else
                     cta_fail(L.h(), SOP_ERR_NONFINITE);
-                    pb = p_old;
-                }
             }
             // the new position into every copy of the cluster
             for (int q = 0; q < C; ++q) X->rpos[nxt][q][b] = pb;

@@ -53,10 +53,47 @@ __device__ __forceinline__ float3 external_force(const StepArgs &a, int r, int i
     return f;
 }
 
+// Algorithm 7 (or the BAOAB step of the underdamped integrator) for one bead that moves:
+// F is the total force (pair terms plus external), i the bead's index in its replica (the
+// Philox counter), gidx its index in the per-bead arrays of all replicas (Hybrid Taus
+// state, velocities). p and c are the position and its compensation, updated in place when
+// the result is finite; false (p, c and the velocity untouched) otherwise. Every schedule
+// calls this one function, so all of them take the same arithmetic in the same order.
+__device__ __forceinline__ bool update_position(const StepArgs &a, int r, int i, size_t gidx, float4 &p, float4 &c,
+                                                float3 F, int64_t step) {
+    float3 g;
+    if (a.taus) {
+        uint4 st = a.taus[gidx];
+        g = taus_noise(st);
+        a.taus[gidx] = st;
+    } else {
+        g = bead_noise(a.seed + (uint64_t)r, step, (uint32_t)i);
+    }
+    float4 pn = p, cn = c, w;
+    if (a.vel) {   // underdamped: BAOAB with the stored post-O velocity w
+        w = a.vel[gidx];
+        const float v1x = fmaf(F.x, a.h_m, w.x), v1y = fmaf(F.y, a.h_m, w.y), v1z = fmaf(F.z, a.h_m, w.z);
+        w.x = fmaf(a.c1, v1x, a.c2 * g.x);
+        w.y = fmaf(a.c1, v1y, a.c2 * g.y);
+        w.z = fmaf(a.c1, v1z, a.c2 * g.z);
+        kahan_add(pn.x, cn.x, a.half_h * (v1x + w.x));
+        kahan_add(pn.y, cn.y, a.half_h * (v1y + w.y));
+        kahan_add(pn.z, cn.z, a.half_h * (v1z + w.z));
+    } else {
+        kahan_add(pn.x, cn.x, fmaf(F.x, a.fp.mob, g.x * a.fp.amp));
+        kahan_add(pn.y, cn.y, fmaf(F.y, a.fp.mob, g.y * a.fp.amp));
+        kahan_add(pn.z, cn.z, fmaf(F.z, a.fp.mob, g.z * a.fp.amp));
+    }
+    if (!(isfinite(pn.x) && isfinite(pn.y) && isfinite(pn.z))) return false;
+    if (a.vel) a.vel[gidx] = w;
+    p = pn;
+    c = cn;
+    return true;
+}
+
 // The end of one step for bead i of replica r (global index gb) given the sum f of its
 // pair forces at layer P: a broken bond or an indenter overlap leaves the bead where it
-// is and marks the replica; a fixed bead stays; otherwise r += F h/zeta + g sqrt(2kTh/zeta)
-// with the FP32 compensation of the bead, g from Philox or from the bead's Hybrid Taus state.
+// is and marks the replica; a fixed bead stays; otherwise it moves (update_position).
 __device__ __forceinline__ void advance_bead(const StepArgs &a, int r, int i, int gb, const float4 *P, float3 f,
                                              bool broken, int64_t step, float4 *pos_out, float4 *comp) {
     float4 pi = P[i];
@@ -76,37 +113,12 @@ __device__ __forceinline__ void advance_bead(const StepArgs &a, int r, int i, in
         pos_out[gb] = pi;
         return;
     }
-    float3 g;
-    if (a.taus) {
-        uint4 st = a.taus[gb];
-        g = taus_noise(st);
-        a.taus[gb] = st;
-    } else {
-        g = bead_noise(a.seed + (uint64_t)r, step, (uint32_t)i);
-    }
     float4 c = comp[gb];
-    float4 w;
-    if (a.vel) {   // underdamped: BAOAB with the stored post-O velocity w
-        w = a.vel[gb];
-        const float v1x = fmaf(f.x + fe.x, a.h_m, w.x), v1y = fmaf(f.y + fe.y, a.h_m, w.y),
-                    v1z = fmaf(f.z + fe.z, a.h_m, w.z);
-        w.x = fmaf(a.c1, v1x, a.c2 * g.x);
-        w.y = fmaf(a.c1, v1y, a.c2 * g.y);
-        w.z = fmaf(a.c1, v1z, a.c2 * g.z);
-        kahan_add(pi.x, c.x, a.half_h * (v1x + w.x));
-        kahan_add(pi.y, c.y, a.half_h * (v1y + w.y));
-        kahan_add(pi.z, c.z, a.half_h * (v1z + w.z));
-    } else {
-        kahan_add(pi.x, c.x, fmaf(f.x + fe.x, a.fp.mob, g.x * a.fp.amp));
-        kahan_add(pi.y, c.y, fmaf(f.y + fe.y, a.fp.mob, g.y * a.fp.amp));
-        kahan_add(pi.z, c.z, fmaf(f.z + fe.z, a.fp.mob, g.z * a.fp.amp));
-    }
-    if (!(isfinite(pi.x) && isfinite(pi.y) && isfinite(pi.z))) {
+    if (!update_position(a, r, i, gb, pi, c, make_float3(f.x + fe.x, f.y + fe.y, f.z + fe.z), step)) {
         set_status(&a.rep_status[r], (int32_t)SOP_ERR_NONFINITE);
         pos_out[gb] = P[i];
         return;
     }
-    if (a.vel) a.vel[gb] = w;
     comp[gb] = c;
     pos_out[gb] = pi;
 }

@@ -194,7 +194,23 @@ __global__ void k_seg_setup(RebuildArgs a, int32_t *pl_cursor, const int64_t *pl
     }
     float mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
     bool bad = false;
-    for (int b = lo + threadIdx.x; b < hi; b += blockDim.x) {
+    // four independent loads in flight per thread (a segment can hold 10^5 beads)
+    const int T = blockDim.x;
+    int b = lo + threadIdx.x;
+    for (; b + 3 * T < hi; b += 4 * T) {
+        const float4 q[4] = {a.pos[b], a.pos[b + T], a.pos[b + 2 * T], a.pos[b + 3 * T]};
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const float v[3] = {q[u].x, q[u].y, q[u].z};
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                if (!isfinite(v[k])) bad = true;
+                mn[k] = fminf(mn[k], v[k]);
+                mx[k] = fmaxf(mx[k], v[k]);
+            }
+        }
+    }
+    for (; b < hi; b += T) {
         const float4 p = a.pos[b];
         const float v[3] = {p.x, p.y, p.z};
 #pragma unroll
@@ -794,7 +810,9 @@ void launch_rebuild(const StepArgs &sa, const DevCells &c, const DevPairList &pl
     a.cell_base0 = rg.c_lo;
     a.rep_status = sa.rep_status;
     const int nb = rg.b_hi - rg.b_lo, nc = rg.c_hi - rg.c_lo;
-    k_seg_setup<<<rg.g_hi - rg.g_lo, 128, 0, s>>>(a, pl.cursor, pl.seg_base);
+    // large segments get a full CTA each for their bounding box
+    const int setup_threads = (int64_t)nb > 2048 * (int64_t)(rg.g_hi - rg.g_lo) ? 1024 : 128;
+    k_seg_setup<<<rg.g_hi - rg.g_lo, setup_threads, 0, s>>>(a, pl.cursor, pl.seg_base);
     k_cell_count<<<blocks_for(nb, 256), 256, 0, s>>>(a, rg.b_lo, rg.b_hi);
     scan_exclusive(c.cell_cnt + rg.c_lo, c.cell_start, nc, c.scan_tmp, s, launches);
     k_cell_scatter<<<blocks_for(nb, 256), 256, 0, s>>>(a, rg.b_lo, rg.b_hi);

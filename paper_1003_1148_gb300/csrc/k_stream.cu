@@ -708,11 +708,8 @@ __global__ void __launch_bounds__(kObsThreads) k_obs_partial(ObsArgs q) {
     }
 }
 
-__global__ void k_obs_final(ObsArgs q, int n_seg) {
-    const int64_t step = *q.a.d_step + q.k_off;
-    if (q.gate > 0 && step % q.gate != 0) return;
-    const int g = blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= n_seg) return;
+// The record of segment g at `step` from its chunks' partial sums, into ring slot `slot`.
+__device__ void write_record(const ObsArgs &q, int g, int64_t step, int64_t slot) {
     double acc[6] = {0, 0, 0, 0, 0, 0};
     for (int ch = q.o.seg_chunk_lo[g]; ch < q.o.seg_chunk_lo[g + 1]; ++ch)
         for (int k = 0; k < 6; ++k) acc[k] += q.o.partial[(size_t)ch * 8 + k];
@@ -730,8 +727,22 @@ __global__ void k_obs_final(ObsArgs q, int n_seg) {
     const int np = q.a.topo.sys_nat_pairs[s];
     rec.q = np > 0 ? acc[3] / (double)np : 0.0;
     rec.r_ee = acc[5];
-    const int64_t slot = (*q.o.events * n_seg + g) % q.o.cap;
     q.o.ring[slot] = rec;
+}
+
+__global__ void k_obs_final(ObsArgs q, int n_seg) {
+    const int64_t step = *q.a.d_step + q.k_off;
+    if (q.gate > 0 && step % q.gate != 0) return;
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= n_seg) return;
+    write_record(q, g, step, (*q.o.events * n_seg + g) % q.o.cap);
+}
+
+// One segment's record (the plain form, which runs the segments one after another): the
+// event is the device counter plus event_off.
+__global__ void k_obs_final_one(ObsArgs q, int g, int n_seg, int64_t event_off) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    write_record(q, g, *q.a.d_step + q.k_off, ((*q.o.events + event_off) * n_seg + g) % q.o.cap);
 }
 
 // Per-replica energy (for sop_forces): sum of the replica's chunk partials.
@@ -901,6 +912,17 @@ void launch_energy(const StepArgs &a, const DevPairList &pl, const DevObs &o, co
     q.chunk0 = ch_lo;
     k_obs_partial<<<ch_hi - ch_lo, kObsThreads, 0, s>>>(q);
     k_energy_sum<<<1, 32, 0, s>>>(o.partial, o.seg_chunk_lo, g_lo, g_hi, out);
+    if (launches) *launches += 2;
+}
+
+void launch_observables_seg(const StepArgs &a, const DevPairList &pl, const DevObs &o, const float4 *pos, int32_t g,
+                            int32_t n_seg, int32_t ch_lo, int32_t ch_hi, int32_t k_off, int64_t event_off,
+                            cudaStream_t s, int64_t *launches) {
+    if (ch_hi <= ch_lo) return;
+    ObsArgs q = make_obs_args(a, pl, o, pos, k_off, 0);
+    q.chunk0 = ch_lo;
+    k_obs_partial<<<ch_hi - ch_lo, kObsThreads, 0, s>>>(q);
+    k_obs_final_one<<<1, 32, 0, s>>>(q, g, n_seg, event_off);
     if (launches) *launches += 2;
 }
 

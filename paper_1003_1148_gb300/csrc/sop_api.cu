@@ -403,21 +403,36 @@ sop_status step_streamed(sop_ctx *c, int64_t n_steps) {
 // ---- plain schedule: one system after another, per-step launches, no graph ---------------
 sop_status step_plain(sop_ctx *c, int64_t n_steps) {
     const int K = c->prm.rebuild_every;
+    const int32_t every = c->prm.obs_every;
     const int64_t s0 = c->step;
     for (int g = 0; g < c->n_seg; ++g) {
         if (*(volatile int32_t *)c->h_abort) break;
         const SegRange rg = seg_range(c, g, g + 1);
         int b = c->cur;
+        bool built = false;   // the list of the current step was built for the observables
         for (int64_t k = 0; k < n_steps; ++k) {
             const int64_t s = s0 + k;
-            if (s % K == 0 && !(k == 0 && c->list_step == s))
+            if (s % K == 0 && !(k == 0 && c->list_step == s) && !built)
                 launch_rebuild(c->sa, c->cells, c->pl, c->d_pos[b], c->d_snap, rg, c->stream, &c->st.kernel_launches);
+            built = false;
             launch_step(c->sa, c->pl, c->d_pos[b], c->d_pos[b ^ 1], c->d_comp, rg.b_lo, rg.b_hi, (int32_t)k, c->lanes,
                         c->stream, &c->st.kernel_launches);
             b ^= 1;
+            if (every > 0 && (s + 1) % every == 0) {   // this segment's record of step s + 1
+                if ((s + 1) % K == 0) {
+                    launch_rebuild(c->sa, c->cells, c->pl, c->d_pos[b], c->d_snap, rg, c->stream,
+                                   &c->st.kernel_launches);
+                    built = true;
+                }
+                launch_observables_seg(c->sa, c->pl, c->obs, c->d_pos[b], g, c->n_seg, c->h_seg_chunk_lo[g],
+                                       c->h_seg_chunk_lo[g + 1], (int32_t)(k + 1), events_in(s0, s + 1, every) - 1,
+                                       c->stream, &c->st.kernel_launches);
+            }
         }
     }
-    launch_tick(c->d_step, n_steps, c->d_events, 0, 0, c->stream, &c->st.kernel_launches);
+    launch_tick(c->d_step, n_steps, c->d_events, 0, events_in(s0, s0 + n_steps, every), c->stream,
+                &c->st.kernel_launches);
+    note_events(c, s0, s0 + n_steps);
     if (n_steps & 1) c->cur ^= 1;
     c->step = s0 + n_steps;
     // the list in use is the one built at the last multiple of K inside this call, if any

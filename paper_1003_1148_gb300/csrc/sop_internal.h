@@ -149,6 +149,12 @@ void launch_forces(const StepArgs &a, const DevPairList &pl, const float4 *pos, 
 void launch_observables(const StepArgs &a, const DevPairList &pl, const DevObs &o, const float4 *pos, int32_t n_seg,
                         int32_t k_off, int32_t gate, cudaStream_t s, int64_t *launches);
 
+// Observables of segment g alone (chunks [ch_lo, ch_hi)) at step *d_step + k_off, written as
+// cadence event *events + event_off.
+void launch_observables_seg(const StepArgs &a, const DevPairList &pl, const DevObs &o, const float4 *pos, int32_t g,
+                            int32_t n_seg, int32_t ch_lo, int32_t ch_hi, int32_t k_off, int64_t event_off,
+                            cudaStream_t s, int64_t *launches);
+
 // FP64 energy of the segments [g_lo, g_hi) at pos into *out (device), via the observable partials.
 // Chunks [ch_lo, ch_hi) must be exactly the chunks of segments [g_lo, g_hi).
 void launch_energy(const StepArgs &a, const DevPairList &pl, const DevObs &o, const float4 *pos, int32_t g_lo,

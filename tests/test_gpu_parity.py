@@ -156,7 +156,7 @@ def test_plain_equals_streamed_bitwise(sop, synth):
 
 
 def test_observables_match_oracle_at_gpu_positions(sop, orc, synth):
-    for schedule in ("streamed", "batched", "pairs"):
+    for schedule in ("streamed", "batched", "pairs", "plain"):
         w = synth.uneven(n_chains=4, lo=60, hi=200, steps=100)
         sim = sop.from_workload(w, n_replicas=2, schedule=schedule, obs_every=20)
         x0 = sim.get_positions(0)

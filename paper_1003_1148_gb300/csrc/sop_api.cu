@@ -20,7 +20,12 @@ namespace {
 thread_local std::string g_create_error;
 
 constexpr int kObsChunk = 2048;        // beads per FP64 observable partial
-constexpr int kBatchedMaxBeads = 8192; // largest system the batched schedule takes
+// Largest system the batched schedule takes: its state lives in shared memory, one CTA per
+// system up to about 3,400 beads (rows in global memory beyond 512), and the cluster form,
+// which keeps a copy of all positions in every CTA of the cluster, up to 4,096.
+constexpr int kBatchedMaxBeads = 4096;
+// Largest system the automatic choice sends to the batched schedule (the one-CTA forms fit).
+constexpr int kBatchedAutoBeads = 3200;
 constexpr int64_t kBatchedChunk = 4096;  // steps per batched launch
 
 // k_B in kcal/(mol K): molar gas constant 8.314462618 J/(mol K) / 4184 J/kcal.
@@ -1240,10 +1245,11 @@ sop_status create_impl(sop_ctx *c, const sop_topology *topo, const double *xyz, 
     const bool batched_ok = c->max_sys <= kBatchedMaxBeads;
     if (sched == SOP_SCHED_AUTO) {
         const int64_t items = (int64_t)c->R * c->n_sys;
-        sched = batched_ok && (c->max_sys <= 512 || items >= 152) ? SOP_SCHED_BATCHED : SOP_SCHED_STREAMED;
+        sched = c->max_sys <= kBatchedAutoBeads && (c->max_sys <= 512 || items >= 152) ? SOP_SCHED_BATCHED
+                                                                                      : SOP_SCHED_STREAMED;
     }
     if (sched == SOP_SCHED_BATCHED && !batched_ok)
-        return fail(c, SOP_ERR_UNSUPPORTED, "the batched schedule takes systems of at most 8192 beads");
+        return fail(c, SOP_ERR_UNSUPPORTED, "the batched schedule takes systems of at most 4096 beads");
     if (sched == SOP_SCHED_PAIRS) {
         s = alloc_pair_tables(c, c->pt);
         if (s != SOP_OK) return s;

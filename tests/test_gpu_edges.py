@@ -67,9 +67,13 @@ def test_chain_without_native_contacts(sop, orc, schedule):
 
 
 def test_largest_batched_system(sop, orc, synth):
-    """One chain of 8,192 beads (the batched limit; its last 32-bead block is full, the
-    4,099-bead chain below leaves a ragged one) against the oracle."""
-    for n in (8192, 4099):
+    """The largest systems of the batched schedule against the oracle: 4,096 beads (the
+    cluster form's limit) and 3,001 beads (one CTA, rows in global memory, a ragged last
+    block of 32 beads); 4,097 beads are refused."""
+    with pytest.raises(sop.SopError) as e:
+        sop.from_workload(synth.fiber4096(n=4097, steps=20), schedule="batched")
+    assert e.value.status == sop.ERR_UNSUPPORTED
+    for n in (4096, 3001):
         w = synth.fiber4096(n=n, steps=20)
         sim = sop.from_workload(w, schedule="batched")
         x0 = sim.get_positions(0)

@@ -70,7 +70,7 @@ def workload(name: str):
 def kernel_revision() -> str:
     """Hash of the batched kernel's sources; a profile summary records the one it measured."""
     h = hashlib.sha256()
-    for f in ("k_batched.cu", "sop_device.cuh", "sop_internal.h"):
+    for f in ("k_batched.cu", "sop_device.cuh", "sop_internal.h", "sop_step.cuh"):
         with open(os.path.join(ROOT, "paper_1003_1148_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]

@@ -336,31 +336,19 @@ __device__ __forceinline__ float3 bead_force(const BatchedArgs &a, const Layout<
     const float *natr = a.nat_ell_r0sq + nat_off + b;
     const uint16_t *rowp = L.row() + p;
     const float A = fp.eps12_h, B = fp.eps6_l;
-    // natives: (12 eps_h / r^2)(s^6 - s^3) with s = r0^2 / r^2
 #pragma unroll 2
-    for (int k = 0; k < nn; ++k) {
+    for (int k = 0; k < tot; ++k) {
+        const bool nat = k < nn;
         const int j = rowp[k * n_s];
-        const float s0 = __ldg(natr + k * n_s);
+        const float s0 = nat ? __ldg(natr + k * n_s) : fp.sigma2;
         const float4 pj = P[j];
         const float dx = pb.x - pj.x, dy = pb.y - pj.y, dz = pb.z - pj.z;
         const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
         const float inv = __fdividef(1.0f, r2);
         const float s = s0 * inv;
         const float s3 = s * s * s;
-        const float c = inv * s3 * fmaf(A, s3, -A);
-        fx = fmaf(c, dx, fx); fy = fmaf(c, dy, fy); fz = fmaf(c, dz, fz);
-    }
-    // Verlet partners: (6 eps_l / r^2) s^3 with s = sigma^2 / r^2
-#pragma unroll 2
-    for (int k = nn; k < tot; ++k) {
-        const int j = rowp[k * n_s];
-        const float4 pj = P[j];
-        const float dx = pb.x - pj.x, dy = pb.y - pj.y, dz = pb.z - pj.z;
-        const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-        const float inv = __fdividef(1.0f, r2);
-        const float s = fp.sigma2 * inv;
-        const float s3 = s * s * s;
-        const float c = inv * s3 * B;
+        // native: (12 eps_h / r^2)(s^6 - s^3); repulsive: (6 eps_l / r^2) s^3 with s = sigma^2/r^2
+        const float c = inv * s3 * (nat ? fmaf(A, s3, -A) : B);
         fx = fmaf(c, dx, fx); fy = fmaf(c, dy, fy); fz = fmaf(c, dz, fz);
     }
     return make_float3(fx, fy, fz);
@@ -812,31 +800,18 @@ __device__ __forceinline__ float3 cluster_force(const BatchedArgs &a, const CLay
     const float *natr = a.nat_ell_r0sq + nat_off + b;
     const uint16_t *rowp = L.row() + p;
     const float A = fp.eps12_h, B = fp.eps6_l;
-    // natives: (12 eps_h / r^2)(s^6 - s^3) with s = r0^2 / r^2
 #pragma unroll 2
-    for (int k = 0; k < nn; ++k) {
+    for (int k = 0; k < tot; ++k) {
+        const bool nat = k < nn;
         const int j = rowp[k * m];
-        const float s0 = __ldg(natr + k * n_s);
+        const float s0 = nat ? __ldg(natr + k * n_s) : fp.sigma2;
         const float4 pj = P[j];
         const float dx = pb.x - pj.x, dy = pb.y - pj.y, dz = pb.z - pj.z;
         const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
         const float inv = __fdividef(1.0f, r2);
         const float s = s0 * inv;
         const float s3 = s * s * s;
-        const float c = inv * s3 * fmaf(A, s3, -A);
-        fx = fmaf(c, dx, fx); fy = fmaf(c, dy, fy); fz = fmaf(c, dz, fz);
-    }
-    // Verlet partners: (6 eps_l / r^2) s^3 with s = sigma^2 / r^2
-#pragma unroll 2
-    for (int k = nn; k < tot; ++k) {
-        const int j = rowp[k * m];
-        const float4 pj = P[j];
-        const float dx = pb.x - pj.x, dy = pb.y - pj.y, dz = pb.z - pj.z;
-        const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-        const float inv = __fdividef(1.0f, r2);
-        const float s = fp.sigma2 * inv;
-        const float s3 = s * s * s;
-        const float c = inv * s3 * B;
+        const float c = inv * s3 * (nat ? fmaf(A, s3, -A) : B);
         fx = fmaf(c, dx, fx); fy = fmaf(c, dy, fy); fz = fmaf(c, dz, fz);
     }
     return make_float3(fx, fy, fz);

@@ -123,3 +123,40 @@ def test_cluster_checkpoint_and_failure(sop, synth):
     sim.step(10, raise_on_error=False)
     assert np.array_equal(sim.get_positions(1), after)
     sim.close()
+
+
+def test_cluster_with_taus_and_underdamped(sop, orc, synth):
+    """The cluster form draws Hybrid Taus noise and takes BAOAB steps like the other forms."""
+    w = small_uneven(synth)
+    R = 2
+    rng = np.random.default_rng(8)
+    st0 = rng.integers(0, 2 ** 32, size=(R, w.n_beads, 4), dtype=np.uint64).astype(np.uint32)
+    st0[..., 0] |= 2
+    st0[..., 1] |= 8
+    st0[..., 2] |= 16
+    sim = clustered(sop, w, 5, n_replicas=R, rng="taus")
+    sim.set_rng_state(st0)
+    x0 = sim.get_positions(0)
+    sim.step(60)
+    st1 = sim.get_rng_state()
+    sys_of = w.system_of_bead()
+    for r in range(R):
+        m = orc.model_from_workload(w)
+        m.start_pulls([(int(sys_of[p.anchor]), p.anchor, p.pulled, p.k_s, p.v) for p in w.pulls], x0)
+        m.set_taus_state(st0[r])
+        xo, _, _, _ = m.run(x0, 60, seed=0)
+        assert np.array_equal(st1[r], m.taus_state())
+        assert float(np.sqrt(((sim.get_positions(r) - xo) ** 2).sum(1).mean())) <= 1e-3
+    sim.close()
+    w.params = dict(w.params, dt=0.02, zeta=0.5)
+    sim = clustered(sop, w, 5, n_replicas=R, integrator="baoab", mass=1.0)
+    sim.step(60)
+    for r in range(R):
+        m = orc.model_from_workload(w)
+        m.start_pulls([(int(sys_of[p.anchor]), p.anchor, p.pulled, p.k_s, p.v) for p in w.pulls], x0)
+        m.set_underdamped(1.0)
+        xo, _, _, _ = m.run(x0, 60, seed=w.seed + r)
+        assert float(np.sqrt(((sim.get_positions(r) - xo) ** 2).sum(1).mean())) <= 1e-3
+        vth = np.sqrt(orc.kB() * w.params["T"] / 1.0)
+        assert float(np.sqrt(((sim.get_velocities(r) - m.velocities()) ** 2).sum(1).mean())) <= 1e-3 * vth
+    sim.close()

@@ -1,7 +1,7 @@
 """FP64 CPU oracle of the SOP-model overdamped Langevin step (Python side).
 
 TEST INFRASTRUCTURE ONLY. This package is the plain, slow restatement of the
-paper's method that the CUDA path is judged against. Only ``tests/``,
+paper's method that the CUDA path is checked against. Only ``tests/``,
 ``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py`` may import
 it. It shares no code with the CUDA library and never imports it; both sides
 take their inputs from the seeded generator in ``paper_1003_1148_gb300.synth``.

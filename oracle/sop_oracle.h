@@ -2,7 +2,7 @@
  * FP64 CPU oracle for the SOP-model overdamped Langevin step.
  *
  * TEST INFRASTRUCTURE ONLY. This is the plain, slow, obviously correct
- * restatement of what the simulation computes, used to judge the CUDA path.
+ * restatement of what the simulation computes, used to check the CUDA path.
  * Only the tests, the smoke check and the CPU-baseline leg of the benchmark
  * may load it. It shares no code, header or constant with the CUDA library.
  *

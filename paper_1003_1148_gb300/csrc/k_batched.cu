@@ -262,7 +262,9 @@ __device__ void rebuild_rows(const BatchedArgs &a, const Layout<RG> &L, const ui
             const float ey = fmaxf(fmaxf(blo.y - pb.y, pb.y - bhi.y), 0.f);
             const float ez = fmaxf(fmaxf(blo.z - pb.z, pb.z - bhi.z), 0.f);
             uint32_t within = 0u, near = 0u;
-            if (fmaf(ez, ez, fmaf(ey, ey, ex * ex)) < hi) {
+            // in a system of a few blocks nearly every box is in range for some lane of the
+            // warp: the test only costs there, so it is skipped
+            if (n_s <= 256 || fmaf(ez, ez, fmaf(ey, ey, ex * ex)) < hi) {
                 if (base + 32 <= n_s) scan32<true>(src, base, 32, pb, lo, hi, &within, &near);
                 else scan32<false>(src, base, n_s - base, pb, lo, hi, &within, &near);
             }

@@ -507,14 +507,12 @@ __device__ __forceinline__ float3 gather_force(const StepArgs &a, const DevPairL
     return make_float3(fx, fy, fz);
 }
 
+// One step of bead gb by its group of L lanes (lane = this thread's lane in the group).
 template <int L>
-__global__ void __launch_bounds__(256) k_step(StepArgs a, DevPairList pl, const float4 *__restrict__ pos_in,
-                                              float4 *__restrict__ pos_out, float4 *__restrict__ comp, int b_lo,
-                                              int b_hi, int k_off) {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    const int gb = b_lo + t / L;
-    const int lane = t % L;
-    if (gb >= b_hi) return;   // whole groups of L lanes leave together
+// (No __restrict__ here: in k_step_coop the same layers are read and written by different
+// steps of one launch, so no load may take the read-only path.)
+__device__ __forceinline__ void step_bead(const StepArgs &a, const DevPairList &pl, const float4 *pos_in,
+                                          float4 *pos_out, float4 *comp, int gb, int lane, int k_off) {
     const int n = a.topo.n;
     const int r = gb / n, i = gb - r * n;
     const float4 *P = pos_in + (size_t)r * n;
@@ -528,6 +526,73 @@ __global__ void __launch_bounds__(256) k_step(StepArgs a, DevPairList pl, const 
     broken = __any_sync(group_mask<L>(), broken);
     if (lane != 0) return;
     advance_bead(a, r, i, gb, P, f, broken, step, pos_out, comp);
+}
+
+template <int L>
+__global__ void __launch_bounds__(256) k_step(StepArgs a, DevPairList pl, const float4 *__restrict__ pos_in,
+                                              float4 *__restrict__ pos_out, float4 *__restrict__ comp, int b_lo,
+                                              int b_hi, int k_off) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int gb = b_lo + t / L;
+    if (gb >= b_hi) return;   // whole groups of L lanes leave together
+    step_bead<L>(a, pl, pos_in, pos_out, comp, gb, t % L, k_off);
+}
+
+// Grid-wide barrier of a cooperative launch (all CTAs co-resident): arrive on a counter,
+// the last arrival resets it and advances the generation, the others wait for that with a
+// bounded spin. False when the wait gave up (a CTA that never arrived): the caller marks
+// its replicas SOP_ERR_TIMEOUT and returns.
+constexpr long long kBarrierSpins = 1ll << 22;   // about a second with the back-off below
+
+__device__ bool grid_barrier(unsigned *bar) {
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned *gen = bar + 1;
+        const unsigned g = *gen;
+        __threadfence();
+        ok = 1;
+        if (atomicAdd(bar, 1u) == gridDim.x - 1) {
+            atomicExch(bar, 0u);
+            __threadfence();
+            atomicAdd(bar + 1, 1u);
+        } else {
+            long long it = 0;
+            while (*gen == g) {
+                if (++it > kBarrierSpins) {
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+// k_steps steps of the beads [b_lo, b_hi) in one cooperative launch: a grid-stride loop of
+// k_step's work per step, a grid barrier between steps; the layers alternate from pos_a.
+// The same arithmetic as k_step, so the results are bit-identical to k_steps launches.
+template <int L>
+__global__ void __launch_bounds__(256) k_step_coop(StepArgs a, DevPairList pl, float4 *pos_a, float4 *pos_b,
+                                                   float4 *comp, int b_lo, int b_hi, int k_off, int k_steps,
+                                                   unsigned *bar) {
+    const int64_t n_thr = (int64_t)(b_hi - b_lo) * L;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;   // a multiple of L: groups stay whole
+    for (int k = 0; k < k_steps; ++k) {
+        const float4 *pin = (k & 1) ? pos_b : pos_a;
+        float4 *pout = (k & 1) ? pos_a : pos_b;
+        for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n_thr; t += stride)
+            step_bead<L>(a, pl, pin, pout, comp, b_lo + (int)(t / L), (int)(t % L), k_off + k);
+        if (k + 1 < k_steps && !grid_barrier(bar)) {
+            if (threadIdx.x == 0)
+                for (int r = b_lo / a.topo.n; r * a.topo.n < b_hi; ++r)
+                    atomicCAS(&a.rep_status[r], 0, (int32_t)SOP_ERR_TIMEOUT);
+            return;
+        }
+    }
 }
 
 // The same step for large systems, with the tail spread over the lanes: a group of L
@@ -865,6 +930,50 @@ void launch_step(const StepArgs &a, const DevPairList &pl, const float4 *pos_in,
     default: k_step<8><<<blocks, 256, 0, s>>>(a, pl, pos_in, pos_out, comp, b_lo, b_hi, k_off); break;
     }
     if (launches) *launches += 1;
+}
+
+int coop_grid(int lanes, int64_t nb) {
+    static int per_sm[3] = {-1, -1, -1};   // co-resident CTAs of 256 threads per SM, by lanes 4/8/16
+    const int li = lanes == 4 ? 0 : lanes == 16 ? 2 : 1;
+    if (per_sm[li] < 0) {
+        int v = 0;
+        const cudaError_t e = lanes == 4    ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_step_coop<4>, 256, 0)
+                              : lanes == 16 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_step_coop<16>, 256, 0)
+                                            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_step_coop<8>, 256, 0);
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        per_sm[li] = (e == cudaSuccess) ? v * sms : 0;
+        cudaGetLastError();
+    }
+    const int need = blocks_for(nb * lanes, 256);
+    return need < per_sm[li] ? need : per_sm[li];
+}
+
+cudaError_t launch_step_coop(const StepArgs &a, const DevPairList &pl, float4 *pos_a, float4 *pos_b, float4 *comp,
+                             int32_t b_lo, int32_t b_hi, int32_t k_off, int32_t k_steps, int lanes, unsigned *bar,
+                             cudaStream_t s, int64_t *launches) {
+    const int64_t nb = b_hi - b_lo;
+    const int grid = coop_grid(lanes, nb);
+    if (nb <= 0 || k_steps <= 0) return cudaSuccess;
+    if (grid <= 0) return cudaErrorCooperativeLaunchTooLarge;
+    cudaLaunchConfig_t lc = {};
+    lc.gridDim = dim3((unsigned)grid, 1, 1);
+    lc.blockDim = dim3(256, 1, 1);
+    lc.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeCooperative;
+    at[0].val.cooperative = 1;
+    lc.attrs = at;
+    lc.numAttrs = 1;
+    cudaError_t e;
+    switch (lanes) {
+    case 4: e = cudaLaunchKernelEx(&lc, k_step_coop<4>, a, pl, pos_a, pos_b, comp, b_lo, b_hi, k_off, k_steps, bar); break;
+    case 16: e = cudaLaunchKernelEx(&lc, k_step_coop<16>, a, pl, pos_a, pos_b, comp, b_lo, b_hi, k_off, k_steps, bar); break;
+    default: e = cudaLaunchKernelEx(&lc, k_step_coop<8>, a, pl, pos_a, pos_b, comp, b_lo, b_hi, k_off, k_steps, bar); break;
+    }
+    if (launches) *launches += 1;
+    return e;
 }
 
 void launch_forces(const StepArgs &a, const DevPairList &pl, const float4 *pos, float4 *force, int32_t b_lo,

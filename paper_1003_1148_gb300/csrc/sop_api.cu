@@ -80,6 +80,9 @@ struct sop_ctx {
     // pair-based form: tables of the run's list (pt) and of the forces-only list (pt2)
     bool pairs = false;
     DevPairTables pt, pt2;
+    // streamed chunks of small launches: the K steps in one cooperative launch
+    bool coop = false;
+    unsigned *d_bar = nullptr;   // its grid barrier (count, generation)
     DevCells cells;
     int64_t pl_cap = 0;
     int ppb = 64;
@@ -321,9 +324,15 @@ void enqueue_streamed_chunk(sop_ctx *c, int start_buf, int64_t *launches) {
     const int K = c->prm.rebuild_every;
     const SegRange all = full_range(c);
     int b = start_buf;
-    for (int k = 0; k < K; ++k) {
-        step_range(c, c->d_pos[b], c->d_pos[b ^ 1], all, k, launches);
-        b ^= 1;
+    if (c->coop) {
+        launch_step_coop(c->sa, c->pl, c->d_pos[b], c->d_pos[b ^ 1], c->d_comp, all.b_lo, all.b_hi, 0, K, c->lanes,
+                         c->d_bar, c->stream, launches);
+        if (K & 1) b ^= 1;
+    } else {
+        for (int k = 0; k < K; ++k) {
+            step_range(c, c->d_pos[b], c->d_pos[b ^ 1], all, k, launches);
+            b ^= 1;
+        }
     }
     // the list of step + K is built from the positions of step + K (the next chunk's first step)
     rebuild_list(c, c->d_pos[b], c->d_snap, all, launches);
@@ -338,9 +347,17 @@ sop_status build_streamed_graph(sop_ctx *c, int start_buf) {
     CUDA_OR_RETURN(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
     enqueue_streamed_chunk(c, start_buf, &launches);
     cudaError_t e = cudaStreamEndCapture(c->stream, &g);
-    if (e != cudaSuccess) return fail(c, SOP_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
-    e = cudaGraphInstantiate(&c->gexec[start_buf], g, 0);
-    cudaGraphDestroy(g);
+    if (e == cudaSuccess) {
+        e = cudaGraphInstantiate(&c->gexec[start_buf], g, 0);
+        cudaGraphDestroy(g);
+        g = nullptr;
+    }
+    if (e != cudaSuccess && c->coop) {   // no cooperative node in the graph: fall back to one launch per step
+        cudaGetLastError();
+        if (g) cudaGraphDestroy(g);
+        c->coop = false;
+        return build_streamed_graph(c, start_buf);
+    }
     c->gexec_launches[start_buf] = launches;
     if (e != cudaSuccess) return fail(c, SOP_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
     return SOP_OK;
@@ -1259,6 +1276,16 @@ sop_status create_impl(sop_ctx *c, const sop_topology *topo, const double *xyz, 
         s = tune_streamed_form(c);
         if (s != SOP_OK) return s;
         if (c->pairs) sched = SOP_SCHED_PAIRS;
+    }
+    // a streamed launch of at most this many beads runs each K-step chunk as one cooperative
+    // launch (SOP_COOP=0 keeps one launch per step)
+    if ((sched == SOP_SCHED_STREAMED) && (int64_t)c->R * c->n <= 38912) {
+        const char *env = std::getenv("SOP_COOP");
+        if (!(env && std::string(env) == "0")) {
+            CUDA_OR_RETURN(c, dalloc(c, &c->d_bar, 2));
+            CUDA_OR_RETURN(c, cudaMemset(c->d_bar, 0, 2 * sizeof(unsigned)));
+            c->coop = true;
+        }
     }
     c->schedule = sched;
     c->st.schedule = sched;

@@ -140,6 +140,13 @@ void launch_rebuild(const StepArgs &a, const DevCells &c, const DevPairList &pl,
 void launch_step(const StepArgs &a, const DevPairList &pl, const float4 *pos_in, float4 *pos_out, float4 *comp,
                  int32_t b_lo, int32_t b_hi, int32_t k_off, int lanes, cudaStream_t s, int64_t *launches);
 
+// k_steps fused steps of the beads [b_lo, b_hi) in one cooperative launch (grid barriers
+// between steps; layers alternate from pos_a, so after an odd count the result is in pos_b).
+// bar: two zero-initialised words of device memory owned by the caller.
+cudaError_t launch_step_coop(const StepArgs &a, const DevPairList &pl, float4 *pos_a, float4 *pos_b, float4 *comp,
+                             int32_t b_lo, int32_t b_hi, int32_t k_off, int32_t k_steps, int lanes, unsigned *bar,
+                             cudaStream_t s, int64_t *launches);
+
 // Forces only (no update) at pos for global beads [b_lo, b_hi); writes F (xyz, w unused).
 void launch_forces(const StepArgs &a, const DevPairList &pl, const float4 *pos, float4 *force, int32_t b_lo,
                    int32_t b_hi, int64_t step, cudaStream_t s, int64_t *launches);

@@ -538,35 +538,56 @@ __global__ void __launch_bounds__(256) k_step(StepArgs a, DevPairList pl, const 
     step_bead<L>(a, pl, pos_in, pos_out, comp, gb, t % L, k_off);
 }
 
-// Grid-wide barrier of a cooperative launch (all CTAs co-resident): arrive on a counter,
-// the last arrival resets it and advances the generation, the others wait for that with a
-// bounded spin. False when the wait gave up (a CTA that never arrived): the caller marks
-// its replicas SOP_ERR_TIMEOUT and returns.
+// Grid-wide barrier of a cooperative launch (all CTAs co-resident). Thread 0 of each CTA
+// reads the generation, arrives on the counter with an acquire-release add (releasing the
+// CTA's writes, which the __syncthreads before it orders first); the last arrival resets
+// the counter and publishes the next generation with a release add; the others poll the
+// generation with acquire loads (first without sleeping, then with a short back-off) up to
+// a bound. False when the wait gave up (a CTA that never arrived): the caller marks its
+// replicas SOP_ERR_TIMEOUT and returns.
 constexpr long long kBarrierSpins = 1ll << 22;   // about a second with the back-off below
+constexpr int kBarrierHotPolls = 2048;           // polls before the back-off starts
+
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned *p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ unsigned atom_add_acq_rel_gpu(unsigned *p, unsigned x) {
+    unsigned old;
+    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(x) : "memory");
+    return old;
+}
+
+__device__ __forceinline__ void red_add_release_gpu(unsigned *p, unsigned x) {
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(x) : "memory");
+}
+
+__device__ __forceinline__ void st_relaxed_gpu(unsigned *p, unsigned x) {
+    asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(x) : "memory");
+}
 
 __device__ bool grid_barrier(unsigned *bar) {
     __shared__ int ok;
     __syncthreads();
     if (threadIdx.x == 0) {
-        volatile unsigned *gen = bar + 1;
-        const unsigned g = *gen;
-        __threadfence();
+        unsigned *gen = bar + 1;
+        const unsigned g = ld_acquire_gpu(gen);   // before arriving: the last arrival changes it only after
         ok = 1;
-        if (atomicAdd(bar, 1u) == gridDim.x - 1) {
-            atomicExch(bar, 0u);
-            __threadfence();
-            atomicAdd(bar + 1, 1u);
+        if (atom_add_acq_rel_gpu(bar, 1u) == gridDim.x - 1) {
+            st_relaxed_gpu(bar, 0u);              // nobody arrives again before the next generation
+            red_add_release_gpu(gen, 1u);
         } else {
             long long it = 0;
-            while (*gen == g) {
+            while (ld_acquire_gpu(gen) == g) {
                 if (++it > kBarrierSpins) {
                     ok = 0;
                     break;
                 }
-                __nanosleep(64);
+                if (it > kBarrierHotPolls) __nanosleep(64);
             }
         }
-        __threadfence();
     }
     __syncthreads();
     return ok != 0;

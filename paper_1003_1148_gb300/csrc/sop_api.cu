@@ -1277,11 +1277,12 @@ sop_status create_impl(sop_ctx *c, const sop_topology *topo, const double *xyz, 
         if (s != SOP_OK) return s;
         if (c->pairs) sched = SOP_SCHED_PAIRS;
     }
-    // a streamed launch of at most this many beads runs each K-step chunk as one cooperative
-    // launch (SOP_COOP=0 keeps one launch per step)
+    // SOP_COOP=1 runs each K-step chunk of a streamed launch of at most this many beads as one
+    // cooperative launch with a grid barrier between steps. Off by default: on GB300 it was
+    // slower than the graph of per-step launches at every size from 512 to 32,768 beads.
     if ((sched == SOP_SCHED_STREAMED) && (int64_t)c->R * c->n <= 38912) {
         const char *env = std::getenv("SOP_COOP");
-        if (!(env && std::string(env) == "0")) {
+        if (env && std::string(env) == "1") {
             CUDA_OR_RETURN(c, dalloc(c, &c->d_bar, 2));
             CUDA_OR_RETURN(c, cudaMemset(c->d_bar, 0, 2 * sizeof(unsigned)));
             c->coop = true;

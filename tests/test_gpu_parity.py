@@ -155,6 +155,22 @@ def test_plain_equals_streamed_bitwise(sop, synth):
     assert np.array_equal(a.get_positions(-1), b.get_positions(-1))
 
 
+def test_cooperative_chunk_equals_plain_bitwise(sop, synth, monkeypatch):
+    """The opt-in cooperative K-step chunk (SOP_COOP=1) does the arithmetic of the per-step
+    launches, with a grid barrier between steps: the trajectory is bit-identical."""
+    w = synth.uneven(n_chains=5, lo=60, hi=300, steps=50)
+    b = sop.from_workload(w, n_replicas=2, schedule="plain")
+    monkeypatch.setenv("SOP_COOP", "1")
+    a = sop.from_workload(w, n_replicas=2, schedule="streamed")
+    monkeypatch.setenv("SOP_COOP", "0")
+    c = sop.from_workload(w, n_replicas=2, schedule="streamed")
+    for sim in (a, b, c):
+        sim.step(37)
+    assert np.array_equal(a.get_positions(-1), b.get_positions(-1))
+    # one cooperative launch replaces the K step launches of each chunk
+    assert a.stats()["kernel_launches"] < c.stats()["kernel_launches"]
+
+
 def test_observables_match_oracle_at_gpu_positions(sop, orc, synth):
     for schedule in ("streamed", "batched", "pairs", "plain"):
         w = synth.uneven(n_chains=4, lo=60, hi=200, steps=100)

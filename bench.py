@@ -348,7 +348,10 @@ def run_ours(args):
                     sop.SCHED_STREAMED: "k_step (one launch per step, CUDA-graph replay) and the cell rebuild",
                     sop.SCHED_PAIRS: "k_pairs + k_pairs_step (two launches per step) and the cell rebuild"}.get(
                         st["schedule"], "per-step kernels"),
-                "kernel_config": {"threads": st["block_threads"], "beads_per_thread": st["beads_per_thread"],
+                "kernel_config": {"schedule": {sop.SCHED_BATCHED: "batched", sop.SCHED_STREAMED: "streamed",
+                                               sop.SCHED_PAIRS: "pairs", sop.SCHED_PLAIN: "plain"}.get(
+                                                   st["schedule"], str(st["schedule"])),
+                                  "threads": st["block_threads"], "beads_per_thread": st["beads_per_thread"],
                                   "register_cap": 65536 // (256 * st["min_blocks"]) if st["min_blocks"] else 64,
                                   "size_buckets": st["buckets"],
                                   "verlet_capacity": st["pairs_per_bead"]},
@@ -404,7 +407,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="replicas8192x128")
-    ap.add_argument("--schedule", default="batched", choices=["batched", "streamed", "pairs", "auto"])
+    ap.add_argument("--schedule", default="auto", choices=["batched", "streamed", "pairs", "auto"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle legs (profiling runs)")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain per-chain comparison")
     args = ap.parse_args()

@@ -296,6 +296,25 @@ typedef struct {
 sop_status sop_brownian_ramp(const sop_ramp_params *params, double *mean, double *var, double *x_final,
                              void *cuda_stream);
 
+/* The noise of the step (Sec. III.C) on its own, for checking it against other
+ * implementations; both calls use the device functions that every step kernel uses.
+ *
+ * sop_box_muller: for each k < n, the four words x[4k .. 4k + 3] (host, uint32) give three
+ * standard normals out[3k .. 3k + 2] (host, FP64 widened from the FP32 results):
+ * radius sqrt(-2 ln u) with u = (x0 + 1) 2^-32 in (0, 1], angle 2 pi x1 2^-32 (cosine,
+ * then sine); the third normal is sqrt(-2 ln((x2 + 1) 2^-32)) cos(2 pi x3 2^-32).
+ *
+ * sop_bead_noise: the three normals out[3k .. 3k + 2] that the step kernels draw for bead
+ * bead_lo + k at step `step` of the replica keyed by `key` (= sop_params.seed + replica):
+ * Philox4x32-10 with key (key lo, key hi) and counter (step lo, step hi, bead, 0), then
+ * the map above. Requires bead_lo + n <= 2^32.
+ *
+ * Both: 0 <= n <= 2^26; they allocate and free their own device memory on cuda_stream
+ * (NULL = default stream) and synchronise it. SOP_ERR_INVALID_ARG on n or a pointer out
+ * of range, SOP_ERR_CUDA / SOP_ERR_OOM on device failure (text in sop_last_error(NULL)). */
+sop_status sop_box_muller(const uint32_t *x, int64_t n, double *out, void *cuda_stream);
+sop_status sop_bead_noise(uint64_t key, int64_t step, uint32_t bead_lo, int64_t n, double *out, void *cuda_stream);
+
 /* Per-replica status ([n_replicas] int32 host): a sop_status value each. */
 sop_status sop_replica_status(sop_ctx *ctx, int32_t *out);
 

@@ -35,16 +35,34 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
     return c;
 }
 
-// -2 ln(u) for u = (x + 1) 2^-32 in (0, 1], accurate to a few ulp everywhere:
-// near u = 1 it uses log1p of the exactly known 1 - u = (2^32 - 1 - x) 2^-32.
+// -2 ln(u) for u = (x + 1) 2^-32 in (0, 1], without branches, to a few ulp. Write
+// u = 2^e (1 - t) with t in [0, 1/2]: then ln u = e ln 2 + ln(1 - t), and
+// ln(1 - t) = -2 atanh(z) with z = t / (2 - t) in [0, 1/3], where atanh is summed by its
+// odd power series z + z^3/3 + ... + z^13/13 (the identity ln((1 + z)/(1 - z)) = 2 atanh z;
+// the first omitted term is below 2^-26 of the sum at z = 1/3). For u >= 1/2 the
+// complement 1 - u = (2^32 - 1 - x) 2^-32 is known exactly (e = 0), so u near 1 keeps its
+// relative accuracy; below, u is rounded to FP32 and its mantissa f in [1/2, 1) gives
+// t = 1 - f exactly. Both terms of the result are >= 0: no cancellation.
 __device__ __forceinline__ float minus_two_log_u(uint32_t x) {
     const float two_m32 = 2.3283064365386963e-10f;  // 2^-32
-    if (x >= 0x80000000u) {
-        const float one_minus_u = (float)(0xFFFFFFFFu - x) * two_m32;
-        return -2.0f * log1pf(-one_minus_u);
-    }
+    const bool upper = x >= 0x80000000u;
     const float u = fmaf((float)x, two_m32, two_m32);
-    return -2.0f * logf(u);
+    const uint32_t ub = __float_as_uint(u);
+    const int e_lo = (int)(ub >> 23) - 126;         // u = f 2^e_lo
+    const float f = __uint_as_float((ub & 0x007FFFFFu) | 0x3F000000u);
+    const float t = upper ? (float)(~x) * two_m32 : 1.0f - f;
+    const float e = upper ? 0.0f : (float)e_lo;
+    const float z = __fdividef(t, 2.0f - t);
+    const float w = z * z;
+    float p = 1.0f / 13.0f;
+    p = fmaf(p, w, 1.0f / 11.0f);
+    p = fmaf(p, w, 1.0f / 9.0f);
+    p = fmaf(p, w, 1.0f / 7.0f);
+    p = fmaf(p, w, 1.0f / 5.0f);
+    p = fmaf(p, w, 1.0f / 3.0f);
+    p = fmaf(p, w, 1.0f);                           // atanh(z) = z p
+    const float ln2 = 0.6931471805599453f;
+    return fmaf(-2.0f * e, ln2, 4.0f * z * p);
 }
 
 // Three standard normals from one Philox block (Box-Muller): the pair

@@ -33,7 +33,8 @@ EXPORTED = ["sop_create", "sop_step", "sop_forces", "sop_pairlist_rebuild", "sop
             "sop_get_positions", "sop_set_positions", "sop_get_pairlist", "sop_get_native_map",
             "sop_get_observables", "sop_get_state", "sop_set_state", "sop_replica_status", "sop_abort",
             "sop_get_stats", "sop_last_error", "sop_destroy", "sop_pairlist_build_noalloc", "sop_get_rng_state",
-            "sop_set_rng_state", "sop_brownian_ramp", "sop_get_velocities", "sop_set_velocities"]
+            "sop_set_rng_state", "sop_brownian_ramp", "sop_get_velocities", "sop_set_velocities",
+            "sop_box_muller", "sop_bead_noise"]
 INTEGRATOR_OVERDAMPED, INTEGRATOR_BAOAB = 0, 1
 INTEGRATORS = {"overdamped": INTEGRATOR_OVERDAMPED, "baoab": INTEGRATOR_BAOAB}
 RNG_PHILOX, RNG_HYBRID_TAUS = 0, 1
@@ -124,6 +125,8 @@ def load(path: str | None = None):
             "sop_brownian_ramp": ([vp, vp, vp, vp, vp], C.c_int),
             "sop_get_velocities": ([vp, i32, vp], C.c_int),
             "sop_set_velocities": ([vp, i32, vp], C.c_int),
+            "sop_box_muller": ([vp, i64, vp, vp], C.c_int),
+            "sop_bead_noise": ([C.c_uint64, i64, C.c_uint32, i64, vp, vp], C.c_int),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -350,6 +353,28 @@ def from_workload(w, n_replicas: int | None = None, schedule="auto", stream=None
         ind = w.indenter
         sim.indenter(ind.center, ind.direction, ind.radius, ind.v)
     return sim
+
+
+def box_muller(x, stream=None):
+    """``sop_box_muller``: three normals per block of four uint32 words, x [n, 4] -> [n, 3]."""
+    L = load()
+    a = np.ascontiguousarray(x, np.uint32).reshape(-1, 4)
+    out = np.zeros((a.shape[0], 3))
+    rc = L.sop_box_muller(_ptr(a), a.shape[0], _ptr(out), _stream_handle(stream))
+    if rc != OK:
+        raise SopError(rc, L.sop_last_error(None).decode())
+    return out
+
+
+def bead_noise(key: int, step: int, bead_lo: int, n: int, stream=None):
+    """``sop_bead_noise``: the normals of beads bead_lo .. bead_lo + n - 1 at `step` for
+    the replica keyed by `key`, [n, 3]."""
+    L = load()
+    out = np.zeros((int(n), 3))
+    rc = L.sop_bead_noise(int(key), int(step), int(bead_lo), int(n), _ptr(out), _stream_handle(stream))
+    if rc != OK:
+        raise SopError(rc, L.sop_last_error(None).decode())
+    return out
 
 
 def brownian_ramp(K, xi, kT, h, r_f, n_runs, n_steps, X0=0.0, order=1, n_out=1, seed=0, x_final=False,

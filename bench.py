@@ -76,6 +76,14 @@ def kernel_revision() -> str:
     return h.hexdigest()[:16]
 
 
+def measured_hbm_gbs():
+    """The measured HBM copy rate of the GB300s (GB/s), else the fallback 6,800."""
+    try:
+        return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"])
+    except (OSError, ValueError, KeyError):
+        return 6800.0
+
+
 def recorded_traffic(name: str):
     """DRAM bytes per launch from profiles/<name>.md, or None when that capture measured
     other kernel sources than the ones built now."""
@@ -359,6 +367,12 @@ def run_ours(args):
                 "peak_note": "FP32 FMA pipe: 152 SMs x 128 lanes x 2 x 2070 MHz (max SM clock), derived"}
     roofline["traffic"] = (recorded_traffic("k_batched_replicas8192x128")
                            if args.workload == "replicas8192x128" and st["schedule"] == sop.SCHED_BATCHED else None)
+    if roofline["traffic"] is not None:
+        # the same launch against the HBM roofline: its measured DRAM bytes over its duration
+        hbm_peak = measured_hbm_gbs()
+        gbs = roofline["traffic"] / per_launch_s / 1e9
+        roofline["hbm"] = {"achieved_gbs": gbs, "peak_gbs": hbm_peak, "frac": gbs / hbm_peak if hbm_peak else None,
+                           "source": "ncu DRAM bytes per launch / CUDA-event launch time; peak of measured copy"}
 
     # plain per-chain GPU form on a subset of replicas (same kernels' math, one chain per launch)
     plain = None

@@ -1204,4 +1204,42 @@ cudaError_t launch_batched(const BatchedArgs &a, const BatchedConfig &cfg, cudaS
     }
 }
 
+// CTAs of this configuration that the device holds at once (0: unknown).
+namespace {
+template <int BPT, int MINB, int MAXT, bool RG>
+int resident_t(const BatchedConfig &cfg) {
+    auto kern = k_batched<BPT, MINB, MAXT, RG>;
+    int per_sm = 0, dev = 0, sms = 0;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cfg.smem) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, cfg.threads, cfg.smem) != cudaSuccess ||
+        cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return per_sm * sms;
+}
+}  // namespace
+
+int batched_resident_ctas(const BatchedConfig &cfg) {
+    if (cfg.cluster > 0) return cluster_capacity(cfg) * cfg.cluster;
+    if (cfg.rows_global) {
+        switch (cfg.beads_per_thread) {
+        case 1: return resident_t<1, 1, 1024, true>(cfg);
+        case 2: return resident_t<2, 1, 1024, true>(cfg);
+        case 4: return resident_t<4, 1, 1024, true>(cfg);
+        default: return resident_t<8, 1, 1024, true>(cfg);
+        }
+    }
+    const int b = cfg.beads_per_thread;
+    switch (cfg.min_blocks) {
+    case 2: return b == 1 ? resident_t<1, 2, 256, false>(cfg) : b == 2 ? resident_t<2, 2, 256, false>(cfg)
+                                                                      : resident_t<4, 2, 256, false>(cfg);
+    case 3: return b == 1 ? resident_t<1, 3, 256, false>(cfg) : b == 2 ? resident_t<2, 3, 256, false>(cfg)
+                                                                      : resident_t<4, 3, 256, false>(cfg);
+    default: return b == 1 ? resident_t<1, 4, 256, false>(cfg) : b == 2 ? resident_t<2, 4, 256, false>(cfg)
+                                                                       : resident_t<4, 4, 256, false>(cfg);
+    }
+}
+
 }  // namespace sop

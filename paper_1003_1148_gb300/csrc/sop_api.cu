@@ -111,6 +111,12 @@ struct sop_ctx {
         int32_t n_items = 0;
         BatchedConfig cfg;
         uint16_t *rows = nullptr;   // rows in global memory (when cfg.rows_global)
+        // tuning: the configuration holding the least SM time (cfg: the fastest alone), the
+        // cache key, and whether this bucket was timed (not taken from the cache or default)
+        BatchedConfig alt;
+        std::string key;
+        float span_ms = 0.f;
+        bool timed = false;
         cudaStream_t stream = nullptr;
         cudaEvent_t done = nullptr;
     };
@@ -771,7 +777,8 @@ sop_status build_buckets(sop_ctx *c, const std::vector<int32_t> &first_len) {
 // Autotuner of one size bucket. Candidates are (threads per CTA, beads per thread, register
 // cap, rows in shared or global memory); each is timed on a 20-step trial of the bucket's
 // first items (up to 16 CTAs per SM) on scratch copies of the state (the run's state,
-// records and statuses are untouched) and the fastest is kept. Results are cached in the
+// records and statuses are untouched) and the fastest is kept (with several buckets, the
+// one holding the least SM time, as the buckets fill each other's last waves). Results are cached in the
 // file named by SOP_TUNE_CACHE, keyed by the bucket's size, row width and trial size;
 // SOP_TUNE=0 skips the trial and takes the default.
 sop_status tune_bucket(sop_ctx *c, sop_ctx::Bucket &bk) {
@@ -850,7 +857,7 @@ sop_status tune_bucket(sop_ctx *c, sop_ctx::Bucket &bk) {
             cudaEvent_t e0, e1;
             CUDA_OR_RETURN(c, cudaEventCreate(&e0));
             CUDA_OR_RETURN(c, cudaEventCreate(&e1));
-            float best_ms = 1e30f;
+            float best_ms = 1e30f, best_cost = 1e30f;
             sop_status status = SOP_OK;
             for (const auto &cf : cands) {
                 BatchedArgs a = batched_args(c, bk);
@@ -888,7 +895,20 @@ sop_status tune_bucket(sop_ctx *c, sop_ctx::Bucket &bk) {
                     if (rep > 0) ms = rep == 1 ? t : std::min(ms, t);
                 }
                 if (status != SOP_OK) break;
+                // Several buckets run side by side, and the partly filled last wave of one is
+                // taken up by the others' CTAs; so beside the fastest alone, keep the one that
+                // holds the least SM time (the time scaled by the filled fraction of its waves).
+                // tune_joint times the two sets together.
+                float cost = ms;
+                if (ms < 1e29f) {
+                    const int slots = batched_resident_ctas(cf);
+                    if (slots > 0) {
+                        const double waves = (double)trial_items * std::max(1, cf.cluster) / slots;
+                        cost = (float)(ms * waves / std::ceil(waves));
+                    }
+                }
                 if (ms < best_ms) { best_ms = ms; bk.cfg = cf; }
+                if (cost < best_cost) { best_cost = cost; bk.alt = cf; }
             }
             cudaEventDestroy(e0);
             cudaEventDestroy(e1);
@@ -899,16 +919,123 @@ sop_status tune_bucket(sop_ctx *c, sop_ctx::Bucket &bk) {
             cudaFree(srows);
             if (status != SOP_OK) return status;
             c->st.tune_ms += best_ms;
-            if (cache)
-                if (FILE *f = std::fopen(cache, "a")) {
-                    std::fprintf(f, "%s -> %d %d %d %d %d %d %.4f\n", key, bk.cfg.threads, bk.cfg.beads_per_thread,
-                                 bk.cfg.min_blocks, (int)bk.cfg.rows_global, bk.cfg.cluster, bk.cfg.m_shift, best_ms);
-                    std::fclose(f);
-                }
+            bk.key = key;
+            bk.span_ms = best_ms;
+            bk.timed = true;
         }
     }
-    if (bk.cfg.rows_global)
-        CUDA_OR_RETURN(c, dalloc(c, &bk.rows, (size_t)bk.n_items * bk.row_width * bk.max_n));
+    return SOP_OK;
+}
+
+bool same_config(const BatchedConfig &x, const BatchedConfig &y) {
+    return x.threads == y.threads && x.beads_per_thread == y.beads_per_thread && x.min_blocks == y.min_blocks &&
+           x.rows_global == y.rows_global && x.cluster == y.cluster && x.m_shift == y.m_shift;
+}
+
+// Buckets run side by side, so the configurations fastest on their own need not be the
+// fastest together. With several buckets, all of them run at once for 100 steps on scratch
+// copies of the state, with every timed bucket on its fastest-alone configuration and then
+// on its least-SM-time one, and the faster set is kept. Then the choices are cached
+// (SOP_TUNE_CACHE) and the global-memory rows are allocated.
+sop_status tune_joint(sop_ctx *c) {
+    bool differ = false;
+    for (const auto &bk : c->buckets) differ |= bk.timed && !same_config(bk.cfg, bk.alt);
+    if (c->buckets.size() > 1 && differ) {
+        const size_t RN = (size_t)c->R * c->n;
+        std::vector<void *> scratch;
+        auto grab = [&](size_t bytes, void **p) {
+            const cudaError_t e = cudaMalloc(p, bytes);
+            if (e == cudaSuccess) scratch.push_back(*p);
+            return e;
+        };
+        auto release = [&]() {
+            for (void *q : scratch) cudaFree(q);
+            for (auto &bk : c->buckets) bk.rows = nullptr;
+        };
+        float4 *sp = nullptr, *sc = nullptr, *ss = nullptr;
+        int32_t *sst = nullptr;
+        cudaError_t e = grab(sizeof(float4) * RN, (void **)&sp);
+        if (e == cudaSuccess) e = grab(sizeof(float4) * RN, (void **)&sc);
+        if (e == cudaSuccess) e = grab(sizeof(float4) * RN, (void **)&ss);
+        if (e == cudaSuccess) e = grab(sizeof(int32_t) * c->R, (void **)&sst);
+        for (auto &bk : c->buckets)
+            if (e == cudaSuccess && (bk.cfg.rows_global || (bk.timed && bk.alt.rows_global)))
+                e = grab(sizeof(uint16_t) * (size_t)bk.n_items * bk.row_width * bk.max_n, (void **)&bk.rows);
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        if (e == cudaSuccess) e = cudaEventCreate(&e0);
+        if (e == cudaSuccess) e = cudaEventCreate(&e1);
+        std::vector<BatchedConfig> fast(c->buckets.size());
+        for (size_t k = 0; k < c->buckets.size(); ++k) fast[k] = c->buckets[k].cfg;
+        sop_status status = SOP_OK;
+        // all buckets at once for 100 steps on the scratch state: the best of two runs after a warm-up
+        auto time_all = [&]() {
+            float best = 1e30f;
+            for (int rep = 0; rep < 3 && e == cudaSuccess && status == SOP_OK; ++rep) {
+                cudaMemcpyAsync(sp, c->d_pos[0], sizeof(float4) * RN, cudaMemcpyDeviceToDevice, c->stream);
+                cudaMemcpyAsync(sc, c->d_comp, sizeof(float4) * RN, cudaMemcpyDeviceToDevice, c->stream);
+                cudaMemcpyAsync(ss, c->d_snap, sizeof(float4) * RN, cudaMemcpyDeviceToDevice, c->stream);
+                cudaMemsetAsync(sst, 0, sizeof(int32_t) * c->R, c->stream);
+                cudaEventRecord(e0, c->stream);
+                status = launch_buckets(
+                    c,
+                    [&](BatchedArgs &a) {
+                        a.pos = sp;
+                        a.comp = sc;
+                        a.snap = ss;
+                        a.sa.rep_status = sst;
+                        a.sa.taus = nullptr;
+                        a.sa.vel = nullptr;
+                        a.obs_every = 0;
+                        a.n_steps = 100;
+                    },
+                    nullptr);
+                cudaEventRecord(e1, c->stream);
+                e = cudaEventSynchronize(e1);
+                float ms = 0.f;
+                if (e == cudaSuccess && status == SOP_OK) {
+                    cudaEventElapsedTime(&ms, e0, e1);
+                    if (rep > 0) best = std::min(best, ms);
+                }
+            }
+            return best;
+        };
+        // the two sets; the faster is kept (per-bucket swaps judged on short joint trials
+        // did not carry over to full launches)
+        std::vector<bool> use_alt(c->buckets.size(), false);
+        auto apply = [&]() {
+            for (size_t k = 0; k < c->buckets.size(); ++k)
+                if (c->buckets[k].timed) c->buckets[k].cfg = use_alt[k] ? c->buckets[k].alt : fast[k];
+        };
+        float t_fast = 1e30f, t_alt = 1e30f;
+        if (e == cudaSuccess) {
+            apply();
+            t_fast = time_all();
+            std::fill(use_alt.begin(), use_alt.end(), true);
+            apply();
+            t_alt = time_all();
+            std::fill(use_alt.begin(), use_alt.end(), t_alt < t_fast);
+            apply();
+        }
+        const float t_best = std::min(t_fast, t_alt);
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+        release();
+        if (status != SOP_OK) return status;
+        if (e != cudaSuccess) return fail(c, SOP_ERR_CUDA, std::string("joint tuning: ") + cudaGetErrorString(e));
+        c->st.tune_ms += t_best;
+    }
+    const char *cache = std::getenv("SOP_TUNE_CACHE");
+    for (auto &bk : c->buckets) {
+        if (cache && bk.timed)
+            if (FILE *f = std::fopen(cache, "a")) {
+                std::fprintf(f, "%s -> %d %d %d %d %d %d %.4f\n", bk.key.c_str(), bk.cfg.threads,
+                             bk.cfg.beads_per_thread, bk.cfg.min_blocks, (int)bk.cfg.rows_global, bk.cfg.cluster,
+                             bk.cfg.m_shift, bk.span_ms);
+                std::fclose(f);
+            }
+        if (bk.cfg.rows_global)
+            CUDA_OR_RETURN(c, dalloc(c, &bk.rows, (size_t)bk.n_items * bk.row_width * bk.max_n));
+    }
     return SOP_OK;
 }
 
@@ -1305,6 +1432,8 @@ sop_status create_impl(sop_ctx *c, const sop_topology *topo, const double *xyz, 
             if (s != SOP_OK) return s;
             if (c->buckets[k].n_items > c->buckets[main_bucket].n_items) main_bucket = k;
         }
+        s = tune_joint(c);
+        if (s != SOP_OK) return s;
         const BatchedConfig &cfg = c->buckets[main_bucket].cfg;
         c->st.block_threads = cfg.threads;
         c->st.pairs_per_bead = c->batched_cap;

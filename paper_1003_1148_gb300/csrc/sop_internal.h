@@ -257,6 +257,9 @@ bool batched_config(int max_n, int row_width, int threads, bool rows_global, int
 // The cluster form: each system is split over ceil(max_n / 2^m_shift) CTAs (at most 16)
 // of `threads` threads that own 2^m_shift consecutive beads each; false when it does not fit.
 bool cluster_config(int max_n, int row_width, int threads, int m_shift, BatchedConfig *cfg);
+// CTAs of the configuration the device holds at once (cluster form: clusters x size); 0 when
+// the occupancy query fails.
+int batched_resident_ctas(const BatchedConfig &cfg);
 // Clusters of the configuration that fit the device at once (0: it cannot launch).
 int cluster_capacity(const BatchedConfig &cfg);
 // Run n_steps (or forces only when a.force_out != null and n_steps == 0).

@@ -64,7 +64,7 @@ __host__ __device__ inline size_t state_bytes(int max_n) {
     size_t s = kHeadBytes;
     s += 3 * sizeof(float4) * (size_t)max_n;       // two layers + compensation
     s += sizeof(float2) * (size_t)max_n;           // bond lengths
-    s += 4 * sizeof(uint16_t) * (size_t)max_n;     // two orders + counts
+    s += 5 * sizeof(uint16_t) * (size_t)max_n;     // two orders, counts, slot of each bead
     s += (size_t)max_n;                            // flags
     s = (s + 15) / 16 * 16;
     s += 2 * sizeof(float4) * (size_t)((max_n + 31) / 32);   // block bounding boxes
@@ -94,11 +94,13 @@ struct Layout {
     // by slot: native entries of the row, and natives + Verlet entries
     __device__ __forceinline__ uint16_t *n_nat() const { return order(2); }
     __device__ __forceinline__ uint16_t *n_tot() const { return order(3); }
+    // by bead: its slot in the current order (kept for systems of more than 256 beads)
+    __device__ __forceinline__ uint16_t *slot_of() const { return order(4); }
     // by bead
-    __device__ __forceinline__ uint8_t *flags() const { return reinterpret_cast<uint8_t *>(order(4)); }
+    __device__ __forceinline__ uint8_t *flags() const { return reinterpret_cast<uint8_t *>(order(5)); }
     // per block of 32 beads: (lo, hi) corners of the bounding box
     __device__ __forceinline__ float4 *bbox() const {
-        const size_t off = (kHeadBytes + 3 * 16 * (size_t)mx + 8 * (size_t)mx + 8 * (size_t)mx + mx + 15) / 16 * 16;
+        const size_t off = (kHeadBytes + 3 * 16 * (size_t)mx + 8 * (size_t)mx + 10 * (size_t)mx + mx + 15) / 16 * 16;
         return reinterpret_cast<float4 *>(g_smem + off);
     }
     // by slot: entry k of slot p at row[k * n + p] (bead indices)
@@ -232,8 +234,13 @@ __device__ __forceinline__ void scan32(const float4 *src, int base, int lim, flo
     *near = nr & ~w;
 }
 
-// Rows of the thread's slots from layer src: the bead in slot p gets its native
-// partners and its Verlet partners in column p. Block boxes must be current.
+// Rows from layer src: the bead in slot p gets its native partners and its Verlet
+// partners in column p. Block boxes must be current. In systems of up to 256 beads a
+// thread builds the rows of its own slots. In larger ones it builds the rows of beads
+// threadIdx.x + k * blockDim (slot_of must be current): a warp then scans for 32
+// consecutive beads, which lie close together, so the box test skips blocks for all its
+// lanes at once (with slots, ordered by row length, the lanes are spread over the whole
+// system and some lane needs nearly every block). The rows are the same either way.
 template <int BPT, bool RG>
 __device__ void rebuild_rows(const BatchedArgs &a, const Layout<RG> &L, const uint16_t *order, const float4 *src,
                              int n_s, int nat_off, int b0) {
@@ -242,11 +249,13 @@ __device__ void rebuild_rows(const BatchedArgs &a, const Layout<RG> &L, const ui
     const float lo = cut2 - cut2 * 1e-4f, hi = cut2 + cut2 * 1e-4f;
     const float4 *bb = L.bbox();
     uint16_t *row = L.row();
+    const bool by_bead = n_s > 256;
 #pragma unroll 1
     for (int k = 0; k < BPT; ++k) {
-        const int p = threadIdx.x + k * T;
-        if (p >= n_s) continue;
-        const int b = order[p];
+        const int idx = threadIdx.x + k * T;
+        if (idx >= n_s) continue;
+        const int p = by_bead ? (int)L.slot_of()[idx] : idx;
+        const int b = by_bead ? idx : (int)order[p];
         const float4 pb = src[b];
         const int nn = a.nat_ell_cnt[b0 + b];
         const uint16_t *natc = a.nat_ell_col + nat_off + b;
@@ -304,6 +313,11 @@ __device__ int rebuild(const BatchedArgs &a, const Layout<RG> &L, const float4 *
                        int ord) {
     block_boxes(L, src, n_s);
     ord = reorder_slots(L, n_s, ord);   // its barriers also publish the boxes
+    if (n_s > 256) {
+        const uint16_t *o = L.order(ord);
+        for (int p = threadIdx.x; p < n_s; p += blockDim.x) L.slot_of()[o[p]] = (uint16_t)p;
+        __syncthreads();
+    }
     rebuild_rows<BPT>(a, L, L.order(ord), src, n_s, nat_off, b0);
     __syncthreads();
     return ord;

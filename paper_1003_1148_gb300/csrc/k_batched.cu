@@ -249,7 +249,9 @@ __device__ void rebuild_rows(const BatchedArgs &a, const Layout<RG> &L, const ui
     const float lo = cut2 - cut2 * 1e-4f, hi = cut2 + cut2 * 1e-4f;
     const float4 *bb = L.bbox();
     uint16_t *row = L.row();
-    const bool by_bead = n_s > 256;
+    // instances with one bead per thread and shared-memory rows never hold more than 256 beads
+    constexpr bool kLarge = RG || BPT > 1;
+    const bool by_bead = kLarge && n_s > 256;
 #pragma unroll 1
     for (int k = 0; k < BPT; ++k) {
         const int idx = threadIdx.x + k * T;
@@ -273,7 +275,7 @@ __device__ void rebuild_rows(const BatchedArgs &a, const Layout<RG> &L, const ui
             uint32_t within = 0u, near = 0u;
             // in a system of a few blocks nearly every box is in range for some lane of the
             // warp: the test only costs there, so it is skipped
-            if (n_s <= 256 || fmaf(ez, ez, fmaf(ey, ey, ex * ex)) < hi) {
+            if (!kLarge || n_s <= 256 || fmaf(ez, ez, fmaf(ey, ey, ex * ex)) < hi) {
                 if (base + 32 <= n_s) scan32<true>(src, base, 32, pb, lo, hi, &within, &near);
                 else scan32<false>(src, base, n_s - base, pb, lo, hi, &within, &near);
             }
@@ -311,9 +313,10 @@ __device__ void rebuild_rows(const BatchedArgs &a, const Layout<RG> &L, const ui
 template <int BPT, bool RG>
 __device__ int rebuild(const BatchedArgs &a, const Layout<RG> &L, const float4 *src, int n_s, int nat_off, int b0,
                        int ord) {
+    constexpr bool kLarge = RG || BPT > 1;   // as in rebuild_rows
     block_boxes(L, src, n_s);
     ord = reorder_slots(L, n_s, ord);   // its barriers also publish the boxes
-    if (n_s > 256) {
+    if (kLarge && n_s > 256) {
         const uint16_t *o = L.order(ord);
         for (int p = threadIdx.x; p < n_s; p += blockDim.x) L.slot_of()[o[p]] = (uint16_t)p;
         __syncthreads();

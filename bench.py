@@ -77,7 +77,7 @@ def kernel_revision() -> str:
 
 
 def measured_hbm_gbs():
-    """The measured HBM copy rate of the GB300s (GB/s), else the fallback 6,800."""
+    """The measured HBM copy rate of the GB300 (GB/s, MEASURED_PEAKS.json), else 6,800."""
     try:
         return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"])
     except (OSError, ValueError, KeyError):

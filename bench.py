@@ -288,7 +288,12 @@ def run_ours(args):
             # size the sample to about 15 s of CPU work
             steps = int(max(200, min(5000, 15.0 * probe_rate / (n_rep * w.n_beads))))
             rate, cores, sample = cpu_baseline_leg(w, n_rep, steps, pool)
-        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+        # one core, one replica at a time (the form of the paper's CPU comparison), about 3 s
+        one_steps = int(max(50, min(50000, 3.0 * probe_rate / max(1, min(n_rep, cpu_cores())) / w.n_beads)))
+        work1, t1 = _oracle_replica((w.xyz, w.chain_offsets, w.seed, one_steps, w.params))
+        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
+               "single_core": {"value": work1 / t1, "unit": UNIT, "cores": 1,
+                               "sample": f"1 replica x {one_steps} steps x {w.xyz.shape[0]} beads in one process"}}
 
     stream = torch.cuda.Stream(device=dev)
     first, _ = dist.replica_range(rank, world, per_rank=R)

@@ -693,9 +693,10 @@ struct CLayout {
     }
     __device__ __forceinline__ uint16_t *n_nat() const { return order(2); }
     __device__ __forceinline__ uint16_t *n_tot() const { return order(3); }
-    __device__ __forceinline__ uint8_t *flags() const { return reinterpret_cast<uint8_t *>(order(4)); }
+    __device__ __forceinline__ uint16_t *slot_of() const { return order(4); }   // by own bead: its slot
+    __device__ __forceinline__ uint8_t *flags() const { return reinterpret_cast<uint8_t *>(order(5)); }
     __device__ __forceinline__ float4 *bbox() const {
-        const size_t off = (kHeadBytes + 32 * (size_t)nmax + 16 * (size_t)m + 8 * (size_t)m + 8 * (size_t)m + m + 15)
+        const size_t off = (kHeadBytes + 32 * (size_t)nmax + 16 * (size_t)m + 8 * (size_t)m + 10 * (size_t)m + m + 15)
                            / 16 * 16;
         return reinterpret_cast<float4 *>(g_smem + off);
     }
@@ -707,7 +708,7 @@ struct CLayout {
 };
 
 __host__ __device__ inline size_t cluster_smem(int m, int nmax, int row_width) {
-    size_t s = kHeadBytes + 32 * (size_t)nmax + 16 * (size_t)m + 8 * (size_t)m + 8 * (size_t)m + m;
+    size_t s = kHeadBytes + 32 * (size_t)nmax + 16 * (size_t)m + 8 * (size_t)m + 10 * (size_t)m + m;
     s = (s + 15) / 16 * 16;
     s += 2 * sizeof(float4) * (size_t)(nmax / 32);
     s += sizeof(uint16_t) * (size_t)row_width * m;
@@ -716,7 +717,9 @@ __host__ __device__ inline size_t cluster_smem(int m, int nmax, int row_width) {
 }
 
 // Rows of this CTA's slots from layer `layer` of its copy (system-local bead indices).
-// The block boxes of the whole system must be current.
+// The block boxes of the whole system and slot_of must be current. A thread builds the
+// rows of own beads threadIdx.x + k * blockDim, so that a warp scans for 32 consecutive
+// beads and the box test skips blocks for all its lanes at once (as in rebuild_rows).
 template <int BPT>
 __device__ void cluster_rows(const BatchedArgs &a, const CLayout &L, const uint16_t *order, int layer, int n_loc,
                              int lo, int n_s, int nat_off, int b0) {
@@ -726,11 +729,12 @@ __device__ void cluster_rows(const BatchedArgs &a, const CLayout &L, const uint1
     const float4 *src = L.pos(layer);
     const float4 *bb = L.bbox();
     uint16_t *row = L.row();
+    (void)order;
 #pragma unroll 1
     for (int k = 0; k < BPT; ++k) {
-        const int p = threadIdx.x + k * T;
-        if (p >= n_loc) continue;
-        const int l = order[p];
+        const int l = threadIdx.x + k * T;
+        if (l >= n_loc) continue;
+        const int p = L.slot_of()[l];
         const int b = lo + l;
         const float4 pb = src[b];
         const int nn = a.nat_ell_cnt[b0 + b];
@@ -786,6 +790,9 @@ __device__ int cluster_rebuild(const BatchedArgs &a, const CLayout &L, int layer
                                int nat_off, int b0, int ord) {
     block_boxes(L, L.pos(layer), n_s);
     ord = reorder_slots(L, n_loc, ord);   // its barriers also publish the boxes
+    const uint16_t *o = L.order(ord);
+    for (int p = threadIdx.x; p < n_loc; p += blockDim.x) L.slot_of()[o[p]] = (uint16_t)p;
+    __syncthreads();
     cluster_rows<BPT>(a, L, L.order(ord), layer, n_loc, lo, n_s, nat_off, b0);
     __syncthreads();
     return ord;

@@ -19,7 +19,7 @@ namespace {
 
 thread_local std::string g_create_error;
 
-constexpr int kObsChunk = 2048;        // beads per FP64 observable partial
+constexpr int kObsChunk = 128;         // beads per FP64 observable partial (FP64 is slow per SM: spread it)
 // Largest system the batched schedule takes: its state lives in shared memory, one CTA per
 // system up to about 3,400 beads (rows in global memory beyond 512), and the cluster form,
 // which keeps a copy of all positions in every CTA of the cluster, up to 4,096.

@@ -998,11 +998,15 @@ cudaError_t launch_step_coop(const StepArgs &a, const DevPairList &pl, float4 *p
 }
 
 void launch_forces(const StepArgs &a, const DevPairList &pl, const float4 *pos, float4 *force, int32_t b_lo,
-                   int32_t b_hi, int64_t step, cudaStream_t s, int64_t *launches) {
-    const int64_t threads = (int64_t)(b_hi - b_lo) * 8;
+                   int32_t b_hi, int64_t step, cudaStream_t s, int64_t *launches, int lanes) {
+    const int64_t threads = (int64_t)(b_hi - b_lo) * lanes;
     const int blocks = blocks_for(threads, 256);
     if (blocks <= 0) return;
-    k_forces<8><<<blocks, 256, 0, s>>>(a, pl, pos, force, b_lo, b_hi, step);
+    switch (lanes) {
+    case 4: k_forces<4><<<blocks, 256, 0, s>>>(a, pl, pos, force, b_lo, b_hi, step); break;
+    case 16: k_forces<16><<<blocks, 256, 0, s>>>(a, pl, pos, force, b_lo, b_hi, step); break;
+    default: k_forces<8><<<blocks, 256, 0, s>>>(a, pl, pos, force, b_lo, b_hi, step); break;
+    }
     if (launches) *launches += 1;
 }
 

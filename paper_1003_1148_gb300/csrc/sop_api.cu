@@ -1093,10 +1093,10 @@ sop_status alloc_pair_tables(sop_ctx *c, DevPairTables &t) {
     return SOP_OK;
 }
 
-// The streamed schedule's choice between the particle-based gather (Algorithm 2) and the
-// pair-based form (Algorithms 4, 5): both force evaluations are timed on the current
-// positions and list (forces only; the run's state is untouched), the faster is kept.
-// SOP_TUNE=0 keeps the particle-based form without a trial.
+// The streamed schedule's choice between the particle-based gather (Algorithm 2) with 4,
+// 8 or 16 lanes per bead and the pair-based form (Algorithms 4, 5): the force evaluations
+// are timed on the current positions and list (forces only; the run's state is untouched)
+// and the fastest is kept. SOP_TUNE=0 keeps the particle-based form with 8 lanes per bead.
 sop_status tune_streamed_form(sop_ctx *c) {
     const char *env = std::getenv("SOP_TUNE");
     if (env && std::string(env) == "0") return SOP_OK;
@@ -1107,14 +1107,16 @@ sop_status tune_streamed_form(sop_ctx *c) {
     cudaEvent_t e0, e1;
     CUDA_OR_RETURN(c, cudaEventCreate(&e0));
     CUDA_OR_RETURN(c, cudaEventCreate(&e1));
-    float ms[2] = {0.f, 0.f};
+    // the particle-based gather with 4, 8 and 16 lanes per bead, and the pair-based form
+    const int gather_lanes[3] = {8, 4, 16};
+    float ms[4] = {0.f, 0.f, 0.f, 0.f};
     const int reps = 20;
-    for (int form = 0; form < 2; ++form) {
+    for (int form = 0; form < 4; ++form) {
         for (int rep = 0; rep <= reps; ++rep) {
             if (rep == 1) cudaEventRecord(e0, c->stream);   // the first launch is a warm-up
-            if (form == 0)
+            if (form < 3)
                 launch_forces(c->sa, c->pl, c->d_pos[c->cur], c->d_force, all.b_lo, all.b_hi, c->step, c->stream,
-                              nullptr);
+                              nullptr, gather_lanes[form]);
             else
                 launch_pairs_forces(c->sa, c->pl, c->pt, c->d_pos[c->cur], c->d_force, all, c->step, c->stream,
                                     nullptr);
@@ -1131,8 +1133,12 @@ sop_status tune_streamed_form(sop_ctx *c) {
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    c->pairs = ms[1] < ms[0];
-    c->st.tune_ms = (c->pairs ? ms[1] : ms[0]) / reps;
+    int best = 0;
+    for (int form = 1; form < 3; ++form)
+        if (ms[form] < ms[best]) best = form;
+    c->pairs = ms[3] < ms[best];
+    c->lanes = c->pairs ? 8 : gather_lanes[best];   // the pair-based trial gathers with 8
+    c->st.tune_ms = (c->pairs ? ms[3] : ms[best]) / reps;
     return SOP_OK;
 }
 

@@ -147,9 +147,10 @@ cudaError_t launch_step_coop(const StepArgs &a, const DevPairList &pl, float4 *p
                              int32_t b_lo, int32_t b_hi, int32_t k_off, int32_t k_steps, int lanes, unsigned *bar,
                              cudaStream_t s, int64_t *launches);
 
-// Forces only (no update) at pos for global beads [b_lo, b_hi); writes F (xyz, w unused).
+// Forces only (no update) at pos for global beads [b_lo, b_hi) with `lanes` (4, 8, 16)
+// lanes per bead; writes F (xyz, w unused).
 void launch_forces(const StepArgs &a, const DevPairList &pl, const float4 *pos, float4 *force, int32_t b_lo,
-                   int32_t b_hi, int64_t step, cudaStream_t s, int64_t *launches);
+                   int32_t b_hi, int64_t step, cudaStream_t s, int64_t *launches, int lanes = 8);
 
 // Observables (FP64) of all segments at pos; step = *d_step + k_off. If gate > 0 the record
 // is written only when the step is a multiple of gate. Writes into the ring.

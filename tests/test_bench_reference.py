@@ -42,3 +42,42 @@ def test_reference_arm_under_torchrun_two_ranks():
     assert len(lines) == 1
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["n_gpus"] == 2
+
+
+def _bench():
+    sys.path.insert(0, ROOT)
+    import bench
+    return bench
+
+
+def test_algorithmic_bytes_per_bead_step_by_hand():
+    """The streamed form's compulsory bytes: 16 + 16 + 32 + 4 v + 8 m + 8 + 12 + (28 + 4 v) / K
+    with v Verlet and m native entries per bead (two per pair)."""
+    b = _bench()
+    counts = {"bonds": 99, "native_pairs": 250, "verlet_pairs": 600}   # 100 beads: m = 5, v = 12
+    got = b.algorithmic_bytes_per_bead_step(counts, 100, 10)
+    assert got == 16 + 16 + 32 + 4 * 12 + 8 * 5 + 8 + 12 + (16 + 4 + 8 + 4 * 12) / 10
+
+
+def test_recorded_traffic_needs_the_current_kernel_revision(tmp_path, monkeypatch):
+    """A profile's DRAM bytes count only when its recorded source revision is the current one."""
+    b = _bench()
+    rev = b.kernel_revision()   # of the repository's sources
+    (tmp_path / "profiles").mkdir()
+    prof = tmp_path / "profiles" / "k_demo.md"
+    monkeypatch.setattr(b, "ROOT", str(tmp_path))
+    monkeypatch.setattr(b, "kernel_revision", lambda: rev)
+    prof.write_text(f"# demo\n\nKernel source revision: `{rev}`\n\ntraffic_bytes_per_launch: 1234\n")
+    assert b.recorded_traffic("k_demo") == 1234
+    prof.write_text("# demo\n\nKernel source revision: `0000000000000000`\n\ntraffic_bytes_per_launch: 1234\n")
+    assert b.recorded_traffic("k_demo") is None
+    assert b.recorded_traffic("k_missing") is None
+
+
+def test_measured_hbm_peak_is_read_from_the_peaks_file():
+    b = _bench()
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        assert b.measured_hbm_gbs() == float(json.load(open(path))["hbm_gbs"])
+    else:
+        assert b.measured_hbm_gbs() == 6800.0

@@ -1112,6 +1112,11 @@ sop_status tune_streamed_form(sop_ctx *c) {
     float ms[4] = {0.f, 0.f, 0.f, 0.f};
     const int reps = 20;
     for (int form = 0; form < 4; ++form) {
+        // the gather kernels index their threads (beads x lanes) with 32-bit integers
+        if (form < 3 && (int64_t)c->R * c->n * gather_lanes[form] > ((int64_t)1 << 31)) {
+            ms[form] = 1e30f;
+            continue;
+        }
         for (int rep = 0; rep <= reps; ++rep) {
             if (rep == 1) cudaEventRecord(e0, c->stream);   // the first launch is a warm-up
             if (form < 3)

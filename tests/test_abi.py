@@ -78,3 +78,18 @@ def test_create_rejects_bad_input_without_gpu_work(lib):
     with pytest.raises(sop.SopError) as e:
         sop.Simulation(np.zeros((2, 3)), [0, 2], params={"dt": -1.0})
     assert e.value.status == sop.ERR_INVALID_ARG
+
+
+def test_noise_calls_validate_before_any_cuda_call(lib):
+    # n out of range and a bead range past 2^32 are rejected before any device work;
+    # n = 0 is a valid empty request that touches no device
+    from paper_1003_1148_gb300 import sop
+    import numpy as np
+    assert sop.box_muller(np.zeros((0, 4), np.uint32)).shape == (0, 3)
+    assert sop.bead_noise(1, 0, 0, 0).shape == (0, 3)
+    with pytest.raises(sop.SopError) as e:
+        sop.bead_noise(1, 0, 2 ** 32 - 2, 4)
+    assert e.value.status == sop.ERR_INVALID_ARG
+    L = sop.load()   # too many items: refused without touching the (NULL) output
+    assert L.sop_bead_noise(1, 0, 0, 2 ** 26 + 1, None, None) == sop.ERR_INVALID_ARG
+    assert L.sop_box_muller(None, -1, None, None) == sop.ERR_INVALID_ARG

@@ -26,6 +26,10 @@
  *   orc_ermak_update              Algorithm 7 (the first-order Ermak-McCammon
  *                                 update, Eq. 2)
  *   orc_run                       the step sequence of Fig. 2 / Sec. III.D
+ *   orc_observables               the readouts of Sec. IV.B and Fig. 3: energy of
+ *                                 Eq. 1, the cantilever force along the pulling
+ *                                 direction and the extension, the end-to-end
+ *                                 distance, and the fraction of native contacts
  *   orc_baoab_update              the underdamped limit named in the Conclusion, as the
  *                                 BAOAB splitting of Leimkuhler and Matthews (2013)
  *   orc_ramp_*                    Sec. IV.C: the harmonic Brownian particle under a
@@ -605,9 +609,11 @@ int orc_observables(const orc_model *m, const double *xyz, int64_t n_pl, const i
     double *E = (double *)calloc((size_t)n_systems, sizeof(double));
     double *fx = (double *)calloc((size_t)n_systems, sizeof(double));
     double *ex = (double *)calloc((size_t)n_systems, sizeof(double));
+    double *fw = (double *)calloc((size_t)n_systems, sizeof(double));
+    int *pulled = (int *)calloc((size_t)n_systems, sizeof(int));
     int64_t *qf = (int64_t *)calloc((size_t)n_systems, sizeof(int64_t));
     int64_t *qn = (int64_t *)calloc((size_t)n_systems, sizeof(int64_t));
-    if (!E || !fx || !ex || !qf || !qn) return ORC_ERR_ARG;
+    if (!E || !fx || !ex || !fw || !pulled || !qf || !qn) return ORC_ERR_ARG;
     const double R02 = m->R0 * m->R0;
     int rc = ORC_OK;
     for (int32_t b = 0; b < m->n_bonds; ++b) {
@@ -640,6 +646,7 @@ int orc_observables(const orc_model *m, const double *xyz, int64_t n_pl, const i
             f += pl->k_s * (pl->tip0[k] + t * pl->dir[k] - xyz[3 * pl->pulled + k]) * pl->dir[k];
         fx[pl->system] = f;
         ex[pl->system] = sqrt(dist2(xyz + 3 * pl->pulled, xyz + 3 * pl->anchor));
+        pulled[pl->system] = 1;
     }
     if (m->indenter) {
         const orc_indenter *in = m->indenter;
@@ -654,9 +661,12 @@ int orc_observables(const orc_model *m, const double *xyz, int64_t n_pl, const i
             double q2 = q * q;
             double q6 = q2 * q2 * q2;
             double coef = 6.0 * m->eps_l * q6 / rho / r;
-            fx[m->sys[i]] += coef * ((e[0] * in->dir[0] + e[1] * in->dir[1]) + e[2] * in->dir[2]);
+            fw[m->sys[i]] += coef * ((e[0] * in->dir[0] + e[1] * in->dir[1]) + e[2] * in->dir[2]);
         }
-        for (int32_t s = 0; s < n_systems; ++s) ex[s] = t;
+        /* a system on a cantilever reports its spring; every other one the indenter's
+           push along its motion and the distance the indenter has travelled */
+        for (int32_t s = 0; s < n_systems; ++s)
+            if (!pulled[s]) { fx[s] = fw[s]; ex[s] = t; }
     }
     /* first chain of each system: from the system's first bead to the last bead of that chain */
     int32_t *first = (int32_t *)malloc(sizeof(int32_t) * (size_t)n_systems);
@@ -680,7 +690,7 @@ int orc_observables(const orc_model *m, const double *xyz, int64_t n_pl, const i
         o[7] = 0.0;
     }
     free(first); free(last);
-    free(E); free(fx); free(ex); free(qf); free(qn);
+    free(E); free(fx); free(ex); free(fw); free(pulled); free(qf); free(qn);
     return rc;
 }
 

@@ -179,9 +179,14 @@ double orc_ramp_run(const orc_ramp *p, uint64_t seed, int64_t run, int64_t n_ste
 void orc_baoab_update(const orc_model *m, double *xyz, const double *F, uint64_t seed, int64_t step);
 
 /* Observables of every system at positions xyz and step `step`. Per system 8
- * doubles: step, system, energy (Eq. 1 over the list), external force along its
- * direction, extension, fraction of native contacts Q, end-to-end distance of
- * the system's first chain, 0. */
+ * doubles: step, system, energy (Eq. 1 over the list), external force, extension,
+ * fraction of native contacts Q (r < r0 + 2 A), end-to-end distance of the
+ * system's first chain (its first bead to that chain's last bead), 0.
+ * External force and extension: a system on a cantilever (Sec. IV.B) gives
+ * k_s (X_tip(n) - r_pulled) . d with X_tip(n) = tip0 + v (n - n0) d, and
+ * |r_pulled - r_anchor|; any other system, when an indenter is set, gives the sum
+ * over its beads of the wall force projected on the indenter's direction of
+ * motion, and the distance v (n - n0) the indenter has travelled; else 0, 0. */
 int orc_observables(const orc_model *m, const double *xyz, int64_t n_pl, const int32_t *pl_i,
                     const int32_t *pl_j, int64_t step, int32_t n_systems, double *out);
 

@@ -45,6 +45,7 @@ struct sop_ctx {
     // host topology
     std::vector<int32_t> chain_off, sys_lo, chain_of, sys_of, sys_ree_last;
     std::vector<uint8_t> flags;
+    std::vector<uint8_t> fixed_by_mask;   // [n] fixed through the topology's fixed_mask (never cleared)
     std::vector<int32_t> h_nat_row, h_nat_col;
     std::vector<double> h_nat_r0;
     std::vector<int32_t> h_seg_bead_lo, h_seg_cell_base, h_seg_chunk_lo;
@@ -567,8 +568,12 @@ sop_status build_host_topology(sop_ctx *c, const sop_topology *t) {
     for (int s = 0; s < c->n_sys; ++s)
         for (int i = c->sys_lo[s]; i < c->sys_lo[s + 1]; ++i) c->sys_of[i] = s;
     c->flags.assign(c->n, 0);
+    c->fixed_by_mask.assign(c->n, 0);
     if (t->fixed_mask)
-        for (int i = 0; i < c->n; ++i) c->flags[i] = t->fixed_mask[i] ? kFlagFixed : 0;
+        for (int i = 0; i < c->n; ++i) {
+            c->fixed_by_mask[i] = t->fixed_mask[i] ? 1 : 0;
+            c->flags[i] = t->fixed_mask[i] ? kFlagFixed : 0;
+        }
     c->sys_ree_last.resize(c->n_sys);
     for (int s = 0; s < c->n_sys; ++s) {
         const int first = c->sys_lo[s];
@@ -635,6 +640,41 @@ sop_status alloc_pull_arrays(sop_ctx *c, size_t n_pull) {
     CUDA_OR_RETURN(c, dalloc(c, &c->d_pull_tip0, 3 * m * (size_t)c->R));
     c->pull_alloc = m;
     return SOP_OK;
+}
+
+// A complete set of pulling records, assembled and checked before it replaces the
+// context's records (so that a failing call leaves the context as it was).
+struct PullSet {
+    std::vector<int32_t> sys, anchor, bead;
+    std::vector<double> ks, v, n0, dir, tip0;
+    void resize(size_t np, int R) {
+        sys.resize(np); anchor.resize(np); bead.resize(np);
+        ks.resize(np); v.resize(np); n0.resize(np); dir.resize(3 * np); tip0.resize(3 * np * (size_t)R);
+    }
+};
+
+// Replace the pulling records. The flags of the old records are cleared first: the
+// pulled mark always, the fixed mark only where the topology's fixed_mask did not set it.
+void install_pulls(sop_ctx *c, PullSet &&ps) {
+    for (size_t k = 0; k < c->pull_bead.size(); ++k) {
+        c->flags[c->pull_bead[k]] &= (uint8_t)~kFlagPulled;
+        const int a = c->pull_anchor[k];
+        if (!c->fixed_by_mask[a]) c->flags[a] &= (uint8_t)~kFlagFixed;
+    }
+    c->pull_sys = std::move(ps.sys);
+    c->pull_anchor = std::move(ps.anchor);
+    c->pull_bead = std::move(ps.bead);
+    c->pull_ks = std::move(ps.ks);
+    c->pull_v = std::move(ps.v);
+    c->pull_n0 = std::move(ps.n0);
+    c->pull_dir = std::move(ps.dir);
+    c->pull_tip0 = std::move(ps.tip0);
+    c->pull_of_sys.assign(c->n_sys, -1);
+    for (size_t k = 0; k < c->pull_bead.size(); ++k) {
+        c->pull_of_sys[c->pull_sys[k]] = (int32_t)k;
+        c->flags[c->pull_bead[k]] |= kFlagPulled;
+        c->flags[c->pull_anchor[k]] |= kFlagFixed;
+    }
 }
 
 sop_status upload_pulls(sop_ctx *c) {
@@ -1624,54 +1664,50 @@ sop_status sop_pairlist_rebuild(sop_ctx *c) {
 sop_status sop_pull(sop_ctx *c, int32_t n, const sop_pull_params *pulls) {
     if (!c) return fail(nullptr, SOP_ERR_INVALID_ARG, "ctx is NULL");
     if (n < 0 || (n > 0 && !pulls)) return fail(c, SOP_ERR_INVALID_ARG, "pulls");
-    std::vector<int> seen(c->n_sys, 0);
-    for (int k = 0; k < n; ++k) {
-        const sop_pull_params &q = pulls[k];
-        if (q.system < 0 || q.system >= c->n_sys || seen[q.system]++)
-            return fail(c, SOP_ERR_INVALID_ARG, "pull: system out of range or repeated");
-        const int lo = c->sys_lo[q.system], hi = c->sys_lo[q.system + 1];
-        if (q.anchor < lo || q.anchor >= hi || q.pulled < lo || q.pulled >= hi || q.anchor == q.pulled)
-            return fail(c, SOP_ERR_INVALID_ARG, "pull: anchor and pulled must be distinct beads of the system");
-        if (!std::isfinite(q.k_s) || q.k_s < 0 || !std::isfinite(q.v))
-            return fail(c, SOP_ERR_INVALID_ARG, "pull: k_s >= 0 and finite v required");
-    }
-    std::vector<float4> h;
-    sop_status s = positions_f4(c, h);
-    if (s != SOP_OK) return s;
-    // clear old pulled flags; anchors stay fixed only while pulled
-    for (size_t k = 0; k < c->pull_bead.size(); ++k) {
-        c->flags[c->pull_bead[k]] &= (uint8_t)~kFlagPulled;
-        c->flags[c->pull_anchor[k]] &= (uint8_t)~kFlagFixed;
-    }
-    c->pull_of_sys.assign(c->n_sys, -1);
-    c->pull_anchor.clear(); c->pull_bead.clear(); c->pull_sys.clear();
-    c->pull_ks.clear(); c->pull_v.clear(); c->pull_dir.clear(); c->pull_n0.clear(); c->pull_tip0.clear();
-    for (int k = 0; k < n; ++k) {
-        const sop_pull_params &q = pulls[k];
-        c->pull_of_sys[q.system] = k;
-        c->pull_anchor.push_back(q.anchor);
-        c->pull_bead.push_back(q.pulled);
-        c->pull_sys.push_back(q.system);
-        c->pull_ks.push_back(q.k_s);
-        c->pull_v.push_back(q.v);
-        c->pull_n0.push_back((double)c->step);
-        // direction anchor -> pulled at the start, from replica 0 (all replicas share it)
-        const float4 a = h[q.anchor], b = h[q.pulled];
-        const double d[3] = {(double)b.x - (double)a.x, (double)b.y - (double)a.y, (double)b.z - (double)a.z};
-        const double len = std::sqrt((d[0] * d[0] + d[1] * d[1]) + d[2] * d[2]);
-        if (!(len > 0)) return fail(c, SOP_ERR_INVALID_ARG, "pull: anchor and pulled coincide");
-        for (int m = 0; m < 3; ++m) c->pull_dir.push_back(d[m] / len);
-        c->flags[q.pulled] |= kFlagPulled;
-        c->flags[q.anchor] |= kFlagFixed;
-    }
-    c->pull_tip0.assign(3 * (size_t)n * c->R, 0.0);
-    for (int r = 0; r < c->R; ++r)
+    try {
+        std::vector<int> seen(c->n_sys, 0);
         for (int k = 0; k < n; ++k) {
-            const float4 b = h[(size_t)r * c->n + c->pull_bead[k]];
-            double *t = &c->pull_tip0[((size_t)r * n + k) * 3];
-            t[0] = b.x; t[1] = b.y; t[2] = b.z;
+            const sop_pull_params &q = pulls[k];
+            if (q.system < 0 || q.system >= c->n_sys || seen[q.system]++)
+                return fail(c, SOP_ERR_INVALID_ARG, "pull: system out of range or repeated");
+            const int lo = c->sys_lo[q.system], hi = c->sys_lo[q.system + 1];
+            if (q.anchor < lo || q.anchor >= hi || q.pulled < lo || q.pulled >= hi || q.anchor == q.pulled)
+                return fail(c, SOP_ERR_INVALID_ARG, "pull: anchor and pulled must be distinct beads of the system");
+            if (!std::isfinite(q.k_s) || q.k_s < 0 || !std::isfinite(q.v))
+                return fail(c, SOP_ERR_INVALID_ARG, "pull: k_s >= 0 and finite v required");
         }
-    return upload_pulls(c);
+        std::vector<float4> h;
+        sop_status s = positions_f4(c, h);
+        if (s != SOP_OK) return s;
+        // every new record is built (and checked) before the context changes
+        PullSet ps;
+        ps.resize(n, c->R);
+        for (int k = 0; k < n; ++k) {
+            const sop_pull_params &q = pulls[k];
+            ps.sys[k] = q.system;
+            ps.anchor[k] = q.anchor;
+            ps.bead[k] = q.pulled;
+            ps.ks[k] = q.k_s;
+            ps.v[k] = q.v;
+            ps.n0[k] = (double)c->step;
+            // direction anchor -> pulled at the start, from replica 0 (all replicas share it)
+            const float4 a = h[q.anchor], b = h[q.pulled];
+            const double d[3] = {(double)b.x - (double)a.x, (double)b.y - (double)a.y, (double)b.z - (double)a.z};
+            const double len = std::sqrt((d[0] * d[0] + d[1] * d[1]) + d[2] * d[2]);
+            if (!(len > 0) || !std::isfinite(len)) return fail(c, SOP_ERR_INVALID_ARG, "pull: anchor and pulled coincide");
+            for (int m = 0; m < 3; ++m) ps.dir[3 * k + m] = d[m] / len;
+        }
+        for (int r = 0; r < c->R; ++r)
+            for (int k = 0; k < n; ++k) {
+                const float4 b = h[(size_t)r * c->n + ps.bead[k]];
+                double *t = &ps.tip0[((size_t)r * n + k) * 3];
+                t[0] = b.x; t[1] = b.y; t[2] = b.z;
+            }
+        install_pulls(c, std::move(ps));
+        return upload_pulls(c);
+    } catch (const std::exception &e) {
+        return fail(c, SOP_ERR_OOM, std::string("host exception: ") + e.what());
+    }
 }
 
 sop_status sop_indenter(sop_ctx *c, const double center[3], const double direction[3], double radius, double v) {
@@ -1929,81 +1965,111 @@ sop_status sop_get_state(sop_ctx *c, void *buf, int64_t cap, int64_t *size) {
 sop_status sop_set_state(sop_ctx *c, const void *buf, int64_t size) {
     if (!c) return fail(nullptr, SOP_ERR_INVALID_ARG, "ctx is NULL");
     if (!buf || size < (int64_t)(16 * sizeof(int64_t))) return fail(c, SOP_ERR_INVALID_ARG, "state buffer");
-    const char *p = static_cast<const char *>(buf);
-    int64_t hdr[16];
-    std::memcpy(hdr, p, sizeof hdr);
-    if (hdr[0] != 0x534f5031 || hdr[1] != SOP_ABI_VERSION || hdr[2] != c->n || hdr[3] != c->R)
-        return fail(c, SOP_ERR_INVALID_ARG, "state does not match this context");
-    const size_t RN = (size_t)c->R * c->n;
-    const size_t np = (size_t)hdr[6];
-    if ((hdr[10] != 0) != (c->d_taus != nullptr))
-        return fail(c, SOP_ERR_INVALID_ARG, "state: noise source differs from this context");
-    if ((hdr[11] != 0) != (c->d_vel != nullptr))
-        return fail(c, SOP_ERR_INVALID_ARG, "state: integrator differs from this context");
-    const size_t tail_vel = c->d_vel ? RN * sizeof(float4) : 0;
-    const size_t need = 16 * sizeof(int64_t) + 3 * RN * sizeof(float4) + c->R * sizeof(int32_t) +
-                        np * (3 * sizeof(int32_t) + 6 * sizeof(double)) + 3 * np * c->R * sizeof(double) +
-                        9 * sizeof(double) + (c->d_taus ? RN * sizeof(uint4) : 0) + tail_vel;
-    if (size < (int64_t)need) return fail(c, SOP_ERR_INVALID_ARG, "state buffer truncated");
-    CUDA_OR_RETURN(c, cudaStreamSynchronize(c->stream));   // no queued work may still use the state
-    if (c->d_taus)
-        CUDA_OR_RETURN(c, cudaMemcpy(c->d_taus, static_cast<const char *>(buf) + need - tail_vel - RN * sizeof(uint4),
-                                     RN * sizeof(uint4), cudaMemcpyHostToDevice));
-    if (c->d_vel)
-        CUDA_OR_RETURN(c, cudaMemcpy(c->d_vel, static_cast<const char *>(buf) + need - tail_vel, tail_vel,
+    try {
+        // Everything in the buffer is read and checked before the context changes.
+        const char *base = static_cast<const char *>(buf);
+        int64_t hdr[16];
+        std::memcpy(hdr, base, sizeof hdr);
+        if (hdr[0] != 0x534f5031 || hdr[1] != SOP_ABI_VERSION || hdr[2] != c->n || hdr[3] != c->R)
+            return fail(c, SOP_ERR_INVALID_ARG, "state does not match this context");
+        if (hdr[6] < 0 || hdr[6] > c->n_sys)
+            return fail(c, SOP_ERR_INVALID_ARG, "state: pulling record count out of range");
+        if (hdr[4] < 0 || hdr[5] < -1 || hdr[5] > hdr[4] || hdr[8] < 0 || hdr[9] < 0 || hdr[9] > hdr[8] ||
+            (hdr[7] != 0 && hdr[7] != 1))
+            return fail(c, SOP_ERR_INVALID_ARG, "state: step, list step or record counters out of range");
+        if ((hdr[10] != 0) != (c->d_taus != nullptr))
+            return fail(c, SOP_ERR_INVALID_ARG, "state: noise source differs from this context");
+        if ((hdr[11] != 0) != (c->d_vel != nullptr))
+            return fail(c, SOP_ERR_INVALID_ARG, "state: integrator differs from this context");
+        const size_t RN = (size_t)c->R * c->n;
+        const size_t np = (size_t)hdr[6];
+        const size_t tail_vel = c->d_vel ? RN * sizeof(float4) : 0;
+        const size_t tail_taus = c->d_taus ? RN * sizeof(uint4) : 0;
+        const size_t need = 16 * sizeof(int64_t) + 3 * RN * sizeof(float4) + c->R * sizeof(int32_t) +
+                            np * (3 * sizeof(int32_t) + 6 * sizeof(double)) + 3 * np * c->R * sizeof(double) +
+                            9 * sizeof(double) + tail_taus + tail_vel;
+        if ((uint64_t)size < need) return fail(c, SOP_ERR_INVALID_ARG, "state buffer truncated");
+        const char *p_pos = base + sizeof hdr;
+        const char *p_status = p_pos + 3 * RN * sizeof(float4);
+        const char *p = p_status + c->R * sizeof(int32_t);
+        std::vector<int32_t> status(c->R);
+        std::memcpy(status.data(), p_status, c->R * sizeof(int32_t));
+        for (int32_t v : status)
+            if (v < SOP_OK || v > SOP_ERR_INDENTER_OVERLAP)
+                return fail(c, SOP_ERR_INVALID_ARG, "state: replica status out of range");
+        auto get = [&p](void *dst, size_t bytes) { if (bytes) std::memcpy(dst, p, bytes); p += bytes; };
+        PullSet ps;
+        ps.resize(np, c->R);
+        get(ps.sys.data(), np * sizeof(int32_t));
+        get(ps.anchor.data(), np * sizeof(int32_t));
+        get(ps.bead.data(), np * sizeof(int32_t));
+        get(ps.ks.data(), np * sizeof(double));
+        get(ps.v.data(), np * sizeof(double));
+        get(ps.n0.data(), np * sizeof(double));
+        get(ps.dir.data(), 3 * np * sizeof(double));
+        get(ps.tip0.data(), 3 * np * c->R * sizeof(double));
+        std::vector<int> seen(c->n_sys, 0);
+        for (size_t k = 0; k < np; ++k) {
+            const int sy = ps.sys[k];
+            if (sy < 0 || sy >= c->n_sys || seen[sy]++)
+                return fail(c, SOP_ERR_INVALID_ARG, "state: pull system out of range or repeated");
+            const int lo = c->sys_lo[sy], hi = c->sys_lo[sy + 1];
+            if (ps.anchor[k] < lo || ps.anchor[k] >= hi || ps.bead[k] < lo || ps.bead[k] >= hi ||
+                ps.anchor[k] == ps.bead[k])
+                return fail(c, SOP_ERR_INVALID_ARG, "state: pull beads out of range");
+            const double *d = &ps.dir[3 * k];
+            const double len2 = (d[0] * d[0] + d[1] * d[1]) + d[2] * d[2];
+            if (!std::isfinite(ps.ks[k]) || ps.ks[k] < 0 || !std::isfinite(ps.v[k]) || !std::isfinite(ps.n0[k]) ||
+                !(std::fabs(len2 - 1.0) < 1e-9))
+                return fail(c, SOP_ERR_INVALID_ARG, "state: pull spring, speed, start or direction invalid");
+        }
+        double ind[9];
+        get(ind, sizeof ind);
+        for (double v : ind)
+            if (!std::isfinite(v)) return fail(c, SOP_ERR_INVALID_ARG, "state: indenter record not finite");
+        if (hdr[7] != 0 && !(ind[6] > 0)) return fail(c, SOP_ERR_INVALID_ARG, "state: indenter radius");
+        const uint32_t *taus = c->d_taus
+            ? reinterpret_cast<const uint32_t *>(base + need - tail_vel - tail_taus) : nullptr;
+        if (taus) {
+            for (size_t k = 0; k < RN; ++k) {
+                uint32_t w[3];
+                std::memcpy(w, taus + 4 * k, sizeof w);
+                if (w[0] < 2u || w[1] < 8u || w[2] < 16u)
+                    return fail(c, SOP_ERR_INVALID_ARG, "state: Hybrid Taus state needs y1 >= 2, y2 >= 8, y3 >= 16");
+            }
+        }
+        // checked: now replace the context's state
+        CUDA_OR_RETURN(c, cudaStreamSynchronize(c->stream));   // no queued work may still use the state
+        if (taus) CUDA_OR_RETURN(c, cudaMemcpy(c->d_taus, taus, tail_taus, cudaMemcpyHostToDevice));
+        if (c->d_vel)
+            CUDA_OR_RETURN(c, cudaMemcpy(c->d_vel, base + need - tail_vel, tail_vel, cudaMemcpyHostToDevice));
+        c->cur = 0;
+        CUDA_OR_RETURN(c, cudaMemcpy(c->d_pos[0], p_pos, RN * sizeof(float4), cudaMemcpyHostToDevice));
+        CUDA_OR_RETURN(c, cudaMemcpy(c->d_comp, p_pos + RN * sizeof(float4), RN * sizeof(float4), cudaMemcpyHostToDevice));
+        CUDA_OR_RETURN(c, cudaMemcpy(c->d_snap, p_pos + 2 * RN * sizeof(float4), RN * sizeof(float4),
                                      cudaMemcpyHostToDevice));
-    p += sizeof hdr;
-    c->cur = 0;
-    CUDA_OR_RETURN(c, cudaMemcpy(c->d_pos[0], p, RN * sizeof(float4), cudaMemcpyHostToDevice));
-    p += RN * sizeof(float4);
-    CUDA_OR_RETURN(c, cudaMemcpy(c->d_comp, p, RN * sizeof(float4), cudaMemcpyHostToDevice));
-    p += RN * sizeof(float4);
-    CUDA_OR_RETURN(c, cudaMemcpy(c->d_snap, p, RN * sizeof(float4), cudaMemcpyHostToDevice));
-    p += RN * sizeof(float4);
-    CUDA_OR_RETURN(c, cudaMemcpy(c->d_rep_status, p, c->R * sizeof(int32_t), cudaMemcpyHostToDevice));
-    p += c->R * sizeof(int32_t);
-    auto get = [&p](void *dst, size_t bytes) { if (bytes) std::memcpy(dst, p, bytes); p += bytes; };
-    for (size_t k = 0; k < c->pull_bead.size(); ++k) {
-        c->flags[c->pull_bead[k]] &= (uint8_t)~kFlagPulled;
-        c->flags[c->pull_anchor[k]] &= (uint8_t)~kFlagFixed;
+        CUDA_OR_RETURN(c, cudaMemcpy(c->d_rep_status, status.data(), c->R * sizeof(int32_t), cudaMemcpyHostToDevice));
+        install_pulls(c, std::move(ps));
+        c->has_ind = hdr[7] != 0;
+        for (int k = 0; k < 3; ++k) { c->ind_c0[k] = ind[k]; c->ind_dir[k] = ind[3 + k]; }
+        c->ind_radius = ind[6];
+        c->ind_v = ind[7];
+        c->ind_n0 = ind[8];
+        c->step = hdr[4];
+        c->events = hdr[8];
+        c->consumed = hdr[9];
+        CUDA_OR_RETURN(c, cudaMemcpy(c->d_step, &c->step, sizeof(int64_t), cudaMemcpyHostToDevice));
+        CUDA_OR_RETURN(c, cudaMemcpy(c->d_events, &c->events, sizeof(int64_t), cudaMemcpyHostToDevice));
+        sop_status s = upload_pulls(c);
+        if (s != SOP_OK) return s;
+        // the list in use is the one built from the snapshot
+        rebuild_list(c, c->d_snap, nullptr, full_range(c), &c->st.kernel_launches);
+        c->list_step = hdr[5];
+        CUDA_OR_RETURN(c, cudaStreamSynchronize(c->stream));
+        return SOP_OK;
+    } catch (const std::exception &e) {
+        return fail(c, SOP_ERR_OOM, std::string("host exception: ") + e.what());
     }
-    c->pull_sys.resize(np); c->pull_anchor.resize(np); c->pull_bead.resize(np);
-    c->pull_ks.resize(np); c->pull_v.resize(np); c->pull_n0.resize(np);
-    c->pull_dir.resize(3 * np); c->pull_tip0.resize(3 * np * c->R);
-    get(c->pull_sys.data(), np * sizeof(int32_t));
-    get(c->pull_anchor.data(), np * sizeof(int32_t));
-    get(c->pull_bead.data(), np * sizeof(int32_t));
-    get(c->pull_ks.data(), np * sizeof(double));
-    get(c->pull_v.data(), np * sizeof(double));
-    get(c->pull_n0.data(), np * sizeof(double));
-    get(c->pull_dir.data(), 3 * np * sizeof(double));
-    get(c->pull_tip0.data(), 3 * np * c->R * sizeof(double));
-    c->pull_of_sys.assign(c->n_sys, -1);
-    for (size_t k = 0; k < np; ++k) {
-        if (c->pull_sys[k] < 0 || c->pull_sys[k] >= c->n_sys) return fail(c, SOP_ERR_INVALID_ARG, "state: pull system");
-        c->pull_of_sys[c->pull_sys[k]] = (int32_t)k;
-        c->flags[c->pull_bead[k]] |= kFlagPulled;
-        c->flags[c->pull_anchor[k]] |= kFlagFixed;
-    }
-    double ind[9];
-    get(ind, sizeof ind);
-    c->has_ind = hdr[7] != 0;
-    for (int k = 0; k < 3; ++k) { c->ind_c0[k] = ind[k]; c->ind_dir[k] = ind[3 + k]; }
-    c->ind_radius = ind[6];
-    c->ind_v = ind[7];
-    c->ind_n0 = ind[8];
-    c->step = hdr[4];
-    c->events = hdr[8];
-    c->consumed = hdr[9];
-    CUDA_OR_RETURN(c, cudaMemcpy(c->d_step, &c->step, sizeof(int64_t), cudaMemcpyHostToDevice));
-    CUDA_OR_RETURN(c, cudaMemcpy(c->d_events, &c->events, sizeof(int64_t), cudaMemcpyHostToDevice));
-    sop_status s = upload_pulls(c);
-    if (s != SOP_OK) return s;
-    // the list in use is the one built from the snapshot
-    rebuild_list(c, c->d_snap, nullptr, full_range(c), &c->st.kernel_launches);
-    c->list_step = hdr[5];
-    CUDA_OR_RETURN(c, cudaStreamSynchronize(c->stream));
-    return SOP_OK;
 }
 
 sop_status sop_get_rng_state(sop_ctx *c, uint32_t *state, int64_t n_words) {

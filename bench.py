@@ -444,7 +444,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="replicas8192x128")
-    ap.add_argument("--schedule", default="auto", choices=["batched", "streamed", "pairs", "auto"])
+    ap.add_argument("--schedule", default="auto", choices=["batched", "streamed", "pairs", "auto", "batched_pairs"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle legs (profiling runs)")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain per-chain comparison")
     args = ap.parse_args()

@@ -42,7 +42,7 @@
 extern "C" {
 #endif
 
-#define SOP_ABI_VERSION 1
+#define SOP_ABI_VERSION 2
 
 typedef enum {
     SOP_OK = 0,
@@ -65,9 +65,16 @@ typedef enum {
     SOP_SCHED_BATCHED = 1,   /* persistent fused kernel, one CTA per (replica, system), state in shared memory */
     SOP_SCHED_STREAMED = 2,  /* per-step kernels over global memory, cell-list rebuilds, CUDA-graph replay */
     SOP_SCHED_PLAIN = 3,     /* the plain form: per-step launches, one system after another, no graph */
-    SOP_SCHED_PAIRS = 4      /* the streamed schedule with pair-based forces (Sec. III.B, Algorithms 4 and 5):
+    SOP_SCHED_PAIRS = 4,     /* the streamed schedule with pair-based forces (Sec. III.B, Algorithms 4 and 5):
                                 one thread per interacting pair writes +df and -df into per-entry force
                                 slots; the per-bead gathering is fused into the update */
+    SOP_SCHED_BATCHED_PAIRS = 5  /* the batched schedule with each pair evaluated once (Sec. III.B, Algorithms
+                                4 and 5, inside one CTA): a pair belongs to the row of one of its beads,
+                                whose thread adds the force to it and leaves the coefficient for the other
+                                bead to add after a barrier; systems of up to 256 beads (larger systems
+                                of the context take the particle-based gather). SOP_SCHED_BATCHED keeps the
+                                gather everywhere; SOP_SCHED_AUTO times both forms per size bucket, so its
+                                summation order (and so its trajectory bits) may follow the timing */
 } sop_schedule;
 
 /* Source of the Gaussian random force (Sec. III.C). */
@@ -170,6 +177,7 @@ typedef struct {
     int32_t cluster_buckets;      /* batched schedule: buckets run in the cluster form (one system over a
                                      thread-block cluster) */
     int32_t cluster_size;         /* CTAs per cluster in the bucket with the most systems (0: not clustered) */
+    int32_t pair_buckets;         /* batched schedule: buckets run in the pair form (each pair evaluated once) */
 } sop_stats;
 
 /* Create a context: validates the arguments, builds the bonds (r0 from the

@@ -33,8 +33,7 @@
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
-#include "sop_internal.h"
-#include "sop_step.cuh"
+#include "batched_common.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -42,24 +41,9 @@ namespace sop {
 
 namespace {
 
-constexpr int kKeys = 257;   // row lengths 0..256
-
-struct SharedHead {
-    int fail;               // first sop_status raised in this CTA
-    int hist[kKeys];        // counting sort of slots by row length
-    double red[32][6];      // FP64 block reductions (up to 1024 threads)
-};
-
-// The arrays follow the head at a 16-byte aligned offset (float4 accesses).
-constexpr size_t kHeadBytes = (sizeof(SharedHead) + 15) / 16 * 16;
-
-__device__ __forceinline__ void cta_fail(SharedHead *h, int code) { atomicCAS(&h->fail, 0, code); }
-
 // Shared-memory layout of one work item, for systems of at most max_n beads. The
 // accessors recompute each array's address from the dynamic shared-memory symbol, so
 // that only a few integers stay live and every access is a 32-bit shared address.
-extern __shared__ __align__(16) unsigned char g_smem[];
-
 __host__ __device__ inline size_t state_bytes(int max_n) {
     size_t s = kHeadBytes;
     s += 3 * sizeof(float4) * (size_t)max_n;       // two layers + compensation
@@ -68,6 +52,7 @@ __host__ __device__ inline size_t state_bytes(int max_n) {
     s += (size_t)max_n;                            // flags
     s = (s + 15) / 16 * 16;
     s += 2 * sizeof(float4) * (size_t)((max_n + 31) / 32);   // block bounding boxes
+    if (max_n <= kSoaMaxBeads) s += 3 * sizeof(float) * (size_t)((max_n + 31) & ~31);   // x, y, z arrays
     return s;
 }
 
@@ -103,6 +88,9 @@ struct Layout {
         const size_t off = (kHeadBytes + 3 * 16 * (size_t)mx + 8 * (size_t)mx + 10 * (size_t)mx + mx + 15) / 16 * 16;
         return reinterpret_cast<float4 *>(g_smem + off);
     }
+    // rebuild scan: x, y, z of the layer being scanned, stride soa_stride()
+    __device__ __forceinline__ int soa_stride() const { return (mx + 31) & ~31; }
+    __device__ __forceinline__ float *soa() const { return reinterpret_cast<float *>(bbox() + 2 * ((mx + 31) / 32)); }
     // by slot: entry k of slot p at row[k * n + p] (bead indices)
     __device__ __forceinline__ uint16_t *row() const {
         if (RG) return grow;
@@ -110,129 +98,9 @@ struct Layout {
     }
 };
 
-// FP64 block sum of 6 values; result valid in thread 0.
-__device__ __forceinline__ void block_sum6(double v[6], SharedHead *h) {
-#pragma unroll
-    for (int k = 0; k < 6; ++k)
-        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    __syncthreads();
-    if (lane == 0)
-        for (int k = 0; k < 6; ++k) h->red[w][k] = v[k];
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        for (int k = 0; k < 6; ++k) {
-            double s = 0.0;
-            for (int q = 0; q < (int)(blockDim.x >> 5); ++q) s += h->red[q][k];
-            v[k] = s;
-        }
-    }
-}
 
-// Bounding boxes of the blocks of 32 consecutive beads of layer src (one warp per block).
-template <class Lay>
-__device__ void block_boxes(const Lay &L, const float4 *src, int n_s) {
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    float4 *bb = L.bbox();
-    for (int blk = w; blk * 32 < n_s; blk += nw) {
-        const int b = blk * 32 + lane;
-        float lx = INFINITY, ly = INFINITY, lz = INFINITY, hx = -INFINITY, hy = -INFINITY, hz = -INFINITY;
-        if (b < n_s) {
-            const float4 p = src[b];
-            lx = hx = p.x; ly = hy = p.y; lz = hz = p.z;
-        }
-        for (int o = 16; o > 0; o >>= 1) {
-            lx = fminf(lx, __shfl_xor_sync(0xffffffffu, lx, o));
-            ly = fminf(ly, __shfl_xor_sync(0xffffffffu, ly, o));
-            lz = fminf(lz, __shfl_xor_sync(0xffffffffu, lz, o));
-            hx = fmaxf(hx, __shfl_xor_sync(0xffffffffu, hx, o));
-            hy = fmaxf(hy, __shfl_xor_sync(0xffffffffu, hy, o));
-            hz = fmaxf(hz, __shfl_xor_sync(0xffffffffu, hz, o));
-        }
-        if (lane == 0) {
-            bb[2 * blk] = make_float4(lx, ly, lz, 0.f);
-            bb[2 * blk + 1] = make_float4(hx, hy, hz, 0.f);
-        }
-    }
-}
 
-// Hand the slots to beads by decreasing row length of the last build (counting sort).
-// Returns the index (0/1) of the new order buffer. Must be called by all threads.
-template <class Lay>
-__device__ int reorder_slots(const Lay &L, int n_s, int cur_order) {
-    const int T = blockDim.x;
-    SharedHead *h = L.h();
-    for (int k = threadIdx.x; k < kKeys; k += T) h->hist[k] = 0;
-    __syncthreads();
-    for (int p = threadIdx.x; p < n_s; p += T) atomicAdd(&h->hist[kKeys - 1 - min((int)L.n_tot()[p], kKeys - 1)], 1);
-    __syncthreads();
-    if (threadIdx.x < 32) {   // exclusive scan of the histogram by one warp
-        const int lane = threadIdx.x;
-        const int per = (kKeys + 31) / 32;
-        int local = 0;
-        for (int k = lane * per; k < min(kKeys, lane * per + per); ++k) local += h->hist[k];
-        int inc = local;
-        for (int o = 1; o < 32; o <<= 1) {
-            const int t = __shfl_up_sync(0xffffffffu, inc, o);
-            if (lane >= o) inc += t;
-        }
-        int run = inc - local;
-        for (int k = lane * per; k < min(kKeys, lane * per + per); ++k) {
-            const int c = h->hist[k];
-            h->hist[k] = run;
-            run += c;
-        }
-    }
-    __syncthreads();
-    const uint16_t *src = L.order(cur_order);
-    uint16_t *dst = L.order(cur_order ^ 1);
-    const int full = n_s - n_s % T;   // slots in complete rounds of T
-    for (int p = threadIdx.x; p < n_s; p += T) {
-        int pos = atomicAdd(&h->hist[kKeys - 1 - min((int)L.n_tot()[p], kKeys - 1)], 1);
-        // boustrophedon: odd rounds run backwards, so a thread owning several slots gets
-        // long and short rows alike and the warps of the CTA finish together
-        if (pos < full && ((pos / T) & 1)) pos = (pos / T) * T + (T - 1 - pos % T);
-        dst[pos] = src[p];
-    }
-    __syncthreads();
-    return cur_order ^ 1;
-}
 
-// One 32-candidate block of the all-pairs scan: bit t of *within is set when
-// candidate base + t is closer than the cutoff, bit t of *near when it lies in
-// the guard band around it (decided later in FP64).
-template <bool kFull>
-__device__ __forceinline__ void scan32(const float4 *src, int base, int lim, float4 pb, float lo, float hi,
-                                       uint32_t *within, uint32_t *near) {
-    uint32_t w = 0u, nr = 0u;
-    if (kFull) {
-        // groups of four candidates form a nibble with constant bit positions
-#pragma unroll 2
-        for (int g = 0; g < 8; ++g) {
-            uint32_t wn = 0u, nn = 0u;
-#pragma unroll
-            for (int t = 0; t < 4; ++t) {
-                const float4 pj = src[base + 4 * g + t];
-                const float dx = pb.x - pj.x, dy = pb.y - pj.y, dz = pb.z - pj.z;
-                const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-                if (r2 < lo) wn |= 1u << t;
-                if (r2 < hi) nn |= 1u << t;
-            }
-            w |= wn << (4 * g);
-            nr |= nn << (4 * g);
-        }
-    } else {
-        for (int t = 0; t < lim; ++t) {
-            const float4 pj = src[base + t];
-            const float dx = pb.x - pj.x, dy = pb.y - pj.y, dz = pb.z - pj.z;
-            const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-            if (r2 < lo) w |= 1u << t;
-            if (r2 < hi) nr |= 1u << t;
-        }
-    }
-    *within = w;
-    *near = nr & ~w;
-}
 
 // Rows from layer src: the bead in slot p gets its native partners and its Verlet
 // partners in column p. Block boxes must be current. In systems of up to 256 beads a
@@ -243,12 +111,15 @@ __device__ __forceinline__ void scan32(const float4 *src, int base, int lim, flo
 // system and some lane needs nearly every block). The rows are the same either way.
 template <int BPT, bool RG>
 __device__ void rebuild_rows(const BatchedArgs &a, const Layout<RG> &L, const uint16_t *order, const float4 *src,
-                             int n_s, int nat_off, int b0) {
+                             int n_s, int nat_off, int b0, int exo) {
     const int T = blockDim.x;
     const float cut2 = a.sa.cut2_f;
     const float lo = cut2 - cut2 * 1e-4f, hi = cut2 + cut2 * 1e-4f;
     const float4 *bb = L.bbox();
+    const float *soa = L.soa();
+    const int S = L.soa_stride();
     uint16_t *row = L.row();
+    const uint32_t *excl = exo >= 0 ? a.excl + exo : nullptr;
     // instances with one bead per thread and shared-memory rows never hold more than 256 beads
     constexpr bool kLarge = RG || BPT > 1;
     const bool by_bead = kLarge && n_s > 256;
@@ -267,36 +138,46 @@ __device__ void rebuild_rows(const BatchedArgs &a, const Layout<RG> &L, const ui
         int next_nat = nn > 0 ? (int)__ldg(natc) : 0x7fffffff;
         int cnt = 0;
         for (int base = 0; base < n_s; base += 32) {
-            // exact cull: every bead of the block is at least as far as its box
-            const float4 blo = bb[base >> 4], bhi = bb[(base >> 4) + 1];
-            const float ex = fmaxf(fmaxf(blo.x - pb.x, pb.x - bhi.x), 0.f);
-            const float ey = fmaxf(fmaxf(blo.y - pb.y, pb.y - bhi.y), 0.f);
-            const float ez = fmaxf(fmaxf(blo.z - pb.z, pb.z - bhi.z), 0.f);
-            uint32_t within = 0u, near = 0u;
-            // in a system of a few blocks nearly every box is in range for some lane of the
-            // warp: the test only costs there, so it is skipped
-            if (!kLarge || n_s <= 256 || fmaf(ez, ez, fmaf(ey, ey, ex * ex)) < hi) {
-                if (base + 32 <= n_s) scan32<true>(src, base, 32, pb, lo, hi, &within, &near);
-                else scan32<false>(src, base, n_s - base, pb, lo, hi, &within, &near);
+            // exact cull: every bead of the block is at least as far as its box. In a system of
+            // a few blocks nearly every box is in range for some lane of the warp: the test only
+            // costs there, so it is skipped
+            bool scan = !kLarge || n_s <= 256;
+            if (!scan) {
+                const float4 blo = bb[base >> 4], bhi = bb[(base >> 4) + 1];
+                const float ex = fmaxf(fmaxf(blo.x - pb.x, pb.x - bhi.x), 0.f);
+                const float ey = fmaxf(fmaxf(blo.y - pb.y, pb.y - bhi.y), 0.f);
+                const float ez = fmaxf(fmaxf(blo.z - pb.z, pb.z - bhi.z), 0.f);
+                scan = fmaf(ez, ez, fmaf(ey, ey, ex * ex)) < hi;
             }
             // exclusions in [base, base + 32): self, bonded neighbours, native partners
             uint32_t ex_mask = 0u;
-            if (b >= base && b < base + 32) ex_mask |= 1u << (b - base);
-            if (bd.x > 0.f && b - 1 >= base && b - 1 < base + 32) ex_mask |= 1u << (b - 1 - base);
-            if (bd.y > 0.f && b + 1 >= base && b + 1 < base + 32) ex_mask |= 1u << (b + 1 - base);
-            while (next_nat < base + 32) {
-                ex_mask |= 1u << (next_nat - base);
-                ++q;
-                next_nat = q < nn ? (int)__ldg(natc + q * n_s) : 0x7fffffff;
+            if (excl) {
+                ex_mask = __ldg(excl + (base >> 5) * n_s + b);
+            } else {
+                if (b >= base && b < base + 32) ex_mask |= 1u << (b - base);
+                if (bd.x > 0.f && b - 1 >= base && b - 1 < base + 32) ex_mask |= 1u << (b - 1 - base);
+                if (bd.y > 0.f && b + 1 >= base && b + 1 < base + 32) ex_mask |= 1u << (b + 1 - base);
+                while (next_nat < base + 32) {
+                    ex_mask |= 1u << (next_nat - base);
+                    ++q;
+                    next_nat = q < nn ? (int)__ldg(natc + q * n_s) : 0x7fffffff;
+                }
             }
-            within &= ~ex_mask;
-            near &= ~ex_mask;
-            while (near) {   // rare: decide within the guard band in FP64
-                const int t = __ffs(near) - 1;
-                near &= near - 1;
-                if (within_cut(pb, src[base + t], cut2, a.sa.cut2_d)) within |= 1u << t;
+            if (!scan) continue;
+            uint32_t within;
+            if (L.mx <= kSoaMaxBeads) {
+                within = block_partners(scan_block(soa, S, base, n_s - base, pb, lo, hi), ex_mask, src, base, pb, cut2,
+                                        a.sa.cut2_d);
+            } else {
+                uint32_t cand = scan_block_f4(src, base, n_s - base, pb, hi) & ~ex_mask;
+                within = 0u;
+                while (cand) {
+                    const int t = __ffs(cand) - 1;
+                    cand &= cand - 1;
+                    if (within_cut(pb, src[base + t], cut2, a.sa.cut2_d)) within |= 1u << t;
+                }
             }
-            while (within) {
+            while (within) {   // ascending
                 const int t = __ffs(within) - 1;
                 within &= within - 1;
                 if (cnt < a.cap) row[(nn + cnt) * n_s + p] = (uint16_t)(base + t);
@@ -312,16 +193,17 @@ __device__ void rebuild_rows(const BatchedArgs &a, const Layout<RG> &L, const ui
 // A full rebuild from layer src: boxes, slot order, rows. Ends with a barrier.
 template <int BPT, bool RG>
 __device__ int rebuild(const BatchedArgs &a, const Layout<RG> &L, const float4 *src, int n_s, int nat_off, int b0,
-                       int ord) {
+                       int ord, int exo) {
     constexpr bool kLarge = RG || BPT > 1;   // as in rebuild_rows
-    block_boxes(L, src, n_s);
-    ord = reorder_slots(L, n_s, ord);   // its barriers also publish the boxes
+    if (kLarge && n_s > 256) block_boxes(L, src, n_s);
+    if (L.mx <= kSoaMaxBeads) soa_fill(src, L.soa(), n_s, L.soa_stride());
+    ord = reorder_slots(L, n_s, ord);   // its barriers also publish the boxes and the x, y, z arrays
     if (kLarge && n_s > 256) {
         const uint16_t *o = L.order(ord);
         for (int p = threadIdx.x; p < n_s; p += blockDim.x) L.slot_of()[o[p]] = (uint16_t)p;
         __syncthreads();
     }
-    rebuild_rows<BPT>(a, L, L.order(ord), src, n_s, nat_off, b0);
+    rebuild_rows<BPT>(a, L, L.order(ord), src, n_s, nat_off, b0, exo);
     __syncthreads();
     return ord;
 }
@@ -352,61 +234,10 @@ __device__ __forceinline__ float3 bead_force(const BatchedArgs &a, const Layout<
         }
     }
     const int nn = L.n_nat()[p], tot = L.n_tot()[p];
-    const float *natr = a.nat_ell_r0sq + nat_off + b;
-    const uint16_t *rowp = L.row() + p;
-    const float A = fp.eps12_h, B = fp.eps6_l;
-#pragma unroll 2
-    for (int k = 0; k < tot; ++k) {
-        const bool nat = k < nn;
-        const int j = rowp[k * n_s];
-        const float s0 = nat ? __ldg(natr + k * n_s) : fp.sigma2;
-        const float4 pj = P[j];
-        const float dx = pb.x - pj.x, dy = pb.y - pj.y, dz = pb.z - pj.z;
-        const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-        const float inv = __fdividef(1.0f, r2);
-        const float s = s0 * inv;
-        const float s3 = s * s * s;
-        // native: (12 eps_h / r^2)(s^6 - s^3); repulsive: (6 eps_l / r^2) s^3 with s = sigma^2/r^2
-        const float c = inv * s3 * (nat ? fmaf(A, s3, -A) : B);
-        fx = fmaf(c, dx, fx); fy = fmaf(c, dy, fy); fz = fmaf(c, dz, fz);
-    }
-    return make_float3(fx, fy, fz);
+    const float3 fr = row_force(P, pb, L.row() + p, a.nat_ell_r0sq + nat_off + b, nn, tot, n_s, n_s, fp);
+    return make_float3(fx + fr.x, fy + fr.y, fz + fr.z);
 }
 
-// Cantilever / indenter force on replica-local bead i.
-__device__ __forceinline__ float3 ext_force(const StepArgs &sa, int r, int i, uint8_t flags, float4 pi, int64_t step,
-                                            bool *overlap) {
-    float3 f = make_float3(0.f, 0.f, 0.f);
-    const DevExternal &e = sa.ext;
-    if (flags & kFlagPulled) {
-        const int q = e.pull_of_sys[sa.topo.sys[i]];
-        if (q >= 0 && e.pull_bead[q] == i) {
-            const double tt = e.pull_v[q] * ((double)step - e.pull_n0[q]);
-            const double *tip0 = e.pull_tip0 + ((size_t)r * e.n_pull + q) * 3;
-            const float ks = (float)e.pull_ks[q];
-            f.x = ks * (float)(tip0[0] + tt * e.pull_dir[3 * q] - (double)pi.x);
-            f.y = ks * (float)(tip0[1] + tt * e.pull_dir[3 * q + 1] - (double)pi.y);
-            f.z = ks * (float)(tip0[2] + tt * e.pull_dir[3 * q + 2] - (double)pi.z);
-        }
-    }
-    if (e.has_indenter) {
-        const double tt = e.ind_v * ((double)step - e.ind_n0);
-        const float ex = pi.x - (float)(e.ind_c0[0] + tt * e.ind_dir[0]);
-        const float ey = pi.y - (float)(e.ind_c0[1] + tt * e.ind_dir[1]);
-        const float ez = pi.z - (float)(e.ind_c0[2] + tt * e.ind_dir[2]);
-        const float rr = sqrtf(fmaf(ez, ez, fmaf(ey, ey, ex * ex)));
-        const float rho = rr - (float)e.ind_radius;
-        if (!(rho > 0.f)) {
-            *overlap = true;
-        } else {
-            const float q = sqrtf(sa.fp.sigma2) / rho;
-            const float q2 = q * q;
-            const float c = sa.fp.eps6_l * (q2 * q2 * q2) / (rho * rr);
-            f.x = fmaf(c, ex, f.x); f.y = fmaf(c, ey, f.y); f.z = fmaf(c, ez, f.z);
-        }
-    }
-    return f;
-}
 
 // FP64 observables of the CTA's system at layer P (same definitions as the streamed kernels).
 template <int BPT, bool RG>
@@ -414,37 +245,17 @@ __device__ __noinline__ void observe(const BatchedArgs &a, const Layout<RG> &L, 
                                      const float4 *P, int n_s, int b0, int r, int s, int g, int64_t step,
                                      int64_t event) {
     const StepArgs &sa = a.sa;
-    const DevTopo &t = sa.topo;
-    const DevExternal &e = sa.ext;
     const int T = blockDim.x;
     const uint16_t *row = L.row();
     double v[6] = {0, 0, 0, 0, 0, 0};   // E, f_pull, ext, formed, f_wall, r_ee
-    const double R02 = sa.R0 * sa.R0, sig2 = sa.sigma * sa.sigma;
+    const double sig2 = sa.sigma * sa.sigma;
     for (int k = 0; k < BPT; ++k) {
         const int p = threadIdx.x + k * T;
         if (p >= n_s) continue;
         const int b = order[p];
-        const int i = b0 + b;
         const float4 pb = P[b];
         const double xi = pb.x, yi = pb.y, zi = pb.z;
-        if (L.bond()[b].y > 0.f) {
-            const float4 pj = P[b + 1];
-            const double rr = __dsqrt_rn(dist2_d(xi, yi, zi, pj.x, pj.y, pj.z));
-            const double dr = rr - t.bond_r0d[i];
-            const double arg = 1.0 - dr * dr / R02;
-            if (arg > 0.0) v[0] += -0.5 * sa.k_fene * R02 * log(arg);
-        }
-        for (int q = t.nat_row[i]; q < t.nat_row[i + 1]; ++q) {
-            const int j = t.nat_col[q];
-            if (j < i) continue;
-            const float4 pj = P[j - b0];
-            const double d2 = dist2_d(xi, yi, zi, pj.x, pj.y, pj.z);
-            const double r0 = t.nat_r0[q];
-            const double u = r0 * r0 / d2;
-            const double u3 = u * u * u;
-            v[0] += sa.eps_h * (u3 * u3 - 2.0 * u3);
-            if (__dsqrt_rn(d2) < r0 + 2.0) v[3] += 1.0;
-        }
+        obs_bonded(sa, P, b, b0, L.bond()[b].y > 0.f, v);
         for (int q = L.n_nat()[p]; q < L.n_tot()[p]; ++q) {
             const int j = row[q * n_s + p];
             if (j < b) continue;
@@ -452,75 +263,13 @@ __device__ __noinline__ void observe(const BatchedArgs &a, const Layout<RG> &L, 
             const double c = sig2 / dist2_d(xi, yi, zi, pj.x, pj.y, pj.z);
             v[0] += sa.eps_l * c * c * c;
         }
-        const uint8_t fl = L.flags()[b];
-        if (fl & kFlagPulled) {
-            const int qq = e.pull_of_sys[s];
-            if (qq >= 0 && e.pull_bead[qq] == i) {
-                const double tt = e.pull_v[qq] * ((double)step - e.pull_n0[qq]);
-                const double *tip0 = e.pull_tip0 + ((size_t)r * e.n_pull + qq) * 3;
-                const double *dir = e.pull_dir + 3 * qq;
-                const double x[3] = {xi, yi, zi};
-                double f = 0.0;
-                for (int c = 0; c < 3; ++c) f += e.pull_ks[qq] * (tip0[c] + tt * dir[c] - x[c]) * dir[c];
-                v[1] += f;
-                const float4 pa = P[e.pull_anchor[qq] - b0];
-                v[2] += __dsqrt_rn(dist2_d(xi, yi, zi, pa.x, pa.y, pa.z));
-            }
-        }
-        if (e.has_indenter) {
-            const double tt = e.ind_v * ((double)step - e.ind_n0);
-            const double c[3] = {e.ind_c0[0] + tt * e.ind_dir[0], e.ind_c0[1] + tt * e.ind_dir[1],
-                                 e.ind_c0[2] + tt * e.ind_dir[2]};
-            const double ex = xi - c[0], ey = yi - c[1], ez = zi - c[2];
-            const double rr = __dsqrt_rn((ex * ex + ey * ey) + ez * ez);
-            const double rho = rr - e.ind_radius;
-            if (rho > 0.0) {
-                const double qq = sa.sigma / rho;
-                const double q2 = qq * qq;
-                const double coef = 6.0 * sa.eps_l * (q2 * q2 * q2) / rho / rr;
-                v[4] += coef * ((ex * e.ind_dir[0] + ey * e.ind_dir[1]) + ez * e.ind_dir[2]);
-            }
-        }
-        if (fl & kFlagFirstOfSystem) {
-            const float4 pl_ = P[t.sys_ree_last[s] - b0];
-            v[5] += __dsqrt_rn(dist2_d(xi, yi, zi, pl_.x, pl_.y, pl_.z));
-        }
+        obs_external(sa, P, b, b0, r, s, step, L.flags()[b], v);
     }
     block_sum6(v, L.h());
-    if (threadIdx.x == 0) {
-        sop_record rec;
-        rec.step = (double)step;
-        rec.replica = (double)r;
-        rec.system = (double)s;
-        rec.energy = v[0];
-        const bool pulled = e.pull_of_sys[s] >= 0;
-        rec.f_ext = pulled ? v[1] : (e.has_indenter ? v[4] : 0.0);
-        rec.extension = pulled ? v[2] : (e.has_indenter ? e.ind_v * ((double)step - e.ind_n0) : 0.0);
-        const int np = t.sys_nat_pairs[s];
-        rec.q = np > 0 ? v[3] / (double)np : 0.0;
-        rec.r_ee = v[5];
-        a.obs.ring[(event * a.n_seg + g) % a.obs.cap] = rec;
-    }
+    if (threadIdx.x == 0) write_record(a, v, r, s, g, step, event);
     __syncthreads();
 }
 
-// Records of the cadence events from `step` to the end of the chunk that this CTA will not
-// take (frozen replica): step, replica and system are set, the values are NaN.
-__device__ void missing_records(const BatchedArgs &a, int r, int s, int g, int64_t step0, int64_t step,
-                                int64_t event) {
-    if (a.obs_every <= 0) return;
-    const int64_t end = step0 + a.n_steps;
-    for (int64_t t = (step / a.obs_every + 1) * a.obs_every; t <= end; t += a.obs_every) {
-        sop_record rec;
-        const double nan = __longlong_as_double(0x7ff8000000000000LL);
-        rec.step = (double)t;
-        rec.replica = (double)r;
-        rec.system = (double)s;
-        rec.energy = rec.f_ext = rec.extension = rec.q = rec.r_ee = nan;
-        a.obs.ring[(event * a.n_seg + g) % a.obs.cap] = rec;
-        ++event;
-    }
-}
 
 // MAXT: largest CTA the instance is compiled for; MINB: CTAs of MAXT threads that must
 // fit an SM, i.e. the register cap 65536 / (MAXT * MINB). RG: rows in global memory.
@@ -537,6 +286,7 @@ __global__ void __launch_bounds__(MAXT, MINB) k_batched(BatchedArgs a) {
     const int gbase = r * t.n + b0;   // replicas x beads < 2^28
     const int g = r * t.n_sys + s;
     const int nat_off = a.nat_ell_off[s];
+    const int exo = a.excl_off[s];
     const int T = blockDim.x;
     const int64_t step0 = *a.d_step;
     const bool forces_only = (a.n_steps == 0 && a.force_out != nullptr);
@@ -572,10 +322,12 @@ __global__ void __launch_bounds__(MAXT, MINB) k_batched(BatchedArgs a) {
         const float4 *P = L.lay(cur);
         float4 *Q = L.lay(cur ^ 1);
         if (it == 0 && k_phase != 0 && !forces_only) {
-            ord = rebuild<BPT>(a, L, Q, n_s, nat_off, b0, ord);   // Q holds the snapshot here
+            ord = rebuild<BPT>(a, L, Q, n_s, nat_off, b0, ord, exo);   // Q holds the snapshot here
         } else if ((k_phase == 0 && !built_now) || forces_only) {
-            ord = rebuild<BPT>(a, L, P, n_s, nat_off, b0, ord);
-            if (!forces_only)
+            ord = rebuild<BPT>(a, L, P, n_s, nat_off, b0, ord, exo);
+            // the snapshot is kept only from the launch's last rebuild: a later launch that
+            // starts between rebuilds builds its first list from it
+            if (!forces_only && it + a.K >= a.n_steps)
                 for (int b = threadIdx.x; b < n_s; b += T) a.snap[gbase + b] = P[b];
         }
         built_now = false;
@@ -631,9 +383,10 @@ __global__ void __launch_bounds__(MAXT, MINB) k_batched(BatchedArgs a) {
         if (a.obs_every > 0 && o_phase == 0) {
             const float4 *Pn = L.lay(cur);
             if (k_phase == 0) {
-                ord = rebuild<BPT>(a, L, Pn, n_s, nat_off, b0, ord);
+                ord = rebuild<BPT>(a, L, Pn, n_s, nat_off, b0, ord, exo);
                 built_now = true;
-                for (int b = threadIdx.x; b < n_s; b += T) a.snap[gbase + b] = Pn[b];
+                if (it + 1 + a.K >= a.n_steps)
+                    for (int b = threadIdx.x; b < n_s; b += T) a.snap[gbase + b] = Pn[b];
             }
             const int64_t ev = (a.d_events ? *a.d_events : 0) + n_events;
             observe<BPT>(a, L, L.order(ord), Pn, n_s, b0, r, s, g, step + 1, ev);
@@ -642,7 +395,7 @@ __global__ void __launch_bounds__(MAXT, MINB) k_batched(BatchedArgs a) {
     }
     if (forces_only) return;
     if (threadIdx.x == 0 && L.h()->fail != 0)
-        missing_records(a, r, s, g, step0, step0 + it, (a.d_events ? *a.d_events : 0) + n_events);
+        missing_records(a, r, s, g, step0, step0 + it - 1, (a.d_events ? *a.d_events : 0) + n_events);
     const float4 *P = L.lay(cur);
     for (int b = threadIdx.x; b < n_s; b += T) {
         a.pos[gbase + b] = P[b];
@@ -725,7 +478,7 @@ __device__ void cluster_rows(const BatchedArgs &a, const CLayout &L, const uint1
                              int lo, int n_s, int nat_off, int b0) {
     const int T = blockDim.x, m = L.m;
     const float cut2 = a.sa.cut2_f;
-    const float lo2 = cut2 - cut2 * 1e-4f, hi2 = cut2 + cut2 * 1e-4f;
+    const float hi2 = cut2 + cut2 * 1e-4f;
     const float4 *src = L.pos(layer);
     const float4 *bb = L.bbox();
     uint16_t *row = L.row();
@@ -749,11 +502,8 @@ __device__ void cluster_rows(const BatchedArgs &a, const CLayout &L, const uint1
             const float ex = fmaxf(fmaxf(blo.x - pb.x, pb.x - bhi.x), 0.f);
             const float ey = fmaxf(fmaxf(blo.y - pb.y, pb.y - bhi.y), 0.f);
             const float ez = fmaxf(fmaxf(blo.z - pb.z, pb.z - bhi.z), 0.f);
-            uint32_t within = 0u, near = 0u;
-            if (fmaf(ez, ez, fmaf(ey, ey, ex * ex)) < hi2) {
-                if (base + 32 <= n_s) scan32<true>(src, base, 32, pb, lo2, hi2, &within, &near);
-                else scan32<false>(src, base, n_s - base, pb, lo2, hi2, &within, &near);
-            }
+            uint32_t cand = 0u;
+            if (fmaf(ez, ez, fmaf(ey, ey, ex * ex)) < hi2) cand = scan_block_f4(src, base, n_s - base, pb, hi2);
             uint32_t ex_mask = 0u;
             if (b >= base && b < base + 32) ex_mask |= 1u << (b - base);
             if (bd.x > 0.f && b - 1 >= base && b - 1 < base + 32) ex_mask |= 1u << (b - 1 - base);
@@ -763,16 +513,11 @@ __device__ void cluster_rows(const BatchedArgs &a, const CLayout &L, const uint1
                 ++q;
                 next_nat = q < nn ? (int)__ldg(natc + q * n_s) : 0x7fffffff;
             }
-            within &= ~ex_mask;
-            near &= ~ex_mask;
-            while (near) {
-                const int t = __ffs(near) - 1;
-                near &= near - 1;
-                if (within_cut(pb, src[base + t], cut2, a.sa.cut2_d)) within |= 1u << t;
-            }
-            while (within) {
-                const int t = __ffs(within) - 1;
-                within &= within - 1;
+            cand &= ~ex_mask;
+            while (cand) {   // ascending: the exact decision, then the row entry
+                const int t = __ffs(cand) - 1;
+                cand &= cand - 1;
+                if (!within_cut(pb, src[base + t], cut2, a.sa.cut2_d)) continue;
                 if (cnt < a.cap) row[(nn + cnt) * m + p] = (uint16_t)(base + t);
                 ++cnt;
             }
@@ -823,24 +568,8 @@ __device__ __forceinline__ float3 cluster_force(const BatchedArgs &a, const CLay
         }
     }
     const int nn = L.n_nat()[p], tot = L.n_tot()[p];
-    const float *natr = a.nat_ell_r0sq + nat_off + b;
-    const uint16_t *rowp = L.row() + p;
-    const float A = fp.eps12_h, B = fp.eps6_l;
-#pragma unroll 2
-    for (int k = 0; k < tot; ++k) {
-        const bool nat = k < nn;
-        const int j = rowp[k * m];
-        const float s0 = nat ? __ldg(natr + k * n_s) : fp.sigma2;
-        const float4 pj = P[j];
-        const float dx = pb.x - pj.x, dy = pb.y - pj.y, dz = pb.z - pj.z;
-        const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-        const float inv = __fdividef(1.0f, r2);
-        const float s = s0 * inv;
-        const float s3 = s * s * s;
-        const float c = inv * s3 * (nat ? fmaf(A, s3, -A) : B);
-        fx = fmaf(c, dx, fx); fy = fmaf(c, dy, fy); fz = fmaf(c, dz, fz);
-    }
-    return make_float3(fx, fy, fz);
+    const float3 fr = row_force(P, pb, L.row() + p, a.nat_ell_r0sq + nat_off + b, nn, tot, m, n_s, fp);
+    return make_float3(fx + fr.x, fy + fr.y, fz + fr.z);
 }
 
 // FP64 observables of the cluster's system at layer P: every CTA sums its own beads, rank
@@ -850,38 +579,18 @@ __device__ __noinline__ void cluster_observe(const BatchedArgs &a, const CLayout
                                              const uint16_t *order, const float4 *P, int n_loc, int lo, int b0,
                                              int r, int s, int g, int64_t step, int64_t event, int rank, int C) {
     const StepArgs &sa = a.sa;
-    const DevTopo &t = sa.topo;
-    const DevExternal &e = sa.ext;
     const int T = blockDim.x, m = L.m;
     const uint16_t *row = L.row();
     double v[6] = {0, 0, 0, 0, 0, 0};   // E, f_pull, ext, formed, f_wall, r_ee
-    const double R02 = sa.R0 * sa.R0, sig2 = sa.sigma * sa.sigma;
+    const double sig2 = sa.sigma * sa.sigma;
     for (int k = 0; k < BPT; ++k) {
         const int p = threadIdx.x + k * T;
         if (p >= n_loc) continue;
         const int l = order[p];
         const int b = lo + l;
-        const int i = b0 + b;
         const float4 pb = P[b];
         const double xi = pb.x, yi = pb.y, zi = pb.z;
-        if (L.bond()[l].y > 0.f) {
-            const float4 pj = P[b + 1];
-            const double rr = __dsqrt_rn(dist2_d(xi, yi, zi, pj.x, pj.y, pj.z));
-            const double dr = rr - t.bond_r0d[i];
-            const double arg = 1.0 - dr * dr / R02;
-            if (arg > 0.0) v[0] += -0.5 * sa.k_fene * R02 * log(arg);
-        }
-        for (int q = t.nat_row[i]; q < t.nat_row[i + 1]; ++q) {
-            const int j = t.nat_col[q];
-            if (j < i) continue;
-            const float4 pj = P[j - b0];
-            const double d2 = dist2_d(xi, yi, zi, pj.x, pj.y, pj.z);
-            const double r0 = t.nat_r0[q];
-            const double u = r0 * r0 / d2;
-            const double u3 = u * u * u;
-            v[0] += sa.eps_h * (u3 * u3 - 2.0 * u3);
-            if (__dsqrt_rn(d2) < r0 + 2.0) v[3] += 1.0;
-        }
+        obs_bonded(sa, P, b, b0, L.bond()[l].y > 0.f, v);
         for (int q = L.n_nat()[p]; q < L.n_tot()[p]; ++q) {
             const int j = row[q * m + p];
             if (j < b) continue;
@@ -889,39 +598,7 @@ __device__ __noinline__ void cluster_observe(const BatchedArgs &a, const CLayout
             const double c = sig2 / dist2_d(xi, yi, zi, pj.x, pj.y, pj.z);
             v[0] += sa.eps_l * c * c * c;
         }
-        const uint8_t fl = L.flags()[l];
-        if (fl & kFlagPulled) {
-            const int qq = e.pull_of_sys[s];
-            if (qq >= 0 && e.pull_bead[qq] == i) {
-                const double tt = e.pull_v[qq] * ((double)step - e.pull_n0[qq]);
-                const double *tip0 = e.pull_tip0 + ((size_t)r * e.n_pull + qq) * 3;
-                const double *dir = e.pull_dir + 3 * qq;
-                const double x[3] = {xi, yi, zi};
-                double f = 0.0;
-                for (int c = 0; c < 3; ++c) f += e.pull_ks[qq] * (tip0[c] + tt * dir[c] - x[c]) * dir[c];
-                v[1] += f;
-                const float4 pa = P[e.pull_anchor[qq] - b0];
-                v[2] += __dsqrt_rn(dist2_d(xi, yi, zi, pa.x, pa.y, pa.z));
-            }
-        }
-        if (e.has_indenter) {
-            const double tt = e.ind_v * ((double)step - e.ind_n0);
-            const double c[3] = {e.ind_c0[0] + tt * e.ind_dir[0], e.ind_c0[1] + tt * e.ind_dir[1],
-                                 e.ind_c0[2] + tt * e.ind_dir[2]};
-            const double ex = xi - c[0], ey = yi - c[1], ez = zi - c[2];
-            const double rr = __dsqrt_rn((ex * ex + ey * ey) + ez * ez);
-            const double rho = rr - e.ind_radius;
-            if (rho > 0.0) {
-                const double qq = sa.sigma / rho;
-                const double q2 = qq * qq;
-                const double coef = 6.0 * sa.eps_l * (q2 * q2 * q2) / rho / rr;
-                v[4] += coef * ((ex * e.ind_dir[0] + ey * e.ind_dir[1]) + ez * e.ind_dir[2]);
-            }
-        }
-        if (fl & kFlagFirstOfSystem) {
-            const float4 pl_ = P[t.sys_ree_last[s] - b0];
-            v[5] += __dsqrt_rn(dist2_d(xi, yi, zi, pl_.x, pl_.y, pl_.z));
-        }
+        obs_external(sa, P, b, b0, r, s, step, L.flags()[l], v);
     }
     block_sum6(v, L.h());
     if (threadIdx.x == 0)
@@ -931,18 +608,7 @@ __device__ __noinline__ void cluster_observe(const BatchedArgs &a, const CLayout
         double w[6] = {0, 0, 0, 0, 0, 0};
         for (int q = 0; q < C; ++q)
             for (int k = 0; k < 6; ++k) w[k] += X->peer[q]->part[k];
-        sop_record rec;
-        rec.step = (double)step;
-        rec.replica = (double)r;
-        rec.system = (double)s;
-        rec.energy = w[0];
-        const bool pulled = e.pull_of_sys[s] >= 0;
-        rec.f_ext = pulled ? w[1] : (e.has_indenter ? w[4] : 0.0);
-        rec.extension = pulled ? w[2] : (e.has_indenter ? e.ind_v * ((double)step - e.ind_n0) : 0.0);
-        const int np = t.sys_nat_pairs[s];
-        rec.q = np > 0 ? w[3] / (double)np : 0.0;
-        rec.r_ee = w[5];
-        a.obs.ring[(event * a.n_seg + g) % a.obs.cap] = rec;
+        write_record(a, w, r, s, g, step, event);
     }
     __syncthreads();
 }
@@ -1012,7 +678,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_cluster(BatchedArgs a, int sh) {
             cl.sync();   // layer 1 is read by every CTA before the step writes it
         } else if ((k_phase == 0 && !built_now) || forces_only) {
             ord = cluster_rebuild<BPT>(a, L, cur, n_loc, lo, n_s, nat_off, b0, ord);
-            if (!forces_only)
+            if (!forces_only && it + a.K >= a.n_steps)
                 for (int l = threadIdx.x; l < n_loc; l += T) a.snap[gbase + lo + l] = L.pos(cur)[lo + l];
         }
         built_now = false;
@@ -1077,7 +743,8 @@ __global__ void __launch_bounds__(MAXT, 1) k_cluster(BatchedArgs a, int sh) {
             if (k_phase == 0) {
                 ord = cluster_rebuild<BPT>(a, L, cur, n_loc, lo, n_s, nat_off, b0, ord);
                 built_now = true;
-                for (int l = threadIdx.x; l < n_loc; l += T) a.snap[gbase + lo + l] = L.pos(cur)[lo + l];
+                if (it + 1 + a.K >= a.n_steps)
+                    for (int l = threadIdx.x; l < n_loc; l += T) a.snap[gbase + lo + l] = L.pos(cur)[lo + l];
             }
             const int64_t ev = (a.d_events ? *a.d_events : 0) + n_events;
             cluster_observe<BPT>(a, L, X, L.order(ord), L.pos(cur), n_loc, lo, b0, r, s, g, step + 1, ev, rank, C);
@@ -1088,7 +755,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_cluster(BatchedArgs a, int sh) {
         bool failed = false;
         for (int q = 0; q < C; ++q) failed |= X->peer[q]->fail_step != kNoFail;
         if (failed && rank == 0 && threadIdx.x == 0)
-            missing_records(a, r, s, g, step0, step0 + it, (a.d_events ? *a.d_events : 0) + n_events);
+            missing_records(a, r, s, g, step0, step0 + it - 1, (a.d_events ? *a.d_events : 0) + n_events);
         for (int l = threadIdx.x; l < n_loc; l += T) {
             a.pos[gbase + lo + l] = L.pos(cur)[lo + l];
             a.comp[gbase + lo + l] = L.comp()[l];
@@ -1211,6 +878,7 @@ int cluster_capacity(const BatchedConfig &cfg) {
 cudaError_t launch_batched(const BatchedArgs &a, const BatchedConfig &cfg, cudaStream_t s, int64_t *launches) {
     if (a.n_items <= 0) return cudaSuccess;
     if (launches) *launches += 1;
+    if (cfg.pair_form) return launch_bpair(a, cfg, s);
     if (cfg.cluster > 0)
         return cfg.beads_per_thread == 1 ? launch_cl<1, 512>(a, cfg, s) : launch_cl<2, 512>(a, cfg, s);
     if (cfg.rows_global) {
@@ -1246,6 +914,7 @@ int resident_t(const BatchedConfig &cfg) {
 }  // namespace
 
 int batched_resident_ctas(const BatchedConfig &cfg) {
+    if (cfg.pair_form) return bpair_resident_ctas(cfg);
     if (cfg.cluster > 0) return cluster_capacity(cfg) * cfg.cluster;
     if (cfg.rows_global) {
         switch (cfg.beads_per_thread) {

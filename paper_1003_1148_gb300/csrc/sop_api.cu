@@ -66,6 +66,14 @@ struct sop_ctx {
     int32_t *d_nat_ell_off = nullptr, *d_nat_ell_cnt = nullptr;
     uint16_t *d_nat_ell_col = nullptr;
     float *d_nat_ell_r0sq = nullptr;
+    // pair form: native pairs split between the rows of their two beads (own / reverse tables)
+    int32_t *d_nat_own_off = nullptr, *d_nat_own_cnt = nullptr, *d_nat_rev_off = nullptr, *d_nat_rev_cnt = nullptr;
+    uint16_t *d_nat_own_col = nullptr, *d_nat_rev_col = nullptr, *d_nat_rev_k = nullptr;
+    float *d_nat_own_r0sq = nullptr;
+    std::vector<int32_t> h_nat_own_cnt, h_nat_rev_cnt;   // per bead
+    // static exclusion masks of the batched rebuild scan (systems of at most 256 beads)
+    int32_t *d_excl_off = nullptr;
+    uint32_t *d_excl = nullptr;
     // state
     float4 *d_pos[2] = {nullptr, nullptr};
     float4 *d_comp = nullptr, *d_snap = nullptr, *d_force = nullptr;
@@ -108,6 +116,7 @@ struct sop_ctx {
         int max_n = 0;          // largest system of the bucket
         int cap = 0;            // Verlet capacity per row
         int row_width = 0;      // natives + cap
+        int pair_pool = 0;      // pair form: shared-memory pool bytes per item (0: the form does not fit)
         int32_t item_off = 0;   // first item in the item arrays
         int32_t n_items = 0;
         BatchedConfig cfg;
@@ -122,6 +131,9 @@ struct sop_ctx {
         cudaEvent_t done = nullptr;
     };
     int schedule = SOP_SCHED_STREAMED;
+    // batched forms the tuner may choose: 0 both (timed), 1 the particle-based gather only,
+    // 2 the pair form wherever it fits (the gather elsewhere)
+    int batched_form = 0;
     std::vector<Bucket> buckets;
     cudaEvent_t fork_ev = nullptr;
     int batched_cap = 64;   // largest Verlet capacity over the buckets
@@ -274,6 +286,17 @@ BatchedArgs batched_args(sop_ctx *c, const sop_ctx::Bucket &bk) {
     a.nat_ell_cnt = c->d_nat_ell_cnt;
     a.nat_ell_col = c->d_nat_ell_col;
     a.nat_ell_r0sq = c->d_nat_ell_r0sq;
+    a.nat_own_off = c->d_nat_own_off;
+    a.nat_own_cnt = c->d_nat_own_cnt;
+    a.nat_own_col = c->d_nat_own_col;
+    a.nat_own_r0sq = c->d_nat_own_r0sq;
+    a.nat_rev_off = c->d_nat_rev_off;
+    a.nat_rev_cnt = c->d_nat_rev_cnt;
+    a.nat_rev_col = c->d_nat_rev_col;
+    a.nat_rev_k = c->d_nat_rev_k;
+    a.pair_pool = bk.pair_pool;
+    a.excl_off = c->d_excl_off;
+    a.excl = c->d_excl;
     a.pos = c->d_pos[0];
     a.comp = c->d_comp;
     a.snap = c->d_snap;
@@ -596,7 +619,7 @@ sop_status validate_params(const sop_params *p) {
     if (p->n_replicas < 1) return fail(nullptr, SOP_ERR_INVALID_ARG, "params: n_replicas >= 1");
     if (p->obs_every < 0 || p->obs_capacity < 0 || p->pairs_per_bead < 0)
         return fail(nullptr, SOP_ERR_INVALID_ARG, "params: obs_every, obs_capacity, pairs_per_bead >= 0");
-    if (p->schedule < SOP_SCHED_AUTO || p->schedule > SOP_SCHED_PAIRS)
+    if (p->schedule < SOP_SCHED_AUTO || p->schedule > SOP_SCHED_BATCHED_PAIRS)
         return fail(nullptr, SOP_ERR_INVALID_ARG, "params: unknown schedule");
     if (p->rng != SOP_RNG_PHILOX && p->rng != SOP_RNG_HYBRID_TAUS)
         return fail(nullptr, SOP_ERR_INVALID_ARG, "params: unknown rng");
@@ -722,6 +745,149 @@ sop_status read_status(sop_ctx *c, bool aborted) {
     return SOP_OK;
 }
 
+// Balanced orientation of the native pairs for the pair form: each pair goes to the row of
+// one of its two beads, and every bead owns half of its native pairs (rounded either way).
+// All pairs are walked as closed trails after the odd-degree beads have been joined in pairs
+// by extra edges (so that every degree is even and a trail can only end where it began);
+// each pair belongs to the bead the trail leaves it from. A closed trail enters and leaves a
+// bead equally often, so a bead's own pairs differ from half its degree by at most the one
+// extra edge. Returns, per CSR entry q of (row i, col j), whether i owns the pair.
+std::vector<uint8_t> orient_natives(int n, const std::vector<int32_t> &row, const std::vector<int32_t> &col) {
+    std::vector<int32_t> eu, ev;   // edges: real pairs (i < j) first, then the extra ones
+    std::vector<int32_t> q_of;     // CSR entry (i -> j) of each real edge
+    for (int i = 0; i < n; ++i)
+        for (int q = row[i]; q < row[i + 1]; ++q)
+            if (col[q] > i) { eu.push_back(i); ev.push_back(col[q]); q_of.push_back(q); }
+    const int n_real = (int)eu.size();
+    int pending = -1;
+    for (int i = 0; i < n; ++i)
+        if ((row[i + 1] - row[i]) & 1) {
+            if (pending < 0) pending = i;
+            else { eu.push_back(pending); ev.push_back(i); pending = -1; }
+        }
+    const int m = (int)eu.size();
+    std::vector<int32_t> adj_off(n + 1, 0), adj;
+    for (int e = 0; e < m; ++e) { ++adj_off[eu[e] + 1]; ++adj_off[ev[e] + 1]; }
+    for (int i = 0; i < n; ++i) adj_off[i + 1] += adj_off[i];
+    adj.resize(adj_off[n]);
+    std::vector<int32_t> fill(adj_off.begin(), adj_off.end() - 1);
+    for (int e = 0; e < m; ++e) { adj[fill[eu[e]]++] = e; adj[fill[ev[e]]++] = e; }
+    std::vector<uint8_t> used(m, 0), tail_is_u(m, 0);
+    std::vector<int32_t> next(adj_off.begin(), adj_off.end() - 1);
+    for (int v0 = 0; v0 < n; ++v0) {
+        for (;;) {
+            int v = v0;
+            bool moved = false;
+            for (;;) {
+                while (next[v] < adj_off[v + 1] && used[adj[next[v]]]) ++next[v];
+                if (next[v] == adj_off[v + 1]) break;
+                const int e = adj[next[v]];
+                used[e] = 1;
+                tail_is_u[e] = (eu[e] == v) ? 1 : 0;
+                v = (eu[e] == v) ? ev[e] : eu[e];
+                moved = true;
+            }
+            if (!moved) break;
+        }
+    }
+    std::vector<uint8_t> owner_is_row(col.size(), 0);
+    for (int e = 0; e < n_real; ++e) {
+        const int q = q_of[e];   // entry (eu -> ev)
+        owner_is_row[q] = tail_is_u[e];
+        // the mirrored entry (ev -> eu)
+        const int j = ev[e];
+        for (int r = row[j]; r < row[j + 1]; ++r)
+            if (col[r] == eu[e]) { owner_is_row[r] = tail_is_u[e] ? 0 : 1; break; }
+    }
+    return owner_is_row;
+}
+
+// The pair form's native tables: per system, column-major ELL by bead of the own pairs
+// (partner, r0^2) and of the reverse pairs (partner, index of the bead among the partner's
+// own pairs), partners ascending.
+sop_status build_pair_tables(sop_ctx *c, const std::vector<float> &h_r0sq) {
+    const std::vector<uint8_t> own = orient_natives(c->n, c->h_nat_row, c->h_nat_col);
+    std::vector<int32_t> own_cnt(c->n, 0), rev_cnt(c->n, 0), own_off(c->n_sys), rev_off(c->n_sys);
+    for (int i = 0; i < c->n; ++i)
+        for (int q = c->h_nat_row[i]; q < c->h_nat_row[i + 1]; ++q) (own[q] ? own_cnt[i] : rev_cnt[i])++;
+    size_t to = 0, tr = 0;
+    for (int s = 0; s < c->n_sys; ++s) {
+        const int lo = c->sys_lo[s], hi = c->sys_lo[s + 1], ns = hi - lo;
+        int wo = 0, wr = 0;
+        for (int i = lo; i < hi; ++i) { wo = std::max(wo, own_cnt[i]); wr = std::max(wr, rev_cnt[i]); }
+        own_off[s] = (int32_t)to;
+        rev_off[s] = (int32_t)tr;
+        to += (size_t)wo * ns;
+        tr += (size_t)wr * ns;
+    }
+    if (to > (size_t)INT32_MAX || tr > (size_t)INT32_MAX) return fail(c, SOP_ERR_UNSUPPORTED, "pair-form native tables too large");
+    std::vector<uint16_t> ocol(std::max<size_t>(1, to), 0), rcol(std::max<size_t>(1, tr), 0), rk(std::max<size_t>(1, tr), 0);
+    std::vector<float> or0(std::max<size_t>(1, to), 0.f);
+    for (int s = 0; s < c->n_sys; ++s) {
+        const int lo = c->sys_lo[s], hi = c->sys_lo[s + 1], ns = hi - lo;
+        for (int i = lo; i < hi; ++i) {
+            int ko = 0, kr = 0;
+            for (int q = c->h_nat_row[i]; q < c->h_nat_row[i + 1]; ++q) {
+                const int j = c->h_nat_col[q];
+                if (own[q]) {
+                    const size_t e = (size_t)own_off[s] + (size_t)ko++ * ns + (i - lo);
+                    ocol[e] = (uint16_t)(j - lo);
+                    or0[e] = h_r0sq[q];
+                } else {
+                    // the index of i among j's own pairs (ascending partners)
+                    int kj = 0;
+                    for (int r = c->h_nat_row[j]; r < c->h_nat_row[j + 1] && c->h_nat_col[r] < i; ++r) kj += own[r];
+                    const size_t e = (size_t)rev_off[s] + (size_t)kr++ * ns + (i - lo);
+                    rcol[e] = (uint16_t)(j - lo);
+                    rk[e] = (uint16_t)kj;
+                }
+            }
+        }
+    }
+    c->h_nat_own_cnt = own_cnt;
+    c->h_nat_rev_cnt = rev_cnt;
+    CUDA_OR_RETURN(c, upload(c, &c->d_nat_own_off, own_off));
+    CUDA_OR_RETURN(c, upload(c, &c->d_nat_own_cnt, own_cnt));
+    CUDA_OR_RETURN(c, upload(c, &c->d_nat_own_col, ocol));
+    CUDA_OR_RETURN(c, upload(c, &c->d_nat_own_r0sq, or0));
+    CUDA_OR_RETURN(c, upload(c, &c->d_nat_rev_off, rev_off));
+    CUDA_OR_RETURN(c, upload(c, &c->d_nat_rev_cnt, rev_cnt));
+    CUDA_OR_RETURN(c, upload(c, &c->d_nat_rev_col, rcol));
+    CUDA_OR_RETURN(c, upload(c, &c->d_nat_rev_k, rk));
+    return SOP_OK;
+}
+
+// Static exclusions of the batched rebuild scan for systems of at most 256 beads: for bead b
+// and candidate block blk (beads 32 blk .. 32 blk + 31 of the system), the bits of the bead
+// itself, its bonded neighbours (bond length > 0, as the kernels test it) and its native
+// partners. Larger systems (offset -1) exclude on the fly.
+sop_status build_exclusions(sop_ctx *c) {
+    std::vector<float> r0(c->n);
+    CUDA_OR_RETURN(c, cudaMemcpy(r0.data(), c->d_bond_r0, sizeof(float) * c->n, cudaMemcpyDeviceToHost));
+    std::vector<int32_t> off(c->n_sys, -1);
+    std::vector<uint32_t> ex;
+    for (int s = 0; s < c->n_sys; ++s) {
+        const int lo = c->sys_lo[s], ns = c->sys_lo[s + 1] - lo;
+        if (ns > 256) continue;
+        const int nblk = (ns + 31) / 32;
+        off[s] = (int32_t)ex.size();
+        ex.resize(ex.size() + (size_t)nblk * ns, 0u);
+        uint32_t *e = ex.data() + off[s];
+        auto mark = [&](int b, int j) { e[(j >> 5) * ns + b] |= 1u << (j & 31); };
+        for (int b = 0; b < ns; ++b) {
+            const int i = lo + b;
+            mark(b, b);
+            if (b > 0 && r0[i - 1] > 0.f) mark(b, b - 1);
+            if (b + 1 < ns && r0[i] > 0.f) mark(b, b + 1);
+            for (int q = c->h_nat_row[i]; q < c->h_nat_row[i + 1]; ++q) mark(b, c->h_nat_col[q] - lo);
+        }
+    }
+    if (ex.empty()) ex.push_back(0u);
+    CUDA_OR_RETURN(c, upload(c, &c->d_excl_off, off));
+    CUDA_OR_RETURN(c, upload(c, &c->d_excl, ex));
+    return SOP_OK;
+}
+
 // Batched natives: per system, column-major ELL of system-local partner indices.
 sop_status build_batched_tables(sop_ctx *c) {
     std::vector<int32_t> off(c->n_sys), cnt(c->n);
@@ -759,14 +925,51 @@ sop_status build_batched_tables(sop_ctx *c) {
     CUDA_OR_RETURN(c, upload(c, &c->d_nat_ell_cnt, cnt));
     CUDA_OR_RETURN(c, upload(c, &c->d_nat_ell_col, col));
     CUDA_OR_RETURN(c, upload(c, &c->d_nat_ell_r0sq, r0sq));
-    return SOP_OK;
+    sop_status se = build_exclusions(c);
+    if (se != SOP_OK) return se;
+    return build_pair_tables(c, h_r0sq);
 }
 
 // Size buckets of the batched schedule: systems of up to 32, 64, 96, 128, 192, 256, 384, 512,
 // 768, 1024, 1536, 2048, 4096 and 8192 beads. Each bucket gets its work items (system,
 // replica; heaviest system first), a Verlet capacity from the first list of its systems and
 // the width of its merged rows.
-sop_status build_buckets(sop_ctx *c, const std::vector<int32_t> &first_len) {
+// Pool bytes of the pair form for the systems `sys` (all at most kPairMaxBeads beads), from
+// their first Verlet list (replica 0): own and reverse entries per bead under the ownership
+// rules of the kernel, slots grouped by 32 in the kernel's order (decreasing 2 own + rev),
+// each group as wide as its widest row, plus a margin of a fifth and one entry per row.
+int pair_pool_for(const sop_ctx *c, const std::vector<int32_t> &sys, const std::vector<int32_t> &first_start,
+                  const std::vector<int32_t> &first_len, const std::vector<int32_t> &first_col) {
+    size_t pool = 0;
+    for (int s : sys) {
+        const int lo = c->sys_lo[s], hi = c->sys_lo[s + 1], ns = hi - lo;
+        std::vector<int> own(ns), rev(ns), key(ns), ord(ns);
+        for (int b = 0; b < ns; ++b) { own[b] = c->h_nat_own_cnt[lo + b]; rev[b] = c->h_nat_rev_cnt[lo + b]; }
+        for (int b = 0; b < ns; ++b)
+            for (int q = 0; q < first_len[lo + b]; ++q) {
+                const int j = first_col[first_start[lo + b] + q] - lo;
+                const bool mine = ((b + j) & 1) ? j > b : j < b;
+                (mine ? own[b] : rev[b])++;
+            }
+        for (int b = 0; b < ns; ++b) { key[b] = 2 * own[b] + rev[b]; ord[b] = b; }
+        std::stable_sort(ord.begin(), ord.end(), [&key](int x, int y) { return key[x] > key[y]; });
+        int so = 0, sr = 0;
+        const int G = (ns + 31) / 32;
+        for (int g = 0; g < G; ++g) {
+            int wo = 0, wr = 0;
+            for (int p = 32 * g; p < std::min(ns, 32 * g + 32); ++p) { wo = std::max(wo, own[ord[p]]); wr = std::max(wr, rev[ord[p]]); }
+            so += 32 * wo;
+            sr += 32 * wr;
+        }
+        so += so / 5 + 32 * G;
+        sr += sr / 5 + 32 * G;
+        pool = std::max(pool, pair_pool_bytes(so, sr, ns));
+    }
+    return (int)pool;
+}
+
+sop_status build_buckets(sop_ctx *c, const std::vector<int32_t> &first_start, const std::vector<int32_t> &first_len,
+                         const std::vector<int32_t> &first_col) {
     static const int bounds[] = {32, 64, 96, 128, 192, 256, 384, 512, 768, 1024, 1536, 2048, 4096, 8192};
     std::vector<int32_t> ir, is;
     int lo = 0;
@@ -793,6 +996,8 @@ sop_status build_buckets(sop_ctx *c, const std::vector<int32_t> &first_len) {
         bk.cap = std::min(128, std::max(32, ((mrow * 3) / 2 + 8 + 7) / 8 * 8));
         bk.row_width = maxnat + bk.cap;
         if (bk.row_width > 256) return fail(c, SOP_ERR_UNSUPPORTED, "batched rows wider than 256 entries");
+        if (bk.max_n <= kPairMaxBeads && c->batched_form != 1)
+            bk.pair_pool = pair_pool_for(c, sys, first_start, first_len, first_col);
         bk.item_off = (int32_t)ir.size();
         for (int s : sys)
             for (int r = 0; r < c->R; ++r) { ir.push_back(r); is.push_back(s); }
@@ -824,23 +1029,34 @@ sop_status build_buckets(sop_ctx *c, const std::vector<int32_t> &first_len) {
 sop_status tune_bucket(sop_ctx *c, sop_ctx::Bucket &bk) {
     std::vector<BatchedConfig> cands;
     const int need = 32 * ((bk.max_n + 31) / 32);
+    // the pair form (each pair evaluated once) where it fits; alone when it was asked for
+    std::vector<BatchedConfig> pairs;
+    if (bk.pair_pool > 0 && c->batched_form != 1)
+        for (int threads : {64, 128, 256})
+            for (int minb : {2, 3, 4}) {
+                BatchedConfig cfg;
+                if (threads > need && threads > 64) continue;
+                if (pair_config(bk.max_n, bk.pair_pool, threads, minb, &cfg)) pairs.push_back(cfg);
+            }
+    const bool pairs_only = c->batched_form == 2 && !pairs.empty();
     for (int threads : {64, 128, 256})
         for (int minb : {2, 3, 4}) {
             BatchedConfig cfg;
-            if (threads > need && threads > 64) continue;   // idle threads only
+            if (pairs_only || (threads > need && threads > 64)) continue;   // idle threads only
             if (batched_config(bk.max_n, bk.row_width, threads, false, minb, &cfg)) cands.push_back(cfg);
         }
     for (int threads : {128, 256, 512, 1024}) {
         BatchedConfig cfg;
-        if (threads > need && threads > 128) continue;
+        if (pairs_only || (threads > need && threads > 128)) continue;
         if (batched_config(bk.max_n, bk.row_width, threads, true, 1, &cfg)) cands.push_back(cfg);
     }
+    cands.insert(cands.end(), pairs.begin(), pairs.end());
     // the cluster form for larger systems: one system over 2..16 CTAs of 2^sh beads each.
     // SOP_FORCE_CLUSTER=sh keeps only the cluster configurations of 2^sh beads per CTA (sh 5
     // to 9, when the bucket has one): a tuning override that makes the form testable at any size
     const char *fc = std::getenv("SOP_FORCE_CLUSTER");
     const int force_sh = fc ? std::atoi(fc) : 0;
-    if (bk.max_n > 256 || force_sh > 0) {
+    if ((bk.max_n > 256 || force_sh > 0) && !pairs_only) {
         std::vector<BatchedConfig> clusters;
         for (int sh = 5; sh <= 9; ++sh) {
             if (force_sh > 0 ? sh != force_sh : sh < 7) continue;
@@ -855,27 +1071,32 @@ sop_status tune_bucket(sop_ctx *c, sop_ctx::Bucket &bk) {
         else cands.insert(cands.end(), clusters.begin(), clusters.end());
     }
     if (cands.empty()) return fail(c, SOP_ERR_UNSUPPORTED, "no batched configuration fits the bucket");
-    // default without a trial: shared-memory rows, the largest CTA at 64 registers; else global rows
+    // default without a trial: shared-memory rows, the largest CTA at 64 registers (the pair
+    // form when it was asked for); else global rows
     bk.cfg = cands[0];
     for (const auto &cf : cands)
-        if (!cf.rows_global && cf.min_blocks == 4 && cf.threads >= bk.cfg.threads) bk.cfg = cf;
+        if (!cf.rows_global && cf.min_blocks == 4 && cf.threads >= bk.cfg.threads && cf.pair_form == pairs_only)
+            bk.cfg = cf;
     const char *env = std::getenv("SOP_TUNE");
     const int trial_items = std::min<int>(bk.n_items, 152 * 16);
     if (!(env && std::string(env) == "0") && cands.size() > 1) {
         char key[128];
-        std::snprintf(key, sizeof key, "batched %d %d %d", bk.max_n, bk.row_width, trial_items);
+        std::snprintf(key, sizeof key, "batched %d %d %d %d %d", bk.max_n, bk.row_width, bk.pair_pool, trial_items,
+                      c->batched_form);
         bool cached = false;
         const char *cache = std::getenv("SOP_TUNE_CACHE");
         if (cache) {
             if (FILE *f = std::fopen(cache, "r")) {
                 char line[256];
                 while (!cached && std::fgets(line, sizeof line, f)) {
-                    int t = 0, bpt = 0, mb = 0, rg = 0, cs = 0, sh = 0;
+                    int t = 0, bpt = 0, mb = 0, rg = 0, cs = 0, sh = 0, pf = 0;
                     if (std::strncmp(line, key, std::strlen(key)) == 0 &&
-                        std::sscanf(line + std::strlen(key), " -> %d %d %d %d %d %d", &t, &bpt, &mb, &rg, &cs, &sh) == 6) {
+                        std::sscanf(line + std::strlen(key), " -> %d %d %d %d %d %d %d", &t, &bpt, &mb, &rg, &cs, &sh,
+                                    &pf) == 7) {
                         for (const auto &cf : cands)
                             if (cf.threads == t && cf.beads_per_thread == bpt && cf.min_blocks == mb &&
-                                (int)cf.rows_global == rg && cf.cluster == cs && cf.m_shift == sh) {
+                                (int)cf.rows_global == rg && cf.cluster == cs && cf.m_shift == sh &&
+                                (int)cf.pair_form == pf) {
                                 bk.cfg = cf;
                                 cached = true;
                             }
@@ -969,7 +1190,8 @@ sop_status tune_bucket(sop_ctx *c, sop_ctx::Bucket &bk) {
 
 bool same_config(const BatchedConfig &x, const BatchedConfig &y) {
     return x.threads == y.threads && x.beads_per_thread == y.beads_per_thread && x.min_blocks == y.min_blocks &&
-           x.rows_global == y.rows_global && x.cluster == y.cluster && x.m_shift == y.m_shift;
+           x.rows_global == y.rows_global && x.cluster == y.cluster && x.m_shift == y.m_shift &&
+           x.pair_form == y.pair_form;
 }
 
 // Buckets run side by side, so the configurations fastest on their own need not be the
@@ -1068,9 +1290,9 @@ sop_status tune_joint(sop_ctx *c) {
     for (auto &bk : c->buckets) {
         if (cache && bk.timed)
             if (FILE *f = std::fopen(cache, "a")) {
-                std::fprintf(f, "%s -> %d %d %d %d %d %d %.4f\n", bk.key.c_str(), bk.cfg.threads,
+                std::fprintf(f, "%s -> %d %d %d %d %d %d %d %.4f\n", bk.key.c_str(), bk.cfg.threads,
                              bk.cfg.beads_per_thread, bk.cfg.min_blocks, (int)bk.cfg.rows_global, bk.cfg.cluster,
-                             bk.cfg.m_shift, bk.span_ms);
+                             bk.cfg.m_shift, (int)bk.cfg.pair_form, bk.span_ms);
                 std::fclose(f);
             }
         if (bk.cfg.rows_global)
@@ -1391,6 +1613,7 @@ sop_status create_impl(sop_ctx *c, const sop_topology *topo, const double *xyz, 
     a.fp.inv_R02 = (float)(1.0 / (p->R0 * p->R0));
     a.fp.eps12_h = (float)(12.0 * p->eps_h);
     a.fp.eps6_l = (float)(6.0 * p->eps_l);
+    a.fp.rep_k = (float)(6.0 * p->eps_l * std::pow(p->sigma, 6));
     a.fp.sigma2 = (float)(p->sigma * p->sigma);
     a.fp.mob = (float)(p->dt / p->zeta);
     a.fp.amp = (float)std::sqrt(2.0 * kT * p->dt / p->zeta);
@@ -1437,6 +1660,12 @@ sop_status create_impl(sop_ctx *c, const sop_topology *topo, const double *xyz, 
     if (s != SOP_OK) return s;
     // ---- schedule: batched for small systems or many of them, streamed for a few large ones
     int sched = p->schedule;
+    if (sched == SOP_SCHED_BATCHED_PAIRS) {
+        sched = SOP_SCHED_BATCHED;
+        c->batched_form = 2;
+    } else if (sched == SOP_SCHED_BATCHED) {
+        c->batched_form = 1;
+    }
     const bool batched_ok = c->max_sys <= kBatchedMaxBeads;
     if (sched == SOP_SCHED_AUTO) {
         const int64_t items = (int64_t)c->R * c->n_sys;
@@ -1471,11 +1700,22 @@ sop_status create_impl(sop_ctx *c, const sop_topology *topo, const double *xyz, 
     c->st.block_threads = 256;
     c->st.pairs_per_bead = c->ppb;
     if (sched == SOP_SCHED_BATCHED) {
-        std::vector<int32_t> first_len(n);
+        // the first list of replica 0 sizes the rows of every bucket
+        std::vector<int32_t> first_start(n), first_len(n), first_col;
+        CUDA_OR_RETURN(c, cudaMemcpy(first_start.data(), c->pl.start, sizeof(int32_t) * n, cudaMemcpyDeviceToHost));
         CUDA_OR_RETURN(c, cudaMemcpy(first_len.data(), c->pl.len, sizeof(int32_t) * n, cudaMemcpyDeviceToHost));
+        int32_t clo = INT32_MAX, chi = 0;
+        for (int i = 0; i < n; ++i)
+            if (first_len[i] > 0) { clo = std::min(clo, first_start[i]); chi = std::max(chi, first_start[i] + first_len[i]); }
+        if (chi > clo) {
+            first_col.resize(chi - clo);
+            CUDA_OR_RETURN(c, cudaMemcpy(first_col.data(), c->pl.col + clo, sizeof(int32_t) * (chi - clo),
+                                         cudaMemcpyDeviceToHost));
+            for (int i = 0; i < n; ++i) first_start[i] = first_len[i] > 0 ? first_start[i] - clo : 0;
+        }
         s = build_batched_tables(c);
         if (s != SOP_OK) return s;
-        s = build_buckets(c, first_len);
+        s = build_buckets(c, first_start, first_len, first_col);
         if (s != SOP_OK) return s;
         size_t main_bucket = 0;
         for (size_t k = 0; k < c->buckets.size(); ++k) {
@@ -1493,7 +1733,11 @@ sop_status create_impl(sop_ctx *c, const sop_topology *topo, const double *xyz, 
         c->st.buckets = (int32_t)c->buckets.size();
         c->st.cluster_size = cfg.cluster;
         c->st.cluster_buckets = 0;
-        for (const auto &bk : c->buckets) c->st.cluster_buckets += bk.cfg.cluster > 0 ? 1 : 0;
+        c->st.pair_buckets = 0;
+        for (const auto &bk : c->buckets) {
+            c->st.cluster_buckets += bk.cfg.cluster > 0 ? 1 : 0;
+            c->st.pair_buckets += bk.cfg.pair_form ? 1 : 0;
+        }
     }
     (void)mrow;
     CUDA_OR_RETURN(c, cudaStreamSynchronize(c->stream));
@@ -1847,7 +2091,11 @@ sop_status sop_get_pairlist(sop_ctx *c, int32_t replica, int32_t *row_ptr, int32
                                           cudaMemcpyDeviceToHost, c->stream));
         CUDA_OR_RETURN(c, cudaMemcpyAsync(cols.data(), c->d_dump_col + (size_t)replica * n * stride,
                                           sizeof(int32_t) * cols.size(), cudaMemcpyDeviceToHost, c->stream));
-        for (int i = 0; i < n; ++i) start[i] = i * stride;
+        CUDA_OR_RETURN(c, cudaStreamSynchronize(c->stream));
+        for (int i = 0; i < n; ++i) {
+            if (len[i] > stride) return fail(c, SOP_ERR_PAIRLIST_OVERFLOW, "a Verlet row is longer than the dump stride");
+            start[i] = i * stride;
+        }
     } else {
         CUDA_OR_RETURN(c, cudaMemcpyAsync(start.data(), c->pl.start + (size_t)replica * n, sizeof(int32_t) * n,
                                           cudaMemcpyDeviceToHost, c->stream));

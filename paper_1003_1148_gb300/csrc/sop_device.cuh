@@ -114,6 +114,7 @@ struct ForceParams {
     float inv_R02;    // 1 / R0^2
     float eps12_h;    // 12 eps_h
     float eps6_l;     // 6 eps_l
+    float rep_k;      // 6 eps_l sigma^6 (repulsion: F = rep_k / r^8 d)
     float sigma2;     // sigma^2
     float mob;        // h / zeta
     float amp;        // sqrt(2 kT h / zeta)
@@ -140,11 +141,11 @@ __device__ __forceinline__ float native_coef(float r2, float r0sq, const ForcePa
     return fp.eps12_h * inv_r2 * (s3 * s3 - s3);
 }
 
-// Repulsion: F_i = (6 eps_l / r^2) (sigma^2 / r^2)^3 d.
+// Repulsion: F_i = (6 eps_l / r^2) (sigma^2 / r^2)^3 d = 6 eps_l sigma^6 / r^8 d.
 __device__ __forceinline__ float repulsive_coef(float r2, const ForceParams &fp) {
     const float inv_r2 = 1.0f / r2;
-    const float q = fp.sigma2 * inv_r2;
-    return fp.eps6_l * inv_r2 * (q * q * q);
+    const float i4 = inv_r2 * inv_r2;
+    return fp.rep_k * (i4 * i4);
 }
 
 // Compensated (Kahan) accumulation of one step's displacement.

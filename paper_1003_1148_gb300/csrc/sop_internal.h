@@ -220,6 +220,25 @@ struct BatchedArgs {
     const int32_t *nat_ell_cnt = nullptr;  // [n] count per bead
     const uint16_t *nat_ell_col = nullptr; // system-local partner
     const float *nat_ell_r0sq = nullptr;
+    // pair form: each native pair belongs to the row of one of its beads (balanced
+    // orientation); ELL tables per system like the ones above, entry k of bead b at
+    // off[s] + k * n_s + b. own: the partners of b's own pairs (ascending) and their r0^2;
+    // rev: the partners whose row holds the pair with b (ascending) and the index of b
+    // among that partner's own natives
+    const int32_t *nat_own_off = nullptr;  // [n_sys]
+    const int32_t *nat_own_cnt = nullptr;  // [n]
+    const uint16_t *nat_own_col = nullptr;
+    const float *nat_own_r0sq = nullptr;
+    const int32_t *nat_rev_off = nullptr;  // [n_sys]
+    const int32_t *nat_rev_cnt = nullptr;  // [n]
+    const uint16_t *nat_rev_col = nullptr;
+    const uint16_t *nat_rev_k = nullptr;
+    int32_t pair_pool = 0;      // pair form: bytes of shared memory for rows, reverse lists and coefficients
+    // static exclusions of the rebuild scan for systems of at most 256 beads: bit t of
+    // excl[excl_off[s] + blk * n_s + b] marks candidate 32 blk + t of bead b as the bead itself,
+    // a bonded neighbour or a native partner; excl_off[s] < 0 for larger systems
+    const int32_t *excl_off = nullptr;   // [n_sys]
+    const uint32_t *excl = nullptr;
     float4 *pos = nullptr;      // [R*n] current positions (read at start, written at end)
     float4 *comp = nullptr;     // [R*n]
     float4 *snap = nullptr;     // [R*n] positions at the last rebuild
@@ -250,6 +269,7 @@ struct BatchedConfig {
     size_t smem = 0;
     int cluster = 0;           // > 0: the cluster form, one system over `cluster` CTAs of 2^m_shift beads each
     int m_shift = 0;
+    bool pair_form = false;    // each pair evaluated once (k_bpair) instead of the particle-based gather
 };
 
 // A configuration for systems of at most max_n beads whose merged rows hold up to
@@ -258,12 +278,22 @@ bool batched_config(int max_n, int row_width, int threads, bool rows_global, int
 // The cluster form: each system is split over ceil(max_n / 2^m_shift) CTAs (at most 16)
 // of `threads` threads that own 2^m_shift consecutive beads each; false when it does not fit.
 bool cluster_config(int max_n, int row_width, int threads, int m_shift, BatchedConfig *cfg);
+// The pair form (Newton's third law inside the CTA) for systems of at most max_n <= 256
+// beads with `pool` bytes (a multiple of 16) of shared memory for the rows, reverse lists and
+// coefficients of one item; false when it does not fit.
+bool pair_config(int max_n, int pool, int threads, int min_blocks, BatchedConfig *cfg);
+// Pool bytes for so own entries and sr reverse entries (group padding included) in a system
+// of n beads.
+size_t pair_pool_bytes(int so, int sr, int n);
+constexpr int kPairMaxBeads = 256;
 // CTAs of the configuration the device holds at once (cluster form: clusters x size); 0 when
 // the occupancy query fails.
 int batched_resident_ctas(const BatchedConfig &cfg);
 // Clusters of the configuration that fit the device at once (0: it cannot launch).
 int cluster_capacity(const BatchedConfig &cfg);
 // Run n_steps (or forces only when a.force_out != null and n_steps == 0).
+cudaError_t launch_bpair(const BatchedArgs &a, const BatchedConfig &cfg, cudaStream_t s);
+int bpair_resident_ctas(const BatchedConfig &cfg);
 cudaError_t launch_batched(const BatchedArgs &a, const BatchedConfig &cfg, cudaStream_t s, int64_t *launches);
 
 }  // namespace sop

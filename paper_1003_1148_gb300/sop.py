@@ -25,9 +25,9 @@ OK, ERR_INVALID_ARG, ERR_CUDA, ERR_OOM, ERR_FENE_BREAK, ERR_NONFINITE, ERR_PAIRL
     ERR_TIMEOUT, ERR_INDENTER_OVERLAP, ERR_UNSUPPORTED, ERR_CAPACITY = range(12)
 STATUS_NAMES = ["OK", "INVALID_ARG", "CUDA", "OOM", "FENE_BREAK", "NONFINITE", "PAIRLIST_OVERFLOW", "ABORTED",
                 "TIMEOUT", "INDENTER_OVERLAP", "UNSUPPORTED", "CAPACITY"]
-SCHED_AUTO, SCHED_BATCHED, SCHED_STREAMED, SCHED_PLAIN, SCHED_PAIRS = range(5)
+SCHED_AUTO, SCHED_BATCHED, SCHED_STREAMED, SCHED_PLAIN, SCHED_PAIRS, SCHED_BATCHED_PAIRS = range(6)
 SCHEDULES = {"auto": SCHED_AUTO, "batched": SCHED_BATCHED, "streamed": SCHED_STREAMED, "plain": SCHED_PLAIN,
-             "pairs": SCHED_PAIRS}
+             "pairs": SCHED_PAIRS, "batched_pairs": SCHED_BATCHED_PAIRS}
 
 EXPORTED = ["sop_create", "sop_step", "sop_forces", "sop_pairlist_rebuild", "sop_pull", "sop_indenter",
             "sop_get_positions", "sop_set_positions", "sop_get_pairlist", "sop_get_native_map",
@@ -86,7 +86,7 @@ class Stats(C.Structure):
                 ("pairs_per_bead", C.c_int32), ("beads_per_thread", C.c_int32), ("min_blocks", C.c_int32),
                 ("buckets", C.c_int32),
                 ("pairlist_entries", C.c_int64), ("native_entries", C.c_int64), ("tune_ms", C.c_double),
-                ("cluster_buckets", C.c_int32), ("cluster_size", C.c_int32)]
+                ("cluster_buckets", C.c_int32), ("cluster_size", C.c_int32), ("pair_buckets", C.c_int32)]
 
 
 def load(path: str | None = None):

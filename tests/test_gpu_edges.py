@@ -15,7 +15,7 @@ def sop():
     return s
 
 
-@pytest.mark.parametrize("schedule", ["batched", "streamed"])
+@pytest.mark.parametrize("schedule", ["batched", "streamed", "batched_pairs"])
 def test_zero_temperature_follows_the_oracle_and_descends(sop, orc, synth, schedule):
     w = synth.chain64()
     w.params = dict(w.params, T=0.0)
@@ -34,7 +34,7 @@ def test_zero_temperature_follows_the_oracle_and_descends(sop, orc, synth, sched
     sim.close()
 
 
-@pytest.mark.parametrize("schedule", ["batched", "streamed", "plain"])
+@pytest.mark.parametrize("schedule", ["batched", "streamed", "plain", "batched_pairs"])
 def test_all_beads_fixed(sop, synth, schedule):
     w = synth.chain64()
     sim = sop.Simulation(w.xyz, w.chain_offsets, None, np.ones(w.n_beads, np.uint8), w.params, n_replicas=2,
@@ -47,7 +47,7 @@ def test_all_beads_fixed(sop, synth, schedule):
     sim.close()
 
 
-@pytest.mark.parametrize("schedule", ["batched", "streamed"])
+@pytest.mark.parametrize("schedule", ["batched", "streamed", "batched_pairs"])
 def test_chain_without_native_contacts(sop, orc, schedule):
     n = 40
     xyz = np.zeros((n, 3))

@@ -74,12 +74,12 @@ def test_native_map_bit_exact(sop, orc, workloads):
         sim.close()
 
 
-@pytest.mark.parametrize("schedule", ["streamed", "batched"])
+@pytest.mark.parametrize("schedule", ["streamed", "batched", "batched_pairs"])
 def test_pairlist_bit_exact_after_steps(sop, orc, workloads, schedule):
     for w in workloads:
-        if schedule == "batched" and max(np.diff(w.chain_offsets)) > 2048:
+        if schedule.startswith("batched") and max(np.diff(w.chain_offsets)) > 2048:
             continue
-        if schedule == "batched" and w.n_systems == 1 and w.n_beads > 2048:
+        if schedule.startswith("batched") and w.n_systems == 1 and w.n_beads > 2048:
             continue
         R = 2
         sim = sop.from_workload(w, n_replicas=R, schedule=schedule)
@@ -108,10 +108,10 @@ def oracle_with_externals(orc, w, x_start):
     return m
 
 
-@pytest.mark.parametrize("schedule", ["streamed", "batched", "pairs"])
+@pytest.mark.parametrize("schedule", ["streamed", "batched", "pairs", "batched_pairs"])
 def test_forces_within_tolerance(sop, orc, workloads, schedule):
     for w in workloads:
-        if schedule == "batched" and w.n_systems == 1 and w.n_beads > 2048:
+        if schedule.startswith("batched") and w.n_systems == 1 and w.n_beads > 2048:
             continue
         sim = sop.from_workload(w, n_replicas=2, schedule=schedule)
         x0 = sim.get_positions(0)
@@ -128,10 +128,10 @@ def test_forces_within_tolerance(sop, orc, workloads, schedule):
         sim.close()
 
 
-@pytest.mark.parametrize("schedule", ["streamed", "batched", "plain", "pairs"])
+@pytest.mark.parametrize("schedule", ["streamed", "batched", "plain", "pairs", "batched_pairs"])
 def test_trajectory_100_steps(sop, orc, workloads, schedule):
     for w in workloads:
-        if schedule == "batched" and w.n_systems == 1 and w.n_beads > 2048:
+        if schedule.startswith("batched") and w.n_systems == 1 and w.n_beads > 2048:
             continue
         R = 2
         sim = sop.from_workload(w, n_replicas=R, schedule=schedule)
@@ -172,7 +172,7 @@ def test_cooperative_chunk_equals_plain_bitwise(sop, synth, monkeypatch):
 
 
 def test_observables_match_oracle_at_gpu_positions(sop, orc, synth):
-    for schedule in ("streamed", "batched", "pairs", "plain"):
+    for schedule in ("streamed", "batched", "pairs", "plain", "batched_pairs"):
         w = synth.uneven(n_chains=4, lo=60, hi=200, steps=100)
         sim = sop.from_workload(w, n_replicas=2, schedule=schedule, obs_every=20)
         x0 = sim.get_positions(0)
@@ -194,7 +194,7 @@ def test_observables_match_oracle_at_gpu_positions(sop, orc, synth):
         sim.close()
 
 
-@pytest.mark.parametrize("schedule", ["streamed", "batched", "pairs"])
+@pytest.mark.parametrize("schedule", ["streamed", "batched", "pairs", "batched_pairs"])
 def test_checkpoint_resume_bit_exact(sop, synth, schedule):
     w = synth.replicas(n_replicas=3, n=100, steps=100)
     sim = sop.from_workload(w, schedule=schedule)
@@ -208,22 +208,23 @@ def test_checkpoint_resume_bit_exact(sop, synth, schedule):
     assert np.array_equal(a, b)
 
 
-def test_replica_sharding_is_exact(sop, synth):
+@pytest.mark.parametrize("schedule", ["batched", "batched_pairs"])
+def test_replica_sharding_is_exact(sop, synth, schedule):
     """Replicas split over two contexts (seed offset) reproduce one context bit for bit."""
     w = synth.replicas(n_replicas=5, n=96, steps=60)
-    whole = sop.from_workload(w, schedule="batched")
+    whole = sop.from_workload(w, schedule=schedule)
     whole.step(60)
     x = whole.get_positions(-1)
     a = sop.Simulation(w.xyz, w.chain_offsets, w.system_offsets, w.fixed, w.params, n_replicas=2, seed=w.seed,
-                       schedule="batched")
+                       schedule=schedule)
     b = sop.Simulation(w.xyz, w.chain_offsets, w.system_offsets, w.fixed, w.params, n_replicas=3, seed=w.seed + 2,
-                       schedule="batched")
+                       schedule=schedule)
     a.step(60)
     b.step(60)
     assert np.array_equal(np.concatenate([a.get_positions(-1), b.get_positions(-1)]), x)
 
 
-@pytest.mark.parametrize("schedule", ["streamed", "batched"])
+@pytest.mark.parametrize("schedule", ["streamed", "batched", "batched_pairs"])
 def test_fene_break_freezes_only_that_replica(sop, synth, schedule):
     w = synth.replicas(n_replicas=3, n=64, steps=10)
     sim = sop.from_workload(w, schedule=schedule)
@@ -313,3 +314,19 @@ def test_spread_step_equals_group_step(sop, synth):
     assert np.array_equal(a.get_positions(-1), b.get_positions(-1))
     a.close()
     b.close()
+
+
+def test_pair_form_is_used_and_reproducible(sop, synth):
+    """The pair form (each pair evaluated once) runs every bucket of systems up to 256 beads
+    when asked for, and two contexts take the same trajectory bit for bit (its sums have a
+    fixed order whatever slot a bead lands in)."""
+    w = synth.uneven(n_chains=6, lo=50, hi=250, steps=100)
+    a = sop.from_workload(w, n_replicas=3, schedule="batched_pairs")
+    b = sop.from_workload(w, n_replicas=3, schedule="batched_pairs")
+    st = a.stats()
+    assert st["pair_buckets"] == st["buckets"] >= 1
+    a.step(57)
+    b.step(57)
+    assert np.array_equal(a.get_positions(-1), b.get_positions(-1))
+    g = sop.from_workload(w, n_replicas=3, schedule="batched")
+    assert g.stats()["pair_buckets"] == 0

@@ -17,7 +17,7 @@ pytestmark = pytest.mark.gpu
 
 # record layout: step, replica, system, energy, f_ext, extension, q, r_ee
 STEP, REP, SYS, E, F, EXT, Q, REE = range(8)
-SCHEDULES = ["batched", "streamed", "pairs", "plain"]
+SCHEDULES = ["batched", "streamed", "pairs", "plain", "batched_pairs"]
 
 
 @pytest.fixture(scope="module")

@@ -38,7 +38,7 @@ def oracle_model(orc, w, x_start):
     return m
 
 
-@pytest.mark.parametrize("schedule", ["batched", "streamed", "pairs", "plain"])
+@pytest.mark.parametrize("schedule", ["batched", "streamed", "pairs", "plain", "batched_pairs"])
 def test_taus_trajectory_and_state_match_oracle(sop, orc, synth, schedule):
     w = synth.uneven(n_chains=5, lo=50, hi=240, steps=100)
     R = 2

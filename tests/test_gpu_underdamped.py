@@ -26,7 +26,7 @@ def sop():
     return s
 
 
-@pytest.mark.parametrize("schedule", ["batched", "streamed", "pairs", "plain"])
+@pytest.mark.parametrize("schedule", ["batched", "streamed", "pairs", "plain", "batched_pairs"])
 def test_baoab_trajectory_matches_oracle(sop, orc, synth, schedule):
     w = synth.uneven(n_chains=5, lo=50, hi=240, steps=100)
     w.params = dict(w.params, **PARAMS)

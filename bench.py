@@ -15,6 +15,10 @@ through the public API with host buffers (every step uploads the positions it
 starts from out of pinned memory and reads back the new positions and the
 observable records). `--impl reference` times the
 FP64 CPU oracle on the host cores on bounded samples of the same workload.
+The same line carries, under "workloads", the other configurations (chain64,
+fiber4096, uneven2048, shell60x2500), each timed in this run with its rate, time per
+MD step and its HBM and FP32 roofline fractions, and the FP32 peak measured in
+this run (sop_fp32_peak).
 Under torchrun every rank runs its own 8,192 replicas (weak scaling).
 """
 from __future__ import annotations
@@ -41,12 +45,18 @@ from paper_1003_1148_gb300 import dist  # noqa: E402  (host-only helpers; loads 
 METRIC = "bead-steps/s on 1 GB300, batched FP32 vs plain per-chain; force err vs FP64"
 UNIT = "bead-steps/s"
 MD_STEPS_PER_STEP = 1000
-FP32_LANES_PER_SM = 128
-N_SM = 152
+FP32_LANES_PER_SM = 128   # FP32 FMA lanes per SM of the Blackwell SM (the derived peak beside the measured one)
 
-# Algorithmic FP32 operations per unique pair term and per bead, an FMA counted as 2: a FENE or
-# native 12-6 term 25, a (sigma/r)^6 term 23; per bead the noise, update and compensation 33.
-FLOP_FENE, FLOP_NATIVE, FLOP_REP, FLOP_BEAD = 25, 25, 23, 33
+# Algorithmic FP32 operations, an FMA counted as 2, each unique interaction once (Newton's
+# third law): a FENE bond 20, a native 12-6 pair 25, a listed (sigma/r)^6 pair 20; per bead
+# the Box-Muller transform 40 and the update with its compensation 30.
+FLOP_FENE, FLOP_NATIVE, FLOP_REP, FLOP_BEAD = 20, 25, 20, 70
+FLOP_MODEL = ("20 per bond, 25 per native pair, 20 per listed pair (each unique pair once), 70 per bead "
+              "(Box-Muller 40, update and compensation 30); an FMA counts 2")
+
+# The other workloads, timed in the same run after the headline (one line carries them all):
+# name -> (MD steps per timed chunk, timed chunks)
+SUB_WORKLOADS = {"chain64": (1000, 3), "fiber4096": (1000, 3), "uneven2048": (1000, 2), "shell60x2500": (1000, 2)}
 
 
 def workload(name: str):
@@ -194,18 +204,102 @@ def cpu_baseline_leg(w, n_replicas: int, n_steps: int, pool=None):
     return work / wall, min(cores, n_replicas), sample
 
 
-def force_error_leg(w, positions, forces_gpu):
+def force_error_leg(w, samples):
     """FP32 GPU forces against the FP64 oracle at identical positions (part of the
-    CPU-baseline leg: the only place the benchmark calls the oracle besides timing)."""
+    CPU-baseline leg: the only place the benchmark calls the oracle besides timing).
+    samples: [(replica, positions, gpu forces)]. Reports the gate's measure (per component,
+    relative to the term-magnitude scale), the plain relative error per component
+    (|dF| / |F64| where |F64| is above 1e-3 of its median) and per bead (|dF_i| / |F64_i|)."""
     import oracle
     n = w.xyz.shape[0]
     m = oracle.Model(w.xyz, np.zeros(n, np.int32), np.zeros(n, np.int32), params=w.params)
-    Fo, Ao, _ = m.forces(positions, step=0)
-    d = np.abs(forces_gpu - Fo)
-    return {"max_rel_to_term_scale": float((d / Ao).max()),
-            "max_abs_kcal_mol_A": float(d.max()),
-            "median_rel": float(np.median(d / np.maximum(np.abs(Fo), 1e-12))),
-            "gate": 1e-5, "sample": "replica 0 after the timed run, all beads, FP64 oracle"}
+    gate = plain_c = plain_b = amax = 0.0
+    med = []
+    for _, x, F in samples:
+        Fo, Ao, _ = m.forces(x, step=0)
+        d = np.abs(F - Fo)
+        gate = max(gate, float((d / Ao).max()))
+        amax = max(amax, float(d.max()))
+        a = np.abs(Fo)
+        big = a > 1e-3 * np.median(a)
+        plain_c = max(plain_c, float((d[big] / a[big]).max()))
+        nb = np.linalg.norm(F - Fo, axis=1) / np.maximum(np.linalg.norm(Fo, axis=1), 1e-30)
+        plain_b = max(plain_b, float(nb.max()))
+        med.append(float(np.median(d / np.maximum(a, 1e-12))))
+    return {"max_rel_to_term_scale": gate, "max_abs_kcal_mol_A": amax,
+            "max_plain_rel_component": plain_c, "max_plain_rel_per_bead": plain_b,
+            "median_rel": float(np.median(med)), "gate": 1e-5,
+            "sample": f"replicas {[r for r, _, _ in samples]} after the timed run, all beads, FP64 oracle; "
+                      "plain per component over components above 1e-3 of the median |F64|"}
+
+
+def fp32_peak_leg(sop, local):
+    """Measured FP32 FMA rate (sop_fp32_peak, about 0.5 s) with the SM clocks sampled
+    during it; the derived peak uses the device's SM count and its maximum SM clock."""
+    with ClockSampler(local) as clk:
+        pk = sop.fp32_peak(0.5)
+    c = clk.summary()
+    derived = None
+    if c["sm_max_mhz"]:
+        derived = pk["sm_count"] * FP32_LANES_PER_SM * 2 * c["sm_max_mhz"] * 1e6 / 1e12
+    return {"tflops": pk["tflops"], "sm_count": pk["sm_count"], "sm_mhz_median": c["sm_mhz"],
+            "sm_max_mhz": c["sm_max_mhz"], "derived_tflops": derived, "launch_ms": pk["ms"],
+            "reasons": c["reasons"]}
+
+
+def sub_workload_leg(name, sop, torch, stream, flush, fp32_peak):
+    """One more workload of the same run: created with the automatic schedule, one chunk of
+    warm-up, then `chunks` timed chunks of MD steps (CUDA events on the library's stream,
+    L2 flushed between chunks; records read back outside the timed region). Rate, time per
+    MD step, and both rooflines from the algorithmic FLOPs and bytes per bead-step."""
+    md, chunks = SUB_WORKLOADS[name]
+    w = workload(name)
+    R = w.n_replicas
+    per_chunk = (md // w.obs_every + 1) if w.obs_every else 0
+    t0 = time.perf_counter()
+    sim = sop.from_workload(w, schedule="auto", stream=stream, obs_capacity=max(4096, 4 * R * w.n_systems * per_chunk))
+    create_s = time.perf_counter() - t0
+    ms = 0.0
+    with torch.cuda.stream(stream):
+        sim.step(md)
+        sim.get_observables()
+        for _ in range(chunks):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            sim.step(md)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms += e0.elapsed_time(e1)
+            sim.get_observables()
+    work = R * w.n_beads * md * chunks
+    rate = work / (ms / 1e3)
+    flop_bs, counts = algorithmic_flops_per_bead_step(sim, w)
+    bps = algorithmic_bytes_per_bead_step(counts, w.n_beads, int(w.params["rebuild_every"]))
+    hbm_peak = measured_hbm_gbs()
+    st = sim.stats()
+    out = {"value": rate, "unit": UNIT, "ms_per_md_step": ms / (md * chunks), "md_steps_timed": md * chunks,
+           "beads": R * w.n_beads, "systems": R * w.n_systems, "schedule": schedule_name(sop, st),
+           "create_s": create_s, "failed_replicas": int(np.count_nonzero(sim.replica_status())),
+           "roofline": {"hbm": {"achieved_gbs": bps * rate / 1e9, "peak_gbs": hbm_peak,
+                                "frac": bps * rate / 1e9 / hbm_peak, "bytes_per_bead_step": bps},
+                        "alu": {"achieved_tflops": flop_bs * rate / 1e12, "peak_tflops": fp32_peak,
+                                "frac": flop_bs * rate / 1e12 / fp32_peak if fp32_peak else None,
+                                "flop_per_bead_step": flop_bs},
+                        "list_sizes_replica0": counts}}
+    sim.close()
+    return out
+
+
+def schedule_name(sop, st):
+    names = {sop.SCHED_BATCHED: "batched", sop.SCHED_STREAMED: "streamed", sop.SCHED_PAIRS: "pairs",
+             sop.SCHED_PLAIN: "plain"}
+    nm = names.get(st["schedule"], str(st["schedule"]))
+    if st["schedule"] == sop.SCHED_BATCHED and st.get("pair_buckets"):
+        nm += f" ({st['pair_buckets']} of {st['buckets']} buckets in the pair form)"
+    if st["schedule"] == sop.SCHED_BATCHED and st.get("cluster_buckets"):
+        nm += f" ({st['cluster_buckets']} of {st['buckets']} buckets in the cluster form)"
+    return nm
 
 
 # ----------------------------------------------------------------------------------------
@@ -360,26 +454,30 @@ def run_ours(args):
     # roofline of the dominant kernel (the batched persistent kernel; one launch per step)
     flop_bs, counts = algorithmic_flops_per_bead_step(sim, w)
     clocks = clk.summary()
-    peak_mhz = 2070.0
-    peak = N_SM * FP32_LANES_PER_SM * 2 * peak_mhz * 1e6 / 1e12
+    fpk = fp32_peak_leg(sop, local)
+    peak = fpk["tflops"]
     per_launch_s = dev_ms / 1e3 / args.steps
     achieved = flop_bs * work_per_step / per_launch_s / 1e12
     st = sim.stats()
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "peak_measured": peak, "peak_derived": fpk["derived_tflops"], "sm_count": fpk["sm_count"],
+                "sm_mhz_median": fpk["sm_mhz_median"], "fp32_peak_clock_reasons": fpk["reasons"],
+                "frac_of_derived": achieved / fpk["derived_tflops"] if fpk["derived_tflops"] else None,
+                "flop_model": FLOP_MODEL,
                 "traffic": None, "kernel": {
                     sop.SCHED_BATCHED: "k_batched (one launch of 1,000 steps per benchmark step)",
                     sop.SCHED_STREAMED: "k_step (one launch per step, CUDA-graph replay) and the cell rebuild",
                     sop.SCHED_PAIRS: "k_pairs + k_pairs_step (two launches per step) and the cell rebuild"}.get(
                         st["schedule"], "per-step kernels"),
-                "kernel_config": {"schedule": {sop.SCHED_BATCHED: "batched", sop.SCHED_STREAMED: "streamed",
-                                               sop.SCHED_PAIRS: "pairs", sop.SCHED_PLAIN: "plain"}.get(
-                                                   st["schedule"], str(st["schedule"])),
+                "kernel_config": {"schedule": schedule_name(sop, st),
                                   "threads": st["block_threads"], "beads_per_thread": st["beads_per_thread"],
                                   "register_cap": 65536 // (256 * st["min_blocks"]) if st["min_blocks"] else 64,
                                   "size_buckets": st["buckets"],
                                   "verlet_capacity": st["pairs_per_bead"]},
                 "flop_per_bead_step": flop_bs, "list_sizes_replica0": counts,
-                "peak_note": "FP32 FMA pipe: 152 SMs x 128 lanes x 2 x 2070 MHz (max SM clock), derived"}
+                "peak_note": "peak: sop_fp32_peak measured in this run (independent FMA chains, about 0.5 s, "
+                             "sm_mhz_median the SM clock sampled during it); peak_derived: SMs x 128 FP32 "
+                             "lanes x 2 x the maximum SM clock"}
     if st["schedule"] in (sop.SCHED_STREAMED, sop.SCHED_PAIRS):
         # the streamed step against the HBM roofline: its algorithmic bytes at the whole-step rate
         hbm_peak = measured_hbm_gbs()
@@ -412,15 +510,36 @@ def run_ours(args):
             e1.record(stream)
             torch.cuda.synchronize()
         pv = n_plain * w.n_beads * s_plain / (e0.elapsed_time(e1) / 1e3)
+        pflop, pcounts = algorithmic_flops_per_bead_step(ps, w)
+        pbytes = algorithmic_bytes_per_bead_step(pcounts, w.n_beads, int(w.params["rebuild_every"]))
+        hbm_peak = measured_hbm_gbs()
         plain = {"value": pv, "unit": UNIT, "sample": f"{n_plain} replicas x {s_plain} steps, one chain per "
                  "launch sequence (per-step fused kernel, cell-list rebuild every 10 steps), chains in sequence",
-                 "batched_over_plain": value / world / pv}
+                 "ms_per_md_step": e0.elapsed_time(e1) / s_plain,
+                 "batched_over_plain": value / world / pv,
+                 "roofline": {"hbm": {"achieved_gbs": pbytes * pv / 1e9, "peak_gbs": hbm_peak,
+                                      "frac": pbytes * pv / 1e9 / hbm_peak, "bytes_per_bead_step": pbytes},
+                              "alu": {"achieved_tflops": pflop * pv / 1e12, "peak_tflops": peak,
+                                      "frac": pflop * pv / 1e12 / peak, "flop_per_bead_step": pflop},
+                              "bound": "launch latency (one chain per launch sequence)"}}
         ps.close()
 
     ferr = None
     if not args.no_cpu:
-        F, _ = sim.forces(0)
-        ferr = force_error_leg(w, sim.get_positions(0), F)
+        samples = []
+        for r in sorted({0, R // 3, (2 * R) // 3, R - 1}):
+            F, _ = sim.forces(r)
+            samples.append((r, sim.get_positions(r), F))
+        ferr = force_error_leg(w, samples)
+
+    # the other workloads of the configuration list, each timed in this run
+    subs = None
+    if world == 1 and not args.no_workloads:
+        subs = {}
+        for name in SUB_WORKLOADS:
+            if name == args.workload:
+                continue
+            subs[name] = sub_workload_leg(name, sop, torch, stream, flush, peak)
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": dev_ms / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -431,6 +550,7 @@ def run_ours(args):
             "gpu_launches": launches, "wall_s_timed_region": wall,
             "clocks": {"sm_mhz": clocks["sm_mhz"], "sm_max_mhz": clocks["sm_max_mhz"], "reasons": clocks["reasons"]},
             "roofline": roofline, "cpu_baseline": cpu, "plain_per_chain": plain, "force_err_vs_fp64": ferr,
+            "workloads": subs,
             "replicas_failed": int(np.count_nonzero(sim.replica_status()))}
     print(json.dumps(line))
     sim.close()
@@ -447,6 +567,7 @@ def main():
     ap.add_argument("--schedule", default="auto", choices=["batched", "streamed", "pairs", "auto", "batched_pairs"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle legs (profiling runs)")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain per-chain comparison")
+    ap.add_argument("--no-workloads", action="store_true", help="skip the other workloads (profiling runs)")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")

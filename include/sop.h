@@ -323,6 +323,17 @@ sop_status sop_brownian_ramp(const sop_ramp_params *params, double *mean, double
 sop_status sop_box_muller(const uint32_t *x, int64_t n, double *out, void *cuda_stream);
 sop_status sop_bead_noise(uint64_t key, int64_t step, uint32_t bead_lo, int64_t n, double *out, void *cuda_stream);
 
+/* FP32 FMA throughput of the current device, the denominator of the FP32 roofline of
+ * the batched kernels (the paper has no counterpart; a measurement utility). A kernel
+ * of independent fmaf chains (four CTAs of 256 threads per SM, eight chains per thread)
+ * runs on the default stream, its launches growing until one lasts about `seconds`
+ * (0 < seconds <= 10); *tflops receives the best rate of the launches (2 FLOP per
+ * FMA), *elapsed_ms (may be NULL) the duration of the last launch and *sm_count (may
+ * be NULL) the SMs of the device. Allocates and frees a small output buffer.
+ * SOP_ERR_INVALID_ARG on an argument out of range, SOP_ERR_CUDA on device failure
+ * (text in sop_last_error(NULL)). */
+sop_status sop_fp32_peak(double seconds, double *tflops, double *elapsed_ms, int32_t *sm_count);
+
 /* Per-replica status ([n_replicas] int32 host): a sop_status value each. */
 sop_status sop_replica_status(sop_ctx *ctx, int32_t *out);
 
@@ -344,8 +355,7 @@ void sop_destroy(sop_ctx *ctx);
 /*
  * Verlet list of one system, built without allocating any device memory.
  * The paper has no counterpart: this is an interface for callers that cannot
- * call cudaMalloc -- code that runs while its stream is being captured into a
- * CUDA graph, hosts whose device memory all belongs to their own pool
+ * call cudaMalloc -- hosts whose device memory all belongs to their own pool
  * allocator, or services that must not allocate after start-up. It runs the
  * same cell-list rebuild as the streamed schedule on caller-provided device
  * buffers; its scratch (1.8 MiB for at most SOP_NOALLOC_MAX_BEADS beads) is a
@@ -363,12 +373,16 @@ void sop_destroy(sop_ctx *ctx);
  *
  * Errors: SOP_ERR_INVALID_ARG when n is outside [1, SOP_NOALLOC_MAX_BEADS], a
  * pointer is NULL or misaligned, or pair_cut <= 0; SOP_ERR_PAIRLIST_OVERFLOW
- * when cap is too small; SOP_ERR_CUDA for a CUDA failure. The text is
- * sop_last_error(NULL). The call synchronises cuda_stream (NULL = the legacy
- * default stream) before it returns.
+ * when cap is too small or a row meets more than 256 candidates within
+ * pair_cut (whatever cap is); SOP_ERR_NONFINITE when a position is NaN or
+ * infinite, or when no grid of at most 2 n + 8 cells of edge >= pair_cut covers
+ * the system (every row is then empty); SOP_ERR_CUDA for a CUDA failure. The
+ * text is sop_last_error(NULL). The call reads its counters back and
+ * synchronises cuda_stream (NULL = the legacy default stream) before it
+ * returns, so it cannot be recorded into a CUDA graph.
  *
  * The first call on a device looks up the scratch array's device address for
- * that device; make that first call before any stream capture. Every call
+ * that device. Every call
  * shares the one scratch array and overwrites it, so calls whose GPU work
  * overlaps (two host threads, or two streams) race and must be serialised by
  * the caller.

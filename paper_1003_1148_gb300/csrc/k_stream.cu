@@ -84,6 +84,7 @@ __global__ void k_native(const double *X, const int32_t *chain, const int32_t *s
 // ---------------------------------------------------------------------------
 constexpr int kScanThreads = 1024;
 constexpr int kScanTile = 2 * kScanThreads;
+static_assert(kScanTile == kScanTileElems, "scan_tmp_elems and the no-alloc scratch assume this tile");
 
 __device__ __forceinline__ int warp_inclusive_scan(int v) {
     const int lane = threadIdx.x & 31;
@@ -343,7 +344,7 @@ __global__ void k_cell_sort(RebuildArgs a, int c_lo, int c_hi) {
 }
 
 constexpr int kBuildWarps = 8;
-constexpr int kRowBuf = 256;   // candidates a row may hold before it is an overflow
+constexpr int kRowBuf = kRowCandidates;   // candidates a row may hold before it is an overflow
 constexpr int kNatBuf = 64;    // native partners kept in shared memory per warp
 
 struct BuildExtra {

@@ -119,6 +119,11 @@ struct DevObs {
 void set_global_error(const std::string &msg);
 
 // ---- launchers (k_stream.cu) ----
+// Elements one block of the scan covers, and candidates one Verlet row of the streamed
+// builder may hold (more is an overflow of that row).
+constexpr int kScanTileElems = 2048;
+constexpr int kRowCandidates = 256;
+
 // Scan: out[0..n] = exclusive prefix sums of in[0..n-1], out[n] = total.
 void scan_exclusive(const int32_t *in, int32_t *out, int64_t n, int32_t *tmp, cudaStream_t s, int64_t *launches);
 int64_t scan_tmp_elems(int64_t n);

@@ -7,7 +7,8 @@
 // cudaMalloc. The caller passes the inputs and the output rows.
 //
 // The array is a fixed 1.8 MiB that every GPU which loads this library keeps
-// until the process exits. Its device address is looked up once per device
+// until the process exits. Each call reads its counters back and synchronises its
+// stream, so it cannot be recorded into a CUDA graph. Its device address is looked up once per device
 // with cudaGetSymbolAddress (host code cannot use the symbol itself: in host
 // code it names a host-side stand-in, not device memory). All calls share the
 // array, so calls whose work overlaps on the GPU race on it.
@@ -22,7 +23,7 @@ namespace {
 
 constexpr int kMaxBeads = SOP_NOALLOC_MAX_BEADS;
 constexpr int kMaxCells = 2 * kMaxBeads + 8;                    // the streamed builder's cell budget
-constexpr int kScanTmp = (kMaxCells + 2047) / 2048 + 2;         // block sums of the cell scan
+constexpr int kScanTmp = (kMaxCells + sop::kScanTileElems - 1) / sop::kScanTileElems + 2;   // block sums of the cell scan
 
 // Scratch layout, in 32-bit words; each block starts on a 16-byte boundary.
 constexpr int align4(int w) { return (w + 3) / 4 * 4; }
@@ -171,9 +172,18 @@ extern "C" sop_status sop_pairlist_build_noalloc(const float *pos4, int32_t n, c
         return SOP_ERR_CUDA;
     }
     *nnz = out[0];
-    if (out[1] != 0) {
-        set_global_error("noalloc: the list outgrew cap (or a row held more than 256 partners)");
+    switch (out[1]) {
+    case 0: return SOP_OK;
+    case SOP_ERR_PAIRLIST_OVERFLOW:
+        set_global_error("noalloc: the list outgrew cap, or a row held more than " + std::to_string(kRowCandidates) +
+                         " candidates");
         return SOP_ERR_PAIRLIST_OVERFLOW;
+    case SOP_ERR_NONFINITE:
+        set_global_error("noalloc: a position is NaN or infinite, or no cell grid within the 2 n + 8 cell budget "
+                         "covers the system at this pair_cut; every row is empty");
+        return SOP_ERR_NONFINITE;
+    default:
+        set_global_error("noalloc: the rebuild stopped with status " + std::to_string(out[1]));
+        return (sop_status)out[1];
     }
-    return SOP_OK;
 }

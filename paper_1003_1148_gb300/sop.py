@@ -34,7 +34,7 @@ EXPORTED = ["sop_create", "sop_step", "sop_forces", "sop_pairlist_rebuild", "sop
             "sop_get_observables", "sop_get_state", "sop_set_state", "sop_replica_status", "sop_abort",
             "sop_get_stats", "sop_last_error", "sop_destroy", "sop_pairlist_build_noalloc", "sop_get_rng_state",
             "sop_set_rng_state", "sop_brownian_ramp", "sop_get_velocities", "sop_set_velocities",
-            "sop_box_muller", "sop_bead_noise"]
+            "sop_box_muller", "sop_bead_noise", "sop_fp32_peak"]
 INTEGRATOR_OVERDAMPED, INTEGRATOR_BAOAB = 0, 1
 INTEGRATORS = {"overdamped": INTEGRATOR_OVERDAMPED, "baoab": INTEGRATOR_BAOAB}
 RNG_PHILOX, RNG_HYBRID_TAUS = 0, 1
@@ -127,6 +127,7 @@ def load(path: str | None = None):
             "sop_set_velocities": ([vp, i32, vp], C.c_int),
             "sop_box_muller": ([vp, i64, vp, vp], C.c_int),
             "sop_bead_noise": ([C.c_uint64, i64, C.c_uint32, i64, vp, vp], C.c_int),
+            "sop_fp32_peak": ([f64, vp, vp, vp], C.c_int),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -353,6 +354,17 @@ def from_workload(w, n_replicas: int | None = None, schedule="auto", stream=None
         ind = w.indenter
         sim.indenter(ind.center, ind.direction, ind.radius, ind.v)
     return sim
+
+
+def fp32_peak(seconds: float = 0.5) -> dict:
+    """``sop_fp32_peak``: the measured FP32 FMA rate of the current device (TFLOP/s), the
+    duration of its last launch (ms) and the SM count."""
+    L = load()
+    t, ms, sms = C.c_double(0.0), C.c_double(0.0), C.c_int32(0)
+    rc = L.sop_fp32_peak(float(seconds), C.byref(t), C.byref(ms), C.byref(sms))
+    if rc != OK:
+        raise SopError(rc, L.sop_last_error(None).decode())
+    return {"tflops": t.value, "ms": ms.value, "sm_count": sms.value}
 
 
 def box_muller(x, stream=None):

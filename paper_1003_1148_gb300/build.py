@@ -19,8 +19,8 @@ ROOT = os.path.dirname(HERE)
 INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(HERE, "_lib")
 SO = os.path.join(OUT_DIR, "libsop.so")
-SOURCES = ["k_stream.cu", "k_pairs.cu", "k_batched.cu", "k_bpair.cu", "k_ramp.cu", "k_noise.cu", "k_peak.cu",
-           "sop_api.cu", "sop_noalloc.cu"]
+SOURCES = ["k_stream.cu", "k_pairs.cu", "k_batched.cu", "k_cluster.cu", "k_bpair.cu", "k_ramp.cu", "k_noise.cu",
+           "k_peak.cu", "sop_api.cu", "sop_noalloc.cu"]
 HEADERS = ["sop_device.cuh", "sop_internal.h", "sop_step.cuh", "batched_common.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -81,8 +81,9 @@ __device__ void block_boxes(const Lay &L, const float4 *src, int n_s) {
 // Hand the slots to beads by decreasing row length of the last build (counting sort).
 // Returns the index (0/1) of the new order buffer. Must be called by all threads.
 template <class Lay>
-__device__ int reorder_slots(const Lay &L, int n_s, int cur_order) {
+__device__ int reorder_slots(const Lay &L, int n_s, int cur_order, int round = 0) {
     const int T = blockDim.x;
+    const int U = round > 0 ? round : T;   // slots handed out per round (threads, or groups of lanes)
     auto *h = L.h();
     for (int k = threadIdx.x; k < kKeys; k += T) h->hist[k] = 0;
     __syncthreads();
@@ -108,12 +109,12 @@ __device__ int reorder_slots(const Lay &L, int n_s, int cur_order) {
     __syncthreads();
     const uint16_t *src = L.order(cur_order);
     uint16_t *dst = L.order(cur_order ^ 1);
-    const int full = n_s - n_s % T;   // slots in complete rounds of T
+    const int full = n_s - n_s % U;   // slots in complete rounds of U
     for (int p = threadIdx.x; p < n_s; p += T) {
         int pos = atomicAdd(&h->hist[kKeys - 1 - min((int)L.n_tot()[p], kKeys - 1)], 1);
         // boustrophedon: odd rounds run backwards, so a thread owning several slots gets
         // long and short rows alike and the warps of the CTA finish together
-        if (pos < full && ((pos / T) & 1)) pos = (pos / T) * T + (T - 1 - pos % T);
+        if (pos < full && ((pos / U) & 1)) pos = (pos / U) * U + (U - 1 - pos % U);
         dst[pos] = src[p];
     }
     __syncthreads();
@@ -306,7 +307,7 @@ __device__ __forceinline__ void obs_bonded(const StepArgs &sa, const float4 *P, 
     const double R02 = sa.R0 * sa.R0;
     if (bond_right) {
         const float4 pj = P[b + 1];
-        const double rr = __dsqrt_rn(dist2_d(xi, yi, zi, pj.x, pj.y, pj.z));
+        const double rr = sqrt_fast(dist2_d(xi, yi, zi, pj.x, pj.y, pj.z));
         const double dr = rr - t.bond_r0d[i];
         const double arg = 1.0 - dr * dr / R02;
         if (arg > 0.0) v[0] += -0.5 * sa.k_fene * R02 * log(arg);
@@ -317,10 +318,10 @@ __device__ __forceinline__ void obs_bonded(const StepArgs &sa, const float4 *P, 
         const float4 pj = P[j - b0];
         const double d2 = dist2_d(xi, yi, zi, pj.x, pj.y, pj.z);
         const double r0 = t.nat_r0[q];
-        const double u = r0 * r0 / d2;
+        const double u = r0 * r0 * rcp_fast(d2);
         const double u3 = u * u * u;
         v[0] += sa.eps_h * (u3 * u3 - 2.0 * u3);
-        if (__dsqrt_rn(d2) < r0 + 2.0) v[3] += 1.0;
+        if (native_formed(d2, r0)) v[3] += 1.0;
     }
 }
 
@@ -354,12 +355,12 @@ __device__ __forceinline__ void obs_external(const StepArgs &sa, const float4 *P
         const double c[3] = {e.ind_c0[0] + tt * e.ind_dir[0], e.ind_c0[1] + tt * e.ind_dir[1],
                              e.ind_c0[2] + tt * e.ind_dir[2]};
         const double ex = xi - c[0], ey = yi - c[1], ez = zi - c[2];
-        const double rr = __dsqrt_rn((ex * ex + ey * ey) + ez * ez);
+        const double rr = sqrt_fast((ex * ex + ey * ey) + ez * ez);
         const double rho = rr - e.ind_radius;
         if (rho > 0.0) {
-            const double qq = sa.sigma / rho;
+            const double qq = sa.sigma * rcp_fast(rho);
             const double q2 = qq * qq;
-            const double coef = 6.0 * sa.eps_l * (q2 * q2 * q2) / rho / rr;
+            const double coef = 6.0 * sa.eps_l * (q2 * q2 * q2) * rcp_fast(rho * rr);
             v[4] += coef * ((ex * e.ind_dir[0] + ey * e.ind_dir[1]) + ez * e.ind_dir[2]);
         }
     }

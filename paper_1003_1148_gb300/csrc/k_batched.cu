@@ -30,12 +30,9 @@
 // shared-memory broadcast). The natives' r0^2 come from a column-major table
 // in global memory shared by all replicas of a system. Observables (FP64) are
 // reduced in the CTA.
-#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include "batched_common.cuh"
-
-namespace cg = cooperative_groups;
 
 namespace sop {
 
@@ -260,7 +257,7 @@ __device__ __noinline__ void observe(const BatchedArgs &a, const Layout<RG> &L, 
             const int j = row[q * n_s + p];
             if (j < b) continue;
             const float4 pj = P[j];
-            const double c = sig2 / dist2_d(xi, yi, zi, pj.x, pj.y, pj.z);
+            const double c = sig2 * rcp_fast(dist2_d(xi, yi, zi, pj.x, pj.y, pj.z));
             v[0] += sa.eps_l * c * c * c;
         }
         obs_external(sa, P, b, b0, r, s, step, L.flags()[b], v);
@@ -404,391 +401,6 @@ __global__ void __launch_bounds__(MAXT, MINB) k_batched(BatchedArgs a) {
     if (threadIdx.x == 0 && L.h()->fail != 0) atomicCAS(&sa.rep_status[r], 0, L.h()->fail);
 }
 
-// ===========================================================================
-// Cluster form: one system over a thread-block cluster (distributed shared
-// memory). CTA q of a cluster of C owns the system's beads [q m, (q + 1) m),
-// m = 2^m_shift a multiple of 32: their compensation, bond lengths, slot orders
-// and rows live in its shared memory, next to a full copy of the positions of the
-// whole system (both time layers). All reads are local: a CTA gathers forces and
-// builds rows exactly as the one-CTA form does, from its own copy. After the
-// update each CTA writes the new positions of its own beads into every copy in
-// the cluster (stores to distributed shared memory), and one cluster barrier
-// (release/acquire) ends the step. A copy's layer is only ever written while
-// every CTA reads the other layer, so no read meets a remote write. Every CTA of
-// a cluster takes the same sequence of cluster barriers: each control decision
-// (a frozen replica, a failure, the rebuild and observable cadence) comes from
-// values every CTA reads after the same barrier.
-// ===========================================================================
-constexpr int kMaxCluster = 16;
-constexpr int kNoFail = 0x7fffffff;
-
-struct ClusterExtra {
-    int fail_step;                        // first step of the launch at which this CTA failed
-    int frozen;                           // rank 0: the replica was frozen at launch
-    double part[6];                       // this CTA's observable sums
-    float4 *rpos[2][kMaxCluster];         // every rank's two position layers (generic addresses)
-    const ClusterExtra *peer[kMaxCluster];
-};
-
-// Shared-memory layout of one CTA of the cluster form: positions of all n_max = C m
-// beads (two layers), then own-bead state for m beads, block boxes of the whole
-// system, rows of the own slots, and the cluster bookkeeping.
-struct CLayout {
-    int nmax, m, rw;
-    __device__ __forceinline__ SharedHead *h() const { return reinterpret_cast<SharedHead *>(g_smem); }
-    __device__ __forceinline__ float4 *pos(int layer) const {
-        return reinterpret_cast<float4 *>(g_smem + kHeadBytes) + (size_t)layer * nmax;
-    }
-    __device__ __forceinline__ float4 *comp() const { return pos(2); }
-    __device__ __forceinline__ float2 *bond() const { return reinterpret_cast<float2 *>(comp() + m); }
-    __device__ __forceinline__ uint16_t *order(int i) const {
-        return reinterpret_cast<uint16_t *>(bond() + m) + i * m;
-    }
-    __device__ __forceinline__ uint16_t *n_nat() const { return order(2); }
-    __device__ __forceinline__ uint16_t *n_tot() const { return order(3); }
-    __device__ __forceinline__ uint16_t *slot_of() const { return order(4); }   // by own bead: its slot
-    __device__ __forceinline__ uint8_t *flags() const { return reinterpret_cast<uint8_t *>(order(5)); }
-    __device__ __forceinline__ float4 *bbox() const {
-        const size_t off = (kHeadBytes + 32 * (size_t)nmax + 16 * (size_t)m + 8 * (size_t)m + 10 * (size_t)m + m + 15)
-                           / 16 * 16;
-        return reinterpret_cast<float4 *>(g_smem + off);
-    }
-    __device__ __forceinline__ uint16_t *row() const { return reinterpret_cast<uint16_t *>(bbox() + nmax / 16); }
-    __device__ __forceinline__ ClusterExtra *extra() const {
-        const size_t off = ((reinterpret_cast<unsigned char *>(row() + (size_t)rw * m) - g_smem) + 15) / 16 * 16;
-        return reinterpret_cast<ClusterExtra *>(g_smem + off);
-    }
-};
-
-__host__ __device__ inline size_t cluster_smem(int m, int nmax, int row_width) {
-    size_t s = kHeadBytes + 32 * (size_t)nmax + 16 * (size_t)m + 8 * (size_t)m + 10 * (size_t)m + m;
-    s = (s + 15) / 16 * 16;
-    s += 2 * sizeof(float4) * (size_t)(nmax / 32);
-    s += sizeof(uint16_t) * (size_t)row_width * m;
-    s = (s + 15) / 16 * 16;
-    return s + (sizeof(ClusterExtra) + 15) / 16 * 16;
-}
-
-// Rows of this CTA's slots from layer `layer` of its copy (system-local bead indices).
-// The block boxes of the whole system and slot_of must be current. A thread builds the
-// rows of own beads threadIdx.x + k * blockDim, so that a warp scans for 32 consecutive
-// beads and the box test skips blocks for all its lanes at once (as in rebuild_rows).
-template <int BPT>
-__device__ void cluster_rows(const BatchedArgs &a, const CLayout &L, const uint16_t *order, int layer, int n_loc,
-                             int lo, int n_s, int nat_off, int b0) {
-    const int T = blockDim.x, m = L.m;
-    const float cut2 = a.sa.cut2_f;
-    const float hi2 = cut2 + cut2 * 1e-4f;
-    const float4 *src = L.pos(layer);
-    const float4 *bb = L.bbox();
-    uint16_t *row = L.row();
-    (void)order;
-#pragma unroll 1
-    for (int k = 0; k < BPT; ++k) {
-        const int l = threadIdx.x + k * T;
-        if (l >= n_loc) continue;
-        const int p = L.slot_of()[l];
-        const int b = lo + l;
-        const float4 pb = src[b];
-        const int nn = a.nat_ell_cnt[b0 + b];
-        const uint16_t *natc = a.nat_ell_col + nat_off + b;
-        for (int q = 0; q < nn; ++q) row[q * m + p] = __ldg(natc + q * n_s);
-        const float2 bd = L.bond()[l];
-        int q = 0;
-        int next_nat = nn > 0 ? (int)__ldg(natc) : 0x7fffffff;
-        int cnt = 0;
-        for (int base = 0; base < n_s; base += 32) {
-            const float4 blo = bb[base >> 4], bhi = bb[(base >> 4) + 1];
-            const float ex = fmaxf(fmaxf(blo.x - pb.x, pb.x - bhi.x), 0.f);
-            const float ey = fmaxf(fmaxf(blo.y - pb.y, pb.y - bhi.y), 0.f);
-            const float ez = fmaxf(fmaxf(blo.z - pb.z, pb.z - bhi.z), 0.f);
-            uint32_t cand = 0u;
-            if (fmaf(ez, ez, fmaf(ey, ey, ex * ex)) < hi2) cand = scan_block_f4(src, base, n_s - base, pb, hi2);
-            uint32_t ex_mask = 0u;
-            if (b >= base && b < base + 32) ex_mask |= 1u << (b - base);
-            if (bd.x > 0.f && b - 1 >= base && b - 1 < base + 32) ex_mask |= 1u << (b - 1 - base);
-            if (bd.y > 0.f && b + 1 >= base && b + 1 < base + 32) ex_mask |= 1u << (b + 1 - base);
-            while (next_nat < base + 32) {
-                ex_mask |= 1u << (next_nat - base);
-                ++q;
-                next_nat = q < nn ? (int)__ldg(natc + q * n_s) : 0x7fffffff;
-            }
-            cand &= ~ex_mask;
-            while (cand) {   // ascending: the exact decision, then the row entry
-                const int t = __ffs(cand) - 1;
-                cand &= cand - 1;
-                if (!within_cut(pb, src[base + t], cut2, a.sa.cut2_d)) continue;
-                if (cnt < a.cap) row[(nn + cnt) * m + p] = (uint16_t)(base + t);
-                ++cnt;
-            }
-        }
-        if (cnt > a.cap) cta_fail(L.h(), SOP_ERR_PAIRLIST_OVERFLOW);
-        L.n_nat()[p] = (uint16_t)nn;
-        L.n_tot()[p] = (uint16_t)(nn + min(cnt, a.cap));
-    }
-}
-
-// Rebuild from layer `layer` of the local copy: boxes of every block of the system, the
-// own slot order and rows. Local only; ends with a CTA barrier.
-template <int BPT>
-__device__ int cluster_rebuild(const BatchedArgs &a, const CLayout &L, int layer, int n_loc, int lo, int n_s,
-                               int nat_off, int b0, int ord) {
-    block_boxes(L, L.pos(layer), n_s);
-    ord = reorder_slots(L, n_loc, ord);   // its barriers also publish the boxes
-    const uint16_t *o = L.order(ord);
-    for (int p = threadIdx.x; p < n_loc; p += blockDim.x) L.slot_of()[o[p]] = (uint16_t)p;
-    __syncthreads();
-    cluster_rows<BPT>(a, L, L.order(ord), layer, n_loc, lo, n_s, nat_off, b0);
-    __syncthreads();
-    return ord;
-}
-
-// Eq. 1 pair forces on own bead l (system bead b, slot p) at layer P of the local copy.
-__device__ __forceinline__ float3 cluster_force(const BatchedArgs &a, const CLayout &L, const float4 *P, int n_s,
-                                                int nat_off, int l, int b, int p, bool *broken) {
-    const ForceParams &fp = a.sa.fp;
-    const int m = L.m;
-    const float4 pb = P[b];
-    float fx = 0.f, fy = 0.f, fz = 0.f;
-    const float2 bd = L.bond()[l];
-#pragma unroll
-    for (int side = 0; side < 2; ++side) {
-        const float r0 = side ? bd.y : bd.x;
-        if (r0 > 0.f) {
-            const float4 pj = P[side ? b + 1 : b - 1];
-            const float dx = pb.x - pj.x, dy = pb.y - pj.y, dz = pb.z - pj.z;
-            const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-            const float r = r2 * rsqrtf(r2);
-            const float dr = r - r0;
-            const float arg = fmaf(-dr * dr, fp.inv_R02, 1.0f);
-            float c = 0.f;
-            if (arg > 0.f) c = __fdividef(-fp.k_fene * dr, arg * r);
-            else *broken = true;
-            fx = fmaf(c, dx, fx); fy = fmaf(c, dy, fy); fz = fmaf(c, dz, fz);
-        }
-    }
-    const int nn = L.n_nat()[p], tot = L.n_tot()[p];
-    const float3 fr = row_force(P, pb, L.row() + p, a.nat_ell_r0sq + nat_off + b, nn, tot, m, n_s, fp);
-    return make_float3(fx + fr.x, fy + fr.y, fz + fr.z);
-}
-
-// FP64 observables of the cluster's system at layer P: every CTA sums its own beads, rank
-// 0 adds the CTA sums after a cluster barrier and writes the record.
-template <int BPT>
-__device__ __noinline__ void cluster_observe(const BatchedArgs &a, const CLayout &L, ClusterExtra *X,
-                                             const uint16_t *order, const float4 *P, int n_loc, int lo, int b0,
-                                             int r, int s, int g, int64_t step, int64_t event, int rank, int C) {
-    const StepArgs &sa = a.sa;
-    const int T = blockDim.x, m = L.m;
-    const uint16_t *row = L.row();
-    double v[6] = {0, 0, 0, 0, 0, 0};   // E, f_pull, ext, formed, f_wall, r_ee
-    const double sig2 = sa.sigma * sa.sigma;
-    for (int k = 0; k < BPT; ++k) {
-        const int p = threadIdx.x + k * T;
-        if (p >= n_loc) continue;
-        const int l = order[p];
-        const int b = lo + l;
-        const float4 pb = P[b];
-        const double xi = pb.x, yi = pb.y, zi = pb.z;
-        obs_bonded(sa, P, b, b0, L.bond()[l].y > 0.f, v);
-        for (int q = L.n_nat()[p]; q < L.n_tot()[p]; ++q) {
-            const int j = row[q * m + p];
-            if (j < b) continue;
-            const float4 pj = P[j];
-            const double c = sig2 / dist2_d(xi, yi, zi, pj.x, pj.y, pj.z);
-            v[0] += sa.eps_l * c * c * c;
-        }
-        obs_external(sa, P, b, b0, r, s, step, L.flags()[l], v);
-    }
-    block_sum6(v, L.h());
-    if (threadIdx.x == 0)
-        for (int k = 0; k < 6; ++k) X->part[k] = v[k];
-    cg::this_cluster().sync();
-    if (rank == 0 && threadIdx.x == 0) {
-        double w[6] = {0, 0, 0, 0, 0, 0};
-        for (int q = 0; q < C; ++q)
-            for (int k = 0; k < 6; ++k) w[k] += X->peer[q]->part[k];
-        write_record(a, w, r, s, g, step, event);
-    }
-    __syncthreads();
-}
-
-template <int BPT, int MAXT>
-__global__ void __launch_bounds__(MAXT, 1) k_cluster(BatchedArgs a, int sh) {
-    cg::cluster_group cl = cg::this_cluster();
-    const int rank = (int)cl.block_rank();
-    const int C = (int)cl.num_blocks();
-    const int item = blockIdx.x / C;
-    CLayout L;
-    L.m = 1 << sh;
-    L.nmax = C << sh;
-    L.rw = a.row_width;
-    ClusterExtra *X = L.extra();
-    const int r = a.item_rep[item], s = a.item_sys[item];
-    const StepArgs &sa = a.sa;
-    const DevTopo &t = sa.topo;
-    const int b0 = t.sys_lo[s], n_s = t.sys_lo[s + 1] - b0;
-    const int lo = rank * L.m;
-    const int n_loc = max(0, min(L.m, n_s - lo));
-    const int gbase = r * t.n + b0;
-    const int g = r * t.n_sys + s;
-    const int nat_off = a.nat_ell_off[s];
-    const int T = blockDim.x;
-    const int64_t step0 = *a.d_step;
-    const bool forces_only = (a.n_steps == 0 && a.force_out != nullptr);
-    if (threadIdx.x == 0) {
-        L.h()->fail = 0;
-        X->fail_step = kNoFail;
-        X->frozen = (!forces_only && (sa.rep_status[r] != 0 || *sa.halt != 0)) ? 1 : 0;
-    }
-    for (int k = threadIdx.x; k < 3 * C; k += T) {
-        if (k < 2 * C) X->rpos[k / C][k % C] = cl.map_shared_rank(L.pos(k / C), k % C);
-        else X->peer[k - 2 * C] = cl.map_shared_rank(X, k - 2 * C);
-    }
-    int k_phase = (int)(step0 % a.K);
-    int o_phase = a.obs_every > 0 ? (int)(step0 % a.obs_every) : 0;
-    // the whole system into the local copy (and the snapshot of the last rebuild into layer 1)
-    for (int b = threadIdx.x; b < n_s; b += T) {
-        L.pos(0)[b] = a.pos[gbase + b];
-        if (k_phase != 0 && !forces_only) L.pos(1)[b] = a.snap[gbase + b];
-    }
-    for (int l = threadIdx.x; l < n_loc; l += T) {
-        const int b = lo + l, i = b0 + b;
-        L.comp()[l] = a.comp[gbase + b];
-        L.bond()[l] = make_float2(b > 0 ? t.bond_r0[i - 1] : -1.f, t.bond_r0[i]);
-        L.flags()[l] = t.flags[i];
-        L.order(0)[l] = (uint16_t)l;
-        L.n_tot()[l] = (uint16_t)a.nat_ell_cnt[i];
-    }
-    cl.sync();   // every copy is loaded before any CTA writes into another
-    const bool frozen = X->peer[0]->frozen != 0;   // rank 0's reading, the same for every CTA
-    if (frozen) {
-        if (rank == 0 && threadIdx.x == 0)
-            missing_records(a, r, s, g, step0, step0, a.d_events ? *a.d_events : 0);
-        cl.sync();   // no CTA leaves while another may still read its shared memory
-        return;
-    }
-
-    int cur = 0, ord = 0, n_events = 0;
-    bool built_now = false;
-    int it = 0;
-    for (; it < a.n_steps || (forces_only && it == 0); ++it) {
-        if (it == 0 && k_phase != 0 && !forces_only) {
-            ord = cluster_rebuild<BPT>(a, L, 1, n_loc, lo, n_s, nat_off, b0, ord);   // from the snapshot
-            cl.sync();   // layer 1 is read by every CTA before the step writes it
-        } else if ((k_phase == 0 && !built_now) || forces_only) {
-            ord = cluster_rebuild<BPT>(a, L, cur, n_loc, lo, n_s, nat_off, b0, ord);
-            if (!forces_only && it + a.K >= a.n_steps)
-                for (int l = threadIdx.x; l < n_loc; l += T) a.snap[gbase + lo + l] = L.pos(cur)[lo + l];
-        }
-        built_now = false;
-        const int64_t step = step0 + it;
-        const uint16_t *order = L.order(ord);
-        const float4 *P = L.pos(cur);
-        if (forces_only) {
-            for (int p = threadIdx.x; p < n_loc; p += T) {
-                const int l = order[p], b = lo + l;
-                bool broken = false, overlap = false;
-                const float3 f = cluster_force(a, L, P, n_s, nat_off, l, b, p, &broken);
-                const float3 fe = ext_force(sa, r, b0 + b, L.flags()[l], P[b], step, &overlap);
-                a.force_out[gbase + b] = make_float4(f.x + fe.x, f.y + fe.y, f.z + fe.z, (broken || overlap) ? 1.f : 0.f);
-                if (a.pl_dump_col) {
-                    const size_t rowi = (size_t)gbase + b;
-                    const int nn = L.n_nat()[p], np = L.n_tot()[p] - nn;
-                    a.pl_dump_start[rowi] = (int)(rowi * a.pl_dump_stride);
-                    a.pl_dump_len[rowi] = np;
-                    for (int q = 0; q < np; ++q)
-                        a.pl_dump_col[rowi * a.pl_dump_stride + q] = b0 + (int)L.row()[(nn + q) * L.m + p];
-                }
-            }
-            break;
-        }
-        const int nxt = cur ^ 1;
-#pragma unroll 1
-        for (int k = 0; k < BPT; ++k) {
-            const int p = threadIdx.x + k * T;
-            if (p >= n_loc) continue;
-            const int l = order[p], b = lo + l;
-            bool broken = false, overlap = false;
-            const float3 f = cluster_force(a, L, P, n_s, nat_off, l, b, p, &broken);
-            const float4 p_old = P[b];
-            const uint8_t fl = L.flags()[l];
-            const float3 fe = ext_force(sa, r, b0 + b, fl, p_old, step, &overlap);
-            float4 pb = p_old;
-            if (broken || overlap) {
-                cta_fail(L.h(), broken ? SOP_ERR_FENE_BREAK : SOP_ERR_INDENTER_OVERLAP);
-            } else if (!(fl & kFlagFixed)) {
-                float4 c = L.comp()[l];
-                if (update_position(sa, r, b0 + b, (size_t)gbase + b, pb, c,
-                                    make_float3(f.x + fe.x, f.y + fe.y, f.z + fe.z), step))
-                    L.comp()[l] = c;
-                else
-                    cta_fail(L.h(), SOP_ERR_NONFINITE);
-            }
-            // the new position into every copy of the cluster
-            for (int q = 0; q < C; ++q) X->rpos[nxt][q][b] = pb;
-        }
-        __syncthreads();
-        if (threadIdx.x == 0 && L.h()->fail != 0 && X->fail_step == kNoFail) X->fail_step = it;
-        cl.sync();   // the next layer is complete in every copy
-        cur = nxt;
-        k_phase = k_phase + 1 == a.K ? 0 : k_phase + 1;
-        if (a.obs_every > 0) o_phase = o_phase + 1 == a.obs_every ? 0 : o_phase + 1;
-        // the replica freezes after the step in which any CTA failed (every CTA decides
-        // from the same values: a CTA's fail_step is written once, before a barrier)
-        bool stop = false;
-        for (int q = 0; q < C; ++q) stop |= X->peer[q]->fail_step <= it;
-        if (stop) { ++it; break; }
-        if (a.obs_every > 0 && o_phase == 0) {
-            if (k_phase == 0) {
-                ord = cluster_rebuild<BPT>(a, L, cur, n_loc, lo, n_s, nat_off, b0, ord);
-                built_now = true;
-                if (it + 1 + a.K >= a.n_steps)
-                    for (int l = threadIdx.x; l < n_loc; l += T) a.snap[gbase + lo + l] = L.pos(cur)[lo + l];
-            }
-            const int64_t ev = (a.d_events ? *a.d_events : 0) + n_events;
-            cluster_observe<BPT>(a, L, X, L.order(ord), L.pos(cur), n_loc, lo, b0, r, s, g, step + 1, ev, rank, C);
-            ++n_events;
-        }
-    }
-    if (!forces_only) {
-        bool failed = false;
-        for (int q = 0; q < C; ++q) failed |= X->peer[q]->fail_step != kNoFail;
-        if (failed && rank == 0 && threadIdx.x == 0)
-            missing_records(a, r, s, g, step0, step0 + it - 1, (a.d_events ? *a.d_events : 0) + n_events);
-        for (int l = threadIdx.x; l < n_loc; l += T) {
-            a.pos[gbase + lo + l] = L.pos(cur)[lo + l];
-            a.comp[gbase + lo + l] = L.comp()[l];
-        }
-        if (threadIdx.x == 0 && L.h()->fail != 0) atomicCAS(&sa.rep_status[r], 0, L.h()->fail);
-    }
-    cl.sync();   // no CTA leaves while another may still read its shared memory
-}
-
-template <int BPT, int MAXT>
-cudaError_t launch_cl(const BatchedArgs &a, const BatchedConfig &cfg, cudaStream_t s) {
-    auto kern = k_cluster<BPT, MAXT>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cfg.smem);
-    if (e != cudaSuccess) return e;
-    if (cfg.cluster > 8) {
-        e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-        if (e != cudaSuccess) return e;
-    }
-    cudaLaunchConfig_t lc = {};
-    lc.gridDim = dim3((unsigned)(a.n_items * cfg.cluster), 1, 1);
-    lc.blockDim = dim3((unsigned)cfg.threads, 1, 1);
-    lc.dynamicSmemBytes = cfg.smem;
-    lc.stream = s;
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeClusterDimension;
-    at[0].val.clusterDim.x = (unsigned)cfg.cluster;
-    at[0].val.clusterDim.y = 1;
-    at[0].val.clusterDim.z = 1;
-    lc.attrs = at;
-    lc.numAttrs = 1;
-    return cudaLaunchKernelEx(&lc, kern, a, cfg.m_shift);
-}
-
 template <int BPT, int MINB, int MAXT, bool RG>
 cudaError_t launch_t(const BatchedArgs &a, const BatchedConfig &cfg, cudaStream_t s) {
     auto kern = k_batched<BPT, MINB, MAXT, RG>;
@@ -829,58 +441,11 @@ bool batched_config(int max_n, int row_width, int threads, bool rows_global, int
     return cfg->smem <= 227 * 1024;
 }
 
-bool cluster_config(int max_n, int row_width, int threads, int m_shift, BatchedConfig *cfg) {
-    if (m_shift < 5 || m_shift > 9 || max_n <= 0 || max_n > 8192 || row_width > kKeys - 1) return false;
-    const int m = 1 << m_shift;
-    const int C = (max_n + m - 1) / m;
-    if (C < 2 || C > kMaxCluster || threads % 32 || threads < 32 || threads > 512) return false;
-    const int bpt = (m + threads - 1) / threads;
-    if (bpt > 2) return false;
-    cfg->threads = threads;
-    cfg->beads_per_thread = bpt;
-    cfg->min_blocks = 1;
-    cfg->rows_global = false;
-    cfg->row_width = row_width;
-    cfg->smem = cluster_smem(m, C * m, row_width);
-    cfg->cluster = C;
-    cfg->m_shift = m_shift;
-    return cfg->smem <= 227 * 1024;
-}
-
-// Clusters of this configuration that can be resident at once (0: it cannot launch).
-int cluster_capacity(const BatchedConfig &cfg) {
-    if (cfg.cluster <= 0) return 0;
-    auto kern = cfg.beads_per_thread == 1 ? k_cluster<1, 512> : k_cluster<2, 512>;
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cfg.smem) != cudaSuccess ||
-        (cfg.cluster > 8 && cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)) {
-        cudaGetLastError();
-        return 0;
-    }
-    cudaLaunchConfig_t lc = {};
-    lc.gridDim = dim3((unsigned)cfg.cluster, 1, 1);
-    lc.blockDim = dim3((unsigned)cfg.threads, 1, 1);
-    lc.dynamicSmemBytes = cfg.smem;
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeClusterDimension;
-    at[0].val.clusterDim.x = (unsigned)cfg.cluster;
-    at[0].val.clusterDim.y = 1;
-    at[0].val.clusterDim.z = 1;
-    lc.attrs = at;
-    lc.numAttrs = 1;
-    int n = 0;
-    if (cudaOccupancyMaxActiveClusters(&n, kern, &lc) != cudaSuccess) {
-        cudaGetLastError();
-        return 0;
-    }
-    return n;
-}
-
 cudaError_t launch_batched(const BatchedArgs &a, const BatchedConfig &cfg, cudaStream_t s, int64_t *launches) {
     if (a.n_items <= 0) return cudaSuccess;
     if (launches) *launches += 1;
     if (cfg.pair_form) return launch_bpair(a, cfg, s);
-    if (cfg.cluster > 0)
-        return cfg.beads_per_thread == 1 ? launch_cl<1, 512>(a, cfg, s) : launch_cl<2, 512>(a, cfg, s);
+    if (cfg.cluster > 0) return launch_cluster(a, cfg, s);
     if (cfg.rows_global) {
         switch (cfg.beads_per_thread) {
         case 1: return launch_t<1, 1, 1024, true>(a, cfg, s);

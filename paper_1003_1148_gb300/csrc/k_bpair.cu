@@ -375,7 +375,7 @@ __device__ __noinline__ void pair_observe(const BatchedArgs &a, const PLayout &L
         const uint16_t *rp = L.rows() + L.h()->b_own[p >> 5] + (p & 31);
         for (int q = L.n_own_nat()[p]; q < L.n_own()[p]; ++q) {
             const float4 pj = P[rp[32 * q]];
-            const double c = sig2 / dist2_d(xi, yi, zi, pj.x, pj.y, pj.z);
+            const double c = sig2 * rcp_fast(dist2_d(xi, yi, zi, pj.x, pj.y, pj.z));
             v[0] += sa.eps_l * c * c * c;
         }
         obs_external(sa, P, b, b0, r, s, step, L.flags()[b], v);

@@ -3,8 +3,10 @@
 //   setup      bonds and the native contact map (Eq. 1, Sec. IV.A), FP64 exact
 //   rebuild    Verlet list (Sec. III.A, Algorithm 3) from a cell list built by
 //              counting sort: per-segment bounding box -> cell id per bead ->
-//              histogram -> exclusive scan -> scatter -> per-cell order; then one
-//              warp per bead scans its 27 cells and writes its sorted row
+//              histogram -> exclusive scan -> scatter (one CTA per segment in shared
+//              memory when every segment of the launch is small, else one kernel per
+//              stage over global memory); then one warp per bead scans its 27 cells
+//              and writes its row, ranked ascending
 //   step       fused forces (Eq. 1 over bonds, natives and the list, each bead
 //              gathered by a group of L lanes with a shuffle reduction, as in
 //              the particle-based Algorithm 2) + cantilever/indenter + Philox
@@ -175,6 +177,40 @@ struct RebuildArgs {
     int32_t *rep_status;
 };
 
+// The cell grid of segment g from its bounding box [l, h]: cubic cells of edge >= cutoff,
+// at most the segment's cell budget of them (the edge grows by a quarter until the grid
+// fits). A skipped segment (bad = true, or no grid fits) gets one empty cell and, when it
+// holds beads, fails its replica.
+__device__ void seg_grid(const RebuildArgs &a, int g, float l[3], const float h[3], bool bad, bool has_beads) {
+    const int budget = a.seg_cell_base[g + 1] - a.seg_cell_base[g];
+    float edge = a.cell_edge;
+    int d[3] = {1, 1, 1};
+    bool skip = bad;
+    if (!skip) {
+        bool fit = false;
+        for (int it = 0; it < 64 && !fit; ++it) {
+            long long prod = 1;
+            for (int k = 0; k < 3; ++k) {
+                const float e = (h[k] - l[k]) / edge;
+                d[k] = e < 1e6f ? (int)floorf(e) + 1 : 1000000;
+                prod *= d[k];
+            }
+            if (prod <= budget) fit = true;
+            else edge *= 1.25f;
+        }
+        if (!fit) {
+            d[0] = d[1] = d[2] = 1;
+            skip = true;
+        }
+    }
+    if (skip) {
+        l[0] = l[1] = l[2] = 0.0f;
+        if (has_beads) atomicCAS(&a.rep_status[g / a.n_sys], 0, (int32_t)SOP_ERR_NONFINITE);
+    }
+    a.seg_lo[g] = make_float4(l[0], l[1], l[2], 1.0f / edge);
+    a.seg_dims[g] = make_int4(d[0], d[1], d[2], skip ? 0 : d[0] * d[1] * d[2]);
+}
+
 // One CTA per segment: bounding box, then a grid of cubic cells of edge >= cutoff
 // with at most the segment's cell budget. A segment whose replica has failed is
 // skipped by the whole rebuild (dims.w = 0: no bead is binned and its rows stay empty):
@@ -245,33 +281,7 @@ __global__ void k_seg_setup(RebuildArgs a, int32_t *pl_cursor, const int64_t *pl
             h[k] = smx[k][0];
             for (int q = 1; q < nw; ++q) { l[k] = fminf(l[k], smn[k][q]); h[k] = fmaxf(h[k], smx[k][q]); }
         }
-        const int budget = a.seg_cell_base[g + 1] - a.seg_cell_base[g];
-        float edge = a.cell_edge;
-        int d[3] = {1, 1, 1};
-        bool skip = sbad != 0 || hi <= lo;
-        if (!skip) {
-            bool fit = false;
-            for (int it = 0; it < 64 && !fit; ++it) {
-                long long prod = 1;
-                for (int k = 0; k < 3; ++k) {
-                    const float e = (h[k] - l[k]) / edge;
-                    d[k] = e < 1e6f ? (int)floorf(e) + 1 : 1000000;
-                    prod *= d[k];
-                }
-                if (prod <= budget) fit = true;
-                else edge *= 1.25f;
-            }
-            if (!fit) {
-                d[0] = d[1] = d[2] = 1;
-                skip = true;
-            }
-        }
-        if (skip) {
-            l[0] = l[1] = l[2] = 0.0f;
-            if (hi > lo) atomicCAS(&a.rep_status[g / a.n_sys], 0, (int32_t)SOP_ERR_NONFINITE);
-        }
-        a.seg_lo[g] = make_float4(l[0], l[1], l[2], 1.0f / edge);
-        a.seg_dims[g] = make_int4(d[0], d[1], d[2], skip ? 0 : d[0] * d[1] * d[2]);
+        seg_grid(a, g, l, h, sbad != 0 || hi <= lo, hi > lo);
         if (pl_cursor) pl_cursor[g] = (int32_t)pl_seg_base[g];
     }
 }
@@ -326,20 +336,118 @@ __global__ void k_cell_scatter(RebuildArgs a, int b_lo, int b_hi) {
     a.sorted[a.sorted_base + a.cell_start[gc - a.cell_base0] + slot] = gb;
 }
 
-// Beads of a cell in ascending order, so that every later traversal is deterministic.
-__global__ void k_cell_sort(RebuildArgs a, int c_lo, int c_hi) {
-    const int c = c_lo + blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= c_hi) return;
-    const int s = a.sorted_base + a.cell_start[c - a.cell_base0];
-    const int e = a.sorted_base + a.cell_start[c - a.cell_base0 + 1];
-    for (int k = s + 1; k < e; ++k) {
-        const int v = a.sorted[k];
-        int m = k - 1;
-        while (m >= s && a.sorted[m] > v) {
-            a.sorted[m + 1] = a.sorted[m];
-            --m;
+constexpr int kFuseBeads = 8192;   // segments up to this size build their cell list in one CTA
+
+// The cell list of one small segment in one CTA, in shared memory: bounding box, grid, cell
+// of each bead, histogram, exclusive scan, scatter. The same grid, cell starts and cell
+// contents as the staged kernels (k_seg_setup, k_cell_count, the scan, k_cell_scatter), in
+// one launch. Dynamic shared memory: the segment's cell budget of counters, then the cell
+// of each of its beads.
+__global__ void k_cell_build(RebuildArgs a, int32_t *pl_cursor, const int64_t *pl_seg_base) {
+    extern __shared__ int32_t sm_cells[];
+    __shared__ float smn[3][32], smx[3][32];
+    __shared__ int sbad;
+    __shared__ int wsum[32];
+    const int g = a.g_lo + blockIdx.x;
+    const int lo = a.seg_bead_lo[g], hi = a.seg_bead_lo[g + 1], nb = hi - lo;
+    const int cb = a.seg_cell_base[g], budget = a.seg_cell_base[g + 1] - cb;
+    int32_t *cnt = sm_cells;
+    int32_t *cof = sm_cells + budget;
+    const int T = blockDim.x, lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = T >> 5;
+    const bool failed = a.rep_status[g / a.n_sys] != 0;   // CTA-uniform
+    for (int k = threadIdx.x; k < budget; k += T) cnt[k] = 0;
+    if (threadIdx.x == 0) sbad = 0;
+    float mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
+    bool bad = false;
+    for (int b = lo + threadIdx.x; b < hi; b += T) {
+        const float4 p = a.pos[b];
+        if (a.snap) a.snap[b] = p;
+        const float v[3] = {p.x, p.y, p.z};
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            if (!isfinite(v[k])) bad = true;
+            mn[k] = fminf(mn[k], v[k]);
+            mx[k] = fmaxf(mx[k], v[k]);
         }
-        a.sorted[m + 1] = v;
+    }
+    __syncthreads();
+    if (bad) sbad = 1;
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+        for (int o = 16; o > 0; o >>= 1) {
+            mn[k] = fminf(mn[k], __shfl_xor_sync(0xffffffffu, mn[k], o));
+            mx[k] = fmaxf(mx[k], __shfl_xor_sync(0xffffffffu, mx[k], o));
+        }
+    if (lane == 0)
+        for (int k = 0; k < 3; ++k) { smn[k][w] = mn[k]; smx[k][w] = mx[k]; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float l[3], h[3];
+        for (int k = 0; k < 3; ++k) {
+            l[k] = smn[k][0];
+            h[k] = smx[k][0];
+            for (int q = 1; q < nw; ++q) { l[k] = fminf(l[k], smn[k][q]); h[k] = fmaxf(h[k], smx[k][q]); }
+        }
+        // a failed replica's segment is skipped (its frozen positions may lie anywhere)
+        seg_grid(a, g, l, h, failed || sbad != 0 || nb <= 0, !failed && nb > 0);
+        if (pl_cursor) pl_cursor[g] = (int32_t)pl_seg_base[g];
+    }
+    __syncthreads();
+    const float4 sl = a.seg_lo[g];
+    const int4 d = a.seg_dims[g];
+    for (int b = lo + threadIdx.x; b < hi; b += T) {
+        if (d.w == 0) {   // skipped segment: the bead is not binned
+            cof[b - lo] = -1;
+            continue;
+        }
+        const float4 p = a.pos[b];
+        int cx = 0, cy = 0, cz = 0;
+        if (isfinite(p.x) && isfinite(p.y) && isfinite(p.z)) {
+            cx = cell_coord(p.x, sl.x, sl.w, d.x);
+            cy = cell_coord(p.y, sl.y, sl.w, d.y);
+            cz = cell_coord(p.z, sl.z, sl.w, d.z);
+        }
+        const int c = (cz * d.y + cy) * d.x + cx;   // < d.w <= budget (seg_grid)
+        cof[b - lo] = c;
+        atomicAdd(&cnt[c], 1);
+    }
+    __syncthreads();
+    // exclusive scan of the counters: contiguous runs per thread, then warp and block sums
+    const int per = (budget + T - 1) / T;
+    const int k0 = min(budget, threadIdx.x * per), k1 = min(budget, k0 + per);
+    int run = 0;
+    for (int k = k0; k < k1; ++k) run += cnt[k];
+    int inc = run;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += t;
+    }
+    if (lane == 31) wsum[w] = inc;
+    __syncthreads();
+    if (w == 0) {
+        int v = lane < nw ? wsum[lane] : 0;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, v, o);
+            if (lane >= o) v += t;
+        }
+        if (lane < nw) wsum[lane] = v;   // inclusive over warps
+    }
+    __syncthreads();
+    int acc = (w > 0 ? wsum[w - 1] : 0) + inc - run;
+    const int base = lo - a.sorted_base;   // the segment's first position in `sorted`
+    int32_t *start = a.cell_start + (cb - a.cell_base0);
+    for (int k = k0; k < k1; ++k) {
+        const int c = cnt[k];
+        cnt[k] = acc;
+        start[k] = base + acc;
+        acc += c;
+    }
+    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) start[budget] = base + nb;   // the launch's end
+    __syncthreads();
+    for (int b = lo + threadIdx.x; b < hi; b += T) {
+        const int c = cof[b - lo];
+        if (c < 0) continue;
+        a.sorted[a.sorted_base + base + atomicAdd(&cnt[c], 1)] = b;
     }
 }
 
@@ -680,7 +788,7 @@ __global__ void __launch_bounds__(256) k_forces(StepArgs a, DevPairList pl, cons
 // ---------------------------------------------------------------------------
 // Observables (FP64)
 // ---------------------------------------------------------------------------
-constexpr int kObsThreads = 256;
+constexpr int kObsThreads = 32;   // one warp per chunk of kObsChunk beads
 
 __device__ __forceinline__ double block_sum_d(double v, double *sh) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -715,7 +823,7 @@ __global__ void __launch_bounds__(kObsThreads) k_obs_partial(ObsArgs q) {
     const DevExternal &e = q.a.ext;
     const int n = t.n;
     double E = 0.0, fpull = 0.0, ext = 0.0, formed = 0.0, fwall = 0.0, ree = 0.0;
-    const double R02 = q.R0 * q.R0;
+    const double R02 = q.R0 * q.R0, inv_R02 = 1.0 / R02;
     const double sig2 = q.sigma * q.sigma;
     for (int gb = lo + threadIdx.x; gb < hi; gb += blockDim.x) {
         const int r = gb / n, i = gb - r * n;
@@ -724,9 +832,9 @@ __global__ void __launch_bounds__(kObsThreads) k_obs_partial(ObsArgs q) {
         const double xi = pi.x, yi = pi.y, zi = pi.z;
         if (t.bond_r0[i] > 0.f) {
             const float4 pj = P[i + 1];
-            const double rr = __dsqrt_rn(dist2_d(xi, yi, zi, pj.x, pj.y, pj.z));
+            const double rr = sqrt_fast(dist2_d(xi, yi, zi, pj.x, pj.y, pj.z));
             const double dr = rr - q.bond_r0d[i];
-            const double arg = 1.0 - dr * dr / R02;
+            const double arg = 1.0 - dr * dr * inv_R02;
             if (arg > 0.0) E += -0.5 * q.k_fene * R02 * log(arg);
         }
         for (int p = t.nat_row[i]; p < t.nat_row[i + 1]; ++p) {
@@ -735,17 +843,17 @@ __global__ void __launch_bounds__(kObsThreads) k_obs_partial(ObsArgs q) {
             const float4 pj = P[j];
             const double d2 = dist2_d(xi, yi, zi, pj.x, pj.y, pj.z);
             const double r0 = t.nat_r0[p];
-            const double s = r0 * r0 / d2;
+            const double s = r0 * r0 * rcp_fast(d2);
             const double s3 = s * s * s;
             E += q.eps_h * (s3 * s3 - 2.0 * s3);
-            if (__dsqrt_rn(d2) < r0 + 2.0) formed += 1.0;
+            if (native_formed(d2, r0)) formed += 1.0;
         }
         const int p0 = q.pl.start[gb], p1 = p0 + q.pl.len[gb];
         for (int p = p0; p < p1; ++p) {
             const int j = q.pl.col[p];
             if (j < i) continue;
             const float4 pj = P[j];
-            const double c = sig2 / dist2_d(xi, yi, zi, pj.x, pj.y, pj.z);
+            const double c = sig2 * rcp_fast(dist2_d(xi, yi, zi, pj.x, pj.y, pj.z));
             E += q.eps_l * c * c * c;
         }
         if (t.flags[i] & kFlagPulled) {
@@ -767,13 +875,13 @@ __global__ void __launch_bounds__(kObsThreads) k_obs_partial(ObsArgs q) {
             const double c[3] = {e.ind_c0[0] + tt * e.ind_dir[0], e.ind_c0[1] + tt * e.ind_dir[1],
                                  e.ind_c0[2] + tt * e.ind_dir[2]};
             const double ex = xi - c[0], ey = yi - c[1], ez = zi - c[2];
-            const double rr = __dsqrt_rn((ex * ex + ey * ey) + ez * ez);
+            const double rr = sqrt_fast((ex * ex + ey * ey) + ez * ez);
             const double rho = rr - e.ind_radius;
             if (rho > 0.0) {
-                const double qq = q.sigma / rho;
+                const double qq = q.sigma * rcp_fast(rho);
                 const double q2 = qq * qq;
                 const double q6 = q2 * q2 * q2;
-                const double coef = 6.0 * q.eps_l * q6 / rho / rr;
+                const double coef = 6.0 * q.eps_l * q6 * rcp_fast(rho * rr);
                 fwall += coef * ((ex * e.ind_dir[0] + ey * e.ind_dir[1]) + ez * e.ind_dir[2]);
             }
         }
@@ -796,10 +904,17 @@ __global__ void __launch_bounds__(kObsThreads) k_obs_partial(ObsArgs q) {
 }
 
 // The record of segment g at `step` from its chunks' partial sums, into ring slot `slot`.
+// Called by a whole warp: lane l adds chunks l, l + 32, ... in order, then a fixed shuffle
+// tree adds the lanes (the same grouping every time); lane 0 writes the record.
 __device__ void write_record(const ObsArgs &q, int g, int64_t step, int64_t slot) {
+    const int lane = threadIdx.x & 31;
     double acc[6] = {0, 0, 0, 0, 0, 0};
-    for (int ch = q.o.seg_chunk_lo[g]; ch < q.o.seg_chunk_lo[g + 1]; ++ch)
+    for (int ch = q.o.seg_chunk_lo[g] + lane; ch < q.o.seg_chunk_lo[g + 1]; ch += 32)
         for (int k = 0; k < 6; ++k) acc[k] += q.o.partial[(size_t)ch * 8 + k];
+#pragma unroll
+    for (int k = 0; k < 6; ++k)
+        for (int o = 16; o > 0; o >>= 1) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], o);
+    if (lane != 0) return;
     const int ns = q.a.topo.n_sys;
     const int r = g / ns, s = g - r * ns;
     const DevExternal &e = q.a.ext;
@@ -817,27 +932,30 @@ __device__ void write_record(const ObsArgs &q, int g, int64_t step, int64_t slot
     q.o.ring[slot] = rec;
 }
 
+// One warp per segment.
 __global__ void k_obs_final(ObsArgs q, int n_seg) {
     const int64_t step = *q.a.d_step + q.k_off;
     if (q.gate > 0 && step % q.gate != 0) return;
-    const int g = blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= n_seg) return;
+    const int g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (g >= n_seg) return;   // whole warps leave together
     write_record(q, g, step, (*q.o.events * n_seg + g) % q.o.cap);
 }
 
 // One segment's record (the plain form, which runs the segments one after another): the
-// event is the device counter plus event_off.
+// event is the device counter plus event_off. One warp.
 __global__ void k_obs_final_one(ObsArgs q, int g, int n_seg, int64_t event_off) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    if (blockIdx.x != 0 || threadIdx.x >= 32) return;
     write_record(q, g, *q.a.d_step + q.k_off, ((*q.o.events + event_off) * n_seg + g) % q.o.cap);
 }
 
-// Per-replica energy (for sop_forces): sum of the replica's chunk partials.
+// Per-replica energy (for sop_forces): sum of the replica's chunk partials (one warp, lanes
+// over the chunks in order, then a fixed shuffle tree).
 __global__ void k_energy_sum(const double *partial, const int32_t *seg_chunk_lo, int g_lo, int g_hi, double *out) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    if (blockIdx.x != 0 || threadIdx.x >= 32) return;
     double e = 0.0;
-    for (int ch = seg_chunk_lo[g_lo]; ch < seg_chunk_lo[g_hi]; ++ch) e += partial[(size_t)ch * 8];
-    *out = e;
+    for (int ch = seg_chunk_lo[g_lo] + threadIdx.x; ch < seg_chunk_lo[g_hi]; ch += 32) e += partial[(size_t)ch * 8];
+    for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
+    if (threadIdx.x == 0) *out = e;
 }
 
 __global__ void k_tick(int64_t *d_step, int64_t k, int64_t *events, int32_t gate, int64_t n_events) {
@@ -908,13 +1026,27 @@ void launch_rebuild(const StepArgs &sa, const DevCells &c, const DevPairList &pl
     a.cell_base0 = rg.c_lo;
     a.rep_status = sa.rep_status;
     const int nb = rg.b_hi - rg.b_lo, nc = rg.c_hi - rg.c_lo;
-    // large segments get a full CTA each for their bounding box
-    const int setup_threads = (int64_t)nb > 2048 * (int64_t)(rg.g_hi - rg.g_lo) ? 1024 : 128;
-    k_seg_setup<<<rg.g_hi - rg.g_lo, setup_threads, 0, s>>>(a, pl.cursor, pl.seg_base);
-    k_cell_count<<<blocks_for(nb, 256), 256, 0, s>>>(a, rg.b_lo, rg.b_hi);
-    scan_exclusive(c.cell_cnt + rg.c_lo, c.cell_start, nc, c.scan_tmp, s, launches);
-    k_cell_scatter<<<blocks_for(nb, 256), 256, 0, s>>>(a, rg.b_lo, rg.b_hi);
-    k_cell_sort<<<blocks_for(nc, 256), 256, 0, s>>>(a, rg.c_lo, rg.c_hi);
+    if (rg.max_seg > 0 && rg.max_seg <= kFuseBeads) {
+        // every segment small: its whole cell list in one CTA, one launch for the range
+        static bool attr_set = false;
+        const int smem = (int)sizeof(int32_t) * (3 * kFuseBeads + 8);   // budget 2 n + 8 counters, n cells
+        if (!attr_set) {
+            cudaFuncSetAttribute(k_cell_build, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+            attr_set = true;
+        }
+        const int threads = rg.max_seg > 512 ? 1024 : 256;
+        k_cell_build<<<rg.g_hi - rg.g_lo, threads, (size_t)sizeof(int32_t) * (3 * rg.max_seg + 8), s>>>(
+            a, pl.cursor, pl.seg_base);
+        if (launches) *launches += 1;
+    } else {
+        // large segments get a full CTA each for their bounding box
+        const int setup_threads = (int64_t)nb > 2048 * (int64_t)(rg.g_hi - rg.g_lo) ? 1024 : 128;
+        k_seg_setup<<<rg.g_hi - rg.g_lo, setup_threads, 0, s>>>(a, pl.cursor, pl.seg_base);
+        k_cell_count<<<blocks_for(nb, 256), 256, 0, s>>>(a, rg.b_lo, rg.b_hi);
+        scan_exclusive(c.cell_cnt + rg.c_lo, c.cell_start, nc, c.scan_tmp, s, launches);
+        k_cell_scatter<<<blocks_for(nb, 256), 256, 0, s>>>(a, rg.b_lo, rg.b_hi);
+        if (launches) *launches += 3;
+    }
     BuildExtra x;
     x.nat_row = sa.topo.nat_row;
     x.nat_col = sa.topo.nat_col;
@@ -927,7 +1059,7 @@ void launch_rebuild(const StepArgs &sa, const DevCells &c, const DevPairList &pl
     x.pl_seg_end = pl.seg_end;
     x.rep_status = sa.rep_status;
     k_pl_build<<<blocks_for(nb, kBuildWarps), kBuildWarps * 32, 0, s>>>(a, x, rg.b_lo, rg.b_hi);
-    if (launches) *launches += 5;
+    if (launches) *launches += 1;
 }
 
 void launch_step(const StepArgs &a, const DevPairList &pl, const float4 *pos_in, float4 *pos_out, float4 *comp,
@@ -938,6 +1070,7 @@ void launch_step(const StepArgs &a, const DevPairList &pl, const float4 *pos_in,
         switch (lanes) {
         case 4: k_step_spread<4><<<blocks, 256, 0, s>>>(a, pl, pos_in, pos_out, comp, b_lo, b_hi, k_off); break;
         case 16: k_step_spread<16><<<blocks, 256, 0, s>>>(a, pl, pos_in, pos_out, comp, b_lo, b_hi, k_off); break;
+        case 32: k_step_spread<32><<<blocks, 256, 0, s>>>(a, pl, pos_in, pos_out, comp, b_lo, b_hi, k_off); break;
         default: k_step_spread<8><<<blocks, 256, 0, s>>>(a, pl, pos_in, pos_out, comp, b_lo, b_hi, k_off); break;
         }
         if (launches) *launches += 1;
@@ -949,6 +1082,7 @@ void launch_step(const StepArgs &a, const DevPairList &pl, const float4 *pos_in,
     switch (lanes) {
     case 4: k_step<4><<<blocks, 256, 0, s>>>(a, pl, pos_in, pos_out, comp, b_lo, b_hi, k_off); break;
     case 16: k_step<16><<<blocks, 256, 0, s>>>(a, pl, pos_in, pos_out, comp, b_lo, b_hi, k_off); break;
+    case 32: k_step<32><<<blocks, 256, 0, s>>>(a, pl, pos_in, pos_out, comp, b_lo, b_hi, k_off); break;
     default: k_step<8><<<blocks, 256, 0, s>>>(a, pl, pos_in, pos_out, comp, b_lo, b_hi, k_off); break;
     }
     if (launches) *launches += 1;
@@ -1006,6 +1140,7 @@ void launch_forces(const StepArgs &a, const DevPairList &pl, const float4 *pos, 
     switch (lanes) {
     case 4: k_forces<4><<<blocks, 256, 0, s>>>(a, pl, pos, force, b_lo, b_hi, step); break;
     case 16: k_forces<16><<<blocks, 256, 0, s>>>(a, pl, pos, force, b_lo, b_hi, step); break;
+    case 32: k_forces<32><<<blocks, 256, 0, s>>>(a, pl, pos, force, b_lo, b_hi, step); break;
     default: k_forces<8><<<blocks, 256, 0, s>>>(a, pl, pos, force, b_lo, b_hi, step); break;
     }
     if (launches) *launches += 1;
@@ -1035,7 +1170,7 @@ void launch_observables(const StepArgs &a, const DevPairList &pl, const DevObs &
     if (o.n_chunks <= 0) return;
     ObsArgs q = make_obs_args(a, pl, o, pos, k_off, gate);
     k_obs_partial<<<o.n_chunks, kObsThreads, 0, s>>>(q);
-    k_obs_final<<<blocks_for(n_seg, 128), 128, 0, s>>>(q, n_seg);
+    k_obs_final<<<blocks_for((int64_t)n_seg * 32, 128), 128, 0, s>>>(q, n_seg);
     if (launches) *launches += 2;
 }
 

@@ -19,7 +19,7 @@ namespace {
 
 thread_local std::string g_create_error;
 
-constexpr int kObsChunk = 128;         // beads per FP64 observable partial (FP64 is slow per SM: spread it)
+constexpr int kObsChunk = 32;          // beads per FP64 observable partial (FP64 is slow per SM: spread it)
 // Largest system the batched schedule takes: its state lives in shared memory, one CTA per
 // system up to about 3,400 beads (rows in global memory beyond 512), and the cluster form,
 // which keeps a copy of all positions in every CTA of the cluster, up to 4,096.
@@ -141,8 +141,9 @@ struct sop_ctx {
     int32_t n_items = 0;
     int32_t *d_item_rep = nullptr, *d_item_sys = nullptr;
     // graphs: [start buffer] for the streamed K-step chunk, one for the batched chunk
-    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
-    int64_t gexec_launches[2] = {0, 0};   // kernels in each streamed chunk graph
+    // streamed K-step chunk graphs by [start buffer][chunk ends at an observation step]
+    cudaGraphExec_t gexec[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+    int64_t gexec_launches[2][2] = {{0, 0}, {0, 0}};   // kernels in each streamed chunk graph
     cudaGraphExec_t bexec = nullptr;
     // in-flight limiter: at most kInFlight chunks queued ahead of the device, so that
     // sop_abort takes effect within a few chunks and the step counter stays exact
@@ -208,8 +209,9 @@ sop_status record_chunk(sop_ctx *c) {
 }
 
 void destroy_graphs(sop_ctx *c) {
-    for (auto &g : c->gexec)
-        if (g) { cudaGraphExecDestroy(g); g = nullptr; }
+    for (auto &row : c->gexec)
+        for (auto &g : row)
+            if (g) { cudaGraphExecDestroy(g); g = nullptr; }
     if (c->bexec) { cudaGraphExecDestroy(c->bexec); c->bexec = nullptr; }
 }
 
@@ -221,6 +223,7 @@ SegRange full_range(const sop_ctx *c) {
     r.b_hi = c->h_seg_bead_lo[c->n_seg];
     r.c_lo = c->h_seg_cell_base[0];
     r.c_hi = c->h_seg_cell_base[c->n_seg];
+    r.max_seg = c->max_sys;
     return r;
 }
 
@@ -232,6 +235,7 @@ SegRange seg_range(const sop_ctx *c, int g_lo, int g_hi) {
     r.b_hi = c->h_seg_bead_lo[g_hi];
     r.c_lo = c->h_seg_cell_base[g_lo];
     r.c_hi = c->h_seg_cell_base[g_hi];
+    r.max_seg = c->max_sys;
     return r;
 }
 
@@ -348,9 +352,9 @@ void note_events(sop_ctx *c, int64_t s0, int64_t s1) { c->events += events_in(s0
 
 // ---- streamed schedule --------------------------------------------------------------
 // One K-step chunk from an aligned step whose list is current: K fused steps, the
-// rebuild for the next chunk, the observables of the chunk's last step (gated on the
-// device), and the step counter advance.
-void enqueue_streamed_chunk(sop_ctx *c, int start_buf, int64_t *launches) {
+// rebuild for the next chunk, the observables of the chunk's last step when it is an
+// observation step (with_obs; also gated on the device), and the step counter advance.
+void enqueue_streamed_chunk(sop_ctx *c, int start_buf, bool with_obs, int64_t *launches) {
     const int K = c->prm.rebuild_every;
     const SegRange all = full_range(c);
     int b = start_buf;
@@ -366,19 +370,19 @@ void enqueue_streamed_chunk(sop_ctx *c, int start_buf, int64_t *launches) {
     }
     // the list of step + K is built from the positions of step + K (the next chunk's first step)
     rebuild_list(c, c->d_pos[b], c->d_snap, all, launches);
-    if (c->prm.obs_every > 0)
+    if (c->prm.obs_every > 0 && with_obs)
         launch_observables(c->sa, c->pl, c->obs, c->d_pos[b], c->n_seg, K, c->prm.obs_every, c->stream, launches);
     launch_tick(c->d_step, K, c->d_events, c->prm.obs_every > 0 ? c->prm.obs_every : 0, 0, c->stream, launches);
 }
 
-sop_status build_streamed_graph(sop_ctx *c, int start_buf) {
+sop_status build_streamed_graph(sop_ctx *c, int start_buf, bool with_obs) {
     cudaGraph_t g = nullptr;
     int64_t launches = 0;
     CUDA_OR_RETURN(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
-    enqueue_streamed_chunk(c, start_buf, &launches);
+    enqueue_streamed_chunk(c, start_buf, with_obs, &launches);
     cudaError_t e = cudaStreamEndCapture(c->stream, &g);
     if (e == cudaSuccess) {
-        e = cudaGraphInstantiate(&c->gexec[start_buf], g, 0);
+        e = cudaGraphInstantiate(&c->gexec[start_buf][with_obs], g, 0);
         cudaGraphDestroy(g);
         g = nullptr;
     }
@@ -386,9 +390,9 @@ sop_status build_streamed_graph(sop_ctx *c, int start_buf) {
         cudaGetLastError();
         if (g) cudaGraphDestroy(g);
         c->coop = false;
-        return build_streamed_graph(c, start_buf);
+        return build_streamed_graph(c, start_buf, with_obs);
     }
-    c->gexec_launches[start_buf] = launches;
+    c->gexec_launches[start_buf][with_obs] = launches;
     if (e != cudaSuccess) return fail(c, SOP_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
     return SOP_OK;
 }
@@ -406,17 +410,18 @@ sop_status step_streamed(sop_ctx *c, int64_t n_steps) {
                 sop_status s = rebuild_streamed(c);
                 if (s != SOP_OK) return s;
             }
-            if (!c->gexec[c->cur]) {
-                sop_status s = build_streamed_graph(c, c->cur);
+            const int wo = every > 0 && (c->step + K) % every == 0 ? 1 : 0;
+            if (!c->gexec[c->cur][wo]) {
+                sop_status s = build_streamed_graph(c, c->cur, wo != 0);
                 if (s != SOP_OK) return s;
             }
             sop_status th = throttle_before_chunk(c);
             if (th != SOP_OK) return th;
-            CUDA_OR_RETURN(c, cudaGraphLaunch(c->gexec[c->cur], c->stream));
+            CUDA_OR_RETURN(c, cudaGraphLaunch(c->gexec[c->cur][wo], c->stream));
             th = record_chunk(c);
             if (th != SOP_OK) return th;
             c->st.graph_launches++;
-            c->st.kernel_launches += c->gexec_launches[c->cur];
+            c->st.kernel_launches += c->gexec_launches[c->cur][wo];
             c->st.rebuilds++;
             if (K & 1) c->cur ^= 1;
             note_events(c, c->step, c->step + K);
@@ -1051,20 +1056,27 @@ sop_status tune_bucket(sop_ctx *c, sop_ctx::Bucket &bk) {
         if (batched_config(bk.max_n, bk.row_width, threads, true, 1, &cfg)) cands.push_back(cfg);
     }
     cands.insert(cands.end(), pairs.begin(), pairs.end());
-    // the cluster form for larger systems: one system over 2..16 CTAs of 2^sh beads each.
-    // SOP_FORCE_CLUSTER=sh keeps only the cluster configurations of 2^sh beads per CTA (sh 5
-    // to 9, when the bucket has one): a tuning override that makes the form testable at any size
+    // the cluster form for larger systems: one system over 2..16 CTAs of 2^sh beads each,
+    // served by 1, 2 or 4 lanes per bead. SOP_FORCE_CLUSTER=sh keeps only the cluster
+    // configurations of 2^sh beads per CTA (sh 5 to 9, when the bucket has one), and
+    // SOP_CLUSTER_LANES=l only those of l lanes per bead: tuning overrides that make the form
+    // testable at any size (one lane per bead sums in the one-CTA form's order)
     const char *fc = std::getenv("SOP_FORCE_CLUSTER");
     const int force_sh = fc ? std::atoi(fc) : 0;
+    const char *fl = std::getenv("SOP_CLUSTER_LANES");
+    const int force_ln = fl ? std::atoi(fl) : 0;
     if ((bk.max_n > 256 || force_sh > 0) && !pairs_only) {
         std::vector<BatchedConfig> clusters;
         for (int sh = 5; sh <= 9; ++sh) {
             if (force_sh > 0 ? sh != force_sh : sh < 7) continue;
-            for (int threads : {1 << sh, (1 << sh) / 2}) {
-                BatchedConfig cfg;
-                if (threads < (force_sh > 0 ? 32 : 64) || threads > 512) continue;
-                if (cluster_config(bk.max_n, bk.row_width, threads, sh, &cfg) && cluster_capacity(cfg) > 0)
-                    clusters.push_back(cfg);
+            for (int ln : {1, 2, 4}) {
+                if (force_ln > 0 && ln != force_ln) continue;
+                for (int threads : {ln << sh, (ln << sh) / 2}) {
+                    BatchedConfig cfg;
+                    if (threads < (force_sh > 0 ? 32 : 64) || threads > 1024) continue;
+                    if (cluster_config(bk.max_n, bk.row_width, threads, sh, ln, &cfg) && cluster_capacity(cfg) > 0)
+                        clusters.push_back(cfg);
+                }
             }
         }
         if (force_sh > 0 && !clusters.empty()) cands = clusters;
@@ -1089,14 +1101,14 @@ sop_status tune_bucket(sop_ctx *c, sop_ctx::Bucket &bk) {
             if (FILE *f = std::fopen(cache, "r")) {
                 char line[256];
                 while (!cached && std::fgets(line, sizeof line, f)) {
-                    int t = 0, bpt = 0, mb = 0, rg = 0, cs = 0, sh = 0, pf = 0;
+                    int t = 0, bpt = 0, mb = 0, rg = 0, cs = 0, sh = 0, pf = 0, lns = 0;
                     if (std::strncmp(line, key, std::strlen(key)) == 0 &&
-                        std::sscanf(line + std::strlen(key), " -> %d %d %d %d %d %d %d", &t, &bpt, &mb, &rg, &cs, &sh,
-                                    &pf) == 7) {
+                        std::sscanf(line + std::strlen(key), " -> %d %d %d %d %d %d %d %d", &t, &bpt, &mb, &rg, &cs, &sh,
+                                    &pf, &lns) == 8) {
                         for (const auto &cf : cands)
                             if (cf.threads == t && cf.beads_per_thread == bpt && cf.min_blocks == mb &&
                                 (int)cf.rows_global == rg && cf.cluster == cs && cf.m_shift == sh &&
-                                (int)cf.pair_form == pf) {
+                                (int)cf.pair_form == pf && cf.lanes == lns) {
                                 bk.cfg = cf;
                                 cached = true;
                             }
@@ -1191,7 +1203,7 @@ sop_status tune_bucket(sop_ctx *c, sop_ctx::Bucket &bk) {
 bool same_config(const BatchedConfig &x, const BatchedConfig &y) {
     return x.threads == y.threads && x.beads_per_thread == y.beads_per_thread && x.min_blocks == y.min_blocks &&
            x.rows_global == y.rows_global && x.cluster == y.cluster && x.m_shift == y.m_shift &&
-           x.pair_form == y.pair_form;
+           x.pair_form == y.pair_form && x.lanes == y.lanes;
 }
 
 // Buckets run side by side, so the configurations fastest on their own need not be the
@@ -1290,9 +1302,9 @@ sop_status tune_joint(sop_ctx *c) {
     for (auto &bk : c->buckets) {
         if (cache && bk.timed)
             if (FILE *f = std::fopen(cache, "a")) {
-                std::fprintf(f, "%s -> %d %d %d %d %d %d %d %.4f\n", bk.key.c_str(), bk.cfg.threads,
+                std::fprintf(f, "%s -> %d %d %d %d %d %d %d %d %.4f\n", bk.key.c_str(), bk.cfg.threads,
                              bk.cfg.beads_per_thread, bk.cfg.min_blocks, (int)bk.cfg.rows_global, bk.cfg.cluster,
-                             bk.cfg.m_shift, (int)bk.cfg.pair_form, bk.span_ms);
+                             bk.cfg.m_shift, (int)bk.cfg.pair_form, bk.cfg.lanes, bk.span_ms);
                 std::fclose(f);
             }
         if (bk.cfg.rows_global)
@@ -1369,19 +1381,20 @@ sop_status tune_streamed_form(sop_ctx *c) {
     cudaEvent_t e0, e1;
     CUDA_OR_RETURN(c, cudaEventCreate(&e0));
     CUDA_OR_RETURN(c, cudaEventCreate(&e1));
-    // the particle-based gather with 4, 8 and 16 lanes per bead, and the pair-based form
-    const int gather_lanes[3] = {8, 4, 16};
-    float ms[4] = {0.f, 0.f, 0.f, 0.f};
+    // the particle-based gather with 4, 8, 16 and 32 lanes per bead, and the pair-based form
+    constexpr int kGather = 4;
+    const int gather_lanes[kGather] = {8, 4, 16, 32};
+    float ms[kGather + 1] = {0.f, 0.f, 0.f, 0.f, 0.f};
     const int reps = 20;
-    for (int form = 0; form < 4; ++form) {
+    for (int form = 0; form <= kGather; ++form) {
         // the gather kernels index their threads (beads x lanes) with 32-bit integers
-        if (form < 3 && (int64_t)c->R * c->n * gather_lanes[form] > ((int64_t)1 << 31)) {
+        if (form < kGather && (int64_t)c->R * c->n * gather_lanes[form] > ((int64_t)1 << 31)) {
             ms[form] = 1e30f;
             continue;
         }
         for (int rep = 0; rep <= reps; ++rep) {
             if (rep == 1) cudaEventRecord(e0, c->stream);   // the first launch is a warm-up
-            if (form < 3)
+            if (form < kGather)
                 launch_forces(c->sa, c->pl, c->d_pos[c->cur], c->d_force, all.b_lo, all.b_hi, c->step, c->stream,
                               nullptr, gather_lanes[form]);
             else
@@ -1401,11 +1414,11 @@ sop_status tune_streamed_form(sop_ctx *c) {
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     int best = 0;
-    for (int form = 1; form < 3; ++form)
+    for (int form = 1; form < kGather; ++form)
         if (ms[form] < ms[best]) best = form;
-    c->pairs = ms[3] < ms[best];
+    c->pairs = ms[kGather] < ms[best];
     c->lanes = c->pairs ? 8 : gather_lanes[best];   // the pair-based trial gathers with 8
-    c->st.tune_ms = (c->pairs ? ms[3] : ms[best]) / reps;
+    c->st.tune_ms = (c->pairs ? ms[kGather] : ms[best]) / reps;
     return SOP_OK;
 }
 

@@ -173,6 +173,37 @@ __device__ __forceinline__ bool within_cut(float4 a, float4 b, float cut2_f, dou
     return d2 < cut2_d;
 }
 
+// 1/x in FP64 for finite x > 0: the FP32 reciprocal (24 bits) refined by two Newton steps
+// y <- y + y (1 - x y), each of which squares the relative error (to about 1e-15 here).
+// Cheaper than an FP64 division on a GPU whose FP64 pipe runs at a small fraction of its
+// FP32 rate; used for the terms of the FP64 readouts, which are compared at 1e-9 relative.
+__device__ __forceinline__ double rcp_fast(double x) {
+    double y = (double)__frcp_rn((float)x);
+    double e = fma(-x, y, 1.0);
+    y = fma(y, e, y);
+    e = fma(-x, y, 1.0);
+    return fma(y, e, y);
+}
+
+// sqrt(x) in FP64 for finite x > 0: the FP32 1/sqrt refined by two Newton steps
+// y <- y (3 - x y^2) / 2, times x (relative error about 1e-15), for the same readouts.
+__device__ __forceinline__ double sqrt_fast(double x) {
+    double y = (double)rsqrtf((float)x);
+    y = y * fma(-0.5 * x * y, y, 1.5);
+    y = y * fma(-0.5 * x * y, y, 1.5);
+    return x * y;
+}
+
+// Is the native pair at squared distance d2 formed, r < r0 + 2 A (Q)? Decided on d2
+// against (r0 + 2)^2 away from the threshold and by the square root of d2 within a relative
+// 1e-12 of it, so that the outcome is that of comparing the correctly rounded square root.
+__device__ __forceinline__ bool native_formed(double d2, double r0) {
+    const double t = r0 + 2.0, t2 = t * t;
+    if (d2 < t2 * (1.0 - 1e-12)) return true;
+    if (d2 > t2 * (1.0 + 1e-12)) return false;
+    return __dsqrt_rn(d2) < t;
+}
+
 // FP64 squared distance ((dx*dx + dy*dy) + dz*dz) with no contraction.
 __device__ __forceinline__ double dist2_d(double ax, double ay, double az, double bx, double by, double bz) {
     const double ex = __dsub_rn(ax, bx);

@@ -84,6 +84,7 @@ struct SegRange {
     int32_t g_lo = 0, g_hi = 0;   // segments
     int32_t b_lo = 0, b_hi = 0;   // global beads
     int32_t c_lo = 0, c_hi = 0;   // cells
+    int32_t max_seg = 0;          // beads of the largest segment (0: unknown)
 };
 
 // Cell-list scratch of the streamed rebuild.
@@ -275,14 +276,17 @@ struct BatchedConfig {
     int cluster = 0;           // > 0: the cluster form, one system over `cluster` CTAs of 2^m_shift beads each
     int m_shift = 0;
     bool pair_form = false;    // each pair evaluated once (k_bpair) instead of the particle-based gather
+    int lanes = 1;             // cluster form: lanes per bead (1, 2 or 4)
 };
 
 // A configuration for systems of at most max_n beads whose merged rows hold up to
 // row_width entries (natives + Verlet capacity); false when no compiled instance fits.
 bool batched_config(int max_n, int row_width, int threads, bool rows_global, int min_blocks, BatchedConfig *cfg);
 // The cluster form: each system is split over ceil(max_n / 2^m_shift) CTAs (at most 16)
-// of `threads` threads that own 2^m_shift consecutive beads each; false when it does not fit.
-bool cluster_config(int max_n, int row_width, int threads, int m_shift, BatchedConfig *cfg);
+// of `threads` threads that own 2^m_shift consecutive beads each, served by groups of
+// `lanes` lanes per bead (1, 2 or 4); false when it does not fit.
+bool cluster_config(int max_n, int row_width, int threads, int m_shift, int lanes, BatchedConfig *cfg);
+cudaError_t launch_cluster(const BatchedArgs &a, const BatchedConfig &cfg, cudaStream_t s);
 // The pair form (Newton's third law inside the CTA) for systems of at most max_n <= 256
 // beads with `pool` bytes (a multiple of 16) of shared memory for the rows, reverse lists and
 // coefficients of one item; false when it does not fit.

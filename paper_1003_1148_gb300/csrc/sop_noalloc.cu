@@ -156,6 +156,7 @@ extern "C" sop_status sop_pairlist_build_noalloc(const float *pos4, int32_t n, c
     rg.b_hi = n;
     rg.c_lo = 0;
     rg.c_hi = 2 * n + 8;
+    rg.max_seg = n;
 
     k_noalloc_init<<<64, 256, 0, s>>>(w, n, cap);
     launch_rebuild(sa, cells, pl, reinterpret_cast<const float4 *>(pos4), nullptr, rg, s, nullptr);

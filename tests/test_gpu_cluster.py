@@ -4,7 +4,8 @@ partners read from the owner CTA's shared memory) through the C ABI (needs a GPU
 The tuning override SOP_FORCE_CLUSTER=sh makes every bucket with systems larger than
 2^sh beads run in the cluster form with 2^sh beads per CTA, so small systems exercise
 clusters of several CTAs (including CTAs that own no bead of a shorter system).
-* same arithmetic in the same order as the one-CTA form: positions bit-identical;
+* with one lane per bead, the same arithmetic in the same order as the one-CTA form:
+  positions bit-identical (SOP_CLUSTER_LANES=1); with 2 or 4 lanes per bead, oracle parity;
 * parity with the FP64 oracle: Verlet lists bit-exact, forces within 1e-5 of the term
   scale, 100-step trajectories within 1e-3 A RMS, FP64 observables;
 * checkpoint/resume bit-exact; a failing replica freezes alone (the failure decision is
@@ -26,12 +27,15 @@ def sop():
     return s
 
 
-def clustered(sop, w, sh, **kw):
+def clustered(sop, w, sh, lanes=None, **kw):
     os.environ["SOP_FORCE_CLUSTER"] = str(sh)
+    if lanes:
+        os.environ["SOP_CLUSTER_LANES"] = str(lanes)
     try:
         sim = sop.from_workload(w, schedule="batched", **kw)
     finally:
         del os.environ["SOP_FORCE_CLUSTER"]
+        os.environ.pop("SOP_CLUSTER_LANES", None)
     assert sim.stats()["cluster_buckets"] > 0
     return sim
 
@@ -47,7 +51,7 @@ def test_cluster_equals_one_cta_form(sop, synth):
         a = sop.from_workload(w, n_replicas=2, schedule="batched")
     finally:
         del os.environ["SOP_TUNE"]
-    b = clustered(sop, w, 5, n_replicas=2)
+    b = clustered(sop, w, 5, lanes=1, n_replicas=2)   # one lane per bead: the one-CTA order
     assert a.stats()["cluster_buckets"] == 0
     a.step(57)
     b.step(57)
@@ -57,11 +61,11 @@ def test_cluster_equals_one_cta_form(sop, synth):
     assert np.array_equal(ra, rb) and np.array_equal(ca, cb)
 
 
-@pytest.mark.parametrize("sh", [5, 6])
-def test_cluster_parity_with_oracle(sop, orc, synth, sh):
+@pytest.mark.parametrize("sh,lanes", [(5, 1), (6, 1), (5, 4), (6, 2), (6, 4)])
+def test_cluster_parity_with_oracle(sop, orc, synth, sh, lanes):
     w = small_uneven(synth)
     R = 2
-    sim = clustered(sop, w, sh, n_replicas=R)
+    sim = clustered(sop, w, sh, lanes, n_replicas=R)
     x0 = sim.get_positions(0)
     m = orc.model_from_workload(w)
     sys_of = w.system_of_bead()
@@ -79,7 +83,7 @@ def test_cluster_parity_with_oracle(sop, orc, synth, sh):
         assert (np.abs(F - Fo) / Ao).max() <= 1e-5
         assert E == pytest.approx(Eo[0] + Eo[1] + Eo[2], rel=1e-9, abs=1e-9)
     sim.close()
-    sim = clustered(sop, w, sh, n_replicas=R, obs_every=20)
+    sim = clustered(sop, w, sh, lanes, n_replicas=R, obs_every=20)
     sim.step(100)
     for r in range(R):
         xo, _, _, _ = m.run(x0, 100, seed=w.seed + r)
@@ -98,9 +102,10 @@ def test_cluster_parity_with_oracle(sop, orc, synth, sh):
     sim.close()
 
 
-def test_cluster_checkpoint_and_failure(sop, synth):
+@pytest.mark.parametrize("lanes", [1, 4])
+def test_cluster_checkpoint_and_failure(sop, synth, lanes):
     w = small_uneven(synth)
-    sim = clustered(sop, w, 5, n_replicas=3)
+    sim = clustered(sop, w, 5, lanes, n_replicas=3)
     sim.step(23)
     state = sim.get_state()
     sim.step(41)

@@ -358,14 +358,15 @@ void sop_destroy(sop_ctx *ctx);
  * call cudaMalloc -- hosts whose device memory all belongs to their own pool
  * allocator, or services that must not allocate after start-up. It runs the
  * same cell-list rebuild as the streamed schedule on caller-provided device
- * buffers; its scratch (1.8 MiB for at most SOP_NOALLOC_MAX_BEADS beads) is a
+ * buffers; its scratch (2.5 MiB for at most SOP_NOALLOC_MAX_BEADS beads) is a
  * fixed array inside this library that every GPU which loads the library holds
  * until the process exits.
  *
  * Inputs (device pointers, read only): pos4 [4*n] floats, bead-major (x, y, z,
  * unused), 16-byte aligned; chain [n] chain id of each bead (beads i, i+1 of
  * one chain are bonded); nat_row [n+1], nat_col: the native contact map as CSR
- * with both directions (e.g. from sop_get_native_map). Outputs (device
+ * with both directions, each row ascending (as sop_get_native_map returns it;
+ * a row that is not ascending may leave native partners in the list). Outputs (device
  * pointers): row_start [n], row_len [n] and col [cap]: row i is
  * col[row_start[i] .. row_start[i] + row_len[i]), ascending partner indices;
  * rows are packed in no particular order. *nnz (host) receives the number of

@@ -303,11 +303,12 @@ __device__ __forceinline__ void obs_bonded(const StepArgs &sa, const float4 *P, 
     const DevTopo &t = sa.topo;
     const int i = b0 + b;
     const float4 pb = P[b];
-    const double xi = pb.x, yi = pb.y, zi = pb.z;
     const double R02 = sa.R0 * sa.R0;
     if (bond_right) {
         const float4 pj = P[b + 1];
-        const double rr = sqrt_fast(dist2_d(xi, yi, zi, pj.x, pj.y, pj.z));
+        float d2f;
+        const double d2 = dist2_two(pb, pj, &d2f);
+        const double rr = sqrt_seeded(d2, d2f);
         const double dr = rr - t.bond_r0d[i];
         const double arg = 1.0 - dr * dr / R02;
         if (arg > 0.0) v[0] += -0.5 * sa.k_fene * R02 * log(arg);
@@ -316,12 +317,13 @@ __device__ __forceinline__ void obs_bonded(const StepArgs &sa, const float4 *P, 
         const int j = t.nat_col[q];
         if (j < i) continue;
         const float4 pj = P[j - b0];
-        const double d2 = dist2_d(xi, yi, zi, pj.x, pj.y, pj.z);
+        float d2f;
+        const double d2 = dist2_two(pb, pj, &d2f);
         const double r0 = t.nat_r0[q];
-        const double u = r0 * r0 * rcp_fast(d2);
+        const double u = r0 * r0 * rcp_seeded(d2, d2f);
         const double u3 = u * u * u;
-        v[0] += sa.eps_h * (u3 * u3 - 2.0 * u3);
-        if (native_formed(d2, r0)) v[3] += 1.0;
+        v[0] = fma(sa.eps_h, u3 * u3 - 2.0 * u3, v[0]);
+        if (native_formed(d2, r0, pb, pj)) v[3] += 1.0;
     }
 }
 

@@ -251,14 +251,15 @@ __device__ __noinline__ void observe(const BatchedArgs &a, const Layout<RG> &L, 
         if (p >= n_s) continue;
         const int b = order[p];
         const float4 pb = P[b];
-        const double xi = pb.x, yi = pb.y, zi = pb.z;
         obs_bonded(sa, P, b, b0, L.bond()[b].y > 0.f, v);
         for (int q = L.n_nat()[p]; q < L.n_tot()[p]; ++q) {
             const int j = row[q * n_s + p];
             if (j < b) continue;
             const float4 pj = P[j];
-            const double c = sig2 * rcp_fast(dist2_d(xi, yi, zi, pj.x, pj.y, pj.z));
-            v[0] += sa.eps_l * c * c * c;
+            float d2f;
+            const double d2 = dist2_two(pb, pj, &d2f);
+            const double c = sig2 * rcp_seeded(d2, d2f);
+            v[0] = fma(sa.eps_l, c * c * c, v[0]);
         }
         obs_external(sa, P, b, b0, r, s, step, L.flags()[b], v);
     }

@@ -256,15 +256,16 @@ __device__ __noinline__ void cluster_observe(const BatchedArgs &a, const CLayout
         const int l = order[p];
         const int b = lo + l;
         const float4 pb = P[b];
-        const double xi = pb.x, yi = pb.y, zi = pb.z;
         if (ln == 0) obs_bonded(sa, P, b, b0, L.bond()[l].y > 0.f, v);
         const uint16_t *rl = L.row() + ln * m + p;
         for (int e = L.lane_nat()[ln * m + p]; e < L.lane_tot()[ln * m + p]; ++e) {
             const int j = rl[e * LN * m];
             if (j < b) continue;
             const float4 pj = P[j];
-            const double c = sig2 * rcp_fast(dist2_d(xi, yi, zi, pj.x, pj.y, pj.z));
-            v[0] += sa.eps_l * c * c * c;
+            float d2f;
+            const double d2 = dist2_two(pb, pj, &d2f);
+            const double c = sig2 * rcp_seeded(d2, d2f);
+            v[0] = fma(sa.eps_l, c * c * c, v[0]);
         }
         if (ln == 0) obs_external(sa, P, b, b0, r, s, step, L.flags()[l], v);
     }

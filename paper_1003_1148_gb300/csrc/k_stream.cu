@@ -17,6 +17,9 @@
 // the replica-major global bead index.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+#include <climits>
+
 #include "sop_internal.h"
 #include "sop_step.cuh"
 
@@ -162,7 +165,7 @@ struct RebuildArgs {
     const int32_t *sys;
     const int32_t *chain;
     int32_t n, n_sys;
-    int32_t g_lo;
+    int32_t g_lo, g_hi;
     float cell_edge;
     const int32_t *seg_bead_lo;
     const int32_t *seg_cell_base;
@@ -171,37 +174,45 @@ struct RebuildArgs {
     int32_t *cell_of;
     int32_t *cell_cnt;
     int32_t *cell_start;   // range-relative offsets
-    int32_t *sorted;       // sorted[sorted_base + k]
+    float4 *sorted;        // sorted[sorted_base + k]: position, bead index (int bits) in w
     int32_t sorted_base;   // first bead of the range
     int32_t cell_base0;    // first cell of the range
     int32_t *rep_status;
+    int32_t *seg_box;
 };
 
+// Dims d and edge of the grid over [l, h]: cubic cells, edge from edge0 growing by a
+// quarter (at most 64 times) until at most `budget` cells cover the box. False if none does.
+__device__ bool fit_grid(const float l[3], const float h[3], float edge0, int budget, int d[3], float *edge) {
+    float e0 = edge0;
+    for (int it = 0; it < 64; ++it) {
+        long long prod = 1;
+        for (int k = 0; k < 3; ++k) {
+            const float e = (h[k] - l[k]) / e0;
+            d[k] = e < 1e6f ? (int)floorf(e) + 1 : 1000000;
+            prod *= d[k];
+        }
+        if (prod <= budget) {
+            *edge = e0;
+            return true;
+        }
+        e0 *= 1.25f;
+    }
+    *edge = e0;
+    return false;
+}
+
 // The cell grid of segment g from its bounding box [l, h]: cubic cells of edge >= cutoff,
-// at most the segment's cell budget of them (the edge grows by a quarter until the grid
-// fits). A skipped segment (bad = true, or no grid fits) gets one empty cell and, when it
-// holds beads, fails its replica.
+// at most the segment's cell budget of them (fit_grid). A skipped segment (bad = true, or
+// no grid fits) gets one empty cell and, when it holds beads, fails its replica.
 __device__ void seg_grid(const RebuildArgs &a, int g, float l[3], const float h[3], bool bad, bool has_beads) {
     const int budget = a.seg_cell_base[g + 1] - a.seg_cell_base[g];
     float edge = a.cell_edge;
     int d[3] = {1, 1, 1};
     bool skip = bad;
-    if (!skip) {
-        bool fit = false;
-        for (int it = 0; it < 64 && !fit; ++it) {
-            long long prod = 1;
-            for (int k = 0; k < 3; ++k) {
-                const float e = (h[k] - l[k]) / edge;
-                d[k] = e < 1e6f ? (int)floorf(e) + 1 : 1000000;
-                prod *= d[k];
-            }
-            if (prod <= budget) fit = true;
-            else edge *= 1.25f;
-        }
-        if (!fit) {
-            d[0] = d[1] = d[2] = 1;
-            skip = true;
-        }
+    if (!skip && !fit_grid(l, h, a.cell_edge, budget, d, &edge)) {
+        d[0] = d[1] = d[2] = 1;
+        skip = true;
     }
     if (skip) {
         l[0] = l[1] = l[2] = 0.0f;
@@ -211,43 +222,39 @@ __device__ void seg_grid(const RebuildArgs &a, int g, float l[3], const float h[
     a.seg_dims[g] = make_int4(d[0], d[1], d[2], skip ? 0 : d[0] * d[1] * d[2]);
 }
 
-// One CTA per segment: bounding box, then a grid of cubic cells of edge >= cutoff
-// with at most the segment's cell budget. A segment whose replica has failed is
-// skipped by the whole rebuild (dims.w = 0: no bead is binned and its rows stay empty):
-// its frozen positions may lie anywhere. A live segment with a non-finite position or
-// an extent that no grid of the budget covers (beads flung ~1e9 A apart) fails its
-// replica and is skipped too.
-__global__ void k_seg_setup(RebuildArgs a, int32_t *pl_cursor, const int64_t *pl_seg_base) {
-    // every thread of the CTA works on segment g
+// Order-preserving integer key of a float (a < b <=> key(a) < key(b) for non-NaN values),
+// so that several CTAs can merge minima and maxima with integer atomics.
+__device__ __forceinline__ int f2key(float f) {
+    const int b = __float_as_int(f);
+    return b >= 0 ? b : b ^ 0x7fffffff;
+}
+__device__ __forceinline__ float key2f(int k) { return __int_as_float(k >= 0 ? k : k ^ 0x7fffffff); }
+
+// Empty accumulator: minima at the largest key, maxima at the smallest, no bad position.
+__device__ __forceinline__ void seg_box_reset(int32_t *bx) {
+    bx[0] = bx[1] = bx[2] = INT_MAX;
+    bx[3] = bx[4] = bx[5] = INT_MIN;
+    bx[6] = 0;
+    bx[7] = 0;
+}
+
+__global__ void k_seg_box_init(int32_t *seg_box, int n_seg) {
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g < n_seg) seg_box_reset(seg_box + 8 * g);
+}
+
+// Bounding boxes of large segments, gridDim.y CTAs per segment: each CTA reduces one slice
+// of the segment's beads and merges it into the segment's accumulator (min and max are
+// independent of the order of the merges).
+__global__ void __launch_bounds__(256) k_seg_bbox(RebuildArgs a) {
     const int g = a.g_lo + blockIdx.x;
+    if (a.rep_status[g / a.n_sys] != 0) return;   // CTA-uniform; k_seg_grid skips the segment
     const int lo = a.seg_bead_lo[g], hi = a.seg_bead_lo[g + 1];
-    if (a.rep_status[g / a.n_sys] != 0) {   // CTA-uniform
-        if (threadIdx.x == 0) {
-            a.seg_lo[g] = make_float4(0.f, 0.f, 0.f, 1.0f / a.cell_edge);
-            a.seg_dims[g] = make_int4(1, 1, 1, 0);
-            if (pl_cursor) pl_cursor[g] = (int32_t)pl_seg_base[g];
-        }
-        return;
-    }
+    const int per = (hi - lo + gridDim.y - 1) / gridDim.y;
+    const int s0 = lo + blockIdx.y * per, s1 = min(hi, s0 + per);
     float mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
     bool bad = false;
-    // four independent loads in flight per thread (a segment can hold 10^5 beads)
-    const int T = blockDim.x;
-    int b = lo + threadIdx.x;
-    for (; b + 3 * T < hi; b += 4 * T) {
-        const float4 q[4] = {a.pos[b], a.pos[b + T], a.pos[b + 2 * T], a.pos[b + 3 * T]};
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const float v[3] = {q[u].x, q[u].y, q[u].z};
-#pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                if (!isfinite(v[k])) bad = true;
-                mn[k] = fminf(mn[k], v[k]);
-                mx[k] = fmaxf(mx[k], v[k]);
-            }
-        }
-    }
-    for (; b < hi; b += T) {
+    for (int b = s0 + threadIdx.x; b < s1; b += blockDim.x) {
         const float4 p = a.pos[b];
         const float v[3] = {p.x, p.y, p.z};
 #pragma unroll
@@ -257,33 +264,55 @@ __global__ void k_seg_setup(RebuildArgs a, int32_t *pl_cursor, const int64_t *pl
             mx[k] = fmaxf(mx[k], v[k]);
         }
     }
-    __shared__ float smn[3][32], smx[3][32];
-    __shared__ int sbad;
-    if (threadIdx.x == 0) sbad = 0;
-    __syncthreads();
-    if (bad) sbad = 1;
 #pragma unroll
-    for (int k = 0; k < 3; ++k) {
+    for (int k = 0; k < 3; ++k)
         for (int o = 16; o > 0; o >>= 1) {
             mn[k] = fminf(mn[k], __shfl_xor_sync(0xffffffffu, mn[k], o));
             mx[k] = fmaxf(mx[k], __shfl_xor_sync(0xffffffffu, mx[k], o));
         }
-    }
+    bad = __any_sync(0xffffffffu, bad);
+    __shared__ float smn[3][8], smx[3][8];
+    __shared__ int sbad[8];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    if (lane == 0)
+    if (lane == 0) {
         for (int k = 0; k < 3; ++k) { smn[k][w] = mn[k]; smx[k][w] = mx[k]; }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        const int nw = blockDim.x >> 5;
-        float l[3], h[3];
-        for (int k = 0; k < 3; ++k) {
-            l[k] = smn[k][0];
-            h[k] = smx[k][0];
-            for (int q = 1; q < nw; ++q) { l[k] = fminf(l[k], smn[k][q]); h[k] = fmaxf(h[k], smx[k][q]); }
-        }
-        seg_grid(a, g, l, h, sbad != 0 || hi <= lo, hi > lo);
-        if (pl_cursor) pl_cursor[g] = (int32_t)pl_seg_base[g];
+        sbad[w] = bad ? 1 : 0;
     }
+    __syncthreads();
+    if (threadIdx.x != 0 || s1 <= s0) return;
+    int32_t *bx = a.seg_box + 8 * g;
+    int any_bad = 0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) any_bad |= sbad[q];
+    for (int k = 0; k < 3; ++k) {
+        float l = smn[k][0], h = smx[k][0];
+        for (int q = 1; q < (int)(blockDim.x >> 5); ++q) { l = fminf(l, smn[k][q]); h = fmaxf(h, smx[k][q]); }
+        atomicMin(&bx[k], f2key(l));
+        atomicMax(&bx[3 + k], f2key(h));
+    }
+    if (any_bad) atomicOr(&bx[6], 1);
+}
+
+// One thread per segment: the grid from the merged box (or the skip of a failed replica's
+// segment: no bead is binned and its rows stay empty; its frozen positions may lie
+// anywhere), then the accumulator back to its empty state. A live segment with a
+// non-finite position or an extent that no grid of the budget covers fails its replica
+// and is skipped too (seg_grid).
+__global__ void k_seg_grid(RebuildArgs a, int n_seg_range, int32_t *pl_cursor, const int64_t *pl_seg_base) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n_seg_range) return;
+    const int g = a.g_lo + k;
+    int32_t *bx = a.seg_box + 8 * g;
+    if (a.rep_status[g / a.n_sys] != 0) {
+        a.seg_lo[g] = make_float4(0.f, 0.f, 0.f, 1.0f / a.cell_edge);
+        a.seg_dims[g] = make_int4(1, 1, 1, 0);
+    } else {
+        const int lo = a.seg_bead_lo[g], hi = a.seg_bead_lo[g + 1];
+        float l[3], h[3];
+        for (int q = 0; q < 3; ++q) { l[q] = key2f(bx[q]); h[q] = key2f(bx[3 + q]); }
+        seg_grid(a, g, l, h, bx[6] != 0 || hi <= lo, hi > lo);
+    }
+    if (pl_cursor) pl_cursor[g] = (int32_t)pl_seg_base[g];
+    seg_box_reset(bx);
 }
 
 __device__ __forceinline__ int cell_coord(float x, float lo, float inv, int dim) {
@@ -314,7 +343,7 @@ __global__ void k_cell_count(RebuildArgs a, int b_lo, int b_hi) {
         cz = cell_coord(p.z, lo.z, lo.w, d.z);
     }
     const int gc = a.seg_cell_base[g] + (cz * d.y + cy) * d.x + cx;
-    // the grid never exceeds the segment's budget (k_seg_setup); a cell outside it is
+    // the grid never exceeds the segment's budget (seg_grid); a cell outside it is
     // recorded as a failure of the replica and the bead goes to the segment's first cell
     if (gc < a.seg_cell_base[g] || gc >= a.seg_cell_base[g + 1]) {
         atomicCAS(&a.rep_status[r], 0, (int32_t)SOP_ERR_NONFINITE);
@@ -333,14 +362,16 @@ __global__ void k_cell_scatter(RebuildArgs a, int b_lo, int b_hi) {
     const int gc = a.cell_of[gb];
     if (gc < 0) return;   // skipped segment
     const int slot = atomicSub(&a.cell_cnt[gc], 1) - 1;
-    a.sorted[a.sorted_base + a.cell_start[gc - a.cell_base0] + slot] = gb;
+    const float4 p = a.pos[gb];
+    a.sorted[a.sorted_base + a.cell_start[gc - a.cell_base0] + slot] = make_float4(p.x, p.y, p.z, __int_as_float(gb));
 }
 
 constexpr int kFuseBeads = 8192;   // segments up to this size build their cell list in one CTA
 
 // The cell list of one small segment in one CTA, in shared memory: bounding box, grid, cell
 // of each bead, histogram, exclusive scan, scatter. The same grid, cell starts and cell
-// contents as the staged kernels (k_seg_setup, k_cell_count, the scan, k_cell_scatter), in
+// contents as the staged kernels (k_seg_bbox, k_seg_grid, k_cell_count, the scan,
+// k_cell_scatter), in
 // one launch. Dynamic shared memory: the segment's cell budget of counters, then the cell
 // of each of its beads.
 __global__ void k_cell_build(RebuildArgs a, int32_t *pl_cursor, const int64_t *pl_seg_base) {
@@ -447,7 +478,8 @@ __global__ void k_cell_build(RebuildArgs a, int32_t *pl_cursor, const int64_t *p
     for (int b = lo + threadIdx.x; b < hi; b += T) {
         const int c = cof[b - lo];
         if (c < 0) continue;
-        a.sorted[a.sorted_base + base + atomicAdd(&cnt[c], 1)] = b;
+        const float4 p = a.pos[b];
+        a.sorted[a.sorted_base + base + atomicAdd(&cnt[c], 1)] = make_float4(p.x, p.y, p.z, __int_as_float(b));
     }
 }
 
@@ -464,17 +496,57 @@ struct BuildExtra {
     int32_t *pl_len;
     int32_t *pl_col;
     int32_t *pl_cursor;         // [n_seg]
+    const int64_t *pl_seg_base; // [n_seg] first column of each segment
     const int64_t *pl_seg_end;  // [n_seg] capacity limit of each segment
     int32_t *rep_status;
 };
 
-// One warp per bead: scan the 27 neighbouring cells (as 9 runs of 3 consecutive
-// cells along x), keep partners j with |i-j| != 1 in a chain, j not native, j != i
-// and r^2 < cut^2; order them ascending (rank sort) and append the row to the
-// segment's column range.
+// Append the row of bead gb (cnt kept partners in the warp's buffer, in any order) to
+// segment g's column range, ranked ascending; a row of more than kRowBuf partners, or one
+// that does not fit the segment's capacity, is an overflow of replica r and stays empty.
+// Called by the whole warp.
+__device__ __forceinline__ void emit_row(const BuildExtra &x, const int32_t *buf, int cnt, int g, int r, int gb,
+                                         int lane, int32_t *rep_status) {
+    __syncwarp();
+    int base = 0;
+    bool ok = cnt <= kRowBuf;
+    if (lane == 0 && ok) {
+        base = atomicAdd(&x.pl_cursor[g], cnt);
+        if ((int64_t)base + cnt > x.pl_seg_end[g]) ok = false;
+    }
+    base = __shfl_sync(0xffffffffu, base, 0);
+    ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+    if (!ok) {
+        if (lane == 0) {
+            set_status(&rep_status[r], (int32_t)SOP_ERR_PAIRLIST_OVERFLOW);
+            x.pl_start[gb] = 0;
+            x.pl_len[gb] = 0;
+        }
+        return;
+    }
+    for (int k = lane; k < cnt; k += 32) {
+        const int v = buf[k];
+        int rank = 0;
+        for (int m2 = 0; m2 < cnt; ++m2) rank += buf[m2] < v;
+        x.pl_col[base + rank] = v;
+    }
+    if (lane == 0) {
+        x.pl_start[gb] = base;
+        x.pl_len[gb] = cnt;
+    }
+}
+
+// One warp per bead: scan the 27 neighbouring cells, keep partners j with |i-j| != 1 in
+// a chain, j not native, j != i and r^2 < cut^2; order them ascending (rank sort) and
+// append the row to the segment's column range. The 27 cells are 9 runs of 3 cells
+// consecutive along x, hence 9 contiguous ranges of the cell-sorted positions; the warp
+// walks their concatenation 32 candidates at a time, so every load of a pass is a
+// coalesced read of sorted positions and no lane idles at the end of a short run.
 __global__ void __launch_bounds__(kBuildWarps * 32) k_pl_build(RebuildArgs a, BuildExtra x, int b_lo, int b_hi) {
     __shared__ int32_t buf[kBuildWarps][kRowBuf];
     __shared__ int32_t nat[kBuildWarps][kNatBuf];
+    __shared__ int32_t run_t0[kBuildWarps][9];   // first candidate of each run in the walk
+    __shared__ int32_t run_q0[kBuildWarps][9];   // its first sorted slot
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int gb = b_lo + blockIdx.x * kBuildWarps + w;
     if (gb >= b_hi) return;
@@ -488,75 +560,283 @@ __global__ void __launch_bounds__(kBuildWarps * 32) k_pl_build(RebuildArgs a, Bu
     const int nlo = x.nat_row[i], nhi = x.nat_row[i + 1];
     const int nn = nhi - nlo;
     for (int k = lane; k < nn && k < kNatBuf; k += 32) nat[w][k] = x.nat_col[nlo + k];
-    __syncwarp();
+    const int ci = a.chain[i];
+    // bonded neighbours are excluded when they lie in the same chain
+    const bool ex_lo = i > 0 && a.chain[i - 1] == ci;
+    const bool ex_hi = i + 1 < a.n && a.chain[i + 1] == ci;
     const float4 lo = a.seg_lo[g];
     const int4 d = a.seg_dims[g];
     const int cx = cell_coord(pi.x, lo.x, lo.w, d.x);
     const int cy = cell_coord(pi.y, lo.y, lo.w, d.y);
     const int cz = cell_coord(pi.z, lo.z, lo.w, d.z);
     const int cbase = a.seg_cell_base[g] - a.cell_base0;
-    const int ci = a.chain[i];
     const int rbase = r * a.n;
-    int cnt = 0;
-    const int x0 = cx > 0 ? cx - 1 : 0, x1 = cx + 1 < d.x ? cx + 1 : d.x - 1;
-    for (int zz = cz - 1; zz <= cz + 1; ++zz) {
-        if (zz < 0 || zz >= d.z) continue;
-        for (int yy = cy - 1; yy <= cy + 1; ++yy) {
-            if (yy < 0 || yy >= d.y) continue;
+    // lane k < 9 reads run k (z = cz - 1 + k / 3, y = cy - 1 + k % 3): its slots [q0, q1)
+    int q0 = 0, len = 0;
+    if (lane < 9) {
+        const int zz = cz - 1 + lane / 3, yy = cy - 1 + lane % 3;
+        if (zz >= 0 && zz < d.z && yy >= 0 && yy < d.y) {
+            const int x0 = cx > 0 ? cx - 1 : 0, x1 = cx + 1 < d.x ? cx + 1 : d.x - 1;
             const int c0 = cbase + (zz * d.y + yy) * d.x + x0;
             const int c1 = cbase + (zz * d.y + yy) * d.x + x1;
-            const int q0 = a.cell_start[c0], q1 = a.cell_start[c1 + 1];
-            for (int q = q0 + lane; q - lane < q1; q += 32) {
-                bool keep = false;
-                int jl = 0;
-                if (q < q1) {
-                    const int j = a.sorted[a.sorted_base + q];
-                    jl = j - rbase;
-                    if (jl != i && !((jl == i + 1 || jl == i - 1) && a.chain[jl] == ci)) {
-                        if (within_cut(pi, a.pos[j], x.cut2_f, x.cut2_d)) {
-                            keep = true;
-                            for (int k = 0; k < nn; ++k) {
-                                const int v = k < kNatBuf ? nat[w][k] : x.nat_col[nlo + k];
-                                if (v == jl) { keep = false; break; }
-                            }
-                        }
-                    }
-                }
-                const unsigned m = __ballot_sync(0xffffffffu, keep);
-                if (keep) {
-                    const int slot = cnt + __popc(m & ((1u << lane) - 1u));
-                    if (slot < kRowBuf) buf[w][slot] = jl;
-                }
-                cnt += __popc(m);
-            }
+            q0 = a.cell_start[c0];
+            len = a.cell_start[c1 + 1] - q0;
         }
+    }
+    int pre = len;   // inclusive prefix over the runs
+#pragma unroll
+    for (int o = 1; o < 16; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, pre, o);
+        if (lane >= o) pre += t;
+    }
+    const int total = __shfl_sync(0xffffffffu, pre, 8);
+    if (lane < 9) {
+        run_t0[w][lane] = pre - len;
+        run_q0[w][lane] = q0;
     }
     __syncwarp();
-    int base = 0;
-    bool ok = cnt <= kRowBuf;
-    if (lane == 0 && ok) {
-        base = atomicAdd(&x.pl_cursor[g], cnt);
-        if ((int64_t)base + cnt > x.pl_seg_end[g]) ok = false;
-    }
-    base = __shfl_sync(0xffffffffu, base, 0);
-    ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
-    if (!ok) {
-        if (lane == 0) {
-            set_status(&a.rep_status[r], (int32_t)SOP_ERR_PAIRLIST_OVERFLOW);
-            x.pl_start[gb] = 0;
-            x.pl_len[gb] = 0;
+    const bool nat_shared = nn <= kNatBuf;
+    const float4 *S = a.sorted + a.sorted_base;
+    int cnt = 0;
+    for (int t0 = 0; t0 < total; t0 += 32) {
+        const int t = t0 + lane;
+        bool keep = false;
+        int jl = 0;
+        if (t < total) {
+            // the last run starting at or before t (empty runs share their start with the
+            // next run, so the last one is the non-empty run holding t)
+            int k = t >= run_t0[w][8] ? 8 : 0;
+            if (k == 0) {
+                if (t >= run_t0[w][4]) k = 4;
+                if (t >= run_t0[w][k + 2]) k += 2;
+                if (t >= run_t0[w][k + 1]) k += 1;
+            }
+            const float4 pj = S[run_q0[w][k] + (t - run_t0[w][k])];
+            jl = __float_as_int(pj.w) - rbase;
+            if (jl != i && !(jl == i + 1 && ex_hi) && !(jl == i - 1 && ex_lo) &&
+                within_cut(pi, pj, x.cut2_f, x.cut2_d)) {
+                if (nat_shared) {   // the native row is ascending: binary search
+                    int a0 = 0, a1 = nn;
+                    while (a0 < a1) {
+                        const int mid = (a0 + a1) >> 1;
+                        if (nat[w][mid] < jl) a0 = mid + 1;
+                        else a1 = mid;
+                    }
+                    keep = !(a0 < nn && nat[w][a0] == jl);
+                } else {
+                    keep = true;
+                    for (int k2 = 0; k2 < nn; ++k2)
+                        if (x.nat_col[nlo + k2] == jl) { keep = false; break; }
+                }
+            }
         }
-        return;
+        const unsigned m = __ballot_sync(0xffffffffu, keep);
+        if (keep) {
+            const int slot = cnt + __popc(m & ((1u << lane) - 1u));
+            if (slot < kRowBuf) buf[w][slot] = jl;
+        }
+        cnt += __popc(m);
     }
-    for (int k = lane; k < cnt; k += 32) {
-        const int v = buf[w][k];
-        int rank = 0;
-        for (int m2 = 0; m2 < cnt; ++m2) rank += buf[w][m2] < v;
-        x.pl_col[base + rank] = v;
+    emit_row(x, buf[w], cnt, g, r, gb, lane, a.rep_status);
+}
+
+constexpr int kBruteBeads = kBruteMaxBeads;   // segments up to this size: k_pl_brute (no cell list)
+constexpr int kBruteSlice = kBruteSliceBeads;
+
+struct BruteArgs {
+    const int32_t *cta_lo;   // [n_seg+1] first k_pl_brute CTA of each segment
+    int32_t *done;           // [n_seg] CTAs finished in the current build (0 between builds)
+    int32_t *used;           // [n_seg] entries of the segment after its last build
+    int32_t k_lo;            // cta_lo[g_lo]: first CTA of the launch
+};
+
+// The Verlet rows of small segments (at most kBruteBeads beads) without a cell list: every
+// CTA holds the positions of its segment in shared memory (x, y, z arrays, each padded to
+// an even length with a point at infinity) and its warps test each of their beads against
+// every bead of the segment, two candidates per lane with packed FP32x2 arithmetic. A
+// candidate whose FP32 squared distance exceeds cut^2 (1 + 1e-4) is out by the FP32
+// screen of within_cut; the others queue in shared memory and, 32 at a time (one per
+// lane, so that the rare survivors of the screen do not idle the warp), take within_cut
+// itself, the bonded and native exclusions and the same compaction, ranking and overflow
+// rules as k_pl_build, so the rows equal the cell-list rows. Each CTA also takes its segment's bounding box and fails
+// the replica, as the cell list does, when a position is not finite or no grid of the
+// segment's cell budget covers it. kBruteSlice beads per CTA; the last CTA of a segment
+// to finish records the entries used and puts the segment's column cursor back to its
+// first column for the next build.
+__global__ void __launch_bounds__(kBuildWarps * 32) k_pl_brute(RebuildArgs a, BuildExtra x, BruteArgs bz) {
+    extern __shared__ float soa[];
+    __shared__ int32_t buf[kBuildWarps][kRowBuf];
+    __shared__ int32_t nat[kBuildWarps][kNatBuf];
+    __shared__ int32_t cand[kBuildWarps][96];   // screened candidates waiting for the exact tests
+    __shared__ float smn[3][kBuildWarps], smx[3][kBuildWarps];
+    __shared__ int sbad[kBuildWarps];
+    __shared__ int s_ok;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int cta = bz.k_lo + blockIdx.x;
+    // the segment of this CTA: cta_lo[g] <= cta < cta_lo[g + 1] (empty segments own no CTA)
+    int g = a.g_lo, g1 = a.g_hi;
+    while (g1 - g > 1) {
+        const int mid = (g + g1) >> 1;
+        if (bz.cta_lo[mid] <= cta) g = mid;
+        else g1 = mid;
     }
-    if (lane == 0) {
-        x.pl_start[gb] = base;
-        x.pl_len[gb] = cnt;
+    const int lo = a.seg_bead_lo[g], hi = a.seg_bead_lo[g + 1], m = hi - lo, m2 = (m + 1) & ~1;
+    float *sx = soa, *sy = soa + m2, *sz = soa + 2 * m2;
+    const int r = g / a.n_sys;
+    const bool failed = a.rep_status[r] != 0;   // CTA-uniform
+    if (!failed) {
+        float mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
+        bool bad = false;
+        for (int k = threadIdx.x; k < m; k += blockDim.x) {
+            const float4 p = a.pos[lo + k];
+            sx[k] = p.x;
+            sy[k] = p.y;
+            sz[k] = p.z;
+            const float v[3] = {p.x, p.y, p.z};
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                if (!isfinite(v[c])) bad = true;
+                mn[c] = fminf(mn[c], v[c]);
+                mx[c] = fmaxf(mx[c], v[c]);
+            }
+        }
+        if (threadIdx.x == 0 && m2 > m) sx[m] = sy[m] = sz[m] = INFINITY;
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+            for (int o = 16; o > 0; o >>= 1) {
+                mn[c] = fminf(mn[c], __shfl_xor_sync(0xffffffffu, mn[c], o));
+                mx[c] = fmaxf(mx[c], __shfl_xor_sync(0xffffffffu, mx[c], o));
+            }
+        bad = __any_sync(0xffffffffu, bad);
+        if (lane == 0) {
+            for (int c = 0; c < 3; ++c) { smn[c][w] = mn[c]; smx[c][w] = mx[c]; }
+            sbad[w] = bad ? 1 : 0;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            float l[3], h[3];
+            int any_bad = 0;
+            for (int c = 0; c < 3; ++c) {
+                l[c] = smn[c][0];
+                h[c] = smx[c][0];
+            }
+            for (int q = 0; q < kBuildWarps; ++q) {
+                any_bad |= sbad[q];
+                for (int c = 0; c < 3; ++c) { l[c] = fminf(l[c], smn[c][q]); h[c] = fmaxf(h[c], smx[c][q]); }
+            }
+            int d[3];
+            float edge;
+            const bool ok = !any_bad && fit_grid(l, h, a.cell_edge, a.seg_cell_base[g + 1] - a.seg_cell_base[g], d, &edge);
+            if (!ok) atomicCAS(&a.rep_status[r], 0, (int32_t)SOP_ERR_NONFINITE);
+            s_ok = ok ? 1 : 0;
+        }
+    }
+    __syncthreads();
+    const bool skip = failed || s_ok == 0;
+    const int b0 = lo + (cta - bz.cta_lo[g]) * kBruteSlice, b1 = min(hi, b0 + kBruteSlice);
+    if (a.snap)
+        for (int b = b0 + threadIdx.x; b < b1; b += blockDim.x) a.snap[b] = a.pos[b];
+    const int rbase = r * a.n, jbase = lo - rbase;   // replica-local index of the segment's first bead
+    const float band = x.cut2_f * 1e-4f, screen = x.cut2_f + band;
+    const float2 m1 = make_float2(-1.f, -1.f);
+    for (int gb = b0 + w; gb < b1; gb += kBuildWarps) {
+        if (skip) {
+            if (lane == 0) { x.pl_start[gb] = 0; x.pl_len[gb] = 0; }
+            continue;
+        }
+        const int i = gb - rbase;
+        const int nlo = x.nat_row[i], nn = x.nat_row[i + 1] - nlo;
+        __syncwarp();   // the previous bead's row is out of buf and nat
+        for (int k = lane; k < nn && k < kNatBuf; k += 32) nat[w][k] = x.nat_col[nlo + k];
+        const int ci = a.chain[i];
+        const bool ex_lo = i > 0 && a.chain[i - 1] == ci;
+        const bool ex_hi = i + 1 < a.n && a.chain[i + 1] == ci;
+        const bool nat_shared = nn <= kNatBuf;
+        const float4 pi = make_float4(sx[gb - lo], sy[gb - lo], sz[gb - lo], 0.f);
+        const float2 px = make_float2(pi.x, pi.x), py = make_float2(pi.y, pi.y), pz = make_float2(pi.z, pi.z);
+        __syncwarp();
+        int cnt = 0, pend = 0;
+        // the exact tests of the candidates that passed the FP32 screen, cand[w][0 .. np)
+        // with np <= 32, one per lane; kept partners are compacted into buf[w]
+        auto settle = [&](int np) {
+            bool keep = false;
+            int jl = 0;
+            if (lane < np) {
+                const int kk = cand[w][lane];
+                jl = jbase + kk;
+                if (jl != i && !(jl == i + 1 && ex_hi) && !(jl == i - 1 && ex_lo) &&
+                    within_cut(pi, make_float4(sx[kk], sy[kk], sz[kk], 0.f), x.cut2_f, x.cut2_d)) {
+                    if (nat_shared) {   // the native row is ascending: binary search
+                        int a0 = 0, a1 = nn;
+                        while (a0 < a1) {
+                            const int mid = (a0 + a1) >> 1;
+                            if (nat[w][mid] < jl) a0 = mid + 1;
+                            else a1 = mid;
+                        }
+                        keep = !(a0 < nn && nat[w][a0] == jl);
+                    } else {
+                        keep = true;
+                        for (int q = 0; q < nn; ++q)
+                            if (x.nat_col[nlo + q] == jl) { keep = false; break; }
+                    }
+                }
+            }
+            const unsigned msk = __ballot_sync(0xffffffffu, keep);
+            if (keep) {
+                const int slot = cnt + __popc(msk & ((1u << lane) - 1u));
+                if (slot < kRowBuf) buf[w][slot] = jl;
+            }
+            cnt += __popc(msk);
+        };
+        const unsigned below = (1u << lane) - 1u;
+        for (int k0 = 2 * lane; k0 - 2 * lane < m2; k0 += 64) {
+            bool in0 = false, in1 = false;
+            if (k0 < m2) {
+                const float2 X = *reinterpret_cast<const float2 *>(sx + k0);
+                const float2 Y = *reinterpret_cast<const float2 *>(sy + k0);
+                const float2 Z = *reinterpret_cast<const float2 *>(sz + k0);
+                const float2 dx = __ffma2_rn(X, m1, px);   // pi - pj, exactly rounded
+                const float2 dy = __ffma2_rn(Y, m1, py);
+                const float2 dz = __ffma2_rn(Z, m1, pz);
+                const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
+                in0 = r2.x <= screen;
+                in1 = r2.y <= screen;
+            }
+            const unsigned q0 = __ballot_sync(0xffffffffu, in0), q1 = __ballot_sync(0xffffffffu, in1);
+            if ((q0 | q1) == 0u) continue;
+            if (in0) cand[w][pend + __popc(q0 & below)] = k0;
+            pend += __popc(q0);
+            if (in1) cand[w][pend + __popc(q1 & below)] = k0 + 1;
+            pend += __popc(q1);
+            if (pend >= 32) {
+                __syncwarp();
+                settle(32);
+                // move the rest (at most 63) to the front
+                const int v0 = lane + 32 < pend ? cand[w][lane + 32] : 0;
+                const int v1 = lane + 64 < pend ? cand[w][lane + 64] : 0;
+                __syncwarp();
+                if (lane + 32 < pend) cand[w][lane] = v0;
+                if (lane + 64 < pend) cand[w][lane + 32] = v1;
+                pend -= 32;
+                __syncwarp();
+            }
+        }
+        __syncwarp();
+        if (pend > 0) settle(pend);
+        emit_row(x, buf[w], cnt, g, r, gb, lane, a.rep_status);
+    }
+    // the last CTA of the segment records its entries and resets its cursor
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const int n_cta = bz.cta_lo[g + 1] - bz.cta_lo[g];
+        if (atomicAdd(&bz.done[g], 1) == n_cta - 1) {
+            __threadfence();
+            const int32_t base = (int32_t)x.pl_seg_base[g];
+            bz.used[g] = atomicAdd(&x.pl_cursor[g], 0) - base;
+            x.pl_cursor[g] = base;
+            bz.done[g] = 0;
+        }
     }
 }
 
@@ -593,6 +873,7 @@ __device__ __forceinline__ float3 gather_force(const StepArgs &a, const DevPairL
         }
     }
     const int n0 = t.nat_row[i], n1 = t.nat_row[i + 1];
+#pragma unroll 2
     for (int p = n0 + lane; p < n1; p += L) {
         const float4 pj = P[t.nat_col[p]];
         const float dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
@@ -600,6 +881,7 @@ __device__ __forceinline__ float3 gather_force(const StepArgs &a, const DevPairL
         fx = fmaf(c, dx, fx); fy = fmaf(c, dy, fy); fz = fmaf(c, dz, fz);
     }
     const int p0 = pl.start[gb], p1 = p0 + pl.len[gb];
+#pragma unroll 2
     for (int p = p0 + lane; p < p1; p += L) {
         const float4 pj = P[pl.col[p]];
         const float dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
@@ -788,18 +1070,25 @@ __global__ void __launch_bounds__(256) k_forces(StepArgs a, DevPairList pl, cons
 // ---------------------------------------------------------------------------
 // Observables (FP64)
 // ---------------------------------------------------------------------------
-constexpr int kObsThreads = 32;   // one warp per chunk of kObsChunk beads
+constexpr int kObsLanes = 4;                        // lanes per bead in k_obs_partial's counting
+constexpr int kObsThreads = kObsChunkBeads * kObsLanes;
+static_assert(kObsChunkBeads == 32, "k_obs_partial scans its chunk's beads in one warp");
 
-__device__ __forceinline__ double block_sum_d(double v, double *sh) {
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+// Sum of v[0..5] over the CTA, valid in thread 0: a fixed shuffle tree in each warp, then
+// thread 0 adds the warps in order. The grouping depends only on the launch shape, so
+// the result is the same on every run. sh holds 6 doubles per warp.
+__device__ __forceinline__ void block_sum6_d(double v[6], double *sh) {
+#pragma unroll
+    for (int k = 0; k < 6; ++k)
+        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     __syncthreads();
-    if (lane == 0) sh[w] = v;
+    if (lane == 0)
+        for (int k = 0; k < 6; ++k) sh[w * 6 + k] = v[k];
     __syncthreads();
-    double s = 0.0;
     if (threadIdx.x == 0)
-        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) s += sh[k];
-    return s;   // valid in thread 0
+        for (int q = 1; q < (int)(blockDim.x >> 5); ++q)
+            for (int k = 0; k < 6; ++k) v[k] += sh[q * 6 + k];
 }
 
 struct ObsArgs {
@@ -814,7 +1103,20 @@ struct ObsArgs {
     const double *bond_r0d;   // [n] FP64 bond lengths
 };
 
+// Partial FP64 sums of one chunk of beads (energy, pull force, extension, formed native
+// contacts, indenter force, end-to-end distance). Each pair is taken once, from its lower
+// index: rows are ascending (the list builders and the native map write them so), so the
+// partners j > i of bead i are a suffix of each of its rows. The CTA counts those suffixes
+// (kObsLanes lanes per bead), lays them end to end, and its threads then stride over the
+// concatenation, native pairs first: the FP64 pipe, narrow on this GPU and busy for a
+// whole warp instruction whatever the number of active lanes, sees full warps except at
+// the tails. The terms of the beads themselves (bond, pulling, indenter, end-to-end
+// distance) take one thread per bead. The grouping of every sum depends only on the
+// chunk, so the result is the same on every run.
 __global__ void __launch_bounds__(kObsThreads) k_obs_partial(ObsArgs q) {
+    constexpr int kB = kObsThreads / kObsLanes;   // beads of a chunk
+    __shared__ int s_nat0[kB], s_ver0[kB];        // first suffix entry of each bead's rows
+    __shared__ int s_natp[kB + 1], s_verp[kB + 1]; // exclusive prefix of the suffix lengths
     const int64_t step = *q.a.d_step + q.k_off;
     if (q.gate > 0 && step % q.gate != 0) return;
     const int ch = q.chunk0 + blockIdx.x;
@@ -822,39 +1124,90 @@ __global__ void __launch_bounds__(kObsThreads) k_obs_partial(ObsArgs q) {
     const DevTopo &t = q.a.topo;
     const DevExternal &e = q.a.ext;
     const int n = t.n;
-    double E = 0.0, fpull = 0.0, ext = 0.0, formed = 0.0, fwall = 0.0, ree = 0.0;
-    const double R02 = q.R0 * q.R0, inv_R02 = 1.0 / R02;
+    const int lane = threadIdx.x & 31;
+    // a chunk lies in one segment, hence in one replica r; bead b of the chunk is i0 + b
+    const int r = lo / n, i0 = lo - r * n;
+    const float4 *P = q.pos + (size_t)r * n;
+    double acc[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};   // E, fpull, ext, formed, fwall, ree
+    {   // suffix lengths: kObsLanes lanes per bead count the entries above the bead's index
+        const int bl = threadIdx.x / kObsLanes, gl = threadIdx.x % kObsLanes;
+        const int gb = lo + bl;
+        int cn = 0, cv = 0, n1 = 0, v1 = 0;
+        if (gb < hi) {
+            const int i = i0 + bl;
+            n1 = t.nat_row[i + 1];
+            for (int p = t.nat_row[i] + gl; p < n1; p += kObsLanes) cn += t.nat_col[p] > i;
+            v1 = q.pl.start[gb] + q.pl.len[gb];
+            for (int p = q.pl.start[gb] + gl; p < v1; p += kObsLanes) cv += q.pl.col[p] > i;
+        }
+#pragma unroll
+        for (int o = kObsLanes / 2; o > 0; o >>= 1) {
+            cn += __shfl_xor_sync(0xffffffffu, cn, o, kObsLanes);
+            cv += __shfl_xor_sync(0xffffffffu, cv, o, kObsLanes);
+        }
+        if (gl == 0) {
+            s_nat0[bl] = n1 - cn;
+            s_ver0[bl] = v1 - cv;
+            s_natp[bl + 1] = cn;
+            s_verp[bl + 1] = cv;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {   // inclusive scans of the lengths (kB <= 32)
+        int a = lane < kB ? s_natp[lane + 1] : 0, b = lane < kB ? s_verp[lane + 1] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int ta = __shfl_up_sync(0xffffffffu, a, o), tb = __shfl_up_sync(0xffffffffu, b, o);
+            if (lane >= o) { a += ta; b += tb; }
+        }
+        if (lane < kB) { s_natp[lane + 1] = a; s_verp[lane + 1] = b; }
+        if (lane == 0) { s_natp[0] = 0; s_verp[0] = 0; }
+    }
+    __syncthreads();
+    // the bead of flat entry f: the last b with prefix[b] <= f
+    auto bead_of = [](const int *pre, int f) {
+        int b = 0;
+#pragma unroll
+        for (int step2 = kB / 2; step2 > 0; step2 >>= 1)
+            if (pre[b + step2] <= f) b += step2;
+        return b;
+    };
     const double sig2 = q.sigma * q.sigma;
-    for (int gb = lo + threadIdx.x; gb < hi; gb += blockDim.x) {
-        const int r = gb / n, i = gb - r * n;
-        const float4 *P = q.pos + (size_t)r * n;
+    const int tot_nat = s_natp[kB], tot_ver = s_verp[kB];
+    for (int f = threadIdx.x; f < tot_nat; f += kObsThreads) {
+        const int b = bead_of(s_natp, f);
+        const int p = s_nat0[b] + (f - s_natp[b]);
+        const float4 pi = P[i0 + b], pj = P[t.nat_col[p]];
+        float d2f;
+        const double d2 = dist2_two(pi, pj, &d2f);
+        const double r0 = t.nat_r0[p];
+        const double s = r0 * r0 * rcp_seeded(d2, d2f);
+        const double s3 = s * s * s;
+        acc[0] = fma(q.eps_h, s3 * s3 - 2.0 * s3, acc[0]);
+        if (native_formed(d2, r0, pi, pj)) acc[3] += 1.0;
+    }
+    for (int f = threadIdx.x; f < tot_ver; f += kObsThreads) {
+        const int b = bead_of(s_verp, f);
+        const float4 pi = P[i0 + b], pj = P[q.pl.col[s_ver0[b] + (f - s_verp[b])]];
+        float d2f;
+        const double d2 = dist2_two(pi, pj, &d2f);
+        const double c = sig2 * rcp_seeded(d2, d2f);
+        acc[0] = fma(q.eps_l, c * c * c, acc[0]);
+    }
+    const int gb = lo + (int)threadIdx.x;
+    if (threadIdx.x < kB && gb < hi) {   // the terms of the bead itself
+        const int i = i0 + (int)threadIdx.x;
         const float4 pi = P[i];
         const double xi = pi.x, yi = pi.y, zi = pi.z;
         if (t.bond_r0[i] > 0.f) {
             const float4 pj = P[i + 1];
-            const double rr = sqrt_fast(dist2_d(xi, yi, zi, pj.x, pj.y, pj.z));
+            float d2f;
+            const double d2 = dist2_two(pi, pj, &d2f);
+            const double rr = sqrt_seeded(d2, d2f);
+            const double R02 = q.R0 * q.R0;
             const double dr = rr - q.bond_r0d[i];
-            const double arg = 1.0 - dr * dr * inv_R02;
-            if (arg > 0.0) E += -0.5 * q.k_fene * R02 * log(arg);
-        }
-        for (int p = t.nat_row[i]; p < t.nat_row[i + 1]; ++p) {
-            const int j = t.nat_col[p];
-            if (j < i) continue;
-            const float4 pj = P[j];
-            const double d2 = dist2_d(xi, yi, zi, pj.x, pj.y, pj.z);
-            const double r0 = t.nat_r0[p];
-            const double s = r0 * r0 * rcp_fast(d2);
-            const double s3 = s * s * s;
-            E += q.eps_h * (s3 * s3 - 2.0 * s3);
-            if (native_formed(d2, r0)) formed += 1.0;
-        }
-        const int p0 = q.pl.start[gb], p1 = p0 + q.pl.len[gb];
-        for (int p = p0; p < p1; ++p) {
-            const int j = q.pl.col[p];
-            if (j < i) continue;
-            const float4 pj = P[j];
-            const double c = sig2 * rcp_fast(dist2_d(xi, yi, zi, pj.x, pj.y, pj.z));
-            E += q.eps_l * c * c * c;
+            const double arg = 1.0 - dr * dr * (1.0 / R02);
+            if (arg > 0.0) acc[0] += -0.5 * q.k_fene * R02 * log(arg);
         }
         if (t.flags[i] & kFlagPulled) {
             const int qq = e.pull_of_sys[t.sys[i]];
@@ -863,11 +1216,11 @@ __global__ void __launch_bounds__(kObsThreads) k_obs_partial(ObsArgs q) {
                 const double *tip0 = e.pull_tip0 + ((size_t)r * e.n_pull + qq) * 3;
                 const double *dir = e.pull_dir + 3 * qq;
                 const double x[3] = {xi, yi, zi};
-                double f = 0.0;
-                for (int k = 0; k < 3; ++k) f += e.pull_ks[qq] * (tip0[k] + tt * dir[k] - x[k]) * dir[k];
-                fpull += f;
+                double fs = 0.0;
+                for (int k = 0; k < 3; ++k) fs += e.pull_ks[qq] * (tip0[k] + tt * dir[k] - x[k]) * dir[k];
+                acc[1] += fs;
                 const float4 pa = P[e.pull_anchor[qq]];
-                ext += __dsqrt_rn(dist2_d(xi, yi, zi, pa.x, pa.y, pa.z));
+                acc[2] += __dsqrt_rn(dist2_d(xi, yi, zi, pa.x, pa.y, pa.z));
             }
         }
         if (e.has_indenter) {
@@ -882,39 +1235,42 @@ __global__ void __launch_bounds__(kObsThreads) k_obs_partial(ObsArgs q) {
                 const double q2 = qq * qq;
                 const double q6 = q2 * q2 * q2;
                 const double coef = 6.0 * q.eps_l * q6 * rcp_fast(rho * rr);
-                fwall += coef * ((ex * e.ind_dir[0] + ey * e.ind_dir[1]) + ez * e.ind_dir[2]);
+                acc[4] += coef * ((ex * e.ind_dir[0] + ey * e.ind_dir[1]) + ez * e.ind_dir[2]);
             }
         }
         if (t.flags[i] & kFlagFirstOfSystem) {
             const float4 pl_ = P[t.sys_ree_last[t.sys[i]]];
-            ree += __dsqrt_rn(dist2_d(xi, yi, zi, pl_.x, pl_.y, pl_.z));
+            acc[5] += __dsqrt_rn(dist2_d(xi, yi, zi, pl_.x, pl_.y, pl_.z));
         }
     }
-    __shared__ double sh[kObsThreads / 32];
-    const double v0 = block_sum_d(E, sh);
-    const double v1 = block_sum_d(fpull, sh);
-    const double v2 = block_sum_d(ext, sh);
-    const double v3 = block_sum_d(formed, sh);
-    const double v4 = block_sum_d(fwall, sh);
-    const double v5 = block_sum_d(ree, sh);
+    __shared__ double sh[6 * (kObsThreads / 32)];
+    block_sum6_d(acc, sh);
     if (threadIdx.x == 0) {
         double *out = q.o.partial + (size_t)ch * 8;
-        out[0] = v0; out[1] = v1; out[2] = v2; out[3] = v3; out[4] = v4; out[5] = v5; out[6] = 0; out[7] = 0;
+        for (int k = 0; k < 6; ++k) out[k] = acc[k];
+        out[6] = 0;
+        out[7] = 0;
     }
 }
 
+// Sum of the chunk partials [ch_lo, ch_hi) over the CTA (thread t adds chunks t, t + T, ...
+// in order, then block_sum6_d); valid in thread 0.
+__device__ __forceinline__ void chunk_sums(const DevObs &o, int ch_lo, int ch_hi, double acc[6], double *sh) {
+    for (int k = 0; k < 6; ++k) acc[k] = 0.0;
+    for (int ch = ch_lo + threadIdx.x; ch < ch_hi; ch += blockDim.x)
+        for (int k = 0; k < 6; ++k) acc[k] += o.partial[(size_t)ch * 8 + k];
+    block_sum6_d(acc, sh);
+}
+
+constexpr int kObsFinalMaxThreads = 256;
+
 // The record of segment g at `step` from its chunks' partial sums, into ring slot `slot`.
-// Called by a whole warp: lane l adds chunks l, l + 32, ... in order, then a fixed shuffle
-// tree adds the lanes (the same grouping every time); lane 0 writes the record.
+// Called by the whole CTA; thread 0 writes the record.
 __device__ void write_record(const ObsArgs &q, int g, int64_t step, int64_t slot) {
-    const int lane = threadIdx.x & 31;
-    double acc[6] = {0, 0, 0, 0, 0, 0};
-    for (int ch = q.o.seg_chunk_lo[g] + lane; ch < q.o.seg_chunk_lo[g + 1]; ch += 32)
-        for (int k = 0; k < 6; ++k) acc[k] += q.o.partial[(size_t)ch * 8 + k];
-#pragma unroll
-    for (int k = 0; k < 6; ++k)
-        for (int o = 16; o > 0; o >>= 1) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], o);
-    if (lane != 0) return;
+    __shared__ double sh[6 * (kObsFinalMaxThreads / 32)];
+    double acc[6];
+    chunk_sums(q.o, q.o.seg_chunk_lo[g], q.o.seg_chunk_lo[g + 1], acc, sh);
+    if (threadIdx.x != 0) return;
     const int ns = q.a.topo.n_sys;
     const int r = g / ns, s = g - r * ns;
     const DevExternal &e = q.a.ext;
@@ -932,31 +1288,31 @@ __device__ void write_record(const ObsArgs &q, int g, int64_t step, int64_t slot
     q.o.ring[slot] = rec;
 }
 
-// One warp per segment.
-__global__ void k_obs_final(ObsArgs q, int n_seg) {
+// One CTA per segment.
+__global__ void __launch_bounds__(kObsFinalMaxThreads) k_obs_final(ObsArgs q, int n_seg) {
     const int64_t step = *q.a.d_step + q.k_off;
     if (q.gate > 0 && step % q.gate != 0) return;
-    const int g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (g >= n_seg) return;   // whole warps leave together
+    const int g = blockIdx.x;
     write_record(q, g, step, (*q.o.events * n_seg + g) % q.o.cap);
 }
 
 // One segment's record (the plain form, which runs the segments one after another): the
-// event is the device counter plus event_off. One warp.
-__global__ void k_obs_final_one(ObsArgs q, int g, int n_seg, int64_t event_off) {
-    if (blockIdx.x != 0 || threadIdx.x >= 32) return;
+// event is the device counter plus event_off. One CTA.
+__global__ void __launch_bounds__(kObsFinalMaxThreads) k_obs_final_one(ObsArgs q, int g, int n_seg,
+                                                                        int64_t event_off) {
     write_record(q, g, *q.a.d_step + q.k_off, ((*q.o.events + event_off) * n_seg + g) % q.o.cap);
 }
 
-// Per-replica energy (for sop_forces): sum of the replica's chunk partials (one warp, lanes
-// over the chunks in order, then a fixed shuffle tree).
-__global__ void k_energy_sum(const double *partial, const int32_t *seg_chunk_lo, int g_lo, int g_hi, double *out) {
-    if (blockIdx.x != 0 || threadIdx.x >= 32) return;
-    double e = 0.0;
-    for (int ch = seg_chunk_lo[g_lo] + threadIdx.x; ch < seg_chunk_lo[g_hi]; ch += 32) e += partial[(size_t)ch * 8];
-    for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
-    if (threadIdx.x == 0) *out = e;
+// Per-replica energy (for sop_forces): sum of the energy partials of segments [g_lo, g_hi).
+__global__ void __launch_bounds__(kObsFinalMaxThreads) k_energy_sum(DevObs o, int g_lo, int g_hi, double *out) {
+    __shared__ double sh[6 * (kObsFinalMaxThreads / 32)];
+    double acc[6];
+    chunk_sums(o, o.seg_chunk_lo[g_lo], o.seg_chunk_lo[g_hi], acc, sh);
+    if (threadIdx.x == 0) *out = acc[0];
 }
+
+// Threads of the final reductions: a warp when segments hold few chunks, else a full CTA.
+inline int final_threads(const DevObs &o) { return o.max_seg_chunks > 64 ? kObsFinalMaxThreads : 32; }
 
 __global__ void k_tick(int64_t *d_step, int64_t k, int64_t *events, int32_t gate, int64_t n_events) {
     if (threadIdx.x == 0 && blockIdx.x == 0) {
@@ -1002,6 +1358,10 @@ void launch_native_fill(const double *X, const int32_t *chain, const int32_t *sy
     k_native<true><<<blocks_for(n, 128), 128, 0, s>>>(X, chain, sys, sys_lo, n, cut, nullptr, row, col, r0, r0sq);
 }
 
+void launch_seg_box_init(int32_t *seg_box, int32_t n_seg, cudaStream_t s) {
+    if (n_seg > 0) k_seg_box_init<<<blocks_for(n_seg, 128), 128, 0, s>>>(seg_box, n_seg);
+}
+
 void launch_rebuild(const StepArgs &sa, const DevCells &c, const DevPairList &pl, const float4 *pos, float4 *snap,
                     const SegRange &rg, cudaStream_t s, int64_t *launches) {
     if (rg.g_hi <= rg.g_lo) return;
@@ -1013,6 +1373,7 @@ void launch_rebuild(const StepArgs &sa, const DevCells &c, const DevPairList &pl
     a.n = sa.topo.n;
     a.n_sys = sa.topo.n_sys;
     a.g_lo = rg.g_lo;
+    a.g_hi = rg.g_hi;
     a.cell_edge = sqrtf(sa.cut2_f);
     a.seg_bead_lo = c.seg_bead_lo;
     a.seg_cell_base = c.seg_cell_base;
@@ -1025,7 +1386,38 @@ void launch_rebuild(const StepArgs &sa, const DevCells &c, const DevPairList &pl
     a.sorted_base = rg.b_lo;
     a.cell_base0 = rg.c_lo;
     a.rep_status = sa.rep_status;
+    a.seg_box = c.seg_box;
     const int nb = rg.b_hi - rg.b_lo, nc = rg.c_hi - rg.c_lo;
+    BuildExtra x;
+    x.nat_row = sa.topo.nat_row;
+    x.nat_col = sa.topo.nat_col;
+    x.cut2_d = sa.cut2_d;
+    x.cut2_f = sa.cut2_f;
+    x.pl_start = pl.start;
+    x.pl_len = pl.len;
+    x.pl_col = pl.col;
+    x.pl_cursor = pl.cursor;
+    x.pl_seg_base = pl.seg_base;
+    x.pl_seg_end = pl.seg_end;
+    x.rep_status = sa.rep_status;
+    if (rg.max_seg > 0 && rg.max_seg <= kBruteBeads && c.brute_cta_lo && rg.k_hi > rg.k_lo) {
+        // small segments: every bead against every bead, no cell list
+        static bool brute_attr = false;
+        if (!brute_attr) {
+            cudaFuncSetAttribute(k_pl_brute, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)sizeof(float) * 3 * kBruteBeads);
+            brute_attr = true;
+        }
+        BruteArgs bz;
+        bz.cta_lo = c.brute_cta_lo;
+        bz.done = c.brute_done;
+        bz.used = c.brute_used;
+        bz.k_lo = rg.k_lo;
+        const size_t smem = sizeof(float) * 3 * (size_t)((rg.max_seg + 1) & ~1);
+        k_pl_brute<<<rg.k_hi - rg.k_lo, kBuildWarps * 32, smem, s>>>(a, x, bz);
+        if (launches) *launches += 1;
+        return;
+    }
     if (rg.max_seg > 0 && rg.max_seg <= kFuseBeads) {
         // every segment small: its whole cell list in one CTA, one launch for the range
         static bool attr_set = false;
@@ -1039,25 +1431,16 @@ void launch_rebuild(const StepArgs &sa, const DevCells &c, const DevPairList &pl
             a, pl.cursor, pl.seg_base);
         if (launches) *launches += 1;
     } else {
-        // large segments get a full CTA each for their bounding box
-        const int setup_threads = (int64_t)nb > 2048 * (int64_t)(rg.g_hi - rg.g_lo) ? 1024 : 128;
-        k_seg_setup<<<rg.g_hi - rg.g_lo, setup_threads, 0, s>>>(a, pl.cursor, pl.seg_base);
+        // bounding boxes: one CTA per 4096 beads of the largest segment (at most 128 per
+        // segment), merged by atomics, then the grids
+        const int slices = std::min(128, std::max(1, (rg.max_seg + 4095) / 4096));
+        k_seg_bbox<<<dim3(rg.g_hi - rg.g_lo, slices), 256, 0, s>>>(a);
+        k_seg_grid<<<blocks_for(rg.g_hi - rg.g_lo, 128), 128, 0, s>>>(a, rg.g_hi - rg.g_lo, pl.cursor, pl.seg_base);
         k_cell_count<<<blocks_for(nb, 256), 256, 0, s>>>(a, rg.b_lo, rg.b_hi);
         scan_exclusive(c.cell_cnt + rg.c_lo, c.cell_start, nc, c.scan_tmp, s, launches);
         k_cell_scatter<<<blocks_for(nb, 256), 256, 0, s>>>(a, rg.b_lo, rg.b_hi);
-        if (launches) *launches += 3;
+        if (launches) *launches += 4;
     }
-    BuildExtra x;
-    x.nat_row = sa.topo.nat_row;
-    x.nat_col = sa.topo.nat_col;
-    x.cut2_d = sa.cut2_d;
-    x.cut2_f = sa.cut2_f;
-    x.pl_start = pl.start;
-    x.pl_len = pl.len;
-    x.pl_col = pl.col;
-    x.pl_cursor = pl.cursor;
-    x.pl_seg_end = pl.seg_end;
-    x.rep_status = sa.rep_status;
     k_pl_build<<<blocks_for(nb, kBuildWarps), kBuildWarps * 32, 0, s>>>(a, x, rg.b_lo, rg.b_hi);
     if (launches) *launches += 1;
 }
@@ -1170,7 +1553,7 @@ void launch_observables(const StepArgs &a, const DevPairList &pl, const DevObs &
     if (o.n_chunks <= 0) return;
     ObsArgs q = make_obs_args(a, pl, o, pos, k_off, gate);
     k_obs_partial<<<o.n_chunks, kObsThreads, 0, s>>>(q);
-    k_obs_final<<<blocks_for((int64_t)n_seg * 32, 128), 128, 0, s>>>(q, n_seg);
+    k_obs_final<<<n_seg, final_threads(o), 0, s>>>(q, n_seg);
     if (launches) *launches += 2;
 }
 
@@ -1181,7 +1564,7 @@ void launch_energy(const StepArgs &a, const DevPairList &pl, const DevObs &o, co
     ObsArgs q = make_obs_args(a, pl, o, pos, 0, 0);
     q.chunk0 = ch_lo;
     k_obs_partial<<<ch_hi - ch_lo, kObsThreads, 0, s>>>(q);
-    k_energy_sum<<<1, 32, 0, s>>>(o.partial, o.seg_chunk_lo, g_lo, g_hi, out);
+    k_energy_sum<<<1, kObsFinalMaxThreads, 0, s>>>(o, g_lo, g_hi, out);
     if (launches) *launches += 2;
 }
 
@@ -1192,7 +1575,7 @@ void launch_observables_seg(const StepArgs &a, const DevPairList &pl, const DevO
     ObsArgs q = make_obs_args(a, pl, o, pos, k_off, 0);
     q.chunk0 = ch_lo;
     k_obs_partial<<<ch_hi - ch_lo, kObsThreads, 0, s>>>(q);
-    k_obs_final_one<<<1, 32, 0, s>>>(q, g, n_seg, event_off);
+    k_obs_final_one<<<1, final_threads(o), 0, s>>>(q, g, n_seg, event_off);
     if (launches) *launches += 2;
 }
 

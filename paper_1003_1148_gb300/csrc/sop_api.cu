@@ -19,7 +19,7 @@ namespace {
 
 thread_local std::string g_create_error;
 
-constexpr int kObsChunk = 32;          // beads per FP64 observable partial (FP64 is slow per SM: spread it)
+constexpr int kObsChunk = kObsChunkBeads;   // beads per FP64 observable partial (FP64 is slow per SM: spread it)
 // Largest system the batched schedule takes: its state lives in shared memory, one CTA per
 // system up to about 3,400 beads (rows in global memory beyond 512), and the cluster form,
 // which keeps a copy of all positions in every CTA of the cluster, up to 4,096.
@@ -48,7 +48,7 @@ struct sop_ctx {
     std::vector<uint8_t> fixed_by_mask;   // [n] fixed through the topology's fixed_mask (never cleared)
     std::vector<int32_t> h_nat_row, h_nat_col;
     std::vector<double> h_nat_r0;
-    std::vector<int32_t> h_seg_bead_lo, h_seg_cell_base, h_seg_chunk_lo;
+    std::vector<int32_t> h_seg_bead_lo, h_seg_cell_base, h_seg_chunk_lo, h_brute_cta_lo;
     // device memory
     std::vector<void *> allocs;
     int32_t *d_chain = nullptr, *d_sys = nullptr, *d_sys_lo = nullptr, *d_sys_ree_last = nullptr,
@@ -224,6 +224,8 @@ SegRange full_range(const sop_ctx *c) {
     r.c_lo = c->h_seg_cell_base[0];
     r.c_hi = c->h_seg_cell_base[c->n_seg];
     r.max_seg = c->max_sys;
+    r.k_lo = c->h_brute_cta_lo[0];
+    r.k_hi = c->h_brute_cta_lo[c->n_seg];
     return r;
 }
 
@@ -236,6 +238,8 @@ SegRange seg_range(const sop_ctx *c, int g_lo, int g_hi) {
     r.c_lo = c->h_seg_cell_base[g_lo];
     r.c_hi = c->h_seg_cell_base[g_hi];
     r.max_seg = c->max_sys;
+    r.k_lo = c->h_brute_cta_lo[g_lo];
+    r.k_hi = c->h_brute_cta_lo[g_hi];
     return r;
 }
 
@@ -1558,8 +1562,10 @@ sop_status create_impl(sop_ctx *c, const sop_topology *topo, const double *xyz, 
     CUDA_OR_RETURN(c, dalloc(c, &c->cells.cell_cnt, cells));
     CUDA_OR_RETURN(c, cudaMemset(c->cells.cell_cnt, 0, sizeof(int32_t) * cells));
     CUDA_OR_RETURN(c, dalloc(c, &c->cells.cell_start, cells + 1));
-    CUDA_OR_RETURN(c, dalloc(c, &c->cells.sorted, (size_t)R * n));
+    CUDA_OR_RETURN(c, dalloc(c, &c->cells.sorted, (size_t)R * n));   // float4 per bead
     CUDA_OR_RETURN(c, dalloc(c, &c->cells.scan_tmp, scan_tmp_elems(cells)));
+    CUDA_OR_RETURN(c, dalloc(c, &c->cells.seg_box, 8 * (size_t)c->n_seg));
+    launch_seg_box_init(c->cells.seg_box, c->n_seg, c->stream);
     int64_t *d_plb = nullptr, *d_ple = nullptr;
     CUDA_OR_RETURN(c, upload(c, &d_plb, pl_base));
     CUDA_OR_RETURN(c, upload(c, &d_ple, pl_end));
@@ -1573,6 +1579,24 @@ sop_status create_impl(sop_ctx *c, const sop_topology *topo, const double *xyz, 
     CUDA_OR_RETURN(c, dalloc(c, &c->pl.len, (size_t)R * n));
     CUDA_OR_RETURN(c, dalloc(c, &c->pl.col, cols));
     CUDA_OR_RETURN(c, dalloc(c, &c->pl.cursor, c->n_seg));
+    // the all-pairs build of small segments expects each cursor at its first column
+    std::vector<int32_t> cur0(c->n_seg);
+    for (int g = 0; g < c->n_seg; ++g) cur0[g] = (int32_t)pl_base[g];
+    CUDA_OR_RETURN(c, cudaMemcpy(c->pl.cursor, cur0.data(), sizeof(int32_t) * c->n_seg, cudaMemcpyHostToDevice));
+    c->h_brute_cta_lo.assign(c->n_seg + 1, 0);
+    for (int g = 0; g < c->n_seg; ++g) {
+        const int ng = c->h_seg_bead_lo[g + 1] - c->h_seg_bead_lo[g];
+        c->h_brute_cta_lo[g + 1] = c->h_brute_cta_lo[g] + (ng + kBruteSliceBeads - 1) / kBruteSliceBeads;
+    }
+    {
+        int32_t *d_bcl = nullptr;
+        CUDA_OR_RETURN(c, upload(c, &d_bcl, c->h_brute_cta_lo));
+        c->cells.brute_cta_lo = d_bcl;
+    }
+    CUDA_OR_RETURN(c, dalloc(c, &c->cells.brute_done, c->n_seg));
+    CUDA_OR_RETURN(c, cudaMemset(c->cells.brute_done, 0, sizeof(int32_t) * c->n_seg));
+    CUDA_OR_RETURN(c, dalloc(c, &c->cells.brute_used, c->n_seg));
+    CUDA_OR_RETURN(c, cudaMemset(c->cells.brute_used, 0, sizeof(int32_t) * c->n_seg));
     // ---- observables: chunks of at most kObsChunk beads per segment
     std::vector<int32_t> ch_seg, ch_lo, ch_hi;
     c->h_seg_chunk_lo.assign(c->n_seg + 1, 0);
@@ -1595,6 +1619,9 @@ sop_status create_impl(sop_ctx *c, const sop_topology *topo, const double *xyz, 
     c->obs.chunk_lo = d_cl;
     c->obs.chunk_hi = d_chh;
     c->obs.seg_chunk_lo = d_scl;
+    c->obs.max_seg_chunks = 0;
+    for (int g = 0; g < c->n_seg; ++g)
+        c->obs.max_seg_chunks = std::max(c->obs.max_seg_chunks, c->h_seg_chunk_lo[g + 1] - c->h_seg_chunk_lo[g]);
     CUDA_OR_RETURN(c, dalloc(c, &c->obs.partial, 8 * (size_t)c->obs.n_chunks));
     c->obs.cap = std::max<int64_t>(c->prm.obs_capacity, c->n_seg);
     CUDA_OR_RETURN(c, dalloc(c, &c->obs.ring, c->obs.cap));
@@ -1856,6 +1883,8 @@ sop_status sop_forces(sop_ctx *c, int32_t replica, double *out_f, double *out_en
             CUDA_OR_RETURN(c, dalloc(c, &c->pl2.len, (size_t)c->R * c->n));
             CUDA_OR_RETURN(c, dalloc(c, &c->pl2.col, c->pl_cap));
             CUDA_OR_RETURN(c, dalloc(c, &c->pl2.cursor, c->n_seg));
+            CUDA_OR_RETURN(c, cudaMemcpy(c->pl2.cursor, c->pl.cursor, sizeof(int32_t) * c->n_seg,
+                                         cudaMemcpyDeviceToDevice));
             // rows of replicas not rebuilt here must read as empty, never as garbage
             CUDA_OR_RETURN(c, cudaMemset(c->pl2.start, 0, sizeof(int32_t) * (size_t)c->R * c->n));
             CUDA_OR_RETURN(c, cudaMemset(c->pl2.len, 0, sizeof(int32_t) * (size_t)c->R * c->n));

@@ -133,17 +133,18 @@ __device__ __forceinline__ float fene_coef(float r2, float r0, const ForceParams
     return -fp.k_fene * dr / (arg * r);
 }
 
-// Native 12-6: F_i = (12 eps_h / r^2) (s^6 - s^3) d with s = r0^2 / r^2.
+// Native 12-6: F_i = (12 eps_h / r^2) (s^6 - s^3) d with s = r0^2 / r^2. The reciprocal is
+// the fast approximate one (within 2 ulp), as in the batched forms' row_force.
 __device__ __forceinline__ float native_coef(float r2, float r0sq, const ForceParams &fp) {
-    const float inv_r2 = 1.0f / r2;
+    const float inv_r2 = __fdividef(1.0f, r2);
     const float s = r0sq * inv_r2;
     const float s3 = s * s * s;
-    return fp.eps12_h * inv_r2 * (s3 * s3 - s3);
+    return inv_r2 * s3 * fmaf(fp.eps12_h, s3, -fp.eps12_h);
 }
 
 // Repulsion: F_i = (6 eps_l / r^2) (sigma^2 / r^2)^3 d = 6 eps_l sigma^6 / r^8 d.
 __device__ __forceinline__ float repulsive_coef(float r2, const ForceParams &fp) {
-    const float inv_r2 = 1.0f / r2;
+    const float inv_r2 = __fdividef(1.0f, r2);
     const float i4 = inv_r2 * inv_r2;
     return fp.rep_k * (i4 * i4);
 }
@@ -194,14 +195,64 @@ __device__ __forceinline__ double sqrt_fast(double x) {
     return x * y;
 }
 
-// Is the native pair at squared distance d2 formed, r < r0 + 2 A (Q)? Decided on d2
-// against (r0 + 2)^2 away from the threshold and by the square root of d2 within a relative
-// 1e-12 of it, so that the outcome is that of comparing the correctly rounded square root.
-__device__ __forceinline__ bool native_formed(double d2, double r0) {
-    const double t = r0 + 2.0, t2 = t * t;
-    if (d2 < t2 * (1.0 - 1e-12)) return true;
-    if (d2 > t2 * (1.0 + 1e-12)) return false;
-    return __dsqrt_rn(d2) < t;
+// FP32 -> FP64 from the IEEE-754 encodings, in integer operations: a normal float's
+// exponent is rebiased (127 -> 1023) and its 23 fraction bits become the top of the 52.
+// Zero, subnormal, infinite and NaN inputs take the conversion instruction. Exact, like
+// the conversion, but off the FP64 pipe, which is narrow on this GPU (about 2 operations
+// per cycle per SM) and also executes the conversions.
+__device__ __forceinline__ double f2d(float f) {
+    const unsigned b = __float_as_uint(f);
+    if (((b >> 23) & 0xffu) - 1u >= 254u) return (double)f;
+    const unsigned hi = (b & 0x80000000u) | (((b & 0x7fffffffu) >> 3) + (896u << 20));
+    return __hiloint2double((int)hi, (int)(b << 29));
+}
+
+// Knuth's TwoSum: returns s = fl(a + b) and sets e with s + e = a + b exactly.
+__device__ __forceinline__ float two_sum(float a, float b, float &e) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return s;
+}
+
+// |a - b|^2 of two FP32 points as an FP64 value, computed in FP32: each difference exactly
+// as s + e (TwoSum, |e| <= 2^-24 |s|), each s^2 exactly as p + q (an FMA gives q), the three
+// p summed exactly into a two-float P + (u + v), and the small terms u + v + q + 2 s e
+// (at most about 2^-21 of the total) added in FP32. The result is within about 2^-42
+// (2e-13) relative of the exact squared distance; *d2f is the same value in FP32 (relative
+// 2^-24), a seed for rcp_seeded. Against the FP64 evaluation of the definition it trades
+// nine FP64 operations and six conversions for some thirty FP32 ones.
+__device__ __forceinline__ double dist2_two(float4 a, float4 b, float *d2f) {
+    float e0, e1, e2;
+    const float s0 = two_sum(a.x, -b.x, e0);
+    const float s1 = two_sum(a.y, -b.y, e1);
+    const float s2 = two_sum(a.z, -b.z, e2);
+    const float p0 = __fmul_rn(s0, s0), p1 = __fmul_rn(s1, s1), p2 = __fmul_rn(s2, s2);
+    const float q0 = __fmaf_rn(s0, s0, -p0), q1 = __fmaf_rn(s1, s1, -p1), q2 = __fmaf_rn(s2, s2, -p2);
+    float u, v;
+    const float t = two_sum(p0, p1, u);
+    const float P = two_sum(t, p2, v);
+    const float cross = __fmaf_rn(s0, e0, __fmaf_rn(s1, e1, __fmul_rn(s2, e2)));
+    const float lo = __fmaf_rn(2.0f, cross, __fadd_rn(__fadd_rn(u, v), __fadd_rn(__fadd_rn(q0, q1), q2)));
+    *d2f = __fadd_rn(P, lo);
+    return __dadd_rn(f2d(P), f2d(lo));
+}
+
+// 1/x in FP64 for finite x > 0, given xf, x rounded to FP32: the FP32 reciprocal of xf
+// (relative error below 2^-23) refined by one Newton step y + y (1 - x y), which squares
+// the error (to about 1e-14).
+__device__ __forceinline__ double rcp_seeded(double x, float xf) {
+    const double y = f2d(__frcp_rn(xf));
+    return fma(y, fma(-x, y, 1.0), y);
+}
+
+// sqrt(x) in FP64 for finite x > 0, given xf, x rounded to FP32: 1/sqrt(xf) refined by two
+// Newton steps y <- y (3 - x y^2) / 2, times x (relative error about 1e-15).
+__device__ __forceinline__ double sqrt_seeded(double x, float xf) {
+    double y = f2d(rsqrtf(xf));
+    y = y * fma(-0.5 * x * y, y, 1.5);
+    y = y * fma(-0.5 * x * y, y, 1.5);
+    return x * y;
 }
 
 // FP64 squared distance ((dx*dx + dy*dy) + dz*dz) with no contraction.
@@ -210,6 +261,18 @@ __device__ __forceinline__ double dist2_d(double ax, double ay, double az, doubl
     const double ey = __dsub_rn(ay, by);
     const double ez = __dsub_rn(az, bz);
     return __dadd_rn(__dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey)), __dmul_rn(ez, ez));
+}
+
+// Is the native pair (a, b) formed, r < r0 + 2 A (Q)? d2 is their squared distance to a
+// relative 1e-12 or better (dist2_d, dist2_two). Away from the threshold d2 against
+// (r0 + 2)^2 decides; within a relative 1e-10 of it the correctly rounded square root of
+// the FP64 definition ((dx*dx + dy*dy) + dz*dz) of the same FP32 positions does, so the
+// outcome is always that of the definition evaluated in FP64.
+__device__ __forceinline__ bool native_formed(double d2, double r0, float4 a, float4 b) {
+    const double t = r0 + 2.0, t2 = t * t;
+    if (d2 < t2 * (1.0 - 1e-10)) return true;
+    if (d2 > t2 * (1.0 + 1e-10)) return false;
+    return __dsqrt_rn(dist2_d(f2d(a.x), f2d(a.y), f2d(a.z), f2d(b.x), f2d(b.y), f2d(b.z))) < t;
 }
 
 }  // namespace sop

@@ -85,6 +85,7 @@ struct SegRange {
     int32_t b_lo = 0, b_hi = 0;   // global beads
     int32_t c_lo = 0, c_hi = 0;   // cells
     int32_t max_seg = 0;          // beads of the largest segment (0: unknown)
+    int32_t k_lo = 0, k_hi = 0;   // CTAs of the all-pairs list build (DevCells::brute_cta_lo)
 };
 
 // Cell-list scratch of the streamed rebuild.
@@ -97,7 +98,11 @@ struct DevCells {
     int32_t *cell_of = nullptr;             // [R*n] global cell index of each bead
     int32_t *cell_cnt = nullptr;            // [n_cells] zero between rebuilds
     int32_t *cell_start = nullptr;          // [n_cells+1]
-    int32_t *sorted = nullptr;              // [R*n] global bead indices grouped by cell
+    float4 *sorted = nullptr;               // [R*n] positions grouped by cell, bead index (int bits) in w
+    int32_t *seg_box = nullptr;             // [n_seg*8] bounding-box keys of large segments (reset after use)
+    const int32_t *brute_cta_lo = nullptr;  // [n_seg+1] first CTA of each segment in the all-pairs build
+    int32_t *brute_done = nullptr;          // [n_seg] CTAs done in the current all-pairs build (0 between)
+    int32_t *brute_used = nullptr;          // [n_seg] list entries of each segment after its last build
     int32_t *scan_tmp = nullptr;            // scan block sums
     int64_t n_cells = 0;
 };
@@ -109,6 +114,7 @@ struct DevObs {
     const int32_t *chunk_lo = nullptr;      // [n_chunks] global bead range
     const int32_t *chunk_hi = nullptr;
     const int32_t *seg_chunk_lo = nullptr;  // [n_seg+1]
+    int32_t max_seg_chunks = 0;             // most chunks of one segment
     double *partial = nullptr;              // [n_chunks * 8]
     sop_record *ring = nullptr;             // [cap]
     int64_t cap = 0;
@@ -139,6 +145,16 @@ void launch_native_fill(const double *native_xyz, const int32_t *chain, const in
 
 // Streamed rebuild of the Verlet list for global beads [b_lo, b_hi) = segments [g_lo, g_hi).
 // pos: the positions to build from; snap (may be null) receives a copy of them.
+// Beads per chunk of the FP64 observable sums of the streamed forms (one CTA each).
+constexpr int kObsChunkBeads = 32;
+// Segments up to this many beads build their Verlet rows by testing every pair of the
+// segment (no cell list: 16 passes of 64 candidates per bead cost less than the 27-cell
+// walk plus the cell list; at 4,096 beads, measured, the all-pairs build took 37 us on one
+// segment against 33 us for the cell list and its walk); kBruteSliceBeads beads per CTA.
+constexpr int kBruteMaxBeads = 1024;
+constexpr int kBruteSliceBeads = 16;
+// Put every segment's bounding-box accumulator in its empty state (once, after allocation).
+void launch_seg_box_init(int32_t *seg_box, int32_t n_seg, cudaStream_t s);
 void launch_rebuild(const StepArgs &a, const DevCells &c, const DevPairList &pl, const float4 *pos, float4 *snap,
                     const SegRange &rg, cudaStream_t s, int64_t *launches);
 

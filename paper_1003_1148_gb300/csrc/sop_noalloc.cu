@@ -6,7 +6,7 @@
 // buffer it needs lives in the file-scope array below instead of memory from
 // cudaMalloc. The caller passes the inputs and the output rows.
 //
-// The array is a fixed 1.8 MiB that every GPU which loads this library keeps
+// The array is a fixed 2.5 MiB that every GPU which loads this library keeps
 // until the process exits. Each call reads its counters back and synchronises its
 // stream, so it cannot be recorded into a CUDA graph. Its device address is looked up once per device
 // with cudaGetSymbolAddress (host code cannot use the symbol itself: in host
@@ -14,6 +14,7 @@
 // array, so calls whose work overlaps on the GPU race on it.
 #include <cuda_runtime.h>
 
+#include <climits>
 #include <mutex>
 #include <string>
 
@@ -29,8 +30,8 @@ constexpr int kScanTmp = (kMaxCells + sop::kScanTileElems - 1) / sop::kScanTileE
 constexpr int align4(int w) { return (w + 3) / 4 * 4; }
 constexpr int kOffSys = 0;                                      // [n] system id (all 0)
 constexpr int kOffCellOf = kOffSys + align4(kMaxBeads);         // [n]
-constexpr int kOffSorted = kOffCellOf + align4(kMaxBeads);      // [n]
-constexpr int kOffCellCnt = kOffSorted + align4(kMaxBeads);     // [cells]
+constexpr int kOffSorted = kOffCellOf + align4(kMaxBeads);      // float4 [n]
+constexpr int kOffCellCnt = kOffSorted + 4 * kMaxBeads;         // [cells]
 constexpr int kOffCellStart = kOffCellCnt + align4(kMaxCells);  // [cells + 1]
 constexpr int kOffScan = kOffCellStart + align4(kMaxCells + 1); // [scan]
 constexpr int kOffSegLo = kOffScan + align4(kScanTmp);          // float4
@@ -42,7 +43,11 @@ constexpr int kOffCellBase = kOffBeadLo + 2;                    // [2] segment c
 constexpr int kOffCursor = kOffCellBase + 2;                    // [1]
 constexpr int kOffStatus = kOffCursor + 1;                      // [1]
 constexpr int kOffHalt = kOffStatus + 1;                        // [1]
-constexpr int kWords = align4(kOffHalt + 1);
+constexpr int kOffUsed = kOffHalt + 1;                          // [1] entries after an all-pairs build
+constexpr int kOffSegBox = align4(kOffUsed + 1);                // [8] bounding-box accumulator
+constexpr int kOffBruteLo = kOffSegBox + 8;                     // [2] all-pairs build CTAs of the segment
+constexpr int kOffDone = kOffBruteLo + 2;                       // [1] its CTAs done
+constexpr int kWords = align4(kOffDone + 1);
 
 static __device__ __align__(256) int32_t g_noalloc_scratch[kWords];
 
@@ -65,6 +70,13 @@ __global__ void k_noalloc_init(int32_t *w, int n, int64_t cap) {
         w[kOffCursor] = 0;
         w[kOffStatus] = 0;
         w[kOffHalt] = 0;
+        w[kOffSegBox + 0] = w[kOffSegBox + 1] = w[kOffSegBox + 2] = INT_MAX;
+        w[kOffSegBox + 3] = w[kOffSegBox + 4] = w[kOffSegBox + 5] = INT_MIN;
+        w[kOffSegBox + 6] = w[kOffSegBox + 7] = 0;
+        w[kOffUsed] = 0;
+        w[kOffBruteLo] = 0;
+        w[kOffBruteLo + 1] = (n + sop::kBruteSliceBeads - 1) / sop::kBruteSliceBeads;
+        w[kOffDone] = 0;
     }
 }
 
@@ -136,8 +148,12 @@ extern "C" sop_status sop_pairlist_build_noalloc(const float *pos4, int32_t n, c
     cells.cell_of = w + kOffCellOf;
     cells.cell_cnt = w + kOffCellCnt;
     cells.cell_start = w + kOffCellStart;
-    cells.sorted = w + kOffSorted;
+    cells.sorted = reinterpret_cast<float4 *>(w + kOffSorted);
     cells.scan_tmp = w + kOffScan;
+    cells.seg_box = w + kOffSegBox;
+    cells.brute_cta_lo = w + kOffBruteLo;
+    cells.brute_done = w + kOffDone;
+    cells.brute_used = w + kOffUsed;
     cells.n_cells = 2 * (int64_t)n + 8;
 
     DevPairList pl;
@@ -157,6 +173,8 @@ extern "C" sop_status sop_pairlist_build_noalloc(const float *pos4, int32_t n, c
     rg.c_lo = 0;
     rg.c_hi = 2 * n + 8;
     rg.max_seg = n;
+    rg.k_lo = 0;
+    rg.k_hi = (n + kBruteSliceBeads - 1) / kBruteSliceBeads;
 
     k_noalloc_init<<<64, 256, 0, s>>>(w, n, cap);
     launch_rebuild(sa, cells, pl, reinterpret_cast<const float4 *>(pos4), nullptr, rg, s, nullptr);
@@ -165,14 +183,14 @@ extern "C" sop_status sop_pairlist_build_noalloc(const float *pos4, int32_t n, c
         set_global_error(std::string("noalloc: launch: ") + cudaGetErrorString(e));
         return SOP_ERR_CUDA;
     }
-    int32_t out[2] = {0, 0};   // cursor, status
-    e = cudaMemcpyAsync(out, w + kOffCursor, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+    int32_t out[4] = {0, 0, 0, 0};   // cursor, status, halt, entries of an all-pairs build
+    e = cudaMemcpyAsync(out, w + kOffCursor, 4 * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) {
         set_global_error(std::string("noalloc: ") + cudaGetErrorString(e));
         return SOP_ERR_CUDA;
     }
-    *nnz = out[0];
+    *nnz = n <= kBruteMaxBeads ? out[3] : out[0];   // the all-pairs build leaves its cursor reset
     switch (out[1]) {
     case 0: return SOP_OK;
     case SOP_ERR_PAIRLIST_OVERFLOW:

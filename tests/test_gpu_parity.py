@@ -97,6 +97,26 @@ def test_pairlist_bit_exact_after_steps(sop, orc, workloads, schedule):
         sim.close()
 
 
+@pytest.mark.parametrize("n", [1024, 1025, 6000, 9000])
+def test_pairlist_every_build_path_bit_exact(sop, orc, synth, n):
+    """One system of n beads: up to 1,024 beads the rows come from the all-pairs build,
+    up to 8,192 from the one-CTA cell list, above that from the staged cell list; each
+    against the oracle's list at the same positions, after 0 and 23 steps."""
+    w = synth.fiber4096(n=n, steps=100)
+    sim = sop.from_workload(w, n_replicas=1, schedule="streamed")
+    m = orc.model_from_workload(w)
+    for steps in (0, 23):
+        if steps:
+            sim.step(steps)
+            sim.pairlist_rebuild()
+        x = sim.get_positions(0)
+        rp, col = sim.get_pairlist(0)
+        pi, pj = m.pairlist(x, cells=True)
+        assert csr_pairs(rp, col) == set(zip(pi.tolist(), pj.tolist())), (n, steps)
+        assert csr_is_symmetric_sorted(rp, col)
+    sim.close()
+
+
 def oracle_with_externals(orc, w, x_start):
     m = orc.model_from_workload(w)
     if w.pulls:

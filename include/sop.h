@@ -42,8 +42,12 @@
 extern "C" {
 #endif
 
-#define SOP_ABI_VERSION 2
+/* Not in the paper: the version of this interface (also stamped into checkpoints). */
+#define SOP_ABI_VERSION 3
 
+/* Not in the paper: the status every call returns. The failure conditions follow
+ * Eq. 1 (the FENE term is undefined at |r - r0| >= R0) and Sec. III.A (the Verlet
+ * list's capacity). */
 typedef enum {
     SOP_OK = 0,
     SOP_ERR_INVALID_ARG = 1,       /* a pointer, size or parameter was rejected */
@@ -59,7 +63,9 @@ typedef enum {
     SOP_ERR_CAPACITY = 11          /* a caller-provided output buffer is too small */
 } sop_status;
 
-/* How the steps are executed (the schedule). */
+/* How the steps are executed (the schedule): Sec. III's kernels (particle-based,
+ * Sec. III.A; pair-based, Sec. III.B; the fused integration kernel, Sec. III.D) in
+ * forms of this library's own (the persistent batched kernel, graph replay). */
 typedef enum {
     SOP_SCHED_AUTO = 0,      /* choose per workload (autotuned) */
     SOP_SCHED_BATCHED = 1,   /* persistent fused kernel, one CTA per (replica, system), state in shared memory */
@@ -85,7 +91,8 @@ typedef enum {
                                  advances only in steps in which the bead moves */
 } sop_rng;
 
-/* Equations of motion. */
+/* Equations of motion (Eq. 2 and Algorithm 7; the underdamped form is the extension the
+ * Conclusion names). */
 typedef enum {
     SOP_INTEGRATOR_OVERDAMPED = 0,   /* Algorithm 7: r += F h/zeta + g sqrt(2 kT h/zeta) */
     SOP_INTEGRATOR_BAOAB = 1         /* underdamped Langevin dynamics (the limit the Conclusion names), by the
@@ -96,11 +103,13 @@ typedef enum {
                                         is the one after the O sub-step (0 at the start). */
 } sop_integrator;
 
+/* Not in the paper: the opaque handle that owns a simulation's device memory. */
 typedef struct sop_ctx sop_ctx;
 
-/* Topology of one replica. Chains are contiguous bead ranges; systems are
- * contiguous chain ranges. Beads interact (native contacts, repulsion) only
- * with beads of the same system. */
+/* Topology of one replica (the SOP model's chains of C-alpha beads, Sec. IV.A; bonds
+ * join consecutive beads of a chain, Eq. 1's first term). Chains are contiguous bead
+ * ranges; systems are contiguous chain ranges. Beads interact (native contacts,
+ * repulsion) only with beads of the same system. */
 typedef struct {
     int32_t n_beads;                 /* beads per replica, >= 1 */
     int32_t n_chains;                /* >= 1 */
@@ -133,6 +142,10 @@ typedef struct {
     int32_t rng;            /* a sop_rng (0 = Philox) */
     int32_t integrator;     /* a sop_integrator (0 = overdamped) */
     double mass;            /* bead mass, (kcal/mol) ps^2 / A^2 (> 0 for SOP_INTEGRATOR_BAOAB) */
+    int32_t obs_every_q;    /* cadence of Q in steps: 0 = every record; else a multiple of obs_every, and
+                               records at other steps carry NaN in q. Sec. IV.B reads the force-extension
+                               curve f(R) along the pull; Q is a slower structural readout, so the two get
+                               their own cadences (the values are the caller's; the paper gives none) */
 } sop_params;
 
 /* Cantilever on one system (Sec. IV.B): `anchor` is held fixed; a spring of
@@ -147,7 +160,9 @@ typedef struct {
     double v;               /* A per step */
 } sop_pull_params;
 
-/* One observable record (all FP64). */
+/* One observable record (all FP64): Eq. 1's energy and the readouts of Sec. IV.B
+ * (force f and extension R of the force-extension curve, Fig. 3), plus Q and the
+ * end-to-end distance. */
 typedef struct {
     double step;            /* step at which the record was taken */
     double replica;
@@ -159,7 +174,7 @@ typedef struct {
     double r_ee;            /* end-to-end distance of the system's first chain */
 } sop_record;
 
-/* Counters of the work queued so far. */
+/* Not in the paper: counters of the work queued so far. */
 typedef struct {
     int64_t steps;                /* steps completed (the global step counter) */
     int64_t kernel_launches;      /* kernels launched by this context (graph nodes counted) */
@@ -203,60 +218,67 @@ sop_status sop_step(sop_ctx *ctx, int64_t n_steps);
  * double (may be NULL). Does not change the simulation state. */
 sop_status sop_forces(sop_ctx *ctx, int32_t replica, double *out_f, double *out_energy);
 
-/* Rebuild the Verlet list of every replica from the current positions now. */
+/* Rebuild the Verlet list of every replica from the current positions now (Sec. III.A,
+ * Algorithm 3: pairs within pair_cut, not bonded, not native). */
 sop_status sop_pairlist_rebuild(sop_ctx *ctx);
 
-/* Start (or replace) cantilever pulling on the listed systems (all replicas).
- * Anchors become fixed. n = 0 removes all springs. */
+/* Start (or replace) cantilever pulling on the listed systems (all replicas), the
+ * protocol of Sec. IV.B (one end fixed, the other pulled by a spring whose end moves at
+ * constant speed). Anchors become fixed. n = 0 removes all springs. */
 sop_status sop_pull(sop_ctx *ctx, int32_t n, const sop_pull_params *pulls);
 
 /* Start (or replace) a repulsive spherical indenter acting on every bead of
- * every replica: V = eps_l (sigma / (|r - c| - radius))^6, centre c starting
+ * every replica (the force-indentation application of the Conclusion; the wall
+ * repels with Eq. 1's (sigma/r)^6 form measured from the sphere's surface): V = eps_l (sigma / (|r - c| - radius))^6, centre c starting
  * at `center` and moving v A/step along unit `direction`. radius <= 0 removes it. */
 sop_status sop_indenter(sop_ctx *ctx, const double center[3], const double direction[3], double radius,
                         double v);
 
-/* Positions of one replica ([3*n_beads] FP64 host), or of all replicas when
- * replica == -1 ([3*n_beads*n_replicas], replica major). */
+/* Not in the paper (state access): positions of one replica ([3*n_beads] FP64 host),
+ * or of all replicas when replica == -1 ([3*n_beads*n_replicas], replica major). */
 sop_status sop_get_positions(sop_ctx *ctx, int32_t replica, double *out_xyz);
-/* Set positions (converted to FP32, compensation reset). replica == -1 sets
+/* Not in the paper (state access): set positions (converted to FP32, compensation
+ * reset; Algorithm 7's compensated sum). replica == -1 sets
  * all replicas from a [3*n_beads*n_replicas] array. The Verlet list is rebuilt from
  * the new positions at once (they replace the snapshot of the last rebuild), so a
  * list built from other positions is never used with them; the step counter, and with
  * it the cantilever tips and the indenter, is unchanged. */
 sop_status sop_set_positions(sop_ctx *ctx, int32_t replica, const double *xyz);
 
-/* Stored velocities of the underdamped integrator (A/ps, the velocity after the O
+/* Not in the paper (state access): stored velocities of the underdamped integrator (A/ps, the velocity after the O
  * sub-step of the last step), FP64 host [3*n_beads] (replica >= 0) or
  * [3*n_beads*n_replicas] (replica == -1). SOP_ERR_UNSUPPORTED for the overdamped
  * integrator. Part of the checkpoint. */
 sop_status sop_get_velocities(sop_ctx *ctx, int32_t replica, double *out_v);
 sop_status sop_set_velocities(sop_ctx *ctx, int32_t replica, const double *v);
 
-/* Verlet list of `replica` as canonical CSR over its beads: row i holds every
- * partner j (both directions, ascending). row_ptr: [n_beads+1]; col: [cap].
+/* The Verlet list of Sec. III.A (Algorithm 3) of `replica`, as canonical CSR over its
+ * beads: row i holds every partner j (both directions, ascending). row_ptr: [n_beads+1]; col: [cap].
  * *nnz receives the entry count; SOP_ERR_CAPACITY when cap < nnz. */
 sop_status sop_get_pairlist(sop_ctx *ctx, int32_t replica, int32_t *row_ptr, int32_t *col, int64_t cap,
                             int64_t *nnz);
 
-/* Native contact map as canonical CSR (both directions, ascending) with the
- * FP64 native distance r0 of each entry. */
+/* The native contacts of Eq. 1's second term (Sec. IV.A: pairs closer than native_cut
+ * in the native structure) as canonical CSR (both directions, ascending) with the FP64
+ * native distance r0 of each entry. */
 sop_status sop_get_native_map(sop_ctx *ctx, int32_t *row_ptr, int32_t *col, double *r0, int64_t cap,
                               int64_t *nnz);
 
-/* Copy out and clear the observable records taken since the last call, in
+/* The readouts of Sec. IV.B (see sop_record). Copy out and clear the records taken
+ * since the last call, in
  * order of step, then replica, then system. When more records were taken than
  * the ring holds, the oldest are lost and *n_lost says how many. */
 sop_status sop_get_observables(sop_ctx *ctx, sop_record *out, int64_t cap, int64_t *n_records, int64_t *n_lost);
 
-/* Checkpoint: the step counter, positions, compensation terms, pulling and
+/* Not in the paper: checkpoint and resume. Saves the step counter, positions, compensation terms, pulling and
  * indenter set-up, status, the Hybrid Taus state and the velocities (when used).
  * Resuming from it continues bit-exactly.
  * With buf == NULL, *size receives the byte count needed. */
 sop_status sop_get_state(sop_ctx *ctx, void *buf, int64_t cap, int64_t *size);
 sop_status sop_set_state(sop_ctx *ctx, const void *buf, int64_t size);
 
-/* Hybrid Taus state of every bead of every replica (SOP_RNG_HYBRID_TAUS only):
+/* State of the Hybrid Taus generator of Sec. III.C (Algorithm 6), every bead of every
+ * replica (SOP_RNG_HYBRID_TAUS only):
  * n_words = 4 * n_replicas * n_beads uint32 host words, replica-major, bead i of
  * replica r at 4 (r n_beads + i), words (y1, y2, y3, y4). sop_create seeds them from
  * params.seed with SplitMix64 (Steele, Lea, Flood, OOPSLA'14): for replica r and bead i
@@ -334,22 +356,23 @@ sop_status sop_bead_noise(uint64_t key, int64_t step, uint32_t bead_lo, int64_t 
  * (text in sop_last_error(NULL)). */
 sop_status sop_fp32_peak(double seconds, double *tflops, double *elapsed_ms, int32_t *sm_count);
 
-/* Per-replica status ([n_replicas] int32 host): a sop_status value each. */
+/* Not in the paper: per-replica status ([n_replicas] int32 host), a sop_status value each
+ * (a replica whose FENE bond breaks, Eq. 1, is frozen and reported here). */
 sop_status sop_replica_status(sop_ctx *ctx, int32_t *out);
 
-/* Ask a running sop_step to stop at the next check (thread-safe, async). */
+/* Not in the paper: ask a running sop_step to stop at the next check (thread-safe, async). */
 void sop_abort(sop_ctx *ctx);
 
-/* Counters and the schedule in use. */
+/* Not in the paper: counters and the schedule in use. */
 sop_status sop_get_stats(sop_ctx *ctx, sop_stats *out);
 
-/* Text of the last error of ctx (or of the last failed sop_create when ctx is NULL). */
+/* Not in the paper: text of the last error of ctx (or of the last failed sop_create when ctx is NULL). */
 const char *sop_last_error(const sop_ctx *ctx);
 
-/* Free all device and host memory of ctx. NULL is allowed. */
+/* Not in the paper: free all device and host memory of ctx. NULL is allowed. */
 void sop_destroy(sop_ctx *ctx);
 
-/* Largest system sop_pairlist_build_noalloc accepts. */
+/* Not in the paper: largest system sop_pairlist_build_noalloc accepts. */
 #define SOP_NOALLOC_MAX_BEADS 65536
 
 /*

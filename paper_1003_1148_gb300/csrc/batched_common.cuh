@@ -388,6 +388,7 @@ __device__ __forceinline__ void write_record(const BatchedArgs &a, const double 
     rec.extension = pulled ? v[2] : (e.has_indenter ? e.ind_v * ((double)step - e.ind_n0) : 0.0);
     const int np = t.sys_nat_pairs[s];
     rec.q = np > 0 ? v[3] / (double)np : 0.0;
+    if (a.obs.q_every > 0 && step % a.obs.q_every != 0) rec.q = __longlong_as_double(0x7ff8000000000000LL);
     rec.r_ee = v[5];
     a.obs.ring[(event * a.n_seg + g) % a.obs.cap] = rec;
 }

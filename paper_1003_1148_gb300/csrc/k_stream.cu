@@ -1284,6 +1284,7 @@ __device__ void write_record(const ObsArgs &q, int g, int64_t step, int64_t slot
     rec.extension = pulled ? acc[2] : (e.has_indenter ? e.ind_v * ((double)step - e.ind_n0) : 0.0);
     const int np = q.a.topo.sys_nat_pairs[s];
     rec.q = np > 0 ? acc[3] / (double)np : 0.0;
+    if (q.o.q_every > 0 && step % q.o.q_every != 0) rec.q = __longlong_as_double(0x7ff8000000000000LL);
     rec.r_ee = acc[5];
     q.o.ring[slot] = rec;
 }

@@ -628,6 +628,8 @@ sop_status validate_params(const sop_params *p) {
     if (p->n_replicas < 1) return fail(nullptr, SOP_ERR_INVALID_ARG, "params: n_replicas >= 1");
     if (p->obs_every < 0 || p->obs_capacity < 0 || p->pairs_per_bead < 0)
         return fail(nullptr, SOP_ERR_INVALID_ARG, "params: obs_every, obs_capacity, pairs_per_bead >= 0");
+    if (p->obs_every_q < 0 || (p->obs_every_q > 0 && (p->obs_every <= 0 || p->obs_every_q % p->obs_every != 0)))
+        return fail(nullptr, SOP_ERR_INVALID_ARG, "params: obs_every_q must be 0 or a multiple of obs_every > 0");
     if (p->schedule < SOP_SCHED_AUTO || p->schedule > SOP_SCHED_BATCHED_PAIRS)
         return fail(nullptr, SOP_ERR_INVALID_ARG, "params: unknown schedule");
     if (p->rng != SOP_RNG_PHILOX && p->rng != SOP_RNG_HYBRID_TAUS)
@@ -1627,6 +1629,7 @@ sop_status create_impl(sop_ctx *c, const sop_topology *topo, const double *xyz, 
     CUDA_OR_RETURN(c, dalloc(c, &c->obs.ring, c->obs.cap));
     c->obs.events = c->d_events;
     c->obs.obs_every = c->prm.obs_every;
+    c->obs.q_every = c->prm.obs_every_q;
     // ---- externals (none yet)
     c->pull_of_sys.assign(c->n_sys, -1);
     CUDA_OR_RETURN(c, upload(c, &c->d_pull_of_sys, c->pull_of_sys));

@@ -120,6 +120,7 @@ struct DevObs {
     int64_t cap = 0;
     int64_t *events = nullptr;              // [1] cadence events recorded
     int32_t obs_every = 0;
+    int32_t q_every = 0;                    // records at steps not a multiple of this carry NaN in q (0: none)
 };
 
 // Set the text returned by sop_last_error(NULL) (sop_api.cu).

@@ -59,7 +59,8 @@ class Params(C.Structure):
                 ("dt", C.c_double), ("pair_cut", C.c_double), ("rebuild_every", C.c_int32),
                 ("n_replicas", C.c_int32), ("seed", C.c_uint64), ("obs_every", C.c_int32),
                 ("obs_capacity", C.c_int32), ("pairs_per_bead", C.c_int32), ("schedule", C.c_int32),
-                ("cuda_stream", C.c_void_p), ("rng", C.c_int32), ("integrator", C.c_int32), ("mass", C.c_double)]
+                ("cuda_stream", C.c_void_p), ("rng", C.c_int32), ("integrator", C.c_int32), ("mass", C.c_double),
+                ("obs_every_q", C.c_int32)]
 
 
 class PullParams(C.Structure):
@@ -160,7 +161,7 @@ class Simulation:
 
     def __init__(self, native_xyz, chain_offsets, system_offsets=None, fixed=None, params=None, n_replicas=1,
                  seed=0, obs_every=0, obs_capacity=0, pairs_per_bead=0, schedule="auto", stream=None,
-                 rng="philox", integrator="overdamped", mass=0.0):
+                 rng="philox", integrator="overdamped", mass=0.0, obs_every_q=0):
         L = load()
         self._L = L
         xyz = np.ascontiguousarray(native_xyz, np.float64).reshape(-1, 3)
@@ -179,7 +180,8 @@ class Simulation:
                      p["dt"], p["pair_cut"], int(p["rebuild_every"]), self.R, int(seed), int(obs_every),
                      int(obs_capacity), int(pairs_per_bead), sched, _stream_handle(stream),
                      RNGS[rng] if isinstance(rng, str) else int(rng),
-                     INTEGRATORS[integrator] if isinstance(integrator, str) else int(integrator), float(mass))
+                     INTEGRATORS[integrator] if isinstance(integrator, str) else int(integrator), float(mass),
+                     int(obs_every_q))
         self.params = p
         self.obs_every = int(obs_every)
         ctx = C.c_void_p()

@@ -166,6 +166,44 @@ def test_trajectory_100_steps(sop, orc, workloads, schedule):
         sim.close()
 
 
+@pytest.mark.parametrize("schedule", ["streamed", "batched", "plain", "pairs", "batched_pairs"])
+def test_indenter_in_contact(sop, orc, synth, schedule):
+    """The indenter's wall term where it matters: a shell assembly with the indenter's
+    surface 3 A (below sigma = 3.8 A) above its topmost bead, so that on the beads under it
+    the wall force (Sec. IV.B's indentation; its repulsion follows Eq. 1's (sigma/r)^6 term)
+    outweighs the sum of the Eq. 1 forces. Forces against the oracle at identical positions
+    within 1e-5 of the term scale, and the same 100 steps within an RMS of 1e-3 A."""
+    import dataclasses
+    from paper_1003_1148_gb300.synth import Indenter
+    base = synth.shell(n_copies=6, n_per=150, r_in=60.0, r_out=80.0, ind_radius=20.0, steps=100)
+    x32 = base.xyz.astype(np.float32).astype(np.float64)
+    top = int(np.argmax(x32[:, 2]))
+    gap, radius = 3.0, 20.0
+    centre = (float(x32[top, 0]), float(x32[top, 1]), float(x32[top, 2]) + radius + gap)
+    w = dataclasses.replace(base, indenter=Indenter(center=centre, direction=(0.0, 0.0, -1.0), radius=radius, v=0.005))
+    # the wall term dominates some beads: the oracle with and without the indenter
+    m_in = oracle_with_externals(orc, w, x32)
+    m_out = orc.model_from_workload(base)
+    f_in, _, _ = m_in.forces(x32, step=0)
+    f_out, _, _ = m_out.forces(x32, step=0)
+    wall = np.linalg.norm(f_in - f_out, axis=1)
+    assert (wall > np.linalg.norm(f_out, axis=1)).sum() >= 1, wall.max()
+    sim = sop.from_workload(w, n_replicas=2, schedule=schedule)
+    x0 = sim.get_positions(0)
+    m = oracle_with_externals(orc, w, x0)
+    if schedule != "plain":
+        F, E = sim.forces(0)
+        Fo, Ao, Eo = m.forces(x0, step=0)
+        err = np.abs(F - Fo) / Ao
+        assert err.max() <= FORCE_TOL, (schedule, err.max())
+    sim.step(100)
+    for r in range(2):
+        xo, _, _, _ = m.run(x0, 100, seed=w.seed + r)
+        rms = float(np.sqrt(((sim.get_positions(r) - xo) ** 2).sum(1).mean()))
+        assert rms <= RMS_TOL, (schedule, r, rms)
+    sim.close()
+
+
 def test_plain_equals_streamed_bitwise(sop, synth):
     w = synth.uneven(n_chains=5, lo=60, hi=300, steps=50)
     a = sop.from_workload(w, n_replicas=2, schedule="streamed")

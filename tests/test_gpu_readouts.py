@@ -97,3 +97,27 @@ def test_indenter_records_are_the_projected_wall_force(sop, schedule):
     assert rec[0, F] == pytest.approx(6.0 / sig * (1 + 0.5 / 2 ** 7) - 6.0 / sig / 3 ** 7, rel=3e-5)
     assert rec[0, EXT] == pytest.approx(v * n1, rel=1e-15)
     sim.close()
+
+
+@pytest.mark.parametrize("schedule", SCHEDULES)
+def test_q_has_its_own_cadence(sop, synth, schedule):
+    """obs_every (the force-extension cadence) 100 and obs_every_q 300: the records are those
+    of the run with Q at every record, bit for bit, except that q is NaN where the step is not
+    a multiple of 300 (Sec. IV.B samples f(R) and Q at different cadences)."""
+    w = synth.replicas(n_replicas=3, n=64, seed=7, steps=900)
+    runs = []
+    for q_every in (0, 300):
+        sim = sop.from_workload(w, schedule=schedule, obs_every=100, obs_every_q=q_every)
+        sim.step(900)
+        rec, lost = sim.get_observables()
+        sim.close()
+        assert lost == 0 and len(rec) == 9 * 3
+        runs.append(rec)
+    a, b = runs
+    on_q = b[:, 0] % 300 == 0
+    assert np.array_equal(np.isnan(b[:, 6]), ~on_q)
+    assert np.array_equal(a[on_q], b[on_q])
+    cols = [0, 1, 2, 3, 4, 5, 7]
+    assert np.array_equal(a[~on_q][:, cols], b[~on_q][:, cols])
+    with pytest.raises(sop.SopError):
+        sop.from_workload(w, schedule=schedule, obs_every=100, obs_every_q=250)

@@ -173,7 +173,8 @@ class Model:
     the positions given to ``start_pulls``.
     """
 
-    def __init__(self, native_xyz, chain, sys, fixed=None, params=None, native_cells: bool = False):
+    def __init__(self, native_xyz, chain, sys, fixed=None, params=None, native_cells: bool = False,
+                 extra_bonds=None):
         p = dict(k_fene=14.0, R0=2.0, eps_h=1.0, native_cut=8.0, eps_l=1.0, sigma=3.8, T=300.0, zeta=50.0,
                  dt=0.1, pair_cut=10.0, rebuild_every=10)
         p.update(params or {})
@@ -187,6 +188,20 @@ class Model:
         self.bond_i, self.bond_j, self.bond_r0 = bonds(self.native_xyz, self.chain)
         self.nat_i, self.nat_j, self.nat_r0 = native_pairs(self.native_xyz, self.chain, self.sys,
                                                            p["native_cut"], cells=native_cells)
+        xb = np.asarray(extra_bonds if extra_bonds is not None else [], np.int32).reshape(-1, 2)
+        if len(xb):
+            # cross-links: more FENE terms of Eq. 1 with their native lengths; a covalently
+            # linked pair is not a (non-covalent) native contact
+            a, b = xb.min(1), xb.max(1)
+            d = self.native_xyz[a] - self.native_xyz[b]
+            r0 = np.sqrt((d[:, 0] * d[:, 0] + d[:, 1] * d[:, 1]) + d[:, 2] * d[:, 2])
+            self.bond_i = np.concatenate([self.bond_i, a]).astype(np.int32)
+            self.bond_j = np.concatenate([self.bond_j, b]).astype(np.int32)
+            self.bond_r0 = np.concatenate([self.bond_r0, r0])
+            linked = set(zip(a.tolist(), b.tolist()))
+            keep = np.array([(i, j) not in linked for i, j in zip(self.nat_i.tolist(), self.nat_j.tolist())],
+                            dtype=bool)
+            self.nat_i, self.nat_j, self.nat_r0 = self.nat_i[keep], self.nat_j[keep], self.nat_r0[keep]
         self.pulls = (_Pull * 1)()
         self.n_pull = 0
         self.indenter = None
@@ -362,5 +377,6 @@ def model_from_workload(w, native_cells: bool | None = None) -> Model:
     chain_of_bead(), system_of_bead(), fixed, params, pulls, indenter)."""
     if native_cells is None:
         native_cells = w.n_beads > 4096
-    m = Model(w.xyz, w.chain_of_bead(), w.system_of_bead(), w.fixed, w.params, native_cells=native_cells)
+    m = Model(w.xyz, w.chain_of_bead(), w.system_of_bead(), w.fixed, w.params, native_cells=native_cells,
+              extra_bonds=getattr(w, "extra_bonds", None))
     return m

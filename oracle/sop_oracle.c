@@ -42,7 +42,12 @@
  * steps 0, K, 2K, ... before that step's forces; a listed pair interacts with
  * no further distance test; F_i = -grad_i V; a FENE bond stretched to
  * |r - r0| >= R0 is a failure; the indenter is V = eps_l (sigma / (|r-c| -
- * R_ind))^6; a native contact counts as formed when r < r0 + 2 A.
+ * R_ind))^6; a native contact counts as formed when r < r0 + 2 A; a
+ * cross-link (a covalent bond joining beads other than i, i+1 of a chain, which
+ * Table I counts among the covalent bonds) is one more FENE term of Eq. 1 with
+ * its native length, and its two beads are neither a native contact nor a
+ * Verlet-list pair (the model's bond list holds it; the lists exclude every
+ * bonded partner).
  */
 #include "sop_oracle.h"
 
@@ -128,21 +133,29 @@ static int adjacency_build(int32_t n, int64_t m, const int32_t *a, const int32_t
 
 static void adjacency_free(adjacency *adj) { free(adj->row); free(adj->col); }
 
-/* Bonded: (i, i+1) inside one chain. */
+/* Bonded: (i, i+1) inside one chain. Cross-links (bonds of the model's list that join
+ * other pairs) are excluded through the bond adjacency instead. */
 static int bonded(const orc_model *m, int32_t i, int32_t j) {
     int32_t lo = i < j ? i : j, hi = i < j ? j : i;
     return hi == lo + 1 && m->chain[lo] == m->chain[hi];
 }
 
+/* Mark (val = 1) or unmark (val = 0) the partners of bead i in adj. */
+static void mark(const adjacency *adj, int32_t i, unsigned char *flag, unsigned char val) {
+    for (int64_t p = adj->row[i]; p < adj->row[i + 1]; ++p) flag[adj->col[p]] = val;
+}
+
 int64_t orc_pairlist_brute(const orc_model *m, const double *xyz, int32_t *out_i, int32_t *out_j, int64_t cap) {
     int32_t n = m->n;
-    adjacency adj;
+    adjacency adj, badj;
     if (adjacency_build(n, m->n_nat, m->nat_i, m->nat_j, &adj) != 0) return -1;
+    if (adjacency_build(n, m->n_bonds, m->bond_i, m->bond_j, &badj) != 0) return -1;
     unsigned char *is_nat = (unsigned char *)calloc((size_t)n, 1);
     double cut2 = m->pair_cut * m->pair_cut;
     int64_t cnt = 0;
     for (int32_t i = 0; i < n && cnt >= 0; ++i) {
-        for (int64_t p = adj.row[i]; p < adj.row[i + 1]; ++p) is_nat[adj.col[p]] = 1;
+        mark(&adj, i, is_nat, 1);
+        mark(&badj, i, is_nat, 1);   /* every covalent partner, cross-links included */
         for (int32_t j = i + 1; j < n; ++j) {
             if (m->sys[i] != m->sys[j] || bonded(m, i, j) || is_nat[j]) continue;
             if (dist2(xyz + 3 * i, xyz + 3 * j) < cut2) {
@@ -152,10 +165,12 @@ int64_t orc_pairlist_brute(const orc_model *m, const double *xyz, int32_t *out_i
                 ++cnt;
             }
         }
-        for (int64_t p = adj.row[i]; p < adj.row[i + 1]; ++p) is_nat[adj.col[p]] = 0;
+        mark(&adj, i, is_nat, 0);
+        mark(&badj, i, is_nat, 0);
     }
     free(is_nat);
     adjacency_free(&adj);
+    adjacency_free(&badj);
     return cnt;
 }
 
@@ -259,8 +274,9 @@ int64_t orc_pairlist_cells(const orc_model *m, const double *xyz, int32_t *out_i
     int32_t n = m->n;
     cellgrid g;
     if (cellgrid_build(n, xyz, m->sys, m->pair_cut, &g) != 0) return -1;
-    adjacency adj;
+    adjacency adj, badj;
     if (adjacency_build(n, m->n_nat, m->nat_i, m->nat_j, &adj) != 0) return -1;
+    if (adjacency_build(n, m->n_bonds, m->bond_i, m->bond_j, &badj) != 0) return -1;
     unsigned char *is_nat = (unsigned char *)calloc((size_t)n + 1, 1);
     int32_t *buf = (int32_t *)malloc(sizeof(int32_t) * ((size_t)n + 1));
     double cut2 = m->pair_cut * m->pair_cut;
@@ -268,7 +284,8 @@ int64_t orc_pairlist_cells(const orc_model *m, const double *xyz, int32_t *out_i
     for (int32_t i = 0; i < n && cnt >= 0; ++i) {
         int64_t nb = cellgrid_candidates(&g, m->sys, i, buf);
         qsort(buf, (size_t)nb, sizeof(int32_t), cmp_i32);
-        for (int64_t p = adj.row[i]; p < adj.row[i + 1]; ++p) is_nat[adj.col[p]] = 1;
+        mark(&adj, i, is_nat, 1);
+        mark(&badj, i, is_nat, 1);
         for (int64_t q = 0; q < nb; ++q) {
             int32_t j = buf[q];
             if (bonded(m, i, j) || is_nat[j]) continue;
@@ -279,11 +296,13 @@ int64_t orc_pairlist_cells(const orc_model *m, const double *xyz, int32_t *out_i
                 ++cnt;
             }
         }
-        for (int64_t p = adj.row[i]; p < adj.row[i + 1]; ++p) is_nat[adj.col[p]] = 0;
+        mark(&adj, i, is_nat, 0);
+        mark(&badj, i, is_nat, 0);
     }
     free(buf);
     free(is_nat);
     adjacency_free(&adj);
+    adjacency_free(&badj);
     cellgrid_free(&g);
     return cnt;
 }

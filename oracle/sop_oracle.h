@@ -44,7 +44,7 @@ typedef struct {
     const int32_t *chain;            /* [n] chain id; chains are contiguous ranges */
     const int32_t *sys;              /* [n] system id; different systems never interact */
     const uint8_t *fixed;            /* [n] 1 = never moved; may be NULL */
-    int32_t n_bonds;                 /* FENE bonds (i, i+1) within chains */
+    int32_t n_bonds;                 /* FENE bonds: (i, i+1) within chains, then any cross-links */
     const int32_t *bond_i, *bond_j;
     const double *bond_r0;
     int64_t n_nat;                   /* native contacts, i < j */

@@ -246,3 +246,53 @@ def test_indenter_wall_value_and_gradient(orc, synth):
             assert abs(fd - F[i, k]) < 1e-6 * A[i, k]
     with pytest.raises(orc.OracleError):     # a bead inside the indenter is an error
         m.forces(xp, pl=pl, step=10_000)
+
+
+def test_crosslink_is_the_chain_bond_term(orc):
+    """A cross-link (a covalent bond between beads that are not i, i+1 of one chain) is the
+    FENE term of Eq. 1: two single-bead chains of one system, linked, give the closed-form
+    FENE energy (k/2) R0^2 ln 2 at (r - r0)^2 = R0^2 / 2, and the same forces as the two
+    beads bonded as one chain."""
+    r = 3.8 + 2.0 / math.sqrt(2.0)
+    nat = np.array([[0.0, 0, 0], [3.8, 0, 0]])
+    now = np.array([[0.0, 0, 0], [r, 0, 0]])
+    none = (np.zeros(0, np.int32), np.zeros(0, np.int32))
+    linked = orc.Model(nat, [0, 1], [0, 0], params=P, extra_bonds=[(0, 1)])
+    chain = orc.Model(nat, [0, 0], [0, 0], params=P)
+    Fl, _, El = linked.forces(now, pl=none)
+    Fc, _, Ec = chain.forces(now, pl=none)
+    assert El[0] == pytest.approx(0.5 * 14.0 * 4.0 * math.log(2.0), rel=1e-14)
+    assert np.array_equal(Fl, Fc) and El[0] == Ec[0]
+    assert len(linked.nat_i) == 0 and len(linked.pairlist(now)[0]) == 0
+
+
+def test_crosslink_leaves_the_native_map_and_the_list(orc, synth):
+    """A linked pair is neither a native contact nor a Verlet-list pair, and its force is
+    that of a lone bond of the same geometry: the KD-tree definition of the list minus the
+    link, and the force difference with and without the link equal to a two-bead chain's."""
+    xn, x = perturbed_chain(synth)
+    n = len(xn)
+    base = orc.Model(xn, np.zeros(n, np.int32), np.zeros(n, np.int32), params=P)
+    nat = set(zip(base.nat_i.tolist(), base.nat_j.tolist()))
+    # a native pair, and a pair far from both cutoffs in the native structure
+    i1, j1 = next((i, j) for i, j in sorted(nat) if j - i > 5)
+    d = np.linalg.norm(xn[:, None, :] - xn[None, :, :], axis=2)
+    i2, j2 = next((i, j) for i in range(n) for j in range(i + 6, n) if d[i, j] > 12.0)
+    m = orc.Model(xn, np.zeros(n, np.int32), np.zeros(n, np.int32), params=P, extra_bonds=[(j1, i1), (i2, j2)])
+    assert set(zip(m.nat_i.tolist(), m.nat_j.tolist())) == nat - {(i1, j1)}
+    tree = cKDTree(x)
+    want = {(a, b) for a, b in tree.query_pairs(P["pair_cut"] - 1e-9)
+            if b != a + 1 and (a, b) not in nat and (a, b) not in {(i1, j1), (i2, j2)}}
+    for cells in (False, True):
+        pi, pj = m.pairlist(x, cells=cells)
+        assert set(zip(pi.tolist(), pj.tolist())) == want
+    # with the list of the linked model, the far link adds exactly a lone bond's force
+    pl = m.pairlist(x)
+    no_far = orc.Model(xn, np.zeros(n, np.int32), np.zeros(n, np.int32), params=P, extra_bonds=[(j1, i1)])
+    dF = m.forces(x, pl=pl)[0] - no_far.forces(x, pl=pl)[0]
+    lone = orc.Model(xn[[i2, j2]], [0, 0], [0, 0], params=P)
+    Fl = lone.forces(x[[i2, j2]], pl=(np.zeros(0, np.int32), np.zeros(0, np.int32)))[0]
+    assert np.allclose(dF[[i2, j2]], Fl, rtol=1e-12, atol=1e-12)
+    others = np.ones(n, bool)
+    others[[i2, j2]] = False
+    assert np.allclose(dF[others], 0.0, atol=1e-12)

@@ -117,6 +117,15 @@ typedef struct {
     int32_t n_systems;               /* 0: every chain is its own system */
     const int32_t *system_offsets;   /* [n_systems+1] in chains, or NULL when n_systems == 0 */
     const uint8_t *fixed_mask;       /* [n_beads], 1 = bead never moves; NULL = none fixed */
+    int32_t n_extra_bonds;           /* cross-links: covalent bonds beyond (i, i+1) of a chain (Table I
+                                        counts such bonds among the covalent ones), e.g. disulfide
+                                        bridges or links between chains; 0 = none */
+    const int32_t *extra_bonds;      /* [2*n_extra_bonds] bead pairs (i, j): one system, i != j, not
+                                        consecutive beads of one chain, no pair twice. Each is a FENE
+                                        term of Eq. 1 with its native length; the pair is neither a
+                                        native contact nor a Verlet-list pair. The streamed schedules
+                                        take them; the batched ones answer SOP_ERR_UNSUPPORTED (AUTO
+                                        then runs streamed). NULL when n_extra_bonds == 0 */
 } sop_topology;
 
 /* Parameters (Eq. 1, Algorithm 7, the Verlet list and the run). */

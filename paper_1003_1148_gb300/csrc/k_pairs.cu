@@ -124,9 +124,10 @@ __global__ void __launch_bounds__(kPairThreads) k_pairs(StepArgs a, DevPairTable
 // bond slots, all lanes stride over the native and Verlet slots), reduced by shuffles.
 template <int L>
 __device__ __forceinline__ float3 gather_slots(const StepArgs &a, const DevPairList &pl, const DevPairTables &t, int r,
-                                               int i, int gb, int lane, bool *broken) {
+                                               int i, int gb, int lane, const float4 *P, bool *broken) {
     float fx = 0.f, fy = 0.f, fz = 0.f;
     bool brk = false;
+    xlink_force<L>(a.topo, a.fp, P, i, P[i], lane, fx, fy, fz, &brk);   // cross-links, gathered
     if (lane < 2) {
         const float4 v = t.fb[2 * (size_t)gb + lane];
         fx += v.x; fy += v.y; fz += v.z;
@@ -169,7 +170,7 @@ __global__ void __launch_bounds__(256) k_pairs_step(StepArgs a, DevPairList pl, 
     }
     const int64_t step = *a.d_step + k_off;
     bool broken = false;
-    const float3 f = gather_slots<L>(a, pl, t, r, i, gb, lane, &broken);
+    const float3 f = gather_slots<L>(a, pl, t, r, i, gb, lane, P, &broken);
     broken = __any_sync(group_mask<L>(), broken);
     if (lane != 0) return;
     advance_bead(a, r, i, gb, P, f, broken, step, pos_out, comp);
@@ -186,7 +187,7 @@ __global__ void __launch_bounds__(256) k_pairs_forces(StepArgs a, DevPairList pl
     const int n = a.topo.n;
     const int r = gb / n, i = gb - r * n;
     bool broken = false;
-    const float3 f = gather_slots<L>(a, pl, t, r, i, gb, lane, &broken);
+    const float3 f = gather_slots<L>(a, pl, t, r, i, gb, lane, pos + (size_t)r * n, &broken);
     broken = __any_sync(group_mask<L>(), broken);
     if (lane != 0) return;
     bool overlap = false;

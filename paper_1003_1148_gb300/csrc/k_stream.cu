@@ -490,6 +490,8 @@ constexpr int kNatBuf = 64;    // native partners kept in shared memory per warp
 struct BuildExtra {
     const int32_t *nat_row;
     const int32_t *nat_col;
+    const int32_t *xb_row;      // cross-links (NULL: none): partners excluded like bonded ones
+    const int32_t *xb_col;
     double cut2_d;
     float cut2_f;
     int32_t *pl_start;
@@ -500,6 +502,13 @@ struct BuildExtra {
     const int64_t *pl_seg_end;  // [n_seg] capacity limit of each segment
     int32_t *rep_status;
 };
+
+// Is j a cross-link partner of bead i (a covalent bond, so not a Verlet-list pair)?
+__device__ __forceinline__ bool xlinked(const BuildExtra &x, int i, int j) {
+    for (int p = x.xb_row[i]; p < x.xb_row[i + 1]; ++p)
+        if (x.xb_col[p] == j) return true;
+    return false;
+}
 
 // Append the row of bead gb (cnt kept partners in the warp's buffer, in any order) to
 // segment g's column range, ranked ascending; a row of more than kRowBuf partners, or one
@@ -628,6 +637,7 @@ __global__ void __launch_bounds__(kBuildWarps * 32) k_pl_build(RebuildArgs a, Bu
                     for (int k2 = 0; k2 < nn; ++k2)
                         if (x.nat_col[nlo + k2] == jl) { keep = false; break; }
                 }
+                if (keep && x.xb_row) keep = !xlinked(x, i, jl);
             }
         }
         const unsigned m = __ballot_sync(0xffffffffu, keep);
@@ -779,6 +789,7 @@ __global__ void __launch_bounds__(kBuildWarps * 32) k_pl_brute(RebuildArgs a, Bu
                         for (int q = 0; q < nn; ++q)
                             if (x.nat_col[nlo + q] == jl) { keep = false; break; }
                     }
+                    if (keep && x.xb_row) keep = !xlinked(x, i, jl);
                 }
             }
             const unsigned msk = __ballot_sync(0xffffffffu, keep);
@@ -872,6 +883,7 @@ __device__ __forceinline__ float3 gather_force(const StepArgs &a, const DevPairL
             fx = fmaf(c, dx, fx); fy = fmaf(c, dy, fy); fz = fmaf(c, dz, fz);
         }
     }
+    xlink_force<L>(t, a.fp, P, i, pi, lane, fx, fy, fz, &brk);
     const int n0 = t.nat_row[i], n1 = t.nat_row[i + 1];
 #pragma unroll 2
     for (int p = n0 + lane; p < n1; p += L) {
@@ -1209,6 +1221,17 @@ __global__ void __launch_bounds__(kObsThreads) k_obs_partial(ObsArgs q) {
             const double arg = 1.0 - dr * dr * (1.0 / R02);
             if (arg > 0.0) acc[0] += -0.5 * q.k_fene * R02 * log(arg);
         }
+        if (t.xb_row)   // cross-links, each from its lower index
+            for (int p = t.xb_row[i]; p < t.xb_row[i + 1]; ++p) {
+                const int j = t.xb_col[p];
+                if (j < i) continue;
+                float d2f;
+                const double d2 = dist2_two(pi, P[j], &d2f);
+                const double R02 = q.R0 * q.R0;
+                const double dr = sqrt_seeded(d2, d2f) - t.xb_r0d[p];
+                const double arg = 1.0 - dr * dr * (1.0 / R02);
+                if (arg > 0.0) acc[0] += -0.5 * q.k_fene * R02 * log(arg);
+            }
         if (t.flags[i] & kFlagPulled) {
             const int qq = e.pull_of_sys[t.sys[i]];
             if (qq >= 0 && e.pull_bead[qq] == i) {
@@ -1392,6 +1415,8 @@ void launch_rebuild(const StepArgs &sa, const DevCells &c, const DevPairList &pl
     BuildExtra x;
     x.nat_row = sa.topo.nat_row;
     x.nat_col = sa.topo.nat_col;
+    x.xb_row = sa.topo.xb_row;
+    x.xb_col = sa.topo.xb_col;
     x.cut2_d = sa.cut2_d;
     x.cut2_f = sa.cut2_f;
     x.pl_start = pl.start;

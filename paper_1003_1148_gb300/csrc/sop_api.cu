@@ -46,6 +46,7 @@ struct sop_ctx {
     std::vector<int32_t> chain_off, sys_lo, chain_of, sys_of, sys_ree_last;
     std::vector<uint8_t> flags;
     std::vector<uint8_t> fixed_by_mask;   // [n] fixed through the topology's fixed_mask (never cleared)
+    std::vector<std::pair<int32_t, int32_t>> xlinks;   // cross-links (i < j) of the topology
     std::vector<int32_t> h_nat_row, h_nat_col;
     std::vector<double> h_nat_r0;
     std::vector<int32_t> h_seg_bead_lo, h_seg_cell_base, h_seg_chunk_lo, h_brute_cta_lo;
@@ -58,6 +59,9 @@ struct sop_ctx {
     float4 *d_vel = nullptr;   // stored velocity per bead (SOP_INTEGRATOR_BAOAB)
     float *d_bond_r0 = nullptr;
     double *d_bond_r0d = nullptr;
+    const int32_t *d_xb_row = nullptr, *d_xb_col = nullptr;   // cross-links (NULL: none)
+    const float *d_xb_r0 = nullptr;
+    const double *d_xb_r0d = nullptr;
     int32_t *d_nat_row = nullptr, *d_nat_col = nullptr;
     float *d_nat_r0sq = nullptr;
     double *d_nat_r0 = nullptr;
@@ -613,6 +617,22 @@ sop_status build_host_topology(sop_ctx *c, const sop_topology *t) {
         c->sys_ree_last[s] = c->chain_off[c->chain_of[first] + 1] - 1;
         c->max_sys = std::max(c->max_sys, c->sys_lo[s + 1] - c->sys_lo[s]);
     }
+    if (t->n_extra_bonds < 0 || (t->n_extra_bonds > 0 && !t->extra_bonds))
+        return fail(nullptr, SOP_ERR_INVALID_ARG, "topology: n_extra_bonds >= 0 and extra_bonds required");
+    for (int k = 0; k < t->n_extra_bonds; ++k) {
+        int32_t i = t->extra_bonds[2 * k], j = t->extra_bonds[2 * k + 1];
+        if (i < 0 || j < 0 || i >= c->n || j >= c->n || i == j)
+            return fail(nullptr, SOP_ERR_INVALID_ARG, "topology: an extra bond names a bead out of range, or one twice");
+        if (i > j) std::swap(i, j);
+        if (c->sys_of[i] != c->sys_of[j])
+            return fail(nullptr, SOP_ERR_INVALID_ARG, "topology: an extra bond joins two systems");
+        if (j == i + 1 && c->chain_of[i] == c->chain_of[j])
+            return fail(nullptr, SOP_ERR_INVALID_ARG, "topology: an extra bond repeats a chain bond (i, i+1)");
+        c->xlinks.emplace_back(i, j);
+    }
+    std::sort(c->xlinks.begin(), c->xlinks.end());
+    if (std::adjacent_find(c->xlinks.begin(), c->xlinks.end()) != c->xlinks.end())
+        return fail(nullptr, SOP_ERR_INVALID_ARG, "topology: an extra bond is listed twice");
     return SOP_OK;
 }
 
@@ -1440,6 +1460,73 @@ sop_status max_row(sop_ctx *c, int *out) {
     return SOP_OK;
 }
 
+// Cross-links: drop the linked pairs from the native map (a covalent link is not a
+// non-covalent native contact) and upload the links as a CSR over beads, both directions,
+// ascending, with their FP64 native lengths ((dx*dx + dy*dy) + dz*dz, rounded square root)
+// and those rounded to FP32.
+sop_status apply_xlinks(sop_ctx *c, const double *xyz) {
+    const int n = c->n;
+    auto linked = [c](int32_t i, int32_t j) {
+        return std::binary_search(c->xlinks.begin(), c->xlinks.end(), std::make_pair(std::min(i, j), std::max(i, j)));
+    };
+    std::vector<int32_t> row(n + 1, 0), col;
+    std::vector<double> r0;
+    col.reserve(c->h_nat_col.size());
+    r0.reserve(c->h_nat_col.size());
+    for (int i = 0; i < n; ++i) {
+        for (int q = c->h_nat_row[i]; q < c->h_nat_row[i + 1]; ++q)
+            if (!linked(i, c->h_nat_col[q])) {
+                col.push_back(c->h_nat_col[q]);
+                r0.push_back(c->h_nat_r0[q]);
+            }
+        row[i + 1] = (int32_t)col.size();
+    }
+    if ((int64_t)col.size() != c->nat_nnz) {   // some links were native contacts: new map
+        std::vector<float> r0sq(r0.size());
+        for (size_t q = 0; q < r0.size(); ++q) r0sq[q] = (float)(r0[q] * r0[q]);
+        c->h_nat_row = row;
+        c->h_nat_col = col;
+        c->h_nat_r0 = r0;
+        c->nat_nnz = (int64_t)col.size();
+        CUDA_OR_RETURN(c, cudaMemcpy(c->d_nat_row, row.data(), sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice));
+        if (c->nat_nnz) {
+            CUDA_OR_RETURN(c, cudaMemcpy(c->d_nat_col, col.data(), sizeof(int32_t) * c->nat_nnz, cudaMemcpyHostToDevice));
+            CUDA_OR_RETURN(c, cudaMemcpy(c->d_nat_r0, r0.data(), sizeof(double) * c->nat_nnz, cudaMemcpyHostToDevice));
+            CUDA_OR_RETURN(c, cudaMemcpy(c->d_nat_r0sq, r0sq.data(), sizeof(float) * c->nat_nnz, cudaMemcpyHostToDevice));
+        }
+    }
+    std::vector<std::vector<int32_t>> adj(n);
+    for (const auto &e : c->xlinks) {
+        adj[e.first].push_back(e.second);
+        adj[e.second].push_back(e.first);
+    }
+    std::vector<int32_t> xrow(n + 1, 0), xcol;
+    std::vector<double> xr0;
+    for (int i = 0; i < n; ++i) {
+        std::sort(adj[i].begin(), adj[i].end());
+        for (int32_t j : adj[i]) {
+            const double dx = xyz[3 * i] - xyz[3 * j], dy = xyz[3 * i + 1] - xyz[3 * j + 1];
+            const double dz = xyz[3 * i + 2] - xyz[3 * j + 2];
+            xcol.push_back(j);
+            xr0.push_back(std::sqrt((dx * dx + dy * dy) + dz * dz));
+        }
+        xrow[i + 1] = (int32_t)xcol.size();
+    }
+    std::vector<float> xr0f(xr0.begin(), xr0.end());
+    int32_t *d_row = nullptr, *d_col = nullptr;
+    float *d_r0 = nullptr;
+    double *d_r0d = nullptr;
+    CUDA_OR_RETURN(c, upload(c, &d_row, xrow));
+    CUDA_OR_RETURN(c, upload(c, &d_col, xcol));
+    CUDA_OR_RETURN(c, upload(c, &d_r0, xr0f));
+    CUDA_OR_RETURN(c, upload(c, &d_r0d, xr0));
+    c->d_xb_row = d_row;
+    c->d_xb_col = d_col;
+    c->d_xb_r0 = d_r0;
+    c->d_xb_r0d = d_r0d;
+    return SOP_OK;
+}
+
 sop_status create_impl(sop_ctx *c, const sop_topology *topo, const double *xyz, const sop_params *p) {
     sop_status s = validate_params(p);
     if (s != SOP_OK) return s;
@@ -1501,6 +1588,10 @@ sop_status create_impl(sop_ctx *c, const sop_topology *topo, const double *xyz, 
                                           cudaMemcpyDeviceToHost, c->stream));
     }
     CUDA_OR_RETURN(c, cudaStreamSynchronize(c->stream));
+    if (!c->xlinks.empty()) {
+        s = apply_xlinks(c, xyz);
+        if (s != SOP_OK) return s;
+    }
     c->st.native_entries = c->nat_nnz / 2;
     std::vector<int32_t> sys_np(c->n_sys, 0);
     for (int i = 0; i < n; ++i)
@@ -1651,6 +1742,10 @@ sop_status create_impl(sop_ctx *c, const sop_topology *topo, const double *xyz, 
     a.topo.sys_lo = c->d_sys_lo;
     a.topo.sys_ree_last = c->d_sys_ree_last;
     a.topo.sys_nat_pairs = c->d_sys_nat_pairs;
+    a.topo.xb_row = c->d_xb_row;
+    a.topo.xb_col = c->d_xb_col;
+    a.topo.xb_r0 = c->d_xb_r0;
+    a.topo.xb_r0d = c->d_xb_r0d;
     const double kT = kBoltzmannKcal * p->T;
     a.fp.k_fene = (float)p->k_fene;
     a.fp.inv_R02 = (float)(1.0 / (p->R0 * p->R0));
@@ -1712,9 +1807,12 @@ sop_status create_impl(sop_ctx *c, const sop_topology *topo, const double *xyz, 
     const bool batched_ok = c->max_sys <= kBatchedMaxBeads;
     if (sched == SOP_SCHED_AUTO) {
         const int64_t items = (int64_t)c->R * c->n_sys;
-        sched = c->max_sys <= kBatchedAutoBeads && (c->max_sys <= 512 || items >= 152) ? SOP_SCHED_BATCHED
-                                                                                      : SOP_SCHED_STREAMED;
+        sched = c->max_sys <= kBatchedAutoBeads && (c->max_sys <= 512 || items >= 152) && c->xlinks.empty()
+                    ? SOP_SCHED_BATCHED
+                    : SOP_SCHED_STREAMED;
     }
+    if (sched == SOP_SCHED_BATCHED && !c->xlinks.empty())
+        return fail(c, SOP_ERR_UNSUPPORTED, "the batched schedules take no extra bonds (use a streamed one)");
     if (sched == SOP_SCHED_BATCHED && !batched_ok)
         return fail(c, SOP_ERR_UNSUPPORTED, "the batched schedule takes systems of at most 4096 beads");
     if (sched == SOP_SCHED_PAIRS) {

@@ -31,6 +31,10 @@ struct DevTopo {
     const int32_t *sys_lo = nullptr;     // [n_sys+1] first bead of each system
     const int32_t *sys_ree_last = nullptr;  // [n_sys] last bead of the system's first chain
     const int32_t *sys_nat_pairs = nullptr; // [n_sys] native contacts (i < j) per system
+    const int32_t *xb_row = nullptr;     // [n+1] cross-link CSR (both directions, ascending); NULL: none
+    const int32_t *xb_col = nullptr;     // [n_xb]
+    const float *xb_r0 = nullptr;        // [n_xb] native length, FP32
+    const double *xb_r0d = nullptr;      // [n_xb] the same in FP64
 };
 
 // Cantilevers (per system) and the indenter, FP64.

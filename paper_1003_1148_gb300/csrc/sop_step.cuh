@@ -15,6 +15,21 @@ __device__ __forceinline__ unsigned group_mask() {
     return L == 32 ? 0xffffffffu : (((1u << L) - 1u) << ((threadIdx.x & 31) & ~(L - 1)));
 }
 
+// FENE forces of bead i's cross-links (the topology's extra bonds, Eq. 1's first term
+// with each link's native length), added to (fx, fy, fz) by lane `lane` of a group of L
+// lanes striding over the bead's cross-link row; *broken is set at |r - r0| >= R0.
+template <int L>
+__device__ __forceinline__ void xlink_force(const DevTopo &t, const ForceParams &fp, const float4 *P, int i,
+                                            float4 pi, int lane, float &fx, float &fy, float &fz, bool *broken) {
+    if (!t.xb_row) return;
+    for (int p = t.xb_row[i] + lane; p < t.xb_row[i + 1]; p += L) {
+        const float4 pj = P[t.xb_col[p]];
+        const float dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
+        const float c = fene_coef(fmaf(dz, dz, fmaf(dy, dy, dx * dx)), t.xb_r0[p], fp, broken);
+        fx = fmaf(c, dx, fx); fy = fmaf(c, dy, fy); fz = fmaf(c, dz, fz);
+    }
+}
+
 // Cantilever and indenter forces on bead i (FP64 tip / centre, FP32 force).
 __device__ __forceinline__ float3 external_force(const StepArgs &a, int r, int i, float4 pi, int64_t step,
                                                  bool *overlap) {

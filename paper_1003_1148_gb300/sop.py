@@ -50,7 +50,8 @@ class SopError(RuntimeError):
 
 class Topology(C.Structure):
     _fields_ = [("n_beads", C.c_int32), ("n_chains", C.c_int32), ("chain_offsets", C.c_void_p),
-                ("n_systems", C.c_int32), ("system_offsets", C.c_void_p), ("fixed_mask", C.c_void_p)]
+                ("n_systems", C.c_int32), ("system_offsets", C.c_void_p), ("fixed_mask", C.c_void_p),
+                ("n_extra_bonds", C.c_int32), ("extra_bonds", C.c_void_p)]
 
 
 class Params(C.Structure):
@@ -161,7 +162,7 @@ class Simulation:
 
     def __init__(self, native_xyz, chain_offsets, system_offsets=None, fixed=None, params=None, n_replicas=1,
                  seed=0, obs_every=0, obs_capacity=0, pairs_per_bead=0, schedule="auto", stream=None,
-                 rng="philox", integrator="overdamped", mass=0.0, obs_every_q=0):
+                 rng="philox", integrator="overdamped", mass=0.0, obs_every_q=0, extra_bonds=None):
         L = load()
         self._L = L
         xyz = np.ascontiguousarray(native_xyz, np.float64).reshape(-1, 3)
@@ -171,7 +172,9 @@ class Simulation:
         so = None if system_offsets is None else np.ascontiguousarray(system_offsets, np.int32)
         fx = None if fixed is None else np.ascontiguousarray(fixed, np.uint8)
         self.n_systems = (len(co) - 1) if so is None else len(so) - 1
-        topo = Topology(self.n, len(co) - 1, _ptr(co), 0 if so is None else len(so) - 1, _ptr(so), _ptr(fx))
+        xb = np.ascontiguousarray(extra_bonds if extra_bonds is not None else np.zeros((0, 2)), np.int32).reshape(-1, 2)
+        topo = Topology(self.n, len(co) - 1, _ptr(co), 0 if so is None else len(so) - 1, _ptr(so), _ptr(fx),
+                        len(xb), _ptr(xb) if len(xb) else None)
         p = dict(k_fene=14.0, R0=2.0, eps_h=1.0, native_cut=8.0, eps_l=1.0, sigma=3.8, T=300.0, zeta=50.0, dt=0.1,
                  pair_cut=10.0, rebuild_every=10)
         p.update(params or {})
@@ -346,6 +349,7 @@ def from_workload(w, n_replicas: int | None = None, schedule="auto", stream=None
     """A Simulation of a synthetic workload (duck-typed: xyz, chain_offsets,
     system_offsets, fixed, params, n_replicas, seed, pulls, indenter, obs_every).
     Pulling and the indenter start at step 0."""
+    kw.setdefault("extra_bonds", getattr(w, "extra_bonds", None) or None)
     sim = Simulation(w.xyz, w.chain_offsets, w.system_offsets, w.fixed, w.params,
                      n_replicas=w.n_replicas if n_replicas is None else n_replicas, seed=w.seed,
                      obs_every=w.obs_every if obs_every is None else obs_every, schedule=schedule, stream=stream, **kw)

@@ -146,6 +146,7 @@ class Workload:
     pulls: list = field(default_factory=list)   # list[Pull], at most one per system
     indenter: Indenter | None = None
     obs_every: int = 0
+    extra_bonds: list = field(default_factory=list)   # cross-links (i, j): more FENE bonds of Eq. 1
 
     @property
     def n_beads(self) -> int:

@@ -388,3 +388,72 @@ def test_pair_form_is_used_and_reproducible(sop, synth):
     assert np.array_equal(a.get_positions(-1), b.get_positions(-1))
     g = sop.from_workload(w, n_replicas=3, schedule="batched")
     assert g.stats()["pair_buckets"] == 0
+
+
+def crosslinked(synth):
+    """Two 120-bead chains of one system with five cross-links: three between the chains at
+    native contact distances (so they leave the native map), two inside the first chain
+    between beads 8.5 to 9.5 A apart (inside the list cutoff, so they leave the list)."""
+    from paper_1003_1148_gb300.synth import Workload, default_params
+    xyz = synth.compact_chain(240, 11)
+    d = np.linalg.norm(xyz[:, None, :] - xyz[None, :, :], axis=2)
+    links, used = [], set()
+    for lo, hi, ok, want in ((0, 240, lambda i, j: i < 120 <= j and 4.5 < d[i, j] < 7.5, 3),
+                             (0, 120, lambda i, j: j > i + 6 and 8.5 < d[i, j] < 9.5, 2)):
+        got = 0
+        for i in range(lo, hi):
+            for j in range(i + 1, hi):
+                if got < want and i not in used and j not in used and ok(i, j):
+                    links.append((i, j))
+                    used |= {i, j}
+                    got += 1
+    assert len(links) == 5
+    return Workload("xlink240", xyz, np.array([0, 120, 240], np.int32), np.array([0, 2], np.int32),
+                    np.zeros(240, np.uint8), 1, 100, 0, default_params(), obs_every=10,
+                    extra_bonds=[(j, i) if k % 2 else (i, j) for k, (i, j) in enumerate(links)])
+
+
+@pytest.mark.parametrize("schedule", ["streamed", "plain", "pairs"])
+def test_crosslinks_against_the_oracle(sop, orc, synth, schedule):
+    """Cross-links on every streamed form: the native map and the Verlet list bit-exact,
+    forces within 1e-5 of the term scale, the energy within 1e-9 and 100 steps within an RMS
+    of 1e-3 A of the oracle's, which takes the links as FENE terms of Eq. 1."""
+    w = crosslinked(synth)
+    sim = sop.from_workload(w, n_replicas=2, schedule=schedule)
+    m = orc.model_from_workload(w)
+    rp, col, _ = sim.get_native_map()
+    assert csr_pairs(rp, col) == set(zip(m.nat_i.tolist(), m.nat_j.tolist()))
+    x0 = sim.get_positions(0)
+    for steps in (0, 30):
+        if steps:
+            sim.step(steps)
+            sim.pairlist_rebuild()
+        x = sim.get_positions(1)
+        rpl, cl = sim.get_pairlist(1)
+        pi, pj = m.pairlist(x)
+        assert csr_pairs(rpl, cl) == set(zip(pi.tolist(), pj.tolist())), steps
+        F, E = sim.forces(1)
+        Fo, Ao, Eo = m.forces(x, step=sim.stats()["steps"])
+        assert (np.abs(F - Fo) / Ao).max() <= FORCE_TOL
+        assert E == pytest.approx(Eo[0] + Eo[1] + Eo[2], rel=1e-9)
+    sim.close()
+    sim = sop.from_workload(w, n_replicas=1, schedule=schedule)
+    sim.step(100)
+    xo, _, _, _ = m.run(x0, 100, seed=w.seed)
+    assert float(np.sqrt(((sim.get_positions(0) - xo) ** 2).sum(1).mean())) <= RMS_TOL
+    sim.close()
+
+
+def test_crosslinks_take_a_streamed_schedule(sop, synth):
+    w = crosslinked(synth)
+    for schedule in ("batched", "batched_pairs"):
+        with pytest.raises(sop.SopError) as e:
+            sop.from_workload(w, n_replicas=2, schedule=schedule)
+        assert e.value.status == sop.ERR_UNSUPPORTED
+    sim = sop.from_workload(w, n_replicas=2, schedule="auto")
+    assert sim.stats()["schedule"] in (sop.SCHED_STREAMED, sop.SCHED_PAIRS)
+    sim.close()
+    bad = [(0, 1)], [(5, 5)], [(3, 300)], [(4, 90), (90, 4)]
+    for links in bad:
+        with pytest.raises(sop.SopError):
+            sop.Simulation(w.xyz, w.chain_offsets, w.system_offsets, params=w.params, extra_bonds=links)

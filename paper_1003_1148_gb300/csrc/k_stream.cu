@@ -366,123 +366,6 @@ __global__ void k_cell_scatter(RebuildArgs a, int b_lo, int b_hi) {
     a.sorted[a.sorted_base + a.cell_start[gc - a.cell_base0] + slot] = make_float4(p.x, p.y, p.z, __int_as_float(gb));
 }
 
-constexpr int kFuseBeads = 8192;   // segments up to this size build their cell list in one CTA
-
-// The cell list of one small segment in one CTA, in shared memory: bounding box, grid, cell
-// of each bead, histogram, exclusive scan, scatter. The same grid, cell starts and cell
-// contents as the staged kernels (k_seg_bbox, k_seg_grid, k_cell_count, the scan,
-// k_cell_scatter), in
-// one launch. Dynamic shared memory: the segment's cell budget of counters, then the cell
-// of each of its beads.
-__global__ void k_cell_build(RebuildArgs a, int32_t *pl_cursor, const int64_t *pl_seg_base) {
-    extern __shared__ int32_t sm_cells[];
-    __shared__ float smn[3][32], smx[3][32];
-    __shared__ int sbad;
-    __shared__ int wsum[32];
-    const int g = a.g_lo + blockIdx.x;
-    const int lo = a.seg_bead_lo[g], hi = a.seg_bead_lo[g + 1], nb = hi - lo;
-    const int cb = a.seg_cell_base[g], budget = a.seg_cell_base[g + 1] - cb;
-    int32_t *cnt = sm_cells;
-    int32_t *cof = sm_cells + budget;
-    const int T = blockDim.x, lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = T >> 5;
-    const bool failed = a.rep_status[g / a.n_sys] != 0;   // CTA-uniform
-    for (int k = threadIdx.x; k < budget; k += T) cnt[k] = 0;
-    if (threadIdx.x == 0) sbad = 0;
-    float mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
-    bool bad = false;
-    for (int b = lo + threadIdx.x; b < hi; b += T) {
-        const float4 p = a.pos[b];
-        if (a.snap) a.snap[b] = p;
-        const float v[3] = {p.x, p.y, p.z};
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            if (!isfinite(v[k])) bad = true;
-            mn[k] = fminf(mn[k], v[k]);
-            mx[k] = fmaxf(mx[k], v[k]);
-        }
-    }
-    __syncthreads();
-    if (bad) sbad = 1;
-#pragma unroll
-    for (int k = 0; k < 3; ++k)
-        for (int o = 16; o > 0; o >>= 1) {
-            mn[k] = fminf(mn[k], __shfl_xor_sync(0xffffffffu, mn[k], o));
-            mx[k] = fmaxf(mx[k], __shfl_xor_sync(0xffffffffu, mx[k], o));
-        }
-    if (lane == 0)
-        for (int k = 0; k < 3; ++k) { smn[k][w] = mn[k]; smx[k][w] = mx[k]; }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        float l[3], h[3];
-        for (int k = 0; k < 3; ++k) {
-            l[k] = smn[k][0];
-            h[k] = smx[k][0];
-            for (int q = 1; q < nw; ++q) { l[k] = fminf(l[k], smn[k][q]); h[k] = fmaxf(h[k], smx[k][q]); }
-        }
-        // a failed replica's segment is skipped (its frozen positions may lie anywhere)
-        seg_grid(a, g, l, h, failed || sbad != 0 || nb <= 0, !failed && nb > 0);
-        if (pl_cursor) pl_cursor[g] = (int32_t)pl_seg_base[g];
-    }
-    __syncthreads();
-    const float4 sl = a.seg_lo[g];
-    const int4 d = a.seg_dims[g];
-    for (int b = lo + threadIdx.x; b < hi; b += T) {
-        if (d.w == 0) {   // skipped segment: the bead is not binned
-            cof[b - lo] = -1;
-            continue;
-        }
-        const float4 p = a.pos[b];
-        int cx = 0, cy = 0, cz = 0;
-        if (isfinite(p.x) && isfinite(p.y) && isfinite(p.z)) {
-            cx = cell_coord(p.x, sl.x, sl.w, d.x);
-            cy = cell_coord(p.y, sl.y, sl.w, d.y);
-            cz = cell_coord(p.z, sl.z, sl.w, d.z);
-        }
-        const int c = (cz * d.y + cy) * d.x + cx;   // < d.w <= budget (seg_grid)
-        cof[b - lo] = c;
-        atomicAdd(&cnt[c], 1);
-    }
-    __syncthreads();
-    // exclusive scan of the counters: contiguous runs per thread, then warp and block sums
-    const int per = (budget + T - 1) / T;
-    const int k0 = min(budget, threadIdx.x * per), k1 = min(budget, k0 + per);
-    int run = 0;
-    for (int k = k0; k < k1; ++k) run += cnt[k];
-    int inc = run;
-    for (int o = 1; o < 32; o <<= 1) {
-        const int t = __shfl_up_sync(0xffffffffu, inc, o);
-        if (lane >= o) inc += t;
-    }
-    if (lane == 31) wsum[w] = inc;
-    __syncthreads();
-    if (w == 0) {
-        int v = lane < nw ? wsum[lane] : 0;
-        for (int o = 1; o < 32; o <<= 1) {
-            const int t = __shfl_up_sync(0xffffffffu, v, o);
-            if (lane >= o) v += t;
-        }
-        if (lane < nw) wsum[lane] = v;   // inclusive over warps
-    }
-    __syncthreads();
-    int acc = (w > 0 ? wsum[w - 1] : 0) + inc - run;
-    const int base = lo - a.sorted_base;   // the segment's first position in `sorted`
-    int32_t *start = a.cell_start + (cb - a.cell_base0);
-    for (int k = k0; k < k1; ++k) {
-        const int c = cnt[k];
-        cnt[k] = acc;
-        start[k] = base + acc;
-        acc += c;
-    }
-    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) start[budget] = base + nb;   // the launch's end
-    __syncthreads();
-    for (int b = lo + threadIdx.x; b < hi; b += T) {
-        const int c = cof[b - lo];
-        if (c < 0) continue;
-        const float4 p = a.pos[b];
-        a.sorted[a.sorted_base + base + atomicAdd(&cnt[c], 1)] = make_float4(p.x, p.y, p.z, __int_as_float(b));
-    }
-}
-
 constexpr int kBuildWarps = 8;
 constexpr int kRowBuf = kRowCandidates;   // candidates a row may hold before it is an overflow
 constexpr int kNatBuf = 64;    // native partners kept in shared memory per warp
@@ -651,6 +534,7 @@ __global__ void __launch_bounds__(kBuildWarps * 32) k_pl_build(RebuildArgs a, Bu
 }
 
 constexpr int kBruteBeads = kBruteMaxBeads;   // segments up to this size: k_pl_brute (no cell list)
+constexpr int kBruteBlocks = (kBruteBeads + 63) / 64;
 constexpr int kBruteSlice = kBruteSliceBeads;
 
 struct BruteArgs {
@@ -660,24 +544,26 @@ struct BruteArgs {
     int32_t k_lo;            // cta_lo[g_lo]: first CTA of the launch
 };
 
-// The Verlet rows of small segments (at most kBruteBeads beads) without a cell list: every
-// CTA holds the positions of its segment in shared memory (x, y, z arrays, each padded to
-// an even length with a point at infinity) and its warps test each of their beads against
-// every bead of the segment, two candidates per lane with packed FP32x2 arithmetic. A
-// candidate whose FP32 squared distance exceeds cut^2 (1 + 1e-4) is out by the FP32
-// screen of within_cut; the others queue in shared memory and, 32 at a time (one per
-// lane, so that the rare survivors of the screen do not idle the warp), take within_cut
-// itself, the bonded and native exclusions and the same compaction, ranking and overflow
-// rules as k_pl_build, so the rows equal the cell-list rows. Each CTA also takes its segment's bounding box and fails
-// the replica, as the cell list does, when a position is not finite or no grid of the
-// segment's cell budget covers it. kBruteSlice beads per CTA; the last CTA of a segment
-// to finish records the entries used and puts the segment's column cursor back to its
-// first column for the next build.
+// The Verlet rows of segments of at most kBruteBeads beads without a cell list. Every CTA
+// holds the positions of its segment in shared memory (x, y, z arrays, each padded to an
+// even length with a point at infinity) and the bounding boxes of its blocks of 64
+// consecutive beads; each warp takes one bead at a time and scans the blocks whose box lies
+// within the screen distance of it, two candidates per lane with packed FP32x2 arithmetic.
+// A candidate whose FP32 squared distance exceeds cut^2 (1 + 1e-4) is out by the FP32
+// screen of within_cut; the others queue in shared memory and, 32 at a time (one per lane,
+// so that the rare survivors of the screen do not idle the warp), take within_cut itself,
+// the bonded, native and cross-link exclusions and the same compaction, ranking and
+// overflow rules as k_pl_build, so the rows equal the cell-list rows. Each CTA also takes
+// its segment's bounding box and fails the replica, as the cell list does, when a position
+// is not finite or no grid of the segment's cell budget covers it. kBruteSlice beads per
+// CTA; the last CTA of a segment to finish records the entries used and puts the segment's
+// column cursor back to its first column for the next build.
 __global__ void __launch_bounds__(kBuildWarps * 32) k_pl_brute(RebuildArgs a, BuildExtra x, BruteArgs bz) {
     extern __shared__ float soa[];
     __shared__ int32_t buf[kBuildWarps][kRowBuf];
     __shared__ int32_t nat[kBuildWarps][kNatBuf];
     __shared__ int32_t cand[kBuildWarps][96];   // screened candidates waiting for the exact tests
+    __shared__ float blo[3][kBruteBlocks], bhi[3][kBruteBlocks];   // boxes of 64-bead blocks
     __shared__ float smn[3][kBuildWarps], smx[3][kBuildWarps];
     __shared__ int sbad[kBuildWarps];
     __shared__ int s_ok;
@@ -743,6 +629,32 @@ __global__ void __launch_bounds__(kBuildWarps * 32) k_pl_brute(RebuildArgs a, Bu
     }
     __syncthreads();
     const bool skip = failed || s_ok == 0;
+    // bounding boxes of the blocks of 64 consecutive beads (consecutive beads of a chain lie
+    // close together), one warp per block
+    const int nblk = (m + 63) >> 6;
+    if (!skip) {
+        for (int blk = w; blk < nblk; blk += kBuildWarps) {
+            float l[3] = {INFINITY, INFINITY, INFINITY}, h[3] = {-INFINITY, -INFINITY, -INFINITY};
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const int k = blk * 64 + lane + 32 * u;
+                if (k < m) {
+                    const float v[3] = {sx[k], sy[k], sz[k]};
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) { l[c] = fminf(l[c], v[c]); h[c] = fmaxf(h[c], v[c]); }
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+                for (int o = 16; o > 0; o >>= 1) {
+                    l[c] = fminf(l[c], __shfl_xor_sync(0xffffffffu, l[c], o));
+                    h[c] = fmaxf(h[c], __shfl_xor_sync(0xffffffffu, h[c], o));
+                }
+            if (lane == 0)
+                for (int c = 0; c < 3; ++c) { blo[c][blk] = l[c]; bhi[c][blk] = h[c]; }
+        }
+    }
+    __syncthreads();
     const int b0 = lo + (cta - bz.cta_lo[g]) * kBruteSlice, b1 = min(hi, b0 + kBruteSlice);
     if (a.snap)
         for (int b = b0 + threadIdx.x; b < b1; b += blockDim.x) a.snap[b] = a.pos[b];
@@ -800,7 +712,9 @@ __global__ void __launch_bounds__(kBuildWarps * 32) k_pl_brute(RebuildArgs a, Bu
             cnt += __popc(msk);
         };
         const unsigned below = (1u << lane) - 1u;
-        for (int k0 = 2 * lane; k0 - 2 * lane < m2; k0 += 64) {
+        // the candidates of block blk, two per lane: screened, and the survivors queued
+        auto scan_block64 = [&](int blk) {
+            const int k0 = blk * 64 + 2 * lane;
             bool in0 = false, in1 = false;
             if (k0 < m2) {
                 const float2 X = *reinterpret_cast<const float2 *>(sx + k0);
@@ -814,7 +728,7 @@ __global__ void __launch_bounds__(kBuildWarps * 32) k_pl_brute(RebuildArgs a, Bu
                 in1 = r2.y <= screen;
             }
             const unsigned q0 = __ballot_sync(0xffffffffu, in0), q1 = __ballot_sync(0xffffffffu, in1);
-            if ((q0 | q1) == 0u) continue;
+            if ((q0 | q1) == 0u) return;
             if (in0) cand[w][pend + __popc(q0 & below)] = k0;
             pend += __popc(q0);
             if (in1) cand[w][pend + __popc(q1 & below)] = k0 + 1;
@@ -830,6 +744,27 @@ __global__ void __launch_bounds__(kBuildWarps * 32) k_pl_brute(RebuildArgs a, Bu
                 if (lane + 64 < pend) cand[w][lane + 32] = v1;
                 pend -= 32;
                 __syncwarp();
+            }
+        };
+        // blocks whose box lies within the screen distance of bead i; the box is no farther
+        // than any of its beads, so no candidate the exact test keeps is culled
+        for (int q = 0; q < nblk; q += 32) {
+            bool near = false;
+            if (q + lane < nblk) {
+                const float v[3] = {pi.x, pi.y, pi.z};
+                float d2 = 0.f;
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const float e = fmaxf(fmaxf(blo[c][q + lane] - v[c], v[c] - bhi[c][q + lane]), 0.f);
+                    d2 = fmaf(e, e, d2);
+                }
+                near = d2 <= screen;
+            }
+            unsigned bm = __ballot_sync(0xffffffffu, near);
+            while (bm != 0u) {
+                const int b = __ffs(bm) - 1;
+                bm &= bm - 1u;
+                scan_block64(q + b);
             }
         }
         __syncwarp();
@@ -1444,19 +1379,7 @@ void launch_rebuild(const StepArgs &sa, const DevCells &c, const DevPairList &pl
         if (launches) *launches += 1;
         return;
     }
-    if (rg.max_seg > 0 && rg.max_seg <= kFuseBeads) {
-        // every segment small: its whole cell list in one CTA, one launch for the range
-        static bool attr_set = false;
-        const int smem = (int)sizeof(int32_t) * (3 * kFuseBeads + 8);   // budget 2 n + 8 counters, n cells
-        if (!attr_set) {
-            cudaFuncSetAttribute(k_cell_build, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-            attr_set = true;
-        }
-        const int threads = rg.max_seg > 512 ? 1024 : 256;
-        k_cell_build<<<rg.g_hi - rg.g_lo, threads, (size_t)sizeof(int32_t) * (3 * rg.max_seg + 8), s>>>(
-            a, pl.cursor, pl.seg_base);
-        if (launches) *launches += 1;
-    } else {
+    {
         // bounding boxes: one CTA per 4096 beads of the largest segment (at most 128 per
         // segment), merged by atomics, then the grids
         const int slices = std::min(128, std::max(1, (rg.max_seg + 4095) / 4096));

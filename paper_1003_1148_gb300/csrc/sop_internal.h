@@ -152,11 +152,10 @@ void launch_native_fill(const double *native_xyz, const int32_t *chain, const in
 // pos: the positions to build from; snap (may be null) receives a copy of them.
 // Beads per chunk of the FP64 observable sums of the streamed forms (one CTA each).
 constexpr int kObsChunkBeads = 32;
-// Segments up to this many beads build their Verlet rows by testing every pair of the
-// segment (no cell list: 16 passes of 64 candidates per bead cost less than the 27-cell
-// walk plus the cell list; at 4,096 beads, measured, the all-pairs build took 37 us on one
-// segment against 33 us for the cell list and its walk); kBruteSliceBeads beads per CTA.
-constexpr int kBruteMaxBeads = 1024;
+// Segments up to this many beads build their Verlet rows without a cell list: each bead
+// tests the blocks of 64 consecutive beads whose bounding box lies within the cutoff;
+// kBruteSliceBeads beads per CTA.
+constexpr int kBruteMaxBeads = 8192;
 constexpr int kBruteSliceBeads = 16;
 // Put every segment's bounding-box accumulator in its empty state (once, after allocation).
 void launch_seg_box_init(int32_t *seg_box, int32_t n_seg, cudaStream_t s);

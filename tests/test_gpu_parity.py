@@ -97,12 +97,17 @@ def test_pairlist_bit_exact_after_steps(sop, orc, workloads, schedule):
         sim.close()
 
 
-@pytest.mark.parametrize("n", [1024, 1025, 6000, 9000])
+@pytest.mark.parametrize("n", [1000, 4096, 8192, 8193])
 def test_pairlist_every_build_path_bit_exact(sop, orc, synth, n):
-    """One system of n beads: up to 1,024 beads the rows come from the all-pairs build,
-    up to 8,192 from the one-CTA cell list, above that from the staged cell list; each
-    against the oracle's list at the same positions, after 0 and 23 steps."""
-    w = synth.fiber4096(n=n, steps=100)
+    """One system of n beads: up to 8,192 beads the rows come from the block-culled all-pairs
+    build (one, 64 and 128 blocks of 64 beads here), above that from the staged cell list;
+    each against the oracle's list at the same positions, after 0 and 23 steps."""
+    if n <= 4096:
+        w = synth.fiber4096(n=n, steps=100)
+    else:   # shell assemblies are quick to generate at these sizes
+        copies = 8 if n == 8192 else 3
+        w = synth.shell(n_copies=copies, n_per=n // copies, r_in=80.0, r_out=110.0, ind_radius=20.0, steps=100)
+        assert w.n_beads == n
     sim = sop.from_workload(w, n_replicas=1, schedule="streamed")
     m = orc.model_from_workload(w)
     for steps in (0, 23):

@@ -254,14 +254,21 @@ __global__ void __launch_bounds__(256) k_seg_bbox(RebuildArgs a) {
     const int s0 = lo + blockIdx.y * per, s1 = min(hi, s0 + per);
     float mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
     bool bad = false;
-    for (int b = s0 + threadIdx.x; b < s1; b += blockDim.x) {
-        const float4 p = a.pos[b];
-        const float v[3] = {p.x, p.y, p.z};
+    constexpr int kLd = 4;   // loads in flight per thread
+    const int T = blockDim.x;
+    for (int b0 = s0 + threadIdx.x; b0 < s1; b0 += kLd * T) {
+        float4 pv[kLd];
 #pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            if (!isfinite(v[k])) bad = true;
-            mn[k] = fminf(mn[k], v[k]);
-            mx[k] = fmaxf(mx[k], v[k]);
+        for (int u = 0; u < kLd; ++u) pv[u] = b0 + u * T < s1 ? a.pos[b0 + u * T] : a.pos[b0];
+#pragma unroll
+        for (int u = 0; u < kLd; ++u) {
+            const float v[3] = {pv[u].x, pv[u].y, pv[u].z};
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                if (!isfinite(v[k])) bad = true;
+                mn[k] = fminf(mn[k], v[k]);
+                mx[k] = fmaxf(mx[k], v[k]);
+            }
         }
     }
 #pragma unroll
@@ -534,7 +541,8 @@ __global__ void __launch_bounds__(kBuildWarps * 32) k_pl_build(RebuildArgs a, Bu
 }
 
 constexpr int kBruteBeads = kBruteMaxBeads;   // segments up to this size: k_pl_brute (no cell list)
-constexpr int kBruteBlocks = (kBruteBeads + 63) / 64;
+constexpr int kBruteBlock = 16;   // beads per culling block (even: candidate pairs stay in one block)
+constexpr int kBruteWarps = 16;   // warps per k_pl_brute CTA, one bead each
 constexpr int kBruteSlice = kBruteSliceBeads;
 
 struct BruteArgs {
@@ -558,14 +566,14 @@ struct BruteArgs {
 // is not finite or no grid of the segment's cell budget covers it. kBruteSlice beads per
 // CTA; the last CTA of a segment to finish records the entries used and puts the segment's
 // column cursor back to its first column for the next build.
-__global__ void __launch_bounds__(kBuildWarps * 32) k_pl_brute(RebuildArgs a, BuildExtra x, BruteArgs bz) {
+__global__ void __launch_bounds__(kBruteWarps * 32) k_pl_brute(RebuildArgs a, BuildExtra x, BruteArgs bz) {
     extern __shared__ float soa[];
-    __shared__ int32_t buf[kBuildWarps][kRowBuf];
-    __shared__ int32_t nat[kBuildWarps][kNatBuf];
-    __shared__ int32_t cand[kBuildWarps][96];   // screened candidates waiting for the exact tests
-    __shared__ float blo[3][kBruteBlocks], bhi[3][kBruteBlocks];   // boxes of 64-bead blocks
-    __shared__ float smn[3][kBuildWarps], smx[3][kBuildWarps];
-    __shared__ int sbad[kBuildWarps];
+    __shared__ int32_t buf[kBruteWarps][kRowBuf];
+    __shared__ int32_t nat[kBruteWarps][kNatBuf];
+    __shared__ int32_t cand[kBruteWarps][96];   // screened candidates waiting for the exact tests
+    __shared__ int32_t near_list[kBruteWarps][32];   // near blocks of the warp's current group
+    __shared__ float smn[3][kBruteWarps], smx[3][kBruteWarps];
+    __shared__ int sbad[kBruteWarps];
     __shared__ int s_ok;
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int cta = bz.k_lo + blockIdx.x;
@@ -578,22 +586,35 @@ __global__ void __launch_bounds__(kBuildWarps * 32) k_pl_brute(RebuildArgs a, Bu
     }
     const int lo = a.seg_bead_lo[g], hi = a.seg_bead_lo[g + 1], m = hi - lo, m2 = (m + 1) & ~1;
     float *sx = soa, *sy = soa + m2, *sz = soa + 2 * m2;
+    const int nblk = (m + kBruteBlock - 1) / kBruteBlock;
+    float *bx = soa + 3 * m2;   // box of block q: lo (x, y, z) at bx[q], bx[nblk + q], bx[2 nblk + q], hi after
     const int r = g / a.n_sys;
     const bool failed = a.rep_status[r] != 0;   // CTA-uniform
     if (!failed) {
         float mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
         bool bad = false;
-        for (int k = threadIdx.x; k < m; k += blockDim.x) {
-            const float4 p = a.pos[lo + k];
-            sx[k] = p.x;
-            sy[k] = p.y;
-            sz[k] = p.z;
-            const float v[3] = {p.x, p.y, p.z};
+        // four loads in flight per thread (a loop of one load each would wait out the
+        // latency of every load in turn)
+        constexpr int kLd = 4;
+        const int T = blockDim.x;
+        for (int k0 = threadIdx.x; k0 < m; k0 += kLd * T) {
+            float4 pv[kLd];
 #pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                if (!isfinite(v[c])) bad = true;
-                mn[c] = fminf(mn[c], v[c]);
-                mx[c] = fmaxf(mx[c], v[c]);
+            for (int u = 0; u < kLd; ++u) pv[u] = k0 + u * T < m ? a.pos[lo + k0 + u * T] : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+            for (int u = 0; u < kLd; ++u) {
+                const int k = k0 + u * T;
+                if (k >= m) break;
+                sx[k] = pv[u].x;
+                sy[k] = pv[u].y;
+                sz[k] = pv[u].z;
+                const float v[3] = {pv[u].x, pv[u].y, pv[u].z};
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    if (!isfinite(v[c])) bad = true;
+                    mn[c] = fminf(mn[c], v[c]);
+                    mx[c] = fmaxf(mx[c], v[c]);
+                }
             }
         }
         if (threadIdx.x == 0 && m2 > m) sx[m] = sy[m] = sz[m] = INFINITY;
@@ -616,7 +637,7 @@ __global__ void __launch_bounds__(kBuildWarps * 32) k_pl_brute(RebuildArgs a, Bu
                 l[c] = smn[c][0];
                 h[c] = smx[c][0];
             }
-            for (int q = 0; q < kBuildWarps; ++q) {
+            for (int q = 0; q < kBruteWarps; ++q) {
                 any_bad |= sbad[q];
                 for (int c = 0; c < 3; ++c) { l[c] = fminf(l[c], smn[c][q]); h[c] = fmaxf(h[c], smx[c][q]); }
             }
@@ -629,31 +650,22 @@ __global__ void __launch_bounds__(kBuildWarps * 32) k_pl_brute(RebuildArgs a, Bu
     }
     __syncthreads();
     const bool skip = failed || s_ok == 0;
-    // bounding boxes of the blocks of 64 consecutive beads (consecutive beads of a chain lie
-    // close together), one warp per block
-    const int nblk = (m + 63) >> 6;
-    if (!skip) {
-        for (int blk = w; blk < nblk; blk += kBuildWarps) {
+    // bounding boxes of the blocks of kBruteBlock consecutive beads (consecutive beads of a
+    // chain lie close together), one thread per block
+    if (!skip)
+        for (int q = threadIdx.x; q < nblk; q += blockDim.x) {
             float l[3] = {INFINITY, INFINITY, INFINITY}, h[3] = {-INFINITY, -INFINITY, -INFINITY};
+            for (int k = q * kBruteBlock; k < min(m, (q + 1) * kBruteBlock); ++k) {
+                const float v[3] = {sx[k], sy[k], sz[k]};
 #pragma unroll
-            for (int u = 0; u < 2; ++u) {
-                const int k = blk * 64 + lane + 32 * u;
-                if (k < m) {
-                    const float v[3] = {sx[k], sy[k], sz[k]};
-#pragma unroll
-                    for (int c = 0; c < 3; ++c) { l[c] = fminf(l[c], v[c]); h[c] = fmaxf(h[c], v[c]); }
-                }
+                for (int c = 0; c < 3; ++c) { l[c] = fminf(l[c], v[c]); h[c] = fmaxf(h[c], v[c]); }
             }
 #pragma unroll
-            for (int c = 0; c < 3; ++c)
-                for (int o = 16; o > 0; o >>= 1) {
-                    l[c] = fminf(l[c], __shfl_xor_sync(0xffffffffu, l[c], o));
-                    h[c] = fmaxf(h[c], __shfl_xor_sync(0xffffffffu, h[c], o));
-                }
-            if (lane == 0)
-                for (int c = 0; c < 3; ++c) { blo[c][blk] = l[c]; bhi[c][blk] = h[c]; }
+            for (int c = 0; c < 3; ++c) {
+                bx[c * nblk + q] = l[c];
+                bx[(3 + c) * nblk + q] = h[c];
+            }
         }
-    }
     __syncthreads();
     const int b0 = lo + (cta - bz.cta_lo[g]) * kBruteSlice, b1 = min(hi, b0 + kBruteSlice);
     if (a.snap)
@@ -661,7 +673,7 @@ __global__ void __launch_bounds__(kBuildWarps * 32) k_pl_brute(RebuildArgs a, Bu
     const int rbase = r * a.n, jbase = lo - rbase;   // replica-local index of the segment's first bead
     const float band = x.cut2_f * 1e-4f, screen = x.cut2_f + band;
     const float2 m1 = make_float2(-1.f, -1.f);
-    for (int gb = b0 + w; gb < b1; gb += kBuildWarps) {
+    for (int gb = b0 + w; gb < b1; gb += kBruteWarps) {
         if (skip) {
             if (lane == 0) { x.pl_start[gb] = 0; x.pl_len[gb] = 0; }
             continue;
@@ -712,9 +724,8 @@ __global__ void __launch_bounds__(kBuildWarps * 32) k_pl_brute(RebuildArgs a, Bu
             cnt += __popc(msk);
         };
         const unsigned below = (1u << lane) - 1u;
-        // the candidates of block blk, two per lane: screened, and the survivors queued
-        auto scan_block64 = [&](int blk) {
-            const int k0 = blk * 64 + 2 * lane;
+        // candidates k0 and k0 + 1 (k0 even, or k0 >= m2 for none): screened, survivors queued
+        auto scan_pair = [&](int k0) {
             bool in0 = false, in1 = false;
             if (k0 < m2) {
                 const float2 X = *reinterpret_cast<const float2 *>(sx + k0);
@@ -746,8 +757,10 @@ __global__ void __launch_bounds__(kBuildWarps * 32) k_pl_brute(RebuildArgs a, Bu
                 __syncwarp();
             }
         };
-        // blocks whose box lies within the screen distance of bead i; the box is no farther
-        // than any of its beads, so no candidate the exact test keeps is culled
+        // blocks whose box lies within the screen distance of bead i (the box is no farther
+        // than any of its beads, so no candidate the exact test keeps is culled), 32 blocks at a
+        // time: their near blocks are listed, and the warp walks the concatenation of their
+        // beads 64 at a time, two per lane
         for (int q = 0; q < nblk; q += 32) {
             bool near = false;
             if (q + lane < nblk) {
@@ -755,17 +768,21 @@ __global__ void __launch_bounds__(kBuildWarps * 32) k_pl_brute(RebuildArgs a, Bu
                 float d2 = 0.f;
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
-                    const float e = fmaxf(fmaxf(blo[c][q + lane] - v[c], v[c] - bhi[c][q + lane]), 0.f);
+                    const float e = fmaxf(fmaxf(bx[c * nblk + q + lane] - v[c], v[c] - bx[(3 + c) * nblk + q + lane]), 0.f);
                     d2 = fmaf(e, e, d2);
                 }
                 near = d2 <= screen;
             }
-            unsigned bm = __ballot_sync(0xffffffffu, near);
-            while (bm != 0u) {
-                const int b = __ffs(bm) - 1;
-                bm &= bm - 1u;
-                scan_block64(q + b);
+            const unsigned bm = __ballot_sync(0xffffffffu, near);
+            if (bm == 0u) continue;
+            if (near) near_list[w][__popc(bm & below)] = q + lane;
+            __syncwarp();
+            const int nc = __popc(bm) * kBruteBlock;
+            for (int t0 = 0; t0 < nc; t0 += 64) {
+                const int t = t0 + 2 * lane;
+                scan_pair(t < nc ? near_list[w][t / kBruteBlock] * kBruteBlock + t % kBruteBlock : m2);
             }
+            __syncwarp();   // near_list is rewritten by the next group
         }
         __syncwarp();
         if (pend > 0) settle(pend);
@@ -1366,7 +1383,7 @@ void launch_rebuild(const StepArgs &sa, const DevCells &c, const DevPairList &pl
         static bool brute_attr = false;
         if (!brute_attr) {
             cudaFuncSetAttribute(k_pl_brute, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)sizeof(float) * 3 * kBruteBeads);
+                                 (int)sizeof(float) * (3 * kBruteBeads + 6 * (kBruteBeads / kBruteBlock)));
             brute_attr = true;
         }
         BruteArgs bz;
@@ -1374,8 +1391,10 @@ void launch_rebuild(const StepArgs &sa, const DevCells &c, const DevPairList &pl
         bz.done = c.brute_done;
         bz.used = c.brute_used;
         bz.k_lo = rg.k_lo;
-        const size_t smem = sizeof(float) * 3 * (size_t)((rg.max_seg + 1) & ~1);
-        k_pl_brute<<<rg.k_hi - rg.k_lo, kBuildWarps * 32, smem, s>>>(a, x, bz);
+        // positions (x, y, z padded to even) and the boxes of the culling blocks
+        const size_t smem = sizeof(float) * (3 * (size_t)((rg.max_seg + 1) & ~1) +
+                                             6 * (size_t)((rg.max_seg + kBruteBlock - 1) / kBruteBlock));
+        k_pl_brute<<<rg.k_hi - rg.k_lo, kBruteWarps * 32, smem, s>>>(a, x, bz);
         if (launches) *launches += 1;
         return;
     }

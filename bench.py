@@ -411,6 +411,10 @@ def run_ours(args):
         dist.barrier(group)
         torch.cuda.synchronize()
         with ClockSampler(local) as clk:
+            # one more untimed step while the sampler starts up (its start can stall the
+            # launches for tens of milliseconds), so that the timed steps do not carry it
+            one_step()
+            torch.cuda.synchronize()
             t0 = time.perf_counter()
             for k in range(args.steps):
                 flush.zero_()                      # L2 flush, outside the timed events

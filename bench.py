@@ -94,19 +94,24 @@ def measured_hbm_gbs():
         return 6800.0
 
 
-def recorded_traffic(name: str):
-    """DRAM bytes per launch from profiles/<name>.md, or None when that capture measured
-    other kernel sources than the ones built now."""
+def recorded_counter(name: str, key: str):
+    """A per-launch count recorded in profiles/<name>.md as "<key>: <integer>", or None when
+    that capture measured other kernel sources than the ones built now."""
     path = os.path.join(ROOT, "profiles", f"{name}.md")
     if not os.path.exists(path):
         return None
-    rev = traffic = None
+    rev = value = None
     for line in open(path):
         if line.startswith("Kernel source revision:"):
             rev = line.split("`")[1] if "`" in line else None
-        elif line.startswith("traffic_bytes_per_launch:"):
-            traffic = int(line.split(":")[1])
-    return traffic if rev == kernel_revision() else None
+        elif line.startswith(key + ":"):
+            value = int(line.split(":")[1])
+    return value if rev == kernel_revision() else None
+
+
+def recorded_traffic(name: str):
+    """DRAM bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)."""
+    return recorded_counter(name, "traffic_bytes_per_launch")
 
 
 # ----------------------------------------------------------------------------------------
@@ -498,6 +503,17 @@ def run_ours(args):
         gbs = roofline["traffic"] / per_launch_s / 1e9
         roofline["hbm"] = {"achieved_gbs": gbs, "peak_gbs": hbm_peak, "frac": gbs / hbm_peak if hbm_peak else None,
                            "source": "ncu DRAM bytes per launch / CUDA-event launch time; peak of measured copy"}
+        # ...and against the instruction-issue rate, its actual bound: the warp instructions of
+        # the same capture over the launch time, against one warp instruction per cycle per
+        # scheduler (4 per SM) at the SM clock sampled during the timed region
+        inst = recorded_counter("k_batched_replicas8192x128", "warp_instructions_per_launch")
+        if inst is not None and clocks["sm_mhz"] and fpk["sm_count"]:
+            rate = inst / per_launch_s / 1e12
+            peak_issue = fpk["sm_count"] * 4 * clocks["sm_mhz"] * 1e6 / 1e12
+            roofline["issue"] = {"achieved_twips": rate, "peak_twips": peak_issue, "frac": rate / peak_issue,
+                                 "warp_instructions_per_launch": inst,
+                                 "source": "ncu smsp__inst_executed.sum per launch / CUDA-event launch time; "
+                                           "peak = SMs x 4 schedulers x sampled SM clock (tera warp instructions/s)"}
 
     # plain per-chain GPU form on a subset of replicas (same kernels' math, one chain per launch)
     plain = None

@@ -261,8 +261,9 @@ __device__ void missing_records(const BatchedArgs &a, int r, int s, int g, int64
 // Verlet partners ((sigma/r)^6); entry k at row[k * row_stride]. Two loops walking
 // pointers, so that no entry pays for a select or an index multiply.
 __device__ __forceinline__ float3 row_force(const float4 *P, float4 pb, const uint16_t *row, const float *natr,
-                                            int nn, int tot, int row_stride, int nat_stride, const ForceParams &fp) {
-    float fx = 0.f, fy = 0.f, fz = 0.f;
+                                            int nn, int tot, int row_stride, int nat_stride, const ForceParams &fp,
+                                            float3 acc = make_float3(0.f, 0.f, 0.f)) {
+    float fx = acc.x, fy = acc.y, fz = acc.z;   // the sum continues from acc
     const float A = fp.eps12_h, K = fp.rep_k;
     int k = 0;
 #pragma unroll 2

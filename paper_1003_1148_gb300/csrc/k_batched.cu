@@ -127,9 +127,11 @@ __device__ void rebuild_rows(const BatchedArgs &a, const Layout<RG> &L, const ui
         const int p = by_bead ? (int)L.slot_of()[idx] : idx;
         const int b = by_bead ? idx : (int)order[p];
         const float4 pb = src[b];
+        // the row holds the Verlet partners only: the natives are read from the
+        // slot-ordered native table in the native phase of the step
         const int nn = a.nat_ell_cnt[b0 + b];
         const uint16_t *natc = a.nat_ell_col + nat_off + b;
-        for (int q = 0; q < nn; ++q) row[q * n_s + p] = __ldg(natc + q * n_s);
+        constexpr int row0 = 0;
         const float2 bd = L.bond()[b];
         int q = 0;   // next native to exclude
         int next_nat = nn > 0 ? (int)__ldg(natc) : 0x7fffffff;
@@ -177,13 +179,13 @@ __device__ void rebuild_rows(const BatchedArgs &a, const Layout<RG> &L, const ui
             while (within) {   // ascending
                 const int t = __ffs(within) - 1;
                 within &= within - 1;
-                if (cnt < a.cap) row[(nn + cnt) * n_s + p] = (uint16_t)(base + t);
+                if (cnt < a.cap) row[(row0 + cnt) * n_s + p] = (uint16_t)(base + t);
                 ++cnt;
             }
         }
         if (cnt > a.cap) cta_fail(L.h(), SOP_ERR_PAIRLIST_OVERFLOW);
-        L.n_nat()[p] = (uint16_t)nn;
-        L.n_tot()[p] = (uint16_t)(nn + min(cnt, a.cap));
+        L.n_nat()[p] = (uint16_t)row0;
+        L.n_tot()[p] = (uint16_t)(row0 + min(cnt, a.cap));
     }
 }
 
@@ -207,9 +209,47 @@ __device__ int rebuild(const BatchedArgs &a, const Layout<RG> &L, const float4 *
 
 // Sum of the Eq. 1 pair forces on bead b (in slot p) at layer P over its bonds and row.
 // Entries k < n_nat are native (12-6 with r0^2 from the table), the rest repulsive.
+// Native phase of a step (Eq. 1's 12-6 term): the bead in native slot t of the system (slots
+// ordered by native count, so that the warps' loops are balanced) gets the sum of its native
+// forces, entries from the slot-ordered native table in global memory (consecutive lanes read
+// consecutive words). Returns its local index. The entries are those of its row in their
+// order, and the Verlet phase continues the same sum, so every force has the bits of one
+// loop over the whole row.
+__device__ __forceinline__ int native_force(const BatchedArgs &a, const float4 *P, int n_s, int nat_off, int b0,
+                                            int t, float3 *f) {
+    const ForceParams &fp = a.sa.fp;
+    const int b = a.nat_slot_bead[b0 + t];
+    const float4 pb = P[b];
+    float fx = 0.f, fy = 0.f, fz = 0.f;
+    const int nn = a.nat_slot_cnt[b0 + t];
+    const uint16_t *col = a.nat_slot_col + nat_off + t;
+    const float *r0sq = a.nat_slot_r0sq + nat_off + t;
+    const float A = fp.eps12_h;
+#pragma unroll 2
+    for (int k = 0; k < nn; ++k) {
+        const int j = __ldg(col);
+        col += n_s;
+        const float s0 = __ldg(r0sq);
+        r0sq += n_s;
+        const float4 pj = P[j];
+        const float dx = pb.x - pj.x, dy = pb.y - pj.y, dz = pb.z - pj.z;
+        const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+        const float inv = __fdividef(1.0f, r2);
+        const float s = s0 * inv;
+        const float s3 = s * s * s;
+        const float c = inv * s3 * fmaf(A, s3, -A);   // (12 eps_h / r^2)(s^6 - s^3), s = r0^2 / r^2
+        fx = fmaf(c, dx, fx); fy = fmaf(c, dy, fy); fz = fmaf(c, dz, fz);
+    }
+    *f = make_float3(fx, fy, fz);
+    return b;
+}
+
+// Verlet phase: the bead in slot p adds its repulsive terms (its row holds Verlet partners
+// only) to its native sum `nat`, and the FENE force of its two bonds is summed apart and added
+// last (Eq. 1; the grouping of the former one-pass bead_force).
 template <bool RG>
-__device__ __forceinline__ float3 bead_force(const BatchedArgs &a, const Layout<RG> &L, const float4 *P, int n_s,
-                                             int nat_off, int b, int p, bool *broken) {
+__device__ __forceinline__ float3 verlet_force(const BatchedArgs &a, const Layout<RG> &L, const float4 *P, int n_s,
+                                               int b, int p, float3 nat, bool *broken) {
     const ForceParams &fp = a.sa.fp;
     const float4 pb = P[b];
     float fx = 0.f, fy = 0.f, fz = 0.f;
@@ -230,11 +270,25 @@ __device__ __forceinline__ float3 bead_force(const BatchedArgs &a, const Layout<
             fx = fmaf(c, dx, fx); fy = fmaf(c, dy, fy); fz = fmaf(c, dz, fz);
         }
     }
-    const int nn = L.n_nat()[p], tot = L.n_tot()[p];
-    const float3 fr = row_force(P, pb, L.row() + p, a.nat_ell_r0sq + nat_off + b, nn, tot, n_s, n_s, fp);
+    const float3 fr = row_force(P, pb, L.row() + p, nullptr, 0, L.n_tot()[p], n_s, n_s, fp, nat);
     return make_float3(fx + fr.x, fy + fr.y, fz + fr.z);
 }
 
+// The native phase over the CTA's native slots: each bead's native sum into F[b]. Ends with
+// a barrier.
+template <int BPT, bool RG>
+__device__ __forceinline__ void native_phase(const BatchedArgs &a, const Layout<RG> &L, const float4 *P, float4 *F,
+                                             int n_s, int nat_off, int b0) {
+#pragma unroll 1
+    for (int k = 0; k < BPT; ++k) {
+        const int t = threadIdx.x + k * blockDim.x;
+        if (t >= n_s) continue;
+        float3 f;
+        const int b = native_force(a, P, n_s, nat_off, b0, t, &f);
+        F[b] = make_float4(f.x, f.y, f.z, 0.f);
+    }
+    __syncthreads();
+}
 
 // FP64 observables of the CTA's system at layer P (same definitions as the streamed kernels).
 template <int BPT, bool RG>
@@ -306,7 +360,7 @@ __global__ void __launch_bounds__(MAXT, MINB) k_batched(BatchedArgs a) {
         L.bond()[b] = make_float2(b > 0 ? t.bond_r0[i - 1] : -1.f, t.bond_r0[i]);
         L.flags()[b] = t.flags[i];
         L.order(0)[b] = (uint16_t)b;
-        L.n_tot()[b] = (uint16_t)a.nat_ell_cnt[i];
+        L.n_tot()[b] = 0;   // the first slot order (no row built yet)
         // the list of the first step comes from the positions at the last rebuild step
         if (k_phase != 0) L.lay(1)[b] = a.snap[gbase + b];
     }
@@ -331,11 +385,15 @@ __global__ void __launch_bounds__(MAXT, MINB) k_batched(BatchedArgs a) {
         built_now = false;
         const int64_t step = step0 + it;
         const uint16_t *order = L.order(ord);
+        // native phase: bonds and natives of every bead into Q (the next layer, free until
+        // the Verlet phase below writes each bead's new position over its own entry)
+        native_phase<BPT>(a, L, P, Q, n_s, nat_off, b0);
         if (forces_only) {
             for (int p = threadIdx.x; p < n_s; p += T) {
                 const int b = order[p];
-                bool broken = false, overlap = false;
-                const float3 f = bead_force(a, L, P, n_s, nat_off, b, p, &broken);
+                bool overlap = false, broken = false;
+                const float4 fn = Q[b];
+                const float3 f = verlet_force(a, L, P, n_s, b, p, make_float3(fn.x, fn.y, fn.z), &broken);
                 const float3 fe = ext_force(sa, r, b0 + b, L.flags()[b], P[b], step, &overlap);
                 a.force_out[gbase + b] = make_float4(f.x + fe.x, f.y + fe.y, f.z + fe.z, (broken || overlap) ? 1.f : 0.f);
                 if (a.pl_dump_col) {
@@ -354,8 +412,9 @@ __global__ void __launch_bounds__(MAXT, MINB) k_batched(BatchedArgs a) {
             const int p = threadIdx.x + k * T;
             if (p >= n_s) continue;
             const int b = order[p];
-            bool broken = false, overlap = false;
-            const float3 f = bead_force(a, L, P, n_s, nat_off, b, p, &broken);
+            bool overlap = false, broken = false;
+            const float4 fn = Q[b];
+            const float3 f = verlet_force(a, L, P, n_s, b, p, make_float3(fn.x, fn.y, fn.z), &broken);
             const float4 p_old = P[b];
             const uint8_t fl = L.flags()[b];
             const float3 fe = ext_force(sa, r, b0 + b, fl, p_old, step, &overlap);

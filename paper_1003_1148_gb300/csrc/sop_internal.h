@@ -246,6 +246,13 @@ struct BatchedArgs {
     const int32_t *nat_ell_cnt = nullptr;  // [n] count per bead
     const uint16_t *nat_ell_col = nullptr; // system-local partner
     const float *nat_ell_r0sq = nullptr;
+    // the same table in native-slot order: slot t of system s holds local bead
+    // nat_slot_bead[sys_lo[s] + t] (beads by native count, descending: the warps of the native
+    // phase get beads of equal count), entry k at nat_ell_off[s] + k * n_s + t
+    const uint16_t *nat_slot_bead = nullptr;  // [n]
+    const uint16_t *nat_slot_cnt = nullptr;   // [n]
+    const uint16_t *nat_slot_col = nullptr;
+    const float *nat_slot_r0sq = nullptr;
     // pair form: each native pair belongs to the row of one of its beads (balanced
     // orientation); ELL tables per system like the ones above, entry k of bead b at
     // off[s] + k * n_s + b. own: the partners of b's own pairs (ascending) and their r0^2;

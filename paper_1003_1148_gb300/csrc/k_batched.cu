@@ -222,15 +222,14 @@ __device__ __forceinline__ int native_force(const BatchedArgs &a, const float4 *
     const float4 pb = P[b];
     float fx = 0.f, fy = 0.f, fz = 0.f;
     const int nn = a.nat_slot_cnt[b0 + t];
-    const uint16_t *col = a.nat_slot_col + nat_off + t;
-    const float *r0sq = a.nat_slot_r0sq + nat_off + t;
+    const uint2 *ent = a.nat_slot_ent + nat_off + t;
     const float A = fp.eps12_h;
 #pragma unroll 2
     for (int k = 0; k < nn; ++k) {
-        const int j = __ldg(col);
-        col += n_s;
-        const float s0 = __ldg(r0sq);
-        r0sq += n_s;
+        const uint2 e = __ldg(ent);   // partner and r0^2 in one load
+        ent += n_s;
+        const int j = (int)e.x;
+        const float s0 = __uint_as_float(e.y);
         const float4 pj = P[j];
         const float dx = pb.x - pj.x, dy = pb.y - pj.y, dz = pb.z - pj.z;
         const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));

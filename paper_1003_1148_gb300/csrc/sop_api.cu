@@ -70,8 +70,8 @@ struct sop_ctx {
     int32_t *d_nat_ell_off = nullptr, *d_nat_ell_cnt = nullptr;
     uint16_t *d_nat_ell_col = nullptr;
     float *d_nat_ell_r0sq = nullptr;
-    uint16_t *d_nat_slot_bead = nullptr, *d_nat_slot_cnt = nullptr, *d_nat_slot_col = nullptr;
-    float *d_nat_slot_r0sq = nullptr;
+    uint16_t *d_nat_slot_bead = nullptr, *d_nat_slot_cnt = nullptr;
+    uint2 *d_nat_slot_ent = nullptr;
     // pair form: native pairs split between the rows of their two beads (own / reverse tables)
     int32_t *d_nat_own_off = nullptr, *d_nat_own_cnt = nullptr, *d_nat_rev_off = nullptr, *d_nat_rev_cnt = nullptr;
     uint16_t *d_nat_own_col = nullptr, *d_nat_rev_col = nullptr, *d_nat_rev_k = nullptr;
@@ -302,8 +302,7 @@ BatchedArgs batched_args(sop_ctx *c, const sop_ctx::Bucket &bk) {
     a.nat_ell_r0sq = c->d_nat_ell_r0sq;
     a.nat_slot_bead = c->d_nat_slot_bead;
     a.nat_slot_cnt = c->d_nat_slot_cnt;
-    a.nat_slot_col = c->d_nat_slot_col;
-    a.nat_slot_r0sq = c->d_nat_slot_r0sq;
+    a.nat_slot_ent = c->d_nat_slot_ent;
     a.nat_own_off = c->d_nat_own_off;
     a.nat_own_cnt = c->d_nat_own_cnt;
     a.nat_own_col = c->d_nat_own_col;
@@ -963,8 +962,8 @@ sop_status build_batched_tables(sop_ctx *c) {
     CUDA_OR_RETURN(c, upload(c, &c->d_nat_ell_col, col));
     CUDA_OR_RETURN(c, upload(c, &c->d_nat_ell_r0sq, r0sq));
     // the same entries in native-slot order (beads by native count, descending, stable)
-    std::vector<uint16_t> sbead(c->n), scnt(c->n), scol(col.size(), 0);
-    std::vector<float> sr0(r0sq.size(), 0.f);
+    std::vector<uint16_t> sbead(c->n), scnt(c->n);
+    std::vector<uint2> sent(col.size(), make_uint2(0u, 0u));
     for (int s = 0; s < c->n_sys; ++s) {
         const int lo = c->sys_lo[s], hi = c->sys_lo[s + 1], ns = hi - lo;
         std::vector<int> ord(ns);
@@ -975,15 +974,16 @@ sop_status build_batched_tables(sop_ctx *c) {
             sbead[lo + t] = (uint16_t)b;
             scnt[lo + t] = (uint16_t)cnt[lo + b];
             for (int k = 0; k < cnt[lo + b]; ++k) {
-                scol[(size_t)off[s] + (size_t)k * ns + t] = col[(size_t)off[s] + (size_t)k * ns + b];
-                sr0[(size_t)off[s] + (size_t)k * ns + t] = r0sq[(size_t)off[s] + (size_t)k * ns + b];
+                const size_t src = (size_t)off[s] + (size_t)k * ns + b;
+                uint32_t bits;
+                std::memcpy(&bits, &r0sq[src], sizeof bits);
+                sent[(size_t)off[s] + (size_t)k * ns + t] = make_uint2(col[src], bits);
             }
         }
     }
     CUDA_OR_RETURN(c, upload(c, &c->d_nat_slot_bead, sbead));
     CUDA_OR_RETURN(c, upload(c, &c->d_nat_slot_cnt, scnt));
-    CUDA_OR_RETURN(c, upload(c, &c->d_nat_slot_col, scol));
-    CUDA_OR_RETURN(c, upload(c, &c->d_nat_slot_r0sq, sr0));
+    CUDA_OR_RETURN(c, upload(c, &c->d_nat_slot_ent, sent));
     sop_status se = build_exclusions(c);
     if (se != SOP_OK) return se;
     return build_pair_tables(c, h_r0sq);

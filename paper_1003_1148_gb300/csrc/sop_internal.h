@@ -251,8 +251,7 @@ struct BatchedArgs {
     // phase get beads of equal count), entry k at nat_ell_off[s] + k * n_s + t
     const uint16_t *nat_slot_bead = nullptr;  // [n]
     const uint16_t *nat_slot_cnt = nullptr;   // [n]
-    const uint16_t *nat_slot_col = nullptr;
-    const float *nat_slot_r0sq = nullptr;
+    const uint2 *nat_slot_ent = nullptr;     // (partner, r0^2 as float bits) per entry
     // pair form: each native pair belongs to the row of one of its beads (balanced
     // orientation); ELL tables per system like the ones above, entry k of bead b at
     // off[s] + k * n_s + b. own: the partners of b's own pairs (ascending) and their r0^2;

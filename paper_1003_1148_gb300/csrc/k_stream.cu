@@ -839,9 +839,10 @@ __device__ __forceinline__ float3 gather_force(const StepArgs &a, const DevPairL
     const int n0 = t.nat_row[i], n1 = t.nat_row[i + 1];
 #pragma unroll 2
     for (int p = n0 + lane; p < n1; p += L) {
-        const float4 pj = P[t.nat_col[p]];
+        const uint2 e = t.nat_ent[p];   // partner and r0^2 in one load
+        const float4 pj = P[e.x];
         const float dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
-        const float c = native_coef(fmaf(dz, dz, fmaf(dy, dy, dx * dx)), t.nat_r0sq[p], a.fp);
+        const float c = native_coef(fmaf(dz, dz, fmaf(dy, dy, dx * dx)), __uint_as_float(e.y), a.fp);
         fx = fmaf(c, dx, fx); fy = fmaf(c, dy, fy); fz = fmaf(c, dz, fz);
     }
     const int p0 = pl.start[gb], p1 = p0 + pl.len[gb];

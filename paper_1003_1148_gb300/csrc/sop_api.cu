@@ -64,6 +64,7 @@ struct sop_ctx {
     const double *d_xb_r0d = nullptr;
     int32_t *d_nat_row = nullptr, *d_nat_col = nullptr;
     float *d_nat_r0sq = nullptr;
+    uint2 *d_nat_ent = nullptr;
     double *d_nat_r0 = nullptr;
     int64_t nat_nnz = 0;
     // batched natives (ELL)
@@ -1621,6 +1622,18 @@ sop_status create_impl(sop_ctx *c, const sop_topology *topo, const double *xyz, 
         if (s != SOP_OK) return s;
     }
     c->st.native_entries = c->nat_nnz / 2;
+    {   // packed (partner, r0^2) entries for the streamed gather
+        std::vector<float> r0sq(c->nat_nnz);
+        if (c->nat_nnz)
+            CUDA_OR_RETURN(c, cudaMemcpy(r0sq.data(), c->d_nat_r0sq, sizeof(float) * c->nat_nnz, cudaMemcpyDeviceToHost));
+        std::vector<uint2> ent(std::max<int64_t>(1, c->nat_nnz), make_uint2(0u, 0u));
+        for (int64_t q = 0; q < c->nat_nnz; ++q) {
+            uint32_t bits;
+            std::memcpy(&bits, &r0sq[q], sizeof bits);
+            ent[q] = make_uint2((uint32_t)c->h_nat_col[q], bits);
+        }
+        CUDA_OR_RETURN(c, upload(c, &c->d_nat_ent, ent));
+    }
     std::vector<int32_t> sys_np(c->n_sys, 0);
     for (int i = 0; i < n; ++i)
         for (int q = c->h_nat_row[i]; q < c->h_nat_row[i + 1]; ++q)
@@ -1767,6 +1780,7 @@ sop_status create_impl(sop_ctx *c, const sop_topology *topo, const double *xyz, 
     a.topo.nat_col = c->d_nat_col;
     a.topo.nat_r0sq = c->d_nat_r0sq;
     a.topo.nat_r0 = c->d_nat_r0;
+    a.topo.nat_ent = c->d_nat_ent;
     a.topo.sys_lo = c->d_sys_lo;
     a.topo.sys_ree_last = c->d_sys_ree_last;
     a.topo.sys_nat_pairs = c->d_sys_nat_pairs;

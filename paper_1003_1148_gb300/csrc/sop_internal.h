@@ -27,6 +27,7 @@ struct DevTopo {
     const int32_t *nat_row = nullptr;    // [n+1] CSR rows, both directions, ascending
     const int32_t *nat_col = nullptr;    // [nnz]
     const float *nat_r0sq = nullptr;     // [nnz] r0^2 rounded to FP32
+    const uint2 *nat_ent = nullptr;      // [nnz] (nat_col, nat_r0sq as float bits): one load per entry
     const double *nat_r0 = nullptr;      // [nnz] FP64 r0
     const int32_t *sys_lo = nullptr;     // [n_sys+1] first bead of each system
     const int32_t *sys_ree_last = nullptr;  // [n_sys] last bead of the system's first chain

@@ -1145,7 +1145,9 @@ sop_status tune_bucket(sop_ctx *c, sop_ctx::Bucket &bk) {
         if (!cf.rows_global && cf.min_blocks == 4 && cf.threads >= bk.cfg.threads && cf.pair_form == pairs_only)
             bk.cfg = cf;
     const char *env = std::getenv("SOP_TUNE");
-    const int trial_items = std::min<int>(bk.n_items, 152 * 16);
+    // the whole bucket up to 64 items per SM: a trial on a few waves can rank configurations
+    // whose last waves fill to different fractions otherwise than the full run does
+    const int trial_items = std::min<int>(bk.n_items, 152 * 64);
     if (!(env && std::string(env) == "0") && cands.size() > 1) {
         char key[128];
         std::snprintf(key, sizeof key, "batched %d %d %d %d %d", bk.max_n, bk.row_width, bk.pair_pool, trial_items,

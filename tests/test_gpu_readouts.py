@@ -100,10 +100,12 @@ def test_indenter_records_are_the_projected_wall_force(sop, schedule):
 
 
 @pytest.mark.parametrize("schedule", SCHEDULES)
-def test_q_has_its_own_cadence(sop, synth, schedule):
+def test_q_has_its_own_cadence(sop, synth, schedule, monkeypatch):
     """obs_every (the force-extension cadence) 100 and obs_every_q 300: the records are those
     of the run with Q at every record, bit for bit, except that q is NaN where the step is not
-    a multiple of 300 (Sec. IV.B samples f(R) and Q at different cadences)."""
+    a multiple of 300 (Sec. IV.B samples f(R) and Q at different cadences). Both contexts take
+    the untuned configuration, so that their FP64 sums group alike."""
+    monkeypatch.setenv("SOP_TUNE", "0")
     w = synth.replicas(n_replicas=3, n=64, seed=7, steps=900)
     runs = []
     for q_every in (0, 300):

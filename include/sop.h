@@ -412,10 +412,11 @@ void sop_destroy(sop_ctx *ctx);
  * the system (every row is then empty); SOP_ERR_CUDA for a CUDA failure. The
  * text is sop_last_error(NULL). The call reads its counters back and
  * synchronises cuda_stream (NULL = the legacy default stream) before it
- * returns, so it cannot be recorded into a CUDA graph.
+ * returns.
  *
  * The first call on a device looks up the scratch array's device address for
- * that device. Every call
+ * that device (cudaGetSymbolAddress, with that device current); make that
+ * first call before any stream capture begins. Every call
  * shares the one scratch array and overwrites it, so calls whose GPU work
  * overlaps (two host threads, or two streams) race and must be serialised by
  * the caller.

@@ -8,10 +8,11 @@
 //
 // The array is a fixed 2.5 MiB that every GPU which loads this library keeps
 // until the process exits. Each call reads its counters back and synchronises its
-// stream, so it cannot be recorded into a CUDA graph. Its device address is looked up once per device
-// with cudaGetSymbolAddress (host code cannot use the symbol itself: in host
-// code it names a host-side stand-in, not device memory). All calls share the
-// array, so calls whose work overlaps on the GPU race on it.
+// stream. The array's device address is looked up once per device, by the
+// first call on that device, with cudaGetSymbolAddress (host code cannot use
+// the symbol itself: in host code it names a host-side stand-in, not device
+// memory); that first call should come before any stream capture begins. All
+// calls share the array, so calls whose work overlaps on the GPU race on it.
 #include <cuda_runtime.h>
 
 #include <climits>

@@ -809,12 +809,12 @@ __global__ void __launch_bounds__(kBruteWarps * 32) k_pl_brute(RebuildArgs a, Bu
 // Sum of the Eq. 1 pair forces on bead i of replica r, gathered by L lanes
 // (particle-based, Algorithm 2): lanes stride over the native row and the
 // Verlet row, bonds go to lanes 0 and 1, a shuffle reduction leaves the sum in
-// every lane.
+// every lane. pi = P[i]; [n0, n1) and [p0, p1) are the bead's native and Verlet rows.
 template <int L>
-__device__ __forceinline__ float3 gather_force(const StepArgs &a, const DevPairList &pl, const float4 *P, int i,
-                                               int gb, int lane, bool *broken) {
+__device__ __forceinline__ float3 gather_force_at(const StepArgs &a, const DevPairList &pl, const float4 *P, int i,
+                                                  int lane, float4 pi, int n0, int n1, int p0, int p1,
+                                                  bool *broken) {
     const DevTopo &t = a.topo;
-    const float4 pi = P[i];
     float fx = 0.f, fy = 0.f, fz = 0.f;
     bool brk = false;
     if (lane == 0 && i > 0) {
@@ -836,7 +836,6 @@ __device__ __forceinline__ float3 gather_force(const StepArgs &a, const DevPairL
         }
     }
     xlink_force<L>(t, a.fp, P, i, pi, lane, fx, fy, fz, &brk);
-    const int n0 = t.nat_row[i], n1 = t.nat_row[i + 1];
 #pragma unroll 2
     for (int p = n0 + lane; p < n1; p += L) {
         const uint2 e = t.nat_ent[p];   // partner and r0^2 in one load
@@ -845,7 +844,6 @@ __device__ __forceinline__ float3 gather_force(const StepArgs &a, const DevPairL
         const float c = native_coef(fmaf(dz, dz, fmaf(dy, dy, dx * dx)), __uint_as_float(e.y), a.fp);
         fx = fmaf(c, dx, fx); fy = fmaf(c, dy, fy); fz = fmaf(c, dz, fz);
     }
-    const int p0 = pl.start[gb], p1 = p0 + pl.len[gb];
 #pragma unroll 2
     for (int p = p0 + lane; p < p1; p += L) {
         const float4 pj = P[pl.col[p]];
@@ -863,6 +861,51 @@ __device__ __forceinline__ float3 gather_force(const StepArgs &a, const DevPairL
     return make_float3(fx, fy, fz);
 }
 
+template <int L>
+__device__ __forceinline__ float3 gather_force(const StepArgs &a, const DevPairList &pl, const float4 *P, int i,
+                                               int gb, int lane, bool *broken) {
+    const int p0 = pl.start[gb];
+    return gather_force_at<L>(a, pl, P, i, lane, P[i], a.topo.nat_row[i], a.topo.nat_row[i + 1], p0,
+                              p0 + pl.len[gb], broken);
+}
+
+// advance_bead for an overdamped step with Philox noise, given the bead's position
+// pi = P[i], compensation c = comp[gb] and flags fl loaded, and its noise g drawn, before
+// the force gather, so that none of them waits behind it. The same decisions as
+// advance_bead and the same Algorithm 7 update as update_position, in the same order.
+__device__ __forceinline__ void advance_bead_pre(const StepArgs &a, int r, int i, int gb, float4 pi, float4 c,
+                                                 uint8_t fl, float3 g, float3 f, bool broken, int64_t step,
+                                                 float4 *pos_out, float4 *comp) {
+    if (broken) {
+        set_status(&a.rep_status[r], (int32_t)SOP_ERR_FENE_BREAK);
+        pos_out[gb] = pi;
+        return;
+    }
+    bool overlap = false;
+    const float3 fe = external_force(a, r, i, pi, step, &overlap);
+    if (overlap) {
+        set_status(&a.rep_status[r], (int32_t)SOP_ERR_INDENTER_OVERLAP);
+        pos_out[gb] = pi;
+        return;
+    }
+    if (fl & kFlagFixed) {
+        pos_out[gb] = pi;
+        return;
+    }
+    const float3 F = make_float3(f.x + fe.x, f.y + fe.y, f.z + fe.z);
+    float4 pn = pi, cn = c;
+    kahan_add(pn.x, cn.x, fmaf(F.x, a.fp.mob, g.x * a.fp.amp));
+    kahan_add(pn.y, cn.y, fmaf(F.y, a.fp.mob, g.y * a.fp.amp));
+    kahan_add(pn.z, cn.z, fmaf(F.z, a.fp.mob, g.z * a.fp.amp));
+    if (!(isfinite(pn.x) && isfinite(pn.y) && isfinite(pn.z))) {
+        set_status(&a.rep_status[r], (int32_t)SOP_ERR_NONFINITE);
+        pos_out[gb] = pi;
+        return;
+    }
+    comp[gb] = cn;
+    pos_out[gb] = pn;
+}
+
 // One step of bead gb by its group of L lanes (lane = this thread's lane in the group).
 template <int L>
 // (No __restrict__ here: in k_step_coop the same layers are read and written by different
@@ -872,16 +915,33 @@ __device__ __forceinline__ void step_bead(const StepArgs &a, const DevPairList &
     const int n = a.topo.n;
     const int r = gb / n, i = gb - r * n;
     const float4 *P = pos_in + (size_t)r * n;
-    if (__any_sync(group_mask<L>(), *a.halt != 0 || a.rep_status[r] != 0)) {   // one decision per group
-        if (lane == 0) pos_out[gb] = P[i];
+    // One round of loads, all in bounds whatever the replica's state: the stop decision,
+    // the step, and the bead's position, row bounds, compensation and flags, so that the
+    // stop test, the update and the gather's first loads do not each wait in turn.
+    const bool stop = *a.halt != 0 || a.rep_status[r] != 0;
+    const int64_t step = *a.d_step + k_off;
+    const float4 pi = P[i];
+    const int n0 = a.topo.nat_row[i], n1 = a.topo.nat_row[i + 1];
+    const int p0 = pl.start[gb], p1 = p0 + pl.len[gb];
+    const float4 c = comp[gb];
+    const uint8_t fl = a.topo.flags[i];
+    if (__any_sync(group_mask<L>(), stop)) {   // one decision per group
+        if (lane == 0) pos_out[gb] = pi;
         return;
     }
-    const int64_t step = *a.d_step + k_off;
+    // The Philox noise does not depend on the forces: in an overdamped step every lane of
+    // the group draws it here (the same words), off the path that follows the reduction.
+    // Hybrid Taus noise (drawn only when the bead moves) and the underdamped update stay
+    // in advance_bead.
+    const bool pre = a.taus == nullptr && a.vel == nullptr;
+    float3 g = make_float3(0.f, 0.f, 0.f);
+    if (pre) g = bead_noise(a.seed + (uint64_t)r, step, (uint32_t)i);
     bool broken = false;
-    const float3 f = gather_force<L>(a, pl, P, i, gb, lane, &broken);
+    const float3 f = gather_force_at<L>(a, pl, P, i, lane, pi, n0, n1, p0, p1, &broken);
     broken = __any_sync(group_mask<L>(), broken);
     if (lane != 0) return;
-    advance_bead(a, r, i, gb, P, f, broken, step, pos_out, comp);
+    if (pre) advance_bead_pre(a, r, i, gb, pi, c, fl, g, f, broken, step, pos_out, comp);
+    else advance_bead(a, r, i, gb, P, f, broken, step, pos_out, comp);
 }
 
 template <int L>

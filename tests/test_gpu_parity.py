@@ -234,6 +234,23 @@ def test_cooperative_chunk_equals_plain_bitwise(sop, synth, monkeypatch):
     assert a.stats()["kernel_launches"] < c.stats()["kernel_launches"]
 
 
+def test_spread_step_equals_per_bead_step_bitwise(sop, synth):
+    """Launches of at least 152 x 256 beads take k_step_spread, whose update is advance_bead's;
+    smaller ones take k_step, which loads the bead's data and draws its Philox noise before
+    the gather and then updates with its own copy of that arithmetic. The streamed form over
+    one batch of about 42,000 beads (one spread launch per step) and the plain form (one
+    k_step launch per chain) must therefore agree bit for bit."""
+    w = synth.uneven(n_chains=200, lo=150, hi=300, steps=50)
+    assert w.n_beads >= 152 * 256
+    a = sop.from_workload(w, n_replicas=1, schedule="streamed")
+    b = sop.from_workload(w, n_replicas=1, schedule="plain")
+    a.step(23)
+    b.step(23)
+    assert np.array_equal(a.get_positions(-1), b.get_positions(-1))
+    a.close()
+    b.close()
+
+
 def test_observables_match_oracle_at_gpu_positions(sop, orc, synth):
     for schedule in ("streamed", "batched", "pairs", "plain", "batched_pairs"):
         w = synth.uneven(n_chains=4, lo=60, hi=200, steps=100)

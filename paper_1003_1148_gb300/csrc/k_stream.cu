@@ -915,7 +915,7 @@ __device__ __forceinline__ void step_bead(const StepArgs &a, const DevPairList &
     const int n = a.topo.n;
     const int r = gb / n, i = gb - r * n;
     const float4 *P = pos_in + (size_t)r * n;
-    // One round of loads, all in bounds whatever the replica's state: the stop decision,
+    // Loads issued together, all in bounds whatever the replica's state: the stop decision,
     // the step, and the bead's position, row bounds, compensation and flags, so that the
     // stop test, the update and the gather's first loads do not each wait in turn.
     const bool stop = *a.halt != 0 || a.rep_status[r] != 0;
